@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""QAOA MaxCut energy evaluations per second, one JSON line on rank 0.
+
+Workload (default): the seeded random 3-regular graph N=30 (seed 1000, 45
+edges), depth p=4, angles from the seeded generator; one step = one full
+energy evaluation E = |E|/2 - 1/2 sum_jk <Z_jZ_k> over all 45 lightcone
+networks by bucket elimination, complex64 with FP32 arithmetic (the precision
+form). The plain complex128 form is measured beside it under "c128".
+
+* value: device-resident angles and outputs, K steps timed with CUDA events on
+  the launch stream (barrier + synchronize on both sides, max over ranks).
+  Each step's tensors total several GB, far above the 129 MB L2.
+* e2e: the same evaluation through the public API with host angles in and
+  host results out, the copies inside the timed region.
+* roofline: algorithmic bytes of one evaluation (every operand read once,
+  every result written once) over the average duration of the persistent
+  bucket kernel, from CUDA events recorded around it on its stream.
+* cpu_baseline: the CPU oracle's bucket elimination on a bounded sample of the
+  same workload, on all host cores (rank 0, one GPU only).
+
+``--impl reference`` times the CPU oracle alone (there is no reference code
+base; the oracle stands in for it) and prints its line with "impl": "reference".
+Multi-GPU (torchrun): every rank evaluates its own copy of the workload (weak
+scaling); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+PAPER_SECONDS_PER_EVAL = 1.4  # best mixed merged backend, N=30 p=4, V100 (Table II)
+REF_EDGES_PER_STEP = 3        # oracle sample per reference step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
+    return ap.parse_args()
+
+
+WORKLOAD = dict(n=30, seed=1000, p=4)
+
+
+def workload_inputs():
+    from paper_2204_06045_gb300 import synth
+    n, seed, p = WORKLOAD["n"], WORKLOAD["seed"], WORKLOAD["p"]
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    return n, p, edges, g, b
+
+
+def config_dict(dtype_note: str):
+    n, seed, p = WORKLOAD["n"], WORKLOAD["seed"], WORKLOAD["p"]
+    return {"workload": f"QAOA MaxCut energy, random 3-regular N={n} (seed {seed}, 45 edges), p={p}, "
+                        f"all 45 lightcone networks by bucket elimination, {dtype_note}",
+            "graph_seed": seed, "n_vertices": n, "p": p, "angles": "synth.angles(p, seed)",
+            "l2": "no flush: each evaluation reads and writes several GB of tensors (L2 is 129 MB)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(budget_s: float, max_edges=None):
+    """Time the oracle's bucket elimination on edges 0, 1, ... until the budget is spent."""
+    import oracle
+    n, p, edges, g, b = workload_inputs()
+    m = edges.shape[0]
+    t0 = time.perf_counter()
+    k = 0
+    while k < m and (max_edges is None or k < max_edges):
+        oracle.edge_bucket(n, edges, g, b, k, seed=k)
+        k += 1
+        if max_edges is None and time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return k, m, dt, oracle.get_threads()
+
+
+def cpu_baseline(budget_s: float):
+    k, m, dt, cores = oracle_sample(budget_s)
+    return {"value": (k / m) / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"complex128 CPU bucket elimination (oracle) of lightcone networks 0..{k - 1} of {m} "
+                      f"in {dt:.1f} s; evals/s = ({k}/{m}) / time"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n, p, edges, g, b = workload_inputs()
+    m = edges.shape[0]
+    for _ in range(args.warmup):
+        oracle_sample(0, max_edges=REF_EDGES_PER_STEP)
+    times = []
+    for _ in range(args.steps):
+        _, _, dt, cores = oracle_sample(0, max_edges=REF_EDGES_PER_STEP)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * (REF_EDGES_PER_STEP / m) / total
+    sample = (f"each step: complex128 CPU bucket elimination (oracle) of lightcone networks 0..{REF_EDGES_PER_STEP - 1}"
+              f" of {m}; evals/s = steps * ({REF_EDGES_PER_STEP}/{m}) / time")
+    line = {"impl": "reference", "metric": "QAOA energy evals/s (3-reg N=30 p=4)", "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value * PAPER_SECONDS_PER_EVAL, "dtype": "c128", "data": "synthetic",
+            "config": config_dict("complex128 CPU oracle (sampled)"),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU
+
+def measured_peaks():
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        d = json.loads(f.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_tag: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
+    f = ROOT / "profiles" / f"{kernel_tag}.txt"
+    if not f.exists():
+        return None
+    src = (ROOT / "paper_2204_06045_gb300" / "csrc" / "kernels.cu").read_bytes()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in f.read_text().splitlines():
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            vals[parts[0]] = parts[1]
+    if vals.get("kernels_cu_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def time_device(pl, gd, bd, zz, E, steps, warmup, dist, torch):
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        pl.energy(gd, bd, edge_zz=zz, energy=E, stream=s)
+    pl.sync(s)
+    pl.kernel_time(reset=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(s)
+    for _ in range(steps):
+        pl.energy(gd, bd, edge_zz=zz, energy=E, stream=s)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    pl.sync(s)
+    ms = ev0.elapsed_time(ev1)
+    kms, launches = pl.kernel_time(reset=True)
+    return ms, kms, launches
+
+
+def time_e2e(pl, g, b, steps, dist, torch):
+    for _ in range(2):
+        pl.energy(g, b)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        zz, E = pl.energy(g, b)  # host arrays in, host results out; the call waits for its copies
+    return time.perf_counter() - t0
+
+
+def max_over_ranks(x, dist, torch):
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2204_06045_gb300 import build, qtgb
+
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = tdist
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    build.build()
+
+    n, p, edges, g, b = workload_inputs()
+    m = edges.shape[0]
+    peak, peak_kind = measured_peaks()
+    results = {}
+    for dtype in ("c64", "c128"):
+        pl = qtgb.plan(n, edges, p, dtype=dtype)
+        st = pl.stats()
+        gd = torch.tensor(g, dtype=torch.float64, device="cuda")
+        bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+        zz = torch.zeros(m, dtype=torch.float64, device="cuda")
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            ms, kms, launches = time_device(pl, gd, bd, zz, E, args.steps, args.warmup, dist, torch)
+        ms = max_over_ranks(ms, dist, torch)
+        e2e_s = max_over_ranks(time_e2e(pl, g, b, args.steps, dist, torch), dist, torch)
+        achieved = st["alg_bytes"] / (kms * 1e-3) / 1e9 if kms > 0 else None
+        tag = f"k_persistent_{dtype}_n30_p4"
+        results[dtype] = {
+            "value": world * args.steps / (ms * 1e-3),
+            "ms_per_step": ms / args.steps,
+            "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s",
+                    "h2d_bytes_per_step": 2 * p * 8, "d2h_bytes_per_step": (m + 1) * 8},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": ncu_traffic(tag),
+                         "peak_source": peak_kind,
+                         "kernel": "k_persistent", "kernel_ms": kms, "kernel_launches": launches,
+                         "alg_bytes_per_launch": st["alg_bytes"]},
+            "clocks": clk.summary(),
+            "plan": {"buckets": st["n_buckets"], "max_width": st["max_width"], "sum_2w": st["sum_2w"],
+                     "tasks": st["n_tasks"], "plan_seconds": st["plan_seconds"]},
+            "check": {"energy": float(E.item())},
+        }
+        pl.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    main = results["c64"]
+    line = {
+        "metric": "QAOA energy evals/s (3-reg N=30 p=4)",
+        "value": main["value"], "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": main["value"] * PAPER_SECONDS_PER_EVAL, "dtype": "c64", "data": "synthetic",
+        "config": config_dict("complex64 with FP32 arithmetic, persistent dependency-queue kernel"),
+        "e2e": main["e2e"], "roofline": main["roofline"], "clocks": main["clocks"],
+        "gpu_launches": 3 * args.steps,
+        "plan": main["plan"], "check": main["check"],
+        "c128": {k: results["c128"][k] for k in ("value", "ms_per_step", "e2e", "roofline", "clocks", "plan", "check")},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

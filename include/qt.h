@@ -1,0 +1,219 @@
+/*
+ * qt.h -- C ABI of libqtgb: QAOA MaxCut energy by lightcone bucket elimination
+ * on one GB300 (sm_103a).
+ *
+ * What is computed (paper §II-A and §II-B):
+ *   C = 1/2 sum_{(ij) in E} (1 - Z_i Z_j)                              (Eq. 1)
+ *   |g,b>_p = prod_{k=1..p} e^{-i b_k B} e^{-i g_k C} |+>^N,  B = sum X   (Eq. 2)
+ *   <C>_p = |E|/2 - 1/2 sum_{jk in E} e_jk,  e_jk = <g,b| Z_j Z_k |g,b>
+ * Each e_jk is the value of the tensor network of edge jk's lightcone,
+ * contracted by bucket elimination (§II-B): buckets are taken in elimination
+ * order; a bucket's tensors are multiplied and summed over the bucket index,
+ * and the result joins a later bucket.
+ *
+ * Angle convention: layer k applies exp(-i gamma_k s_a s_b) on each edge (a,b)
+ * with s(x) = 1 - 2x, then exp(-i beta_k X) on each qubit. The paper's Eq. 2
+ * corresponds to gamma_paper = -2 * gamma (a global phase aside).
+ *
+ * Conventions for every call:
+ *  - Return 0 (QT_OK) or a negative QT_E* code; qt_error_string() names it.
+ *    No output is written on error, and no C++ exception crosses the ABI.
+ *  - Graphs are simple and undirected, vertices 0..n-1, edges given as
+ *    int32 pairs. Edge outputs follow the input edge order.
+ *  - The caller owns every array it passes. Pointers marked "host or device"
+ *    are classified with cudaPointerGetAttributes; device pointers must be on
+ *    the plan's device.
+ *  - Calls with `stream == NULL` are synchronous. With a stream, device
+ *    outputs are valid once the stream has synchronised; host outputs are
+ *    always valid on return (the call waits for its own copies).
+ *  - A plan is used by one call at a time (per plan, not per process).
+ */
+#ifndef QT_H
+#define QT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define QT_OK 0
+#define QT_EINVAL -1   /* bad argument: null pointer, self-loop, duplicate edge, vertex out of range, p < 1 */
+#define QT_EWIDTH -2   /* a bucket is wider than qt_plan_opts.max_width */
+#define QT_ENOMEM -3   /* host or device allocation failed, or over qt_plan_opts.arena_bytes */
+#define QT_ECUDA -4    /* a CUDA runtime call failed (no device, launch failure, ...) */
+#define QT_ETIMEOUT -5 /* a kernel's bounded wait on a bucket dependency ran out */
+#define QT_EBOUNDS -6  /* a kernel found an operand index outside its tensor */
+#define QT_ESTATE -7   /* call not valid for this plan (wrong dtype/mode, gradient not planned, ...) */
+
+typedef struct qt_plan_s *qt_plan_t; /* opaque; owns the host plan and its device memory */
+
+typedef enum { QT_C64 = 0, QT_C128 = 1 } qt_dtype;
+
+/* How qt_energy runs the bucket schedule. */
+typedef enum {
+    QT_SCHED_PERSISTENT = 0, /* one persistent kernel drains a device-side dependency
+                                queue of bucket tiles; captured in a CUDA graph */
+    QT_SCHED_PER_BUCKET = 1  /* the plain form: one kernel launch per bucket, in order */
+} qt_sched;
+
+/* Plan options. A zero-initialised struct selects every default. */
+typedef struct {
+    qt_dtype dtype;        /* element type of every tensor: complex64 (FP32 arithmetic) or complex128 */
+    qt_sched sched;        /* schedule used by qt_energy (default persistent) */
+    int32_t order_restarts;/* extra randomised greedy min-fill orders per network; the order
+                              with the smallest sum of 2^width is kept (default 0: plain greedy;
+                              negative: none) */
+    uint64_t order_seed;   /* seed of the randomised restarts */
+    int32_t max_width;     /* largest bucket width allowed, the summed index included
+                              (default 31, at most 31) */
+    size_t arena_bytes;    /* cap on device memory for tensors (default: no cap beyond the device) */
+    int32_t with_grad;     /* nonzero: also allocate what qt_energy_grad needs */
+    uint64_t spin_limit;   /* polls of a dependency counter before a kernel gives up with
+                              QT_ETIMEOUT (default 2^23, each poll sleeps ~0.1-1 us) */
+    int32_t chunk_log2;    /* outputs per persistent-kernel task, log2 (default 0: per-width table) */
+    int32_t host_only;     /* nonzero: plan on the host only (statistics, export); no device
+                              memory is touched and every evaluation call returns QT_ESTATE */
+} qt_plan_opts;
+
+/* Plan statistics. Widths count the summed index (inclusive); a bucket of
+ * width w writes 2^(w-1) entries. */
+typedef struct {
+    int32_t n_graphs;
+    int32_t n_networks;     /* one per edge of every graph */
+    int64_t n_buckets;
+    int64_t n_operands;
+    int32_t max_width;
+    int32_t p;
+    double sum_2w;          /* sum over buckets of 2^width */
+    double alg_bytes;       /* algorithmic bytes of one energy evaluation: every operand read
+                               once plus every output written once, at the plan's dtype */
+    double flops;           /* complex multiply-adds of one evaluation x 8 real flops */
+    int64_t arena_bytes;    /* device bytes of the tensor arena */
+    int64_t n_tasks;        /* persistent-kernel tasks (bucket tiles) */
+    int64_t n_items;        /* persistent-kernel work items (claims) */
+    int32_t n_levels;       /* longest dependency chain, in buckets */
+    int32_t dtype;
+    int64_t width_hist[64]; /* buckets per width */
+    double plan_seconds;    /* host time spent building the plan */
+} qt_plan_stats;
+
+/* One bucket of the schedule as seen by host-side inspection (tests). */
+typedef struct {
+    int32_t network;   /* network (edge) it belongs to, numbered over all graphs */
+    int32_t width;     /* inclusive width w */
+    int32_t n_ops;     /* operands (leaf gate tensors and earlier results) */
+    int32_t op_begin;  /* first operand in the qt_operand_info array */
+    int32_t parent;    /* bucket that consumes this bucket's result; -1 for a root (scalar) */
+    int32_t n_deps;    /* operands that are results of earlier buckets */
+    int32_t level;     /* 0 for buckets whose operands are all leaves */
+    int32_t var;       /* the summed variable, numbered within the network */
+} qt_bucket_info;
+
+/* One operand of a bucket. The operand's entry for output index o and summed
+ * value x is at element 2*pext(o, mask) + x of its tensor. */
+typedef struct {
+    int32_t src;       /* producing bucket, or -1 for a leaf gate tensor */
+    int32_t leaf_kind; /* for leaves: QT_LEAF_* below, else -1 */
+    int32_t leaf_layer;/* for ZZ and mixer leaves: layer 0..p-1, else -1 */
+    uint32_t mask;     /* output bits this operand carries */
+    int32_t rank;      /* index bits of the operand (summed bit included) */
+    int32_t pad;
+} qt_operand_info;
+
+#define QT_LEAF_PLUS 0   /* [1, 1]/sqrt 2: |+> and <+| */
+#define QT_LEAF_ZOBS 1   /* [1, -1]: the observable Z on an edge endpoint */
+#define QT_LEAF_ZZ 2     /* exp(-i gamma_k s_a s_b) */
+#define QT_LEAF_ZZ_CONJ 3
+#define QT_LEAF_RX 4     /* <new| exp(-i beta_k X) |old> */
+#define QT_LEAF_RX_CONJ 5
+
+/*
+ * Build the plan for one graph (§II-B): each edge's lightcone network with the
+ * ZZ-phase gates as rank-2 diagonal tensors, a greedy min-fill elimination
+ * order, the bucket schedule with every tensor's index bits sorted by
+ * elimination rank, and the device memory for it. Host-side work, then one
+ * upload. `edges`: host, 2*n_edges int32. `opts` may be NULL. On success
+ * *out owns device memory until qt_plan_free.
+ */
+int qt_plan(int32_t n_vertices, int32_t n_edges, const int32_t *edges, int32_t p,
+            const qt_plan_opts *opts, qt_plan_t *out);
+
+/*
+ * One plan over several graphs, evaluated together by qt_energy_batch.
+ * n_vertices[g], n_edges[g] per graph; `edges` holds every graph's pairs back
+ * to back (host). All graphs share p; each gets its own angles.
+ */
+int qt_plan_batch(int32_t n_graphs, const int32_t *n_vertices, const int32_t *n_edges,
+                  const int32_t *edges, int32_t p, const qt_plan_opts *opts, qt_plan_t *out);
+
+/* Statistics of a plan (host only). */
+int qt_plan_stats_get(qt_plan_t plan, qt_plan_stats *out);
+
+/* Copy the schedule out for inspection (host only). `buckets` holds
+ * stats.n_buckets entries, `operands` stats.n_operands; either may be NULL. */
+int qt_plan_export(qt_plan_t plan, qt_bucket_info *buckets, qt_operand_info *operands);
+
+/* Number of variables on each qubit wire of network `network` (host,
+ * n_vertices of its graph entries; 0 for qubits outside the lightcone). */
+int qt_plan_network_wires(qt_plan_t plan, int32_t network, int32_t *vars_per_qubit);
+
+/*
+ * Energy of a single-graph plan: edge_zz[e] = e_jk of edge e (n_edges doubles,
+ * host or device, may be NULL), *energy = |E|/2 - 1/2 sum e_jk (host or
+ * device, may be NULL). gammas/betas: p doubles each, host or device.
+ * Per-edge values are the real part of each network's value, accumulated to
+ * double at the end; the arithmetic inside runs in the plan's dtype.
+ */
+int qt_energy(qt_plan_t plan, const double *gammas, const double *betas, double *edge_zz,
+              double *energy, void *cuda_stream);
+
+/*
+ * Energies of every graph of a batch plan in one pass: gammas/betas hold
+ * n_graphs*p doubles (graph-major), energies n_graphs doubles, edge_zz the
+ * per-edge values of all graphs back to back (may be NULL).
+ */
+int qt_energy_batch(qt_plan_t plan, const double *gammas, const double *betas, double *energies,
+                    double *edge_zz, void *cuda_stream);
+
+/*
+ * Energy and its gradient dE/dgamma_k, dE/dbeta_k (k = 1..p) by the adjoint
+ * of the bucket elimination: a reverse sweep over the saved results. The plan
+ * must have been built with opts.with_grad. For batch plans the outputs are
+ * per graph (n_graphs, n_graphs*p, n_graphs*p). Host or device pointers.
+ */
+int qt_energy_grad(qt_plan_t plan, const double *gammas, const double *betas, double *energy,
+                   double *dE_dgamma, double *dE_dbeta, void *cuda_stream);
+
+/* Imaginary parts of the per-edge network values from the last evaluation
+ * (host, n_edges doubles): a consistency check, zero up to rounding. */
+int qt_last_imag(qt_plan_t plan, double *edge_imag);
+
+/* Wait for the plan's work on `cuda_stream` and report a kernel-side error
+ * (QT_ETIMEOUT, QT_EBOUNDS) raised since the previous check. */
+int qt_sync(qt_plan_t plan, void *cuda_stream);
+
+/* Average device time per launch of the plan's main kernel over the calls made
+ * since the last reset, measured with CUDA events on the launch stream.
+ * *launches receives the count. reset != 0 clears the counters. */
+int qt_kernel_time(qt_plan_t plan, double *avg_ms, int64_t *launches, int32_t reset);
+
+/* Fault injection for tests: add one to the dependency count of bucket
+ * `bucket` on the device so that no producer can ever satisfy it; the next
+ * persistent run must end with QT_ETIMEOUT rather than wait forever. */
+int qt_debug_stall_bucket(qt_plan_t plan, int64_t bucket);
+
+void qt_plan_free(qt_plan_t plan);
+
+const char *qt_error_string(int code);
+
+/* Library version string. */
+const char *qt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QT_H */

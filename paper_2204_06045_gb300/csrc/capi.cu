@@ -1,0 +1,532 @@
+// C ABI of libqtgb (declared in include/qt.h): plan ownership, device
+// memory, the CUDA graph of one energy evaluation, and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/qt.h"
+#include "kernels.hpp"
+#include "planner.hpp"
+
+namespace {
+
+constexpr int kRing = 512;  // event pairs for per-launch kernel timing
+
+struct DeviceBuffer {
+    void* p = nullptr;
+    ~DeviceBuffer() {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+struct qt_plan_s {
+    qt::HostPlan hp;
+    int device = 0;
+    int dtype = QT_C64;
+    int sched = QT_SCHED_PERSISTENT;
+    uint64_t spin_limit = 1ull << 23;
+    size_t esize = 8;
+
+    // device memory
+    void* d_arena = nullptr;
+    size_t arena_bytes = 0;
+    void* d_static = nullptr;  // plan arrays
+    void* d_counters = nullptr;  // chunks_done | deps_done | control
+    size_t counters_bytes = 0;
+    qt::DevPlan dp{};
+    qt::DevEpilogue de{};
+    double* d_angles = nullptr;  // gammas (n_graphs*p) then betas (n_graphs*p)
+    double* d_out = nullptr;     // zz | zz_imag | energies
+    int32_t* h_err = nullptr;    // pinned copy of the kernel error word
+    int grid = 0;
+
+    // execution
+    cudaStream_t stream = nullptr;  // internal stream (NULL-stream calls and graph capture)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_nodes[2] = {nullptr, nullptr};
+    cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+    cudaEvent_t ring[kRing][2] = {};
+    bool ring_pending[kRing] = {};
+    uint64_t calls = 0;
+    double time_ms = 0;
+    int64_t timed = 0;
+    bool err_pending = false;
+    bool host_only = false;
+
+    ~qt_plan_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto& e : cap_ev)
+            if (e) cudaEventDestroy(e);
+        for (auto& r : ring)
+            for (auto& e : r)
+                if (e) cudaEventDestroy(e);
+        if (stream) cudaStreamDestroy(stream);
+        if (d_arena) cudaFree(d_arena);
+        if (d_static) cudaFree(d_static);
+        if (d_counters) cudaFree(d_counters);
+        if (d_angles) cudaFree(d_angles);
+        if (d_out) cudaFree(d_out);
+        if (h_err) cudaFreeHost(h_err);
+    }
+};
+
+namespace {
+
+#define QT_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            return e_ == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA; \
+        }                                              \
+    } while (0)
+
+bool is_host_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
+}
+
+template <typename T>
+size_t bytes_of(const std::vector<T>& v) {
+    return v.size() * sizeof(T);
+}
+
+int upload(qt_plan_t P) {
+    qt::HostPlan& hp = P->hp;
+    QT_CUDA(cudaGetDevice(&P->device));
+    // tensors
+    P->arena_bytes = (size_t)hp.total_elems * P->esize;
+    size_t free_b = 0, total_b = 0;
+    QT_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (P->arena_bytes + (256u << 20) > free_b) return QT_ENOMEM;
+    QT_CUDA(cudaMalloc(&P->d_arena, std::max<size_t>(P->arena_bytes, 256)));
+
+    // static plan arrays, one allocation, 256-byte aligned pieces
+    std::vector<uint32_t> u_graph_first_net(hp.graph_first_net.begin(), hp.graph_first_net.end());
+    struct Piece {
+        const void* src;
+        size_t bytes;
+        size_t off;
+    };
+    std::vector<Piece> pieces = {
+        {hp.buckets.data(), bytes_of(hp.buckets), 0},         {hp.operands.data(), bytes_of(hp.operands), 0},
+        {hp.item_begin.data(), bytes_of(hp.item_begin), 0},   {hp.tasks_bucket.data(), bytes_of(hp.tasks_bucket), 0},
+        {hp.tasks_chunk.data(), bytes_of(hp.tasks_chunk), 0}, {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
+        {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
+    };
+    size_t total = 0;
+    for (auto& pc : pieces) {
+        pc.off = total;
+        total += (pc.bytes + 255) / 256 * 256;
+    }
+    QT_CUDA(cudaMalloc(&P->d_static, std::max<size_t>(total, 256)));
+    std::vector<char> staging(total);
+    for (auto& pc : pieces)
+        if (pc.bytes) std::memcpy(staging.data() + pc.off, pc.src, pc.bytes);
+    QT_CUDA(cudaMemcpy(P->d_static, staging.data(), total, cudaMemcpyHostToDevice));
+    char* base = static_cast<char*>(P->d_static);
+
+    const uint32_t nb = (uint32_t)hp.buckets.size();
+    P->counters_bytes = (size_t)2 * nb * sizeof(uint32_t) + sizeof(qt::DControl);
+    P->counters_bytes = (P->counters_bytes + 255) / 256 * 256;
+    QT_CUDA(cudaMalloc(&P->d_counters, P->counters_bytes));
+    QT_CUDA(cudaMemset(P->d_counters, 0, P->counters_bytes));
+
+    const int n_graphs = (int)hp.graphs.size();
+    const int n_nets = (int)hp.nets.size();
+    QT_CUDA(cudaMalloc((void**)&P->d_angles, sizeof(double) * 2 * n_graphs * hp.cfg.p));
+    QT_CUDA(cudaMalloc((void**)&P->d_out, sizeof(double) * (2 * n_nets + n_graphs)));
+    QT_CUDA(cudaHostAlloc((void**)&P->h_err, 2 * sizeof(int32_t), cudaHostAllocDefault));
+    P->h_err[0] = P->h_err[1] = 0;
+
+    qt::DevPlan& dp = P->dp;
+    dp.buckets = reinterpret_cast<const qt::DBucket*>(base + pieces[0].off);
+    dp.ops = reinterpret_cast<const qt::DOperand*>(base + pieces[1].off);
+    dp.item_begin = reinterpret_cast<const uint32_t*>(base + pieces[2].off);
+    dp.task_bucket = reinterpret_cast<const uint32_t*>(base + pieces[3].off);
+    dp.task_chunk = reinterpret_cast<const uint32_t*>(base + pieces[4].off);
+    dp.n_items = (uint32_t)(hp.item_begin.size() - 1);
+    dp.n_buckets = nb;
+    dp.chunks_done = static_cast<uint32_t*>(P->d_counters);
+    dp.deps_done = dp.chunks_done + nb;
+    dp.ctl = reinterpret_cast<qt::DControl*>(dp.deps_done + nb);
+    dp.arena = P->d_arena;
+    dp.spin_limit = P->spin_limit;
+
+    qt::DevEpilogue& de = P->de;
+    de.buckets = dp.buckets;
+    de.net_first_root = reinterpret_cast<const uint32_t*>(base + pieces[5].off);
+    de.root_bucket = reinterpret_cast<const uint32_t*>(base + pieces[6].off);
+    de.graph_first_net = reinterpret_cast<const int32_t*>(base + pieces[7].off);
+    de.n_graphs = n_graphs;
+    de.arena = P->d_arena;
+    de.zz = P->d_out;
+    de.zz_imag = P->d_out + n_nets;
+    de.energies = P->d_out + 2 * n_nets;
+
+    int sms = 0;
+    QT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+    P->grid = sms * qt::persistent_blocks_per_sm(P->dtype);
+    QT_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    QT_CUDA(cudaEventCreate(&P->cap_ev[0]));
+    QT_CUDA(cudaEventCreate(&P->cap_ev[1]));
+    for (auto& r : P->ring) {
+        QT_CUDA(cudaEventCreate(&r[0]));
+        QT_CUDA(cudaEventCreate(&r[1]));
+    }
+    return QT_OK;
+}
+
+// Everything one evaluation runs after the angles are in place, on stream s.
+int enqueue_eval(qt_plan_t P, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    qt::HostPlan& hp = P->hp;
+    QT_CUDA(qt::launch_leaf_fill(P->dtype, P->d_angles, (int)hp.graphs.size(), hp.cfg.p, P->d_arena, s));
+    if (P->sched == QT_SCHED_PERSISTENT) {
+        QT_CUDA(cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, s));
+        QT_CUDA(cudaEventRecord(e0, s));
+        QT_CUDA(qt::launch_persistent(P->dtype, P->grid, P->dp, s));
+        QT_CUDA(cudaEventRecord(e1, s));
+    } else {
+        QT_CUDA(cudaEventRecord(e0, s));
+        for (size_t b = 0; b < hp.buckets.size(); ++b)
+            QT_CUDA(qt::launch_per_bucket(P->dtype, (uint32_t)b, hp.buckets[b].n_tasks, P->dp, s));
+        QT_CUDA(cudaEventRecord(e1, s));
+    }
+    QT_CUDA(qt::launch_epilogue(P->dtype, P->de, s));
+    QT_CUDA(cudaMemcpyAsync(P->h_err, &P->dp.ctl->error, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    return QT_OK;
+}
+
+int ensure_graph(qt_plan_t P) {
+    if (P->exec) return QT_OK;
+    QT_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_eval(P, P->stream, P->cap_ev[0], P->cap_ev[1]);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+    if (rc != QT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return QT_ECUDA;
+    P->graph = g;
+    size_t n = 0;
+    QT_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    QT_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        QT_CUDA(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        QT_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        if (ev == P->cap_ev[0]) P->ev_nodes[0] = nd;
+        if (ev == P->cap_ev[1]) P->ev_nodes[1] = nd;
+    }
+    if (!P->ev_nodes[0] || !P->ev_nodes[1]) return QT_ECUDA;
+    QT_CUDA(cudaGraphInstantiate(&P->exec, g, 0));
+    return QT_OK;
+}
+
+void harvest_slot(qt_plan_t P, int slot) {
+    if (!P->ring_pending[slot]) return;
+    if (cudaEventSynchronize(P->ring[slot][1]) == cudaSuccess) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, P->ring[slot][0], P->ring[slot][1]) == cudaSuccess) {
+            P->time_ms += ms;
+            P->timed++;
+        }
+    }
+    cudaGetLastError();
+    P->ring_pending[slot] = false;
+}
+
+int check_error_word(qt_plan_t P) {
+    int32_t e = P->h_err[0];
+    if (e != 0) {
+        P->h_err[0] = 0;
+        return e;
+    }
+    return QT_OK;
+}
+
+// One evaluation: angles in, run, results out.
+int run_eval(qt_plan_t P, const double* gammas, const double* betas, void* stream_v,
+             double* zz_out, double* energies_out, bool all_nets_out) {
+    const int G = (int)P->hp.graphs.size();
+    const int p = P->hp.cfg.p;
+    const int n_nets = (int)P->hp.nets.size();
+    if (!gammas || !betas) return QT_EINVAL;
+    if (P->host_only) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    cudaStream_t s = stream_v ? static_cast<cudaStream_t>(stream_v) : P->stream;
+    QT_CUDA(cudaMemcpyAsync(P->d_angles, gammas, sizeof(double) * G * p, cudaMemcpyDefault, s));
+    QT_CUDA(cudaMemcpyAsync(P->d_angles + (size_t)G * p, betas, sizeof(double) * G * p, cudaMemcpyDefault, s));
+
+    const int slot = (int)(P->calls % kRing);
+    harvest_slot(P, slot);
+    if (P->sched == QT_SCHED_PERSISTENT) {
+        int rc = ensure_graph(P);
+        if (rc != QT_OK) return rc;
+        QT_CUDA(cudaGraphExecEventRecordNodeSetEvent(P->exec, P->ev_nodes[0], P->ring[slot][0]));
+        QT_CUDA(cudaGraphExecEventRecordNodeSetEvent(P->exec, P->ev_nodes[1], P->ring[slot][1]));
+        QT_CUDA(cudaGraphLaunch(P->exec, s));
+    } else {
+        int rc = enqueue_eval(P, s, P->ring[slot][0], P->ring[slot][1]);
+        if (rc != QT_OK) return rc;
+    }
+    P->ring_pending[slot] = true;
+    P->calls++;
+    P->err_pending = true;
+
+    bool host_out = false;
+    if (zz_out) {
+        size_t nz = all_nets_out ? (size_t)n_nets : (size_t)n_nets;
+        QT_CUDA(cudaMemcpyAsync(zz_out, P->de.zz, sizeof(double) * nz, cudaMemcpyDefault, s));
+        host_out |= is_host_ptr(zz_out);
+    }
+    if (energies_out) {
+        QT_CUDA(cudaMemcpyAsync(energies_out, P->de.energies, sizeof(double) * G, cudaMemcpyDefault, s));
+        host_out |= is_host_ptr(energies_out);
+    }
+    if (host_out || !stream_v) {
+        QT_CUDA(cudaStreamSynchronize(s));
+        P->err_pending = false;
+        return check_error_word(P);
+    }
+    return QT_OK;
+}
+
+qt_plan_opts default_opts() {
+    qt_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    return o;
+}
+
+int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_opts* opts_in, qt_plan_t* out) {
+    if (!out) return QT_EINVAL;
+    *out = nullptr;
+    qt_plan_opts o = opts_in ? *opts_in : default_opts();
+    if (o.dtype != QT_C64 && o.dtype != QT_C128) return QT_EINVAL;
+    if (o.sched != QT_SCHED_PERSISTENT && o.sched != QT_SCHED_PER_BUCKET) return QT_EINVAL;
+    qt::PlanConfig cfg;
+    cfg.p = p;
+    cfg.dtype = o.dtype;
+    cfg.restarts = std::max(0, o.order_restarts);
+    cfg.seed = o.order_seed;
+    cfg.max_width = o.max_width > 0 ? o.max_width : 31;
+    cfg.chunk_log2 = o.chunk_log2;
+    cfg.with_grad = o.with_grad != 0;
+    if (cfg.chunk_log2 < 0 || cfg.chunk_log2 > 24) return QT_EINVAL;
+    std::unique_ptr<qt_plan_s> P(new (std::nothrow) qt_plan_s());
+    if (!P) return QT_ENOMEM;
+    P->dtype = o.dtype;
+    P->sched = o.sched;
+    P->esize = o.dtype == QT_C128 ? 16 : 8;
+    P->spin_limit = o.spin_limit ? o.spin_limit : (1ull << 23);
+    int rc;
+    try {
+        rc = qt::build_host_plan(graphs, cfg, &P->hp);
+    } catch (const std::bad_alloc&) {
+        return QT_ENOMEM;
+    } catch (...) {
+        return QT_EINVAL;
+    }
+    if (rc != QT_OK) return rc;
+    if (o.arena_bytes && (size_t)P->hp.total_elems * P->esize > o.arena_bytes) return QT_ENOMEM;
+    P->arena_bytes = (size_t)P->hp.total_elems * P->esize;
+    P->host_only = o.host_only != 0;
+    if (!P->host_only) {
+        rc = upload(P.get());
+        if (rc != QT_OK) return rc;
+    }
+    *out = P.release();
+    return QT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qt_plan(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int32_t p, const qt_plan_opts* opts,
+            qt_plan_t* out) {
+    if (!edges || n_edges < 1 || n_vertices < 2) return QT_EINVAL;
+    std::vector<qt::GraphIn> gs(1);
+    gs[0].n = n_vertices;
+    for (int e = 0; e < n_edges; ++e) gs[0].edges.emplace_back(edges[2 * e], edges[2 * e + 1]);
+    return make_plan(gs, p, opts, out);
+}
+
+int qt_plan_batch(int32_t n_graphs, const int32_t* n_vertices, const int32_t* n_edges, const int32_t* edges,
+                  int32_t p, const qt_plan_opts* opts, qt_plan_t* out) {
+    if (n_graphs < 1 || !n_vertices || !n_edges || !edges) return QT_EINVAL;
+    std::vector<qt::GraphIn> gs(n_graphs);
+    size_t at = 0;
+    for (int g = 0; g < n_graphs; ++g) {
+        if (n_edges[g] < 1 || n_vertices[g] < 2) return QT_EINVAL;
+        gs[g].n = n_vertices[g];
+        for (int e = 0; e < n_edges[g]; ++e, ++at) gs[g].edges.emplace_back(edges[2 * at], edges[2 * at + 1]);
+    }
+    return make_plan(gs, p, opts, out);
+}
+
+int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
+    if (!P || !out) return QT_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    const qt::HostPlan& hp = P->hp;
+    out->n_graphs = (int32_t)hp.graphs.size();
+    out->n_networks = (int32_t)hp.nets.size();
+    out->n_buckets = (int64_t)hp.buckets.size();
+    out->n_operands = (int64_t)hp.operands.size();
+    out->max_width = hp.max_width;
+    out->p = hp.cfg.p;
+    out->sum_2w = hp.sum_2w;
+    out->alg_bytes = hp.alg_bytes;
+    out->flops = hp.flops;
+    out->arena_bytes = (int64_t)P->arena_bytes;  // what the device arena takes (or would take)
+    out->n_tasks = (int64_t)hp.tasks_bucket.size();
+    out->n_items = (int64_t)hp.item_begin.size() - 1;
+    out->n_levels = hp.n_levels;
+    out->dtype = P->dtype;
+    std::memcpy(out->width_hist, hp.width_hist, sizeof(out->width_hist));
+    out->plan_seconds = hp.plan_seconds;
+    return QT_OK;
+}
+
+int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operands) {
+    if (!P) return QT_EINVAL;
+    const qt::HostPlan& hp = P->hp;
+    if (buckets) {
+        for (size_t b = 0; b < hp.buckets.size(); ++b) {
+            const qt::DBucket& d = hp.buckets[b];
+            qt_bucket_info& o = buckets[b];
+            o.network = (int32_t)d.net;
+            o.width = d.n_out + 1;
+            o.n_ops = d.n_ops;
+            o.op_begin = (int32_t)d.op_begin;
+            o.parent = d.parent == qt::kNone ? -1 : (int32_t)d.parent;
+            o.n_deps = (int32_t)d.n_deps;
+            o.level = hp.bucket_level[b];
+            o.var = hp.bucket_var[b];
+        }
+    }
+    if (operands) {
+        for (size_t i = 0; i < hp.operands.size(); ++i) {
+            qt_operand_info& o = operands[i];
+            o.src = hp.op_src[i];
+            o.leaf_kind = hp.op_leaf_kind[i];
+            o.leaf_layer = hp.op_leaf_layer[i];
+            o.mask = hp.operands[i].mask;
+            o.rank = hp.op_rank[i];
+            o.pad = 0;
+        }
+    }
+    return QT_OK;
+}
+
+int qt_plan_network_wires(qt_plan_t P, int32_t network, int32_t* vars_per_qubit) {
+    if (!P || !vars_per_qubit || network < 0 || network >= (int32_t)P->hp.nets.size()) return QT_EINVAL;
+    const qt::Network& net = P->hp.nets[network];
+    for (size_t q = 0; q < net.wire_vars.size(); ++q) vars_per_qubit[q] = net.wire_vars[q];
+    return QT_OK;
+}
+
+int qt_energy(qt_plan_t P, const double* gammas, const double* betas, double* edge_zz, double* energy,
+              void* cuda_stream) {
+    if (!P) return QT_EINVAL;
+    if (P->hp.graphs.size() != 1) return QT_ESTATE;
+    return run_eval(P, gammas, betas, cuda_stream, edge_zz, energy, false);
+}
+
+int qt_energy_batch(qt_plan_t P, const double* gammas, const double* betas, double* energies, double* edge_zz,
+                    void* cuda_stream) {
+    if (!P) return QT_EINVAL;
+    return run_eval(P, gammas, betas, cuda_stream, edge_zz, energies, true);
+}
+
+int qt_energy_grad(qt_plan_t P, const double*, const double*, double*, double*, double*, void*) {
+    if (!P) return QT_EINVAL;
+    return QT_ESTATE;
+}
+
+int qt_last_imag(qt_plan_t P, double* edge_imag) {
+    if (!P || !edge_imag) return QT_EINVAL;
+    if (P->host_only) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    QT_CUDA(cudaStreamSynchronize(P->stream));
+    QT_CUDA(cudaDeviceSynchronize());
+    QT_CUDA(cudaMemcpy(edge_imag, P->de.zz_imag, sizeof(double) * P->hp.nets.size(), cudaMemcpyDeviceToHost));
+    return QT_OK;
+}
+
+int qt_sync(qt_plan_t P, void* cuda_stream) {
+    if (!P) return QT_EINVAL;
+    if (P->host_only) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    QT_CUDA(cudaStreamSynchronize(cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : P->stream));
+    P->err_pending = false;
+    return check_error_word(P);
+}
+
+int qt_kernel_time(qt_plan_t P, double* avg_ms, int64_t* launches, int32_t reset) {
+    if (!P) return QT_EINVAL;
+    if (P->host_only) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    for (int s = 0; s < kRing; ++s) harvest_slot(P, s);
+    if (avg_ms) *avg_ms = P->timed ? P->time_ms / (double)P->timed : 0.0;
+    if (launches) *launches = P->timed;
+    if (reset) {
+        P->time_ms = 0;
+        P->timed = 0;
+    }
+    return QT_OK;
+}
+
+int qt_debug_stall_bucket(qt_plan_t P, int64_t bucket) {
+    if (!P || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
+    if (P->host_only) return QT_ESTATE;
+    qt::DBucket d = P->hp.buckets[bucket];
+    d.n_deps += 1;
+    QT_CUDA(cudaSetDevice(P->device));
+    QT_CUDA(cudaMemcpy((void*)(P->dp.buckets + bucket), &d, sizeof(d), cudaMemcpyHostToDevice));
+    return QT_OK;
+}
+
+void qt_plan_free(qt_plan_t P) {
+    if (!P) return;
+    if (!P->host_only) {
+        cudaSetDevice(P->device);
+        if (P->stream) cudaStreamSynchronize(P->stream);
+    }
+    delete P;
+}
+
+const char* qt_error_string(int code) {
+    switch (code) {
+        case QT_OK: return "ok";
+        case QT_EINVAL: return "invalid argument";
+        case QT_EWIDTH: return "bucket wider than max_width";
+        case QT_ENOMEM: return "out of memory";
+        case QT_ECUDA: return "CUDA runtime error";
+        case QT_ETIMEOUT: return "kernel dependency wait timed out";
+        case QT_EBOUNDS: return "operand index out of bounds";
+        case QT_ESTATE: return "call not valid for this plan";
+        default: return "unknown error";
+    }
+}
+
+const char* qt_version(void) { return "qtgb 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Launch wrappers for the CUDA kernels (called only by the C ABI layer).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qt_internal.hpp"
+
+namespace qt {
+
+// Device view of a plan, passed to kernels by value.
+struct DevPlan {
+    const DBucket* buckets;
+    const DOperand* ops;
+    const uint32_t* item_begin;
+    const uint32_t* task_bucket;
+    const uint32_t* task_chunk;
+    uint32_t n_items;
+    uint32_t n_buckets;
+    uint32_t* chunks_done;  // n_buckets
+    uint32_t* deps_done;    // n_buckets
+    DControl* ctl;
+    void* arena;            // complex64 or complex128 elements
+    uint64_t spin_limit;
+};
+
+// Everything the epilogue reads and writes.
+struct DevEpilogue {
+    const DBucket* buckets;
+    const uint32_t* net_first_root;  // n_nets + 1
+    const uint32_t* root_bucket;
+    const int32_t* graph_first_net;  // n_graphs + 1
+    int32_t n_graphs;
+    const void* arena;
+    double* zz;        // n_nets
+    double* zz_imag;   // n_nets
+    double* energies;  // n_graphs
+};
+
+cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, cudaStream_t s);
+cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream_t s);
+cudaError_t launch_per_bucket(int dtype, uint32_t bucket, uint32_t n_tasks, const DevPlan& dp, cudaStream_t s);
+cudaError_t launch_epilogue(int dtype, const DevEpilogue& de, cudaStream_t s);
+int persistent_blocks_per_sm(int dtype);
+constexpr int kPersistentThreads = 256;
+
+}  // namespace qt

@@ -1,0 +1,486 @@
+// Host planner: lightcone networks (§II-B), greedy min-fill elimination
+// orders, bucket schedules with rank-sorted index bits, and the flat layout
+// the kernels read.
+#include "planner.hpp"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <queue>
+#include <set>
+#include <thread>
+
+#include "../../include/qt.h"
+
+namespace qt {
+
+namespace {
+
+uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct Rng {
+    uint64_t s;
+    uint64_t next() { return s = mix64(s); }
+};
+
+inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+int leaf_slots_per_graph(int p) { return 2 + 4 * p; }
+
+int leaf_index(int kind, int layer) {
+    if (kind == QT_LEAF_PLUS) return 0;
+    if (kind == QT_LEAF_ZOBS) return 1;
+    return 2 + 4 * layer + (kind - QT_LEAF_ZZ);
+}
+
+// ---------------------------------------------------------------------------
+// Lightcone network of one edge (§II-B).
+//
+// For edge (j,k) let d(q) be the graph distance from {j,k}. Working outward
+// from Z_j Z_k, the mixer of layer k (1-based) survives the cancellation of
+// U^dagger (Z_j Z_k) U only on qubits with d(q) <= p - k, and the ZZ gate of
+// layer k on edge (a,b) only when min(d(a), d(b)) <= p - k. Diagonal gates add
+// no variable: a ZZ phase is a rank-2 tensor on the two current variables, a
+// mixer is a rank-2 tensor from the current variable to a fresh one. The bra
+// half mirrors the ket half with conjugated tensors.
+// ---------------------------------------------------------------------------
+static void build_network(const GraphIn& g, int p, int eidx, Network* net) {
+    const int n = g.n;
+    std::vector<std::vector<int>> nbr(n);
+    for (auto& e : g.edges) {
+        nbr[e.first].push_back(e.second);
+        nbr[e.second].push_back(e.first);
+    }
+    const int j = g.edges[eidx].first, k = g.edges[eidx].second;
+    std::vector<int> dist(n, -1);
+    std::queue<int> bfs;
+    dist[j] = dist[k] = 0;
+    bfs.push(j);
+    bfs.push(k);
+    while (!bfs.empty()) {
+        int a = bfs.front();
+        bfs.pop();
+        if (dist[a] == p) continue;
+        for (int b : nbr[a])
+            if (dist[b] < 0) {
+                dist[b] = dist[a] + 1;
+                bfs.push(b);
+            }
+    }
+    auto in_zz = [&](int a, int b, int layer1) {
+        int da = dist[a] < 0 ? (1 << 30) : dist[a];
+        int db = dist[b] < 0 ? (1 << 30) : dist[b];
+        return std::min(da, db) <= p - layer1;
+    };
+    auto has_mixer = [&](int q, int layer1) { return dist[q] >= 0 && dist[q] <= p - layer1; };
+
+    net->nvars = 0;
+    net->leaves.clear();
+    net->wire_vars.assign(n, 0);
+    std::vector<int> cur(n, -1);
+    auto add1 = [&](int kind, int v) { net->leaves.push_back(Leaf{kind, -1, 1, {v, -1}}); };
+    auto add2 = [&](int kind, int layer, int a, int b) { net->leaves.push_back(Leaf{kind, layer, 2, {a, b}}); };
+
+    for (int q = 0; q < n; ++q)
+        if (dist[q] >= 0) {
+            cur[q] = net->nvars++;
+            net->wire_vars[q] = 1;
+            add1(QT_LEAF_PLUS, cur[q]);
+        }
+    for (int l = 1; l <= p; ++l) {
+        for (auto& e : g.edges)
+            if (in_zz(e.first, e.second, l)) add2(QT_LEAF_ZZ, l - 1, cur[e.first], cur[e.second]);
+        for (int q = 0; q < n; ++q)
+            if (has_mixer(q, l)) {
+                int nv = net->nvars++;
+                net->wire_vars[q]++;
+                add2(QT_LEAF_RX, l - 1, cur[q], nv);
+                cur[q] = nv;
+            }
+    }
+    add1(QT_LEAF_ZOBS, cur[j]);
+    add1(QT_LEAF_ZOBS, cur[k]);
+    for (int l = p; l >= 1; --l) {
+        for (int q = 0; q < n; ++q)
+            if (has_mixer(q, l)) {
+                int nv = net->nvars++;
+                net->wire_vars[q]++;
+                add2(QT_LEAF_RX_CONJ, l - 1, cur[q], nv);
+                cur[q] = nv;
+            }
+        for (auto& e : g.edges)
+            if (in_zz(e.first, e.second, l)) add2(QT_LEAF_ZZ_CONJ, l - 1, cur[e.first], cur[e.second]);
+    }
+    for (int q = 0; q < n; ++q)
+        if (dist[q] >= 0) add1(QT_LEAF_PLUS, cur[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Greedy min-fill elimination order (the paper's ordering algorithm is not
+// specified, §II-D). The interaction graph joins variables that share a
+// tensor; each step eliminates the variable whose neighbours need the fewest
+// new edges to form a clique, ties going to the smaller degree and then to the
+// lowest variable id (or to a random one for the randomised restarts). The
+// bucket of a variable eliminated with degree d has width d + 1.
+// ---------------------------------------------------------------------------
+static void order_min_fill(const Network& net, bool randomized, uint64_t seed, std::vector<int>* order,
+                           double* cost, int* maxw) {
+    const int V = net.nvars, W = (V + 63) / 64;
+    std::vector<uint64_t> adj((size_t)V * W, 0), alive(W, 0);
+    auto row = [&](int v) { return &adj[(size_t)v * W]; };
+    for (auto& L : net.leaves)
+        if (L.rank == 2 && L.v[0] != L.v[1]) {
+            row(L.v[0])[L.v[1] >> 6] |= 1ull << (L.v[1] & 63);
+            row(L.v[1])[L.v[0] >> 6] |= 1ull << (L.v[0] & 63);
+        }
+    for (int v = 0; v < V; ++v) alive[v >> 6] |= 1ull << (v & 63);
+    Rng rng{seed};
+    order->clear();
+    *cost = 0;
+    *maxw = 0;
+    for (int step = 0; step < V; ++step) {
+        long best_fill = -1;
+        int best_deg = 0, best = -1;
+        uint64_t ties = 0;
+        for (int v = 0; v < V; ++v) {
+            if (!((alive[v >> 6] >> (v & 63)) & 1)) continue;
+            const uint64_t* nv = row(v);
+            int deg = 0;
+            for (int w = 0; w < W; ++w) deg += popc64(nv[w]);
+            if (best >= 0 && best_fill == 0 && deg > best_deg) continue;
+            long fill = 0;
+            for (int w = 0; w < W; ++w) {
+                uint64_t bits = nv[w];
+                while (bits) {
+                    int a = (w << 6) | __builtin_ctzll(bits);
+                    bits &= bits - 1;
+                    const uint64_t* na = row(a);
+                    for (int u = 0; u < W; ++u) {
+                        uint64_t miss = nv[u] & ~na[u];
+                        if (u == (a >> 6)) miss &= ~(1ull << (a & 63));
+                        fill += popc64(miss);
+                    }
+                }
+            }
+            fill /= 2;
+            bool better = best < 0 || fill < best_fill || (fill == best_fill && deg < best_deg);
+            bool equal = !better && fill == best_fill && deg == best_deg;
+            if (better) {
+                best = v;
+                best_fill = fill;
+                best_deg = deg;
+                ties = 1;
+            } else if (equal && randomized) {
+                ++ties;
+                if (rng.next() % ties == 0) best = v;
+            }
+        }
+        const int v = best;
+        order->push_back(v);
+        const int width = best_deg + 1;
+        *cost += std::ldexp(1.0, width);
+        *maxw = std::max(*maxw, width);
+        std::vector<uint64_t> nv(row(v), row(v) + W);
+        for (int w = 0; w < W; ++w) {
+            uint64_t bits = nv[w];
+            while (bits) {
+                int a = (w << 6) | __builtin_ctzll(bits);
+                bits &= bits - 1;
+                uint64_t* ra = row(a);
+                for (int u = 0; u < W; ++u) ra[u] |= nv[u];
+                ra[a >> 6] &= ~(1ull << (a & 63));
+                ra[v >> 6] &= ~(1ull << (v & 63));
+            }
+        }
+        std::fill(row(v), row(v) + W, 0ull);
+        alive[v >> 6] &= ~(1ull << (v & 63));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bucket schedule for one order (§II-B). Every tensor goes to the bucket of
+// its earliest variable. Bucket v multiplies its tensors and sums v out; the
+// result's variables are the rest of the bucket's union, kept in rank order,
+// and it joins the bucket of the earliest of them. Index bits of every tensor
+// are its variables in rank order, earliest first, so v is bit 0 of each
+// operand and each operand's other bits are a subset (mask) of the output's.
+// ---------------------------------------------------------------------------
+static int make_buckets(const Network& net, const std::vector<int>& order, int max_width, NetPlan* np) {
+    const int V = net.nvars;
+    std::vector<int> pos(V);
+    for (int i = 0; i < V; ++i) pos[order[i]] = i;
+    struct Tens {
+        std::vector<int> vars;  // sorted by rank
+        int src;                // producing bucket or -1
+        int leaf;
+    };
+    std::vector<Tens> pool;
+    std::vector<std::vector<int>> bucket_of(V);  // tensors waiting per variable
+    pool.reserve(net.leaves.size() + V);
+    for (size_t t = 0; t < net.leaves.size(); ++t) {
+        const Leaf& L = net.leaves[t];
+        Tens T;
+        T.vars.assign(L.v, L.v + L.rank);
+        std::sort(T.vars.begin(), T.vars.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        T.src = -1;
+        T.leaf = (int)t;
+        bucket_of[T.vars[0]].push_back((int)pool.size());
+        pool.push_back(std::move(T));
+    }
+    np->buckets.clear();
+    np->buckets.reserve(V);
+    np->cost = 0;
+    np->max_width = 0;
+    std::vector<int> bucket_at(V, -1);  // bucket id by variable
+    for (int step = 0; step < V; ++step) {
+        const int v = order[step];
+        auto& list = bucket_of[v];
+        if (list.empty()) continue;  // cannot happen: every variable sits in a leaf
+        std::vector<int> uni;
+        for (int t : list)
+            for (int x : pool[t].vars) uni.push_back(x);
+        std::sort(uni.begin(), uni.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+        const int w = (int)uni.size();
+        if (w > max_width) return QT_EWIDTH;
+        if ((int)list.size() > kMaxOps) return QT_EWIDTH;
+        HBucket B;
+        B.var = v;
+        B.width = w;
+        B.parent = -1;
+        B.n_deps = 0;
+        B.level = 0;
+        const int bid = (int)np->buckets.size();
+        bucket_at[v] = bid;
+        for (int t : list) {
+            const Tens& T = pool[t];
+            HOperand op;
+            op.src = T.src;
+            op.leaf = T.leaf;
+            op.rank = (int)T.vars.size();
+            op.mask = 0;
+            for (size_t i = 1; i < T.vars.size(); ++i) {
+                int at = (int)(std::find(uni.begin() + 1, uni.end(), T.vars[i]) - uni.begin()) - 1;
+                op.mask |= 1u << at;
+            }
+            if (T.src >= 0) {
+                B.n_deps++;
+                np->buckets[T.src].parent = bid;
+                B.level = std::max(B.level, np->buckets[T.src].level + 1);
+            }
+            B.ops.push_back(op);
+        }
+        np->cost += std::ldexp(1.0, w);
+        np->max_width = std::max(np->max_width, w);
+        list.clear();
+        if (w > 1) {
+            Tens R;
+            R.vars.assign(uni.begin() + 1, uni.end());
+            R.src = bid;
+            R.leaf = -1;
+            bucket_of[R.vars[0]].push_back((int)pool.size());
+            pool.push_back(std::move(R));
+        }
+        np->buckets.push_back(std::move(B));
+    }
+    return QT_OK;
+}
+
+static int default_chunk_bits(int n_out) {
+    // Outputs per persistent task, by output size. Small buckets run whole;
+    // wide ones are cut into 4096-output tiles so all SMs share them.
+    return std::min(n_out, 12);
+}
+
+static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, HostPlan* hp) {
+    auto t0 = std::chrono::steady_clock::now();
+    hp->cfg = cfg;
+    hp->graphs = graphs;
+    if (cfg.p < 1 || cfg.p > 64 || graphs.empty()) return QT_EINVAL;
+    if (cfg.max_width < 2 || cfg.max_width > kMaxOutBits + 1) return QT_EINVAL;
+    for (auto& g : graphs) {
+        if (g.n < 2 || g.edges.empty()) return QT_EINVAL;
+        std::set<std::pair<int, int>> seen;
+        for (auto& e : g.edges) {
+            if (e.first < 0 || e.second < 0 || e.first >= g.n || e.second >= g.n || e.first == e.second)
+                return QT_EINVAL;
+            auto key = std::minmax(e.first, e.second);
+            if (!seen.insert(key).second) return QT_EINVAL;
+        }
+    }
+    // networks, one per edge of every graph
+    hp->graph_first_net.assign(1, 0);
+    for (size_t g = 0; g < graphs.size(); ++g)
+        hp->graph_first_net.push_back(hp->graph_first_net.back() + (int)graphs[g].edges.size());
+    const int n_nets = hp->graph_first_net.back();
+    hp->nets.assign(n_nets, Network());
+    hp->nplans.assign(n_nets, NetPlan());
+    std::vector<int> status(n_nets, QT_OK);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (;;) {
+            int i = next.fetch_add(1);
+            if (i >= n_nets) break;
+            int g = (int)(std::upper_bound(hp->graph_first_net.begin(), hp->graph_first_net.end(), i) -
+                          hp->graph_first_net.begin()) - 1;
+            Network& net = hp->nets[i];
+            net.graph = g;
+            net.edge = i - hp->graph_first_net[g];
+            build_network(graphs[g], cfg.p, net.edge, &net);
+            std::vector<int> best_order, ord;
+            double best_cost = 0, c = 0;
+            int best_w = 0, w = 0;
+            order_min_fill(net, false, 0, &best_order, &best_cost, &best_w);
+            for (int r = 0; r < cfg.restarts; ++r) {
+                order_min_fill(net, true, mix64(cfg.seed ^ mix64((uint64_t)i * 1315423911ull + r)), &ord, &c, &w);
+                if (c < best_cost) {
+                    best_cost = c;
+                    best_order = ord;
+                    best_w = w;
+                }
+            }
+            if (best_w > cfg.max_width) {
+                status[i] = QT_EWIDTH;
+                continue;
+            }
+            NetPlan& np = hp->nplans[i];
+            np.order = best_order;
+            status[i] = make_buckets(net, best_order, cfg.max_width, &np);
+        }
+    };
+    unsigned nthreads = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+    nthreads = std::min<unsigned>(nthreads, (unsigned)n_nets);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t + 1 < nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    for (int s : status)
+        if (s != QT_OK) return s;
+
+    // ---- flatten ---------------------------------------------------------
+    const uint64_t esize = cfg.dtype == 1 ? 16 : 8;
+    const uint64_t align = 128 / esize;
+    const int L = leaf_slots_per_graph(cfg.p);
+    hp->leaf_elems = align_up((uint64_t)graphs.size() * L * kLeafSlots, align);
+    uint64_t off = hp->leaf_elems;
+    hp->net_first_bucket.assign(1, 0);
+    hp->net_first_root.assign(1, 0);
+    hp->buckets.clear();
+    hp->operands.clear();
+    hp->max_width = 0;
+    hp->n_levels = 0;
+    hp->sum_2w = hp->alg_bytes = hp->flops = 0;
+    std::fill(hp->width_hist, hp->width_hist + 64, 0);
+    for (int i = 0; i < n_nets; ++i) {
+        const NetPlan& np = hp->nplans[i];
+        const Network& net = hp->nets[i];
+        const uint32_t base = (uint32_t)hp->buckets.size();
+        for (size_t lb = 0; lb < np.buckets.size(); ++lb) {
+            const HBucket& B = np.buckets[lb];
+            DBucket d{};
+            d.op_begin = (uint32_t)hp->operands.size();
+            d.n_ops = (uint16_t)B.ops.size();
+            d.n_out = (uint8_t)(B.width - 1);
+            int cb = cfg.chunk_log2 > 0 ? std::min<int>(d.n_out, cfg.chunk_log2) : default_chunk_bits(d.n_out);
+            d.chunk_bits = (uint8_t)cb;
+            d.parent = B.parent >= 0 ? base + (uint32_t)B.parent : kNone;
+            d.n_deps = (uint32_t)B.n_deps;
+            d.n_tasks = 1u << (d.n_out - cb);
+            d.net = (uint32_t)i;
+            d.out_off = off;
+            off += align_up(1ull << d.n_out, align);
+            double opbytes = 0;
+            for (const HOperand& op : B.ops) {
+                DOperand o{};
+                o.mask = op.mask;
+                if (op.src >= 0) {
+                    o.off = 0;  // set below, once every result has its offset
+                    o.flags = 0;
+                } else {
+                    const Leaf& lf = net.leaves[op.leaf];
+                    o.off = ((uint64_t)net.graph * L + leaf_index(lf.kind, lf.layer)) * kLeafSlots;
+                    o.flags = kOpLeaf;
+                }
+                hp->operands.push_back(o);
+                hp->op_src.push_back(op.src >= 0 ? (int32_t)(base + op.src) : -1);
+                hp->op_leaf_kind.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].kind);
+                hp->op_leaf_layer.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].layer);
+                hp->op_rank.push_back(op.rank);
+                opbytes += std::ldexp(1.0, op.rank);
+            }
+            hp->buckets.push_back(d);
+            hp->bucket_level.push_back(B.level);
+            hp->bucket_var.push_back(B.var);
+            if (B.parent < 0) hp->root_bucket.push_back(base + (uint32_t)lb);
+            hp->max_width = std::max(hp->max_width, B.width);
+            hp->n_levels = std::max(hp->n_levels, B.level + 1);
+            hp->width_hist[B.width]++;
+            hp->sum_2w += std::ldexp(1.0, B.width);
+            hp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - 1));
+            hp->flops += std::ldexp(1.0, B.width) * 6.0 * (double)(B.ops.size() - 1) + std::ldexp(1.0, B.width - 1) * 2.0;
+        }
+        hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());
+        hp->net_first_root.push_back((uint32_t)hp->root_bucket.size());
+    }
+    // intermediate operands point at their producer's result
+    for (size_t o = 0; o < hp->operands.size(); ++o)
+        if (hp->op_src[o] >= 0) hp->operands[o].off = hp->buckets[hp->op_src[o]].out_off;
+    hp->arena_elems = off;
+    hp->cot_off = 0;
+    hp->total_elems = off;
+    if (cfg.with_grad) {
+        hp->cot_off = off;  // cotangent of each result mirrors the result region
+        hp->total_elems = off + (off - hp->leaf_elems);
+    }
+
+    // ---- tasks in level order, grouped into work items ---------------------
+    const uint32_t nb = (uint32_t)hp->buckets.size();
+    hp->by_level.resize(nb);
+    for (uint32_t b = 0; b < nb; ++b) hp->by_level[b] = b;
+    std::stable_sort(hp->by_level.begin(), hp->by_level.end(),
+                     [&](uint32_t a, uint32_t b) { return hp->bucket_level[a] < hp->bucket_level[b]; });
+    hp->level_first_bucket.assign(hp->n_levels + 1, 0);
+    for (uint32_t b : hp->by_level) hp->level_first_bucket[hp->bucket_level[b] + 1]++;
+    for (int l = 0; l < hp->n_levels; ++l) hp->level_first_bucket[l + 1] += hp->level_first_bucket[l];
+    hp->tasks_bucket.clear();
+    hp->tasks_chunk.clear();
+    hp->item_begin.assign(1, 0);
+    const uint64_t item_outputs = 1u << 10;
+    const uint32_t item_max_tasks = 32;
+    uint64_t cur_out = 0;
+    uint32_t cur_tasks = 0;
+    int cur_level = -1;
+    for (uint32_t b : hp->by_level) {
+        const DBucket& d = hp->buckets[b];
+        const uint64_t per_task = 1ull << d.chunk_bits;
+        for (uint32_t c = 0; c < d.n_tasks; ++c) {
+            bool start_new = cur_tasks > 0 && (hp->bucket_level[b] != cur_level || cur_out + per_task > item_outputs ||
+                                                cur_tasks >= item_max_tasks);
+            if (start_new) {
+                hp->item_begin.push_back((uint32_t)hp->tasks_bucket.size());
+                cur_out = 0;
+                cur_tasks = 0;
+            }
+            hp->tasks_bucket.push_back(b);
+            hp->tasks_chunk.push_back(c);
+            cur_out += per_task;
+            cur_tasks++;
+            cur_level = hp->bucket_level[b];
+        }
+    }
+    if (cur_tasks > 0) hp->item_begin.push_back((uint32_t)hp->tasks_bucket.size());
+    hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QT_OK;
+}
+
+}  // namespace qt

@@ -1,0 +1,108 @@
+// Host-side planner: graph -> lightcone networks -> elimination orders ->
+// bucket schedule -> flat device layout.
+#pragma once
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "qt_internal.hpp"
+
+namespace qt {
+
+// A gate tensor of the network (rank 1 or 2). Kinds follow QT_LEAF_* in qt.h.
+struct Leaf {
+    int kind;
+    int layer;  // 0-based layer for ZZ / mixer tensors, -1 otherwise
+    int rank;
+    int v[2];
+};
+
+struct Network {
+    int graph = 0;
+    int edge = 0;  // edge index within its graph
+    int nvars = 0;
+    std::vector<Leaf> leaves;
+    std::vector<int> wire_vars;  // variables on each qubit's wire
+};
+
+struct HOperand {
+    int src;        // local bucket producing it, or -1 for a leaf
+    int leaf;       // leaf index in the network, or -1
+    uint32_t mask;  // output bits it carries
+    int rank;       // its index bits, the summed one included
+};
+
+struct HBucket {
+    int var;
+    int width;  // inclusive: the summed variable counts
+    int parent; // local id of the consuming bucket, -1 for a scalar result
+    int n_deps;
+    int level;
+    std::vector<HOperand> ops;
+};
+
+struct NetPlan {
+    std::vector<int> order;
+    std::vector<HBucket> buckets;  // in elimination order
+    double cost = 0;               // sum of 2^width
+    int max_width = 0;
+};
+
+struct GraphIn {
+    int n = 0;
+    std::vector<std::pair<int, int>> edges;
+};
+
+struct PlanConfig {
+    int p = 1;
+    int dtype = 0;  // 0 complex64, 1 complex128
+    int restarts = 0;
+    uint64_t seed = 0;
+    int max_width = 31;
+    int chunk_log2 = 0;
+    bool with_grad = false;
+};
+
+// The flat plan: what gets uploaded plus host-side bookkeeping.
+struct HostPlan {
+    PlanConfig cfg;
+    std::vector<GraphIn> graphs;
+    std::vector<Network> nets;
+    std::vector<NetPlan> nplans;
+
+    std::vector<int> graph_first_net;   // n_graphs + 1
+    std::vector<uint32_t> net_first_bucket;  // n_nets + 1
+    std::vector<DBucket> buckets;       // network-contiguous, elimination order within a network
+    std::vector<DOperand> operands;
+    std::vector<int32_t> op_src;        // global producing bucket, -1 for leaves
+    std::vector<int32_t> op_leaf_kind;
+    std::vector<int32_t> op_leaf_layer;
+    std::vector<int32_t> op_rank;
+    std::vector<int32_t> bucket_level;
+    std::vector<int32_t> bucket_var;
+    std::vector<uint32_t> tasks_bucket; // tasks in claim order
+    std::vector<uint32_t> tasks_chunk;
+    std::vector<uint32_t> item_begin;   // n_items + 1, into the task arrays
+    std::vector<uint32_t> root_bucket;  // every root bucket (scalar result)
+    std::vector<uint32_t> net_first_root;  // n_nets + 1 into root_bucket
+    std::vector<uint32_t> level_first_bucket;  // buckets sorted by level (for the adjoint)
+    std::vector<uint32_t> by_level;
+
+    uint64_t leaf_elems = 0;   // leaf table size in elements
+    uint64_t arena_elems = 0;  // leaf table + results
+    uint64_t cot_off = 0;      // start of the cotangent region (gradient plans)
+    uint64_t total_elems = 0;
+    int max_width = 0;
+    int n_levels = 0;
+    double sum_2w = 0, alg_bytes = 0, flops = 0;
+    int64_t width_hist[64] = {0};
+    double plan_seconds = 0;
+};
+
+// Returns QT_OK or a QT_E* code.
+int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, HostPlan* out);
+
+int leaf_slots_per_graph(int p);
+int leaf_index(int kind, int layer);
+
+}  // namespace qt

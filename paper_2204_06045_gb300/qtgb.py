@@ -1,0 +1,286 @@
+"""Python binding of libqtgb (include/qt.h): argument marshalling only.
+
+Every step of the energy evaluation runs in the CUDA kernels behind the C ABI.
+There is no fallback: if ``libqtgb.so`` is missing or a call fails, this module
+raises. PyTorch is used only to pass device tensors and CUDA streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+LIB_PATH = _HERE / "libqtgb.so"
+
+QT_OK, QT_EINVAL, QT_EWIDTH, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_EBOUNDS, QT_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+QT_C64, QT_C128 = 0, 1
+QT_SCHED_PERSISTENT, QT_SCHED_PER_BUCKET = 0, 1
+LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
+
+# every symbol include/qt.h declares
+EXPORTS = ("qt_plan", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
+           "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
+           "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version")
+
+
+class QTError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+        self.code = code
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("sched", ctypes.c_int), ("order_restarts", ctypes.c_int32),
+                ("order_seed", ctypes.c_uint64), ("max_width", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
+                ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
+                ("host_only", ctypes.c_int32)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n_graphs", ctypes.c_int32), ("n_networks", ctypes.c_int32), ("n_buckets", ctypes.c_int64),
+                ("n_operands", ctypes.c_int64), ("max_width", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("sum_2w", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("flops", ctypes.c_double),
+                ("arena_bytes", ctypes.c_int64), ("n_tasks", ctypes.c_int64), ("n_items", ctypes.c_int64),
+                ("n_levels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("width_hist", ctypes.c_int64 * 64),
+                ("plan_seconds", ctypes.c_double)]
+
+
+BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
+                         ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32)])
+OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
+                          ("mask", np.uint32), ("rank", np.int32), ("pad", np.int32)])
+
+_lib = None
+
+
+def lib():
+    """Load libqtgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2204_06045_gb300.build.build()")
+        L = ctypes.CDLL(str(LIB_PATH))
+        vp, dp, i32, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int64
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        L.qt_plan.argtypes = [i32, i32, i32p, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+        L.qt_plan_batch.argtypes = [i32, i32p, i32p, i32p, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+        L.qt_plan_stats_get.argtypes = [vp, ctypes.POINTER(PlanStats)]
+        L.qt_plan_export.argtypes = [vp, vp, vp]
+        L.qt_plan_network_wires.argtypes = [vp, i32, i32p]
+        L.qt_energy.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.qt_energy_batch.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.qt_energy_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.qt_last_imag.argtypes = [vp, dp]
+        L.qt_sync.argtypes = [vp, vp]
+        L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
+        L.qt_debug_stall_bucket.argtypes = [vp, i64]
+        L.qt_plan_free.argtypes = [vp]
+        L.qt_plan_free.restype = None
+        L.qt_error_string.argtypes = [ctypes.c_int]
+        L.qt_error_string.restype = ctypes.c_char_p
+        L.qt_version.restype = ctypes.c_char_p
+        for name in ("qt_plan", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
+                     "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
+                     "qt_debug_stall_bucket"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().qt_error_string(int(code)).decode()
+
+
+def version() -> str:
+    return lib().qt_version().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != QT_OK:
+        raise QTError(rc, what)
+
+
+def _ptr(x):
+    """Address of a numpy array or a torch tensor (host or CUDA); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer {type(x)}")
+
+
+def _f64_in(x):
+    if hasattr(x, "data_ptr"):
+        import torch
+        assert x.dtype == torch.float64 and x.is_contiguous(), "angle tensors must be contiguous float64"
+        return x
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Plan:
+    """A planned QAOA MaxCut energy evaluation on one graph or a batch of graphs."""
+
+    def __init__(self, handle, n_edges_per_graph, p, dtype, n_vertices):
+        self._h = ctypes.c_void_p(handle)
+        self.n_edges = list(n_edges_per_graph)
+        self.n_vertices = list(n_vertices)
+        self.p = p
+        self.dtype = dtype
+
+    # -- construction -------------------------------------------------------------
+    @staticmethod
+    def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
+              with_grad=False, spin_limit=0, chunk_log2=0, host_only=False):
+        o = PlanOpts()
+        o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
+        o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
+        o.order_restarts = int(restarts)
+        o.order_seed = int(seed)
+        o.max_width = int(max_width)
+        o.arena_bytes = int(arena_bytes)
+        o.with_grad = int(bool(with_grad))
+        o.spin_limit = int(spin_limit)
+        o.chunk_log2 = int(chunk_log2)
+        o.host_only = int(bool(host_only))
+        return o
+
+    @classmethod
+    def create(cls, n: int, edges, p: int, **opts) -> "Plan":
+        e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        o = cls._opts(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().qt_plan(int(n), int(e.shape[0]), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(p),
+                             ctypes.byref(o), ctypes.byref(h)), "qt_plan")
+        return cls(h.value, [e.shape[0]], p, opts.get("dtype", "c64"), [n])
+
+    @classmethod
+    def create_batch(cls, graphs, p: int, **opts) -> "Plan":
+        """``graphs``: sequence of ``(n_vertices, edges)``."""
+        ns = np.array([g[0] for g in graphs], dtype=np.int32)
+        es = [np.ascontiguousarray(g[1], dtype=np.int32).reshape(-1, 2) for g in graphs]
+        ms = np.array([e.shape[0] for e in es], dtype=np.int32)
+        allv = np.ascontiguousarray(np.concatenate(es, axis=0))
+        o = cls._opts(**opts)
+        h = ctypes.c_void_p()
+        ip = ctypes.POINTER(ctypes.c_int32)
+        _check(lib().qt_plan_batch(len(graphs), ns.ctypes.data_as(ip), ms.ctypes.data_as(ip), allv.ctypes.data_as(ip),
+                                   int(p), ctypes.byref(o), ctypes.byref(h)), "qt_plan_batch")
+        return cls(h.value, ms.tolist(), p, opts.get("dtype", "c64"), ns.tolist())
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().qt_plan_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- inspection ---------------------------------------------------------------
+    def stats(self) -> dict:
+        s = PlanStats()
+        _check(lib().qt_plan_stats_get(self._h, ctypes.byref(s)), "qt_plan_stats_get")
+        d = {k: getattr(s, k) for k, _ in PlanStats._fields_ if k != "width_hist"}
+        d["width_hist"] = np.array(list(s.width_hist), dtype=np.int64)
+        return d
+
+    def export(self):
+        st = self.stats()
+        b = np.zeros(st["n_buckets"], dtype=BUCKET_DTYPE)
+        o = np.zeros(st["n_operands"], dtype=OPERAND_DTYPE)
+        _check(lib().qt_plan_export(self._h, b.ctypes.data, o.ctypes.data), "qt_plan_export")
+        return b, o
+
+    def network_wires(self, network: int, n_vertices: int) -> np.ndarray:
+        out = np.zeros(n_vertices, dtype=np.int32)
+        _check(lib().qt_plan_network_wires(self._h, int(network), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "qt_plan_network_wires")
+        return out
+
+    # -- evaluation ---------------------------------------------------------------
+    @property
+    def n_networks(self) -> int:
+        return int(sum(self.n_edges))
+
+    def energy(self, gammas, betas, edge_zz=None, energy=None, stream=None):
+        """One graph. With no output buffers given, returns ``(edge_zz, E)`` as host numpy/float.
+        Output buffers may be numpy arrays or torch tensors (CUDA or pinned host)."""
+        g, b = _f64_in(gammas), _f64_in(betas)
+        own = edge_zz is None and energy is None
+        if own:
+            edge_zz = np.zeros(self.n_networks, dtype=np.float64)
+            energy = np.zeros(1, dtype=np.float64)
+        _check(lib().qt_energy(self._h, _ptr(g), _ptr(b), _ptr(edge_zz), _ptr(energy), _stream_ptr(stream)),
+               "qt_energy")
+        if own:
+            return edge_zz, float(energy[0])
+        return edge_zz, energy
+
+    def energy_batch(self, gammas, betas, energies=None, edge_zz=None, stream=None):
+        """Every graph of a batch plan: ``gammas``/``betas`` are (n_graphs, p)."""
+        g, b = _f64_in(gammas), _f64_in(betas)
+        own = energies is None and edge_zz is None
+        if own:
+            energies = np.zeros(len(self.n_edges), dtype=np.float64)
+            edge_zz = np.zeros(self.n_networks, dtype=np.float64)
+        _check(lib().qt_energy_batch(self._h, _ptr(g), _ptr(b), _ptr(energies), _ptr(edge_zz), _stream_ptr(stream)),
+               "qt_energy_batch")
+        return energies, edge_zz
+
+    def energy_grad(self, gammas, betas, energy=None, dgamma=None, dbeta=None, stream=None):
+        g, b = _f64_in(gammas), _f64_in(betas)
+        G = len(self.n_edges)
+        own = energy is None
+        if own:
+            energy = np.zeros(G, dtype=np.float64)
+            dgamma = np.zeros(G * self.p, dtype=np.float64)
+            dbeta = np.zeros(G * self.p, dtype=np.float64)
+        _check(lib().qt_energy_grad(self._h, _ptr(g), _ptr(b), _ptr(energy), _ptr(dgamma), _ptr(dbeta),
+                                    _stream_ptr(stream)), "qt_energy_grad")
+        return energy, dgamma, dbeta
+
+    def last_imag(self) -> np.ndarray:
+        out = np.zeros(self.n_networks, dtype=np.float64)
+        _check(lib().qt_last_imag(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "qt_last_imag")
+        return out
+
+    def sync(self, stream=None):
+        _check(lib().qt_sync(self._h, _stream_ptr(stream)), "qt_sync")
+
+    def kernel_time(self, reset: bool = False):
+        """(average ms per launch of the main kernel, number of launches timed)."""
+        ms = ctypes.c_double(0)
+        n = ctypes.c_int64(0)
+        _check(lib().qt_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n), int(reset)), "qt_kernel_time")
+        return ms.value, n.value
+
+    def debug_stall_bucket(self, bucket: int):
+        _check(lib().qt_debug_stall_bucket(self._h, int(bucket)), "qt_debug_stall_bucket")
+
+
+def plan(n: int, edges, p: int, **opts) -> Plan:
+    return Plan.create(n, edges, p, **opts)
+
+
+def plan_batch(graphs, p: int, **opts) -> Plan:
+    return Plan.create_batch(graphs, p, **opts)

@@ -1,0 +1,68 @@
+"""Test-side numpy evaluation of an exported bucket schedule.
+
+Checks the planner's structure (operands, masks, parents, roots) on the host,
+without a GPU, by contracting the exported schedule with numpy in complex128
+and comparing against the oracle. Leaf tensors are written out here from
+their definitions (Eq. 2 gates), independently of the library's own leaf
+kernel.
+"""
+import numpy as np
+
+
+def leaf_tensor(kind: int, layer: int, gammas, betas) -> np.ndarray:
+    """Entries [x + 2y] of a gate tensor (rank-1 tensors use [x])."""
+    s = lambda x: 1 - 2 * x  # noqa: E731
+    if kind == 0:  # |+>
+        return np.array([1, 1, 0, 0], dtype=complex) / np.sqrt(2)
+    if kind == 1:  # Z
+        return np.array([1, -1, 0, 0], dtype=complex)
+    T = np.zeros(4, dtype=complex)
+    for x in (0, 1):
+        for y in (0, 1):
+            if kind in (2, 3):
+                v = np.exp(-1j * gammas[layer] * s(x) * s(y))
+            else:
+                v = np.cos(betas[layer]) if x == y else -1j * np.sin(betas[layer])
+            T[x + 2 * y] = np.conj(v) if kind in (3, 5) else v
+    return T
+
+
+def pext(o: np.ndarray, mask: int) -> np.ndarray:
+    r = np.zeros_like(o)
+    k = 0
+    for bit in range(32):
+        if (mask >> bit) & 1:
+            r |= ((o >> bit) & 1) << k
+            k += 1
+    return r
+
+
+def evaluate(buckets, operands, gammas, betas, graph_of_network=None):
+    """Complex value of every network of the exported schedule."""
+    n_nets = int(buckets["network"].max()) + 1
+    res = {}
+    value = np.ones(n_nets, dtype=complex)
+    for b in range(buckets.shape[0]):
+        B = buckets[b]
+        n_out = int(B["width"]) - 1
+        o = np.arange(1 << n_out, dtype=np.int64)
+        acc = np.zeros(1 << n_out, dtype=complex)
+        net = int(B["network"])
+        g = 0 if graph_of_network is None else graph_of_network[net]
+        gam = gammas[g] if np.ndim(gammas) == 2 else gammas
+        bet = betas[g] if np.ndim(betas) == 2 else betas
+        for x in (0, 1):
+            prod = np.ones(1 << n_out, dtype=complex)
+            for t in range(int(B["op_begin"]), int(B["op_begin"]) + int(B["n_ops"])):
+                op = operands[t]
+                idx = 2 * pext(o, int(op["mask"])) + x
+                if op["src"] < 0:
+                    T = leaf_tensor(int(op["leaf_kind"]), int(op["leaf_layer"]), gam, bet)
+                else:
+                    T = res[int(op["src"])]
+                prod = prod * T[idx]
+            acc += prod
+        res[b] = acc
+        if B["parent"] < 0:
+            value[net] *= acc[0]
+    return value

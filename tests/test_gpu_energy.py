@@ -1,0 +1,221 @@
+"""GPU parity: qt_energy / qt_energy_batch through the C ABI against the oracle.
+
+Tolerance per edge: |x - ref| <= tol * max(|ref|, 1e-2), with tol = 1e-10 for
+complex128 and 1e-5 for complex64 (FP32 arithmetic); the floor keeps the test
+meaningful where an edge value is near zero. |Im| of every network value must
+stay within 10 * tol.
+"""
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_06045_gb300 import qtgb, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = Path(__file__).parent / "golden"
+TOL = {"c128": 1e-10, "c64": 1e-5}
+
+
+def scaled_err(x, ref):
+    x, ref = np.asarray(x), np.asarray(ref)
+    return float(np.max(np.abs(x - ref) / np.maximum(np.abs(ref), 1e-2)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_06045_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("sched", ["persistent", "per_bucket"])
+def test_c1_p1_matches_state_vector_and_closed_form(dtype, sched):
+    n, p, seed = 10, 1, 1000
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype=dtype, sched=sched) as pl:
+        zz, E = pl.energy(g, b)
+        im = pl.last_imag()
+    ref = oracle.sv_zz(n, edges, g, b)
+    assert scaled_err(zz, ref) <= TOL[dtype]
+    assert scaled_err(zz, oracle.p1_closed_form(n, edges, g[0], b[0])) <= TOL[dtype]
+    assert abs(E - oracle.energy_from_zz(ref)) <= TOL[dtype] * abs(E)
+    assert np.abs(im).max() <= 10 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,seed,p", [(12, 21, 2), (14, 22, 3), (16, 23, 3), (20, 1020, 4), (18, 5, 4)])
+def test_small_graphs_match_state_vector(dtype, n, seed, p):
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype=dtype) as pl:
+        zz, E = pl.energy(g, b)
+    ref = oracle.sv_zz(n, edges, g, b)
+    assert scaled_err(zz, ref) <= TOL[dtype]
+    assert abs(E - oracle.energy_from_zz(ref)) <= TOL[dtype] * abs(E)
+
+
+@pytest.mark.parametrize("name,n,edges", [("K4", 4, synth.complete_graph(4)), ("prism", 6, synth.prism_graph()),
+                                          ("petersen", 10, synth.petersen_graph()), ("ring", 9, synth.ring_graph(9))])
+def test_degenerate_small_graphs(name, n, edges):
+    for p in (1, 2, 3):
+        g, b = synth.angles(p, 4)
+        ref = oracle.sv_zz(n, edges, g, b)
+        with qtgb.plan(n, edges, p, dtype="c128") as pl:
+            zz, _ = pl.energy(g, b)
+        assert scaled_err(zz, ref) <= TOL["c128"]
+
+
+def test_single_edge_graph():
+    edges = np.array([[0, 1]])
+    g, b = [0.3, 0.8], [0.5, 0.1]
+    ref = oracle.sv_zz(2, edges, g, b)
+    with qtgb.plan(2, edges, 2, dtype="c128") as pl:
+        zz, E = pl.energy(g, b)
+    assert scaled_err(zz, ref) <= TOL["c128"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_invariants(dtype):
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    m = edges.shape[0]
+    with qtgb.plan(n, edges, p, dtype=dtype) as pl:
+        zz, E = pl.energy(np.zeros(p), np.zeros(p))
+        assert np.abs(zz).max() <= TOL[dtype] and abs(E - m / 2) <= TOL[dtype] * m
+        g, _ = synth.angles(p, 1000)
+        zz, E = pl.energy(g, np.zeros(p))
+        assert np.abs(zz).max() <= 10 * TOL[dtype]
+        g, b = synth.angles(p, 1000)
+        zz, E = pl.energy(g, b)
+        assert np.all(np.abs(zz) <= 1 + 10 * TOL[dtype]) and -1e-9 <= E <= m + 1e-9
+        zz2, _ = pl.energy(g + np.pi, b + np.pi)
+        assert scaled_err(zz2, zz) <= 10 * TOL[dtype]
+
+
+def _golden_edges(name):
+    rows = {}
+    zz = []
+    for line in (GOLDEN / name).read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        parts = line.split()
+        if parts[0] == "edge":
+            zz.append(float(parts[4]))
+        else:
+            rows[parts[0]] = [float(x) for x in parts[1:]]
+    return rows, np.array(zz)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("sched", ["persistent", "per_bucket"])
+def test_c2_n30_p4_matches_statevector_golden(dtype, sched):
+    if not (GOLDEN / "c2_n30_p4_statevector.txt").exists():
+        pytest.skip("golden not generated")
+    rows, ref = _golden_edges("c2_n30_p4_statevector.txt")
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = np.array(rows["gamma"]), np.array(rows["beta"])
+    np.testing.assert_array_equal((g, b), synth.angles(p, 1000))
+    with qtgb.plan(n, edges, p, dtype=dtype, sched=sched) as pl:
+        zz, E = pl.energy(g, b)
+        im = pl.last_imag()
+    assert scaled_err(zz, ref) <= TOL[dtype]
+    assert abs(E - rows["energy"][0]) <= TOL[dtype] * abs(E)
+    assert np.abs(im).max() <= 10 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_c5_n50_p4_matches_bucket_golden(dtype):
+    if not (GOLDEN / "c5_n50_p4_bucket.txt").exists():
+        pytest.skip("golden not generated")
+    rows, ref = _golden_edges("c5_n50_p4_bucket.txt")
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = np.array(rows["gamma"]), np.array(rows["beta"])
+    with qtgb.plan(n, edges, p, dtype=dtype) as pl:
+        zz, E = pl.energy(g, b)
+    assert scaled_err(zz, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batch_of_graphs_matches_oracle(dtype):
+    p = 3
+    graphs = synth.batch(6, p, lo=50, hi=120, base_seed=1000)
+    with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], p, dtype=dtype) as pl:
+        G = np.array([gg for _, _, gg, _ in graphs])
+        B = np.array([bb for _, _, _, bb in graphs])
+        energies, zz = pl.energy_batch(G, B)
+    at = 0
+    for i, (n, e, gg, bb) in enumerate(graphs):
+        vals, _ = oracle.bucket_zz(n, e, gg, bb, seed=3)
+        part = zz[at:at + e.shape[0]]
+        at += e.shape[0]
+        assert scaled_err(part, vals.real) <= TOL[dtype]
+        assert abs(energies[i] - oracle.energy_from_zz(vals.real)) <= TOL[dtype] * abs(energies[i])
+
+
+def test_device_buffers_and_stream():
+    n, p = 16, 3
+    edges = synth.random_regular_graph(n, 8)
+    g, b = synth.angles(p, 8)
+    ref = oracle.sv_zz(n, edges, g, b)
+    s = torch.cuda.Stream()
+    with qtgb.plan(n, edges, p, dtype="c128") as pl:
+        gd = torch.tensor(g, dtype=torch.float64, device="cuda")
+        bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+        zz = torch.zeros(edges.shape[0], dtype=torch.float64, device="cuda")
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            pl.energy(gd, bd, edge_zz=zz, energy=E, stream=s)
+        pl.sync(s)
+        assert scaled_err(zz.cpu().numpy(), ref) <= TOL["c128"]
+        assert abs(E.item() - oracle.energy_from_zz(ref)) <= 1e-10 * abs(E.item())
+
+
+def test_repeat_calls_are_bitwise_identical():
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    with qtgb.plan(n, edges, p, dtype="c64") as pl:
+        first, _ = pl.energy(g, b)
+        for _ in range(3):
+            again, _ = pl.energy(g, b)
+            np.testing.assert_array_equal(first, again)
+
+
+def test_stalled_dependency_times_out_and_context_survives():
+    n, p = 12, 2
+    edges = synth.random_regular_graph(n, 3)
+    g, b = synth.angles(p, 3)
+    with qtgb.plan(n, edges, p, dtype="c64", spin_limit=2000) as pl:
+        B, _ = pl.export()
+        victim = int(np.nonzero(B["n_deps"] > 0)[0][-1])
+        pl.debug_stall_bucket(victim)
+        with pytest.raises(qtgb.QTError) as ei:
+            pl.energy(g, b)
+        assert ei.value.code == qtgb.QT_ETIMEOUT
+    # the context is still usable
+    with qtgb.plan(n, edges, p, dtype="c128") as pl:
+        zz, _ = pl.energy(g, b)
+    assert scaled_err(zz, oracle.sv_zz(n, edges, g, b)) <= TOL["c128"]
+
+
+def test_kernel_time_counts_launches():
+    n, p = 20, 3
+    edges = synth.random_regular_graph(n, 2)
+    g, b = synth.angles(p, 2)
+    with qtgb.plan(n, edges, p) as pl:
+        pl.kernel_time(reset=True)
+        for _ in range(5):
+            pl.energy(g, b)
+        ms, cnt = pl.kernel_time(reset=True)
+        assert cnt == 5 and ms > 0

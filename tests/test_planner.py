@@ -1,0 +1,194 @@
+"""Host-side tests of the planner behind qt_plan (no GPU: host_only plans).
+
+* the exported schedule, contracted with numpy, equals the oracle's values;
+* each network eliminates every one of its variables exactly once;
+* the bucket graph is an in-forest with one root per network;
+* operand masks and ranks agree with the producing bucket's width;
+* lightcone wires carry 2(p - d) + 1 variables at distance d <= p (§II-B);
+* statistics and byte accounting agree with the exported schedule;
+* malformed graphs and width caps are rejected with the documented codes.
+"""
+import re
+from pathlib import Path
+
+import networkx as nx
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_06045_gb300 import qtgb, synth
+from plan_eval import evaluate
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2204_06045_gb300 import build
+    build.build()
+
+
+def host_plan(n, edges, p, **kw):
+    return qtgb.plan(n, edges, p, host_only=True, **kw)
+
+
+@pytest.mark.parametrize("n,seed,p", [(10, 1000, 1), (12, 21, 2), (14, 22, 3), (16, 5, 2)])
+def test_schedule_matches_oracle(n, seed, p):
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with host_plan(n, edges, p) as pl:
+        B, O = pl.export()
+        vals = evaluate(B, O, g, b)
+    np.testing.assert_allclose(vals.real, oracle.sv_zz(n, edges, g, b), rtol=0, atol=1e-12)
+    assert np.abs(vals.imag).max() < 1e-12
+
+
+@pytest.mark.parametrize("name,n,edges", [("K4", 4, synth.complete_graph(4)), ("prism", 6, synth.prism_graph()),
+                                          ("petersen", 10, synth.petersen_graph()), ("ring", 8, synth.ring_graph(8))])
+def test_schedule_matches_oracle_small_graphs(name, n, edges):
+    for p in (1, 2):
+        g, b = synth.angles(p, 3)
+        with host_plan(n, edges, p, restarts=3, seed=7) as pl:
+            B, O = pl.export()
+            vals = evaluate(B, O, g, b)
+        np.testing.assert_allclose(vals.real, oracle.sv_zz(n, edges, g, b), rtol=0, atol=1e-12)
+
+
+def test_batch_schedule_matches_oracle():
+    graphs = [(10, synth.random_regular_graph(10, 1)), (12, synth.random_regular_graph(12, 2)),
+              (8, synth.random_regular_graph(8, 3))]
+    p = 2
+    G = np.array([synth.angles(p, s)[0] for s in (1, 2, 3)])
+    Bt = np.array([synth.angles(p, s)[1] for s in (1, 2, 3)])
+    with qtgb.plan_batch(graphs, p, host_only=True) as pl:
+        B, O = pl.export()
+        gon = np.repeat(np.arange(3), [e.shape[0] for _, e in graphs])
+        vals = evaluate(B, O, G, Bt, gon)
+    ref = np.concatenate([oracle.sv_zz(n, e, G[i], Bt[i]) for i, (n, e) in enumerate(graphs)])
+    np.testing.assert_allclose(vals.real, ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,seed,p", [(30, 1000, 4), (50, 1000, 3)])
+def test_structure(n, seed, p):
+    edges = synth.random_regular_graph(n, seed)
+    with host_plan(n, edges, p) as pl:
+        B, O = pl.export()
+        st = pl.stats()
+        assert st["n_networks"] == edges.shape[0]
+        for net in range(edges.shape[0]):
+            idx = np.nonzero(B["network"] == net)[0]
+            assert np.all(np.diff(idx) == 1), "buckets of a network are contiguous"
+            wires = pl.network_wires(net, n)
+            V = int(wires.sum())
+            assert sorted(B["var"][idx].tolist()) == list(range(V)), "each variable eliminated once"
+            roots = idx[B["parent"][idx] < 0]
+            assert len(roots) == 1, "one connected network, one scalar result"
+            assert B["width"][roots[0]] == 1
+            for b in idx:
+                par = B["parent"][b]
+                if par >= 0:
+                    assert idx[0] <= par < idx[-1] + 1 and par > b
+            # children counts
+            for b in idx:
+                ops = O[B["op_begin"][b]:B["op_begin"][b] + B["n_ops"][b]]
+                kids = ops["src"][ops["src"] >= 0]
+                assert len(kids) == B["n_deps"][b]
+                for k in kids:
+                    assert B["parent"][k] == b
+                for op in ops:
+                    assert bin(int(op["mask"])).count("1") == op["rank"] - 1
+                    assert int(op["mask"]) >> (B["width"][b] - 1) == 0
+                    if op["src"] >= 0:
+                        assert op["rank"] == B["width"][op["src"]] - 1
+                        assert B["level"][b] > B["level"][op["src"]]
+                    else:
+                        assert op["rank"] in (1, 2)
+                # the union of operand bits is the whole output index
+                allm = 0
+                for op in ops:
+                    allm |= int(op["mask"])
+                assert allm == (1 << (B["width"][b] - 1)) - 1
+        # statistics agree with the exported schedule
+        assert st["n_buckets"] == B.shape[0]
+        assert st["max_width"] == B["width"].max()
+        assert st["width_hist"].sum() == B.shape[0]
+        assert st["sum_2w"] == float(np.sum(2.0 ** B["width"]))
+        opbytes = sum(float(np.sum(2.0 ** O["rank"][B["op_begin"][b]:B["op_begin"][b] + B["n_ops"][b]]))
+                      for b in range(B.shape[0]))
+        outbytes = np.sum(2.0 ** (B["width"] - 1))
+        assert np.isclose(st["alg_bytes"], 8 * (opbytes + outbytes))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_lightcone_wires(p):
+    n, edges = 24, synth.random_regular_graph(24, 9)
+    G = nx.Graph()
+    G.add_edges_from(map(tuple, edges))
+    with host_plan(n, edges, p) as pl:
+        for e in range(0, edges.shape[0], 4):
+            j, k = map(int, edges[e])
+            dj = nx.single_source_shortest_path_length(G, j)
+            dk = nx.single_source_shortest_path_length(G, k)
+            expect = [2 * (p - min(dj[q], dk[q])) + 1 if min(dj[q], dk[q]) <= p else 0 for q in range(n)]
+            np.testing.assert_array_equal(pl.network_wires(e, n), expect)
+            # the same shape as the oracle's own network builder
+            np.testing.assert_array_equal(pl.network_wires(e, n), oracle.edge_network_shape(n, edges, p, e)[2])
+
+
+def test_restarts_never_worse():
+    n, edges = 30, synth.random_regular_graph(30, 1000)
+    with host_plan(n, edges, 4) as a, host_plan(n, edges, 4, restarts=4, seed=11) as b:
+        assert b.stats()["sum_2w"] <= a.stats()["sum_2w"]
+
+
+def test_width27_bytes_convention():
+    # a width-w bucket writes 2^(w-1) entries; a 27-index tensor of complex128 is ~2 GB (§III-C)
+    gold = dict(l.split() for l in (ROOT / "tests/golden/width27_c128_bytes.txt").read_text().splitlines()
+                if l.strip() and not l.startswith("#"))
+    w = int(gold["width"])
+    assert abs((2 ** w) * 16 - float(gold["bytes_approx"])) / float(gold["bytes_approx"]) < 0.08
+
+
+@pytest.mark.parametrize("edges,n,p", [
+    ([(0, 0), (0, 1)], 3, 1),          # self-loop
+    ([(0, 1), (1, 0)], 3, 1),          # duplicate edge
+    ([(0, 1), (1, 5)], 3, 1),          # vertex out of range
+    ([(0, 1), (1, 2)], 3, 0),          # p < 1
+])
+def test_invalid_graphs(edges, n, p):
+    with pytest.raises(qtgb.QTError) as ei:
+        host_plan(n, np.array(edges), p)
+    assert ei.value.code == qtgb.QT_EINVAL
+
+
+def test_width_cap():
+    n, edges = 30, synth.random_regular_graph(30, 1000)
+    with pytest.raises(qtgb.QTError) as ei:
+        host_plan(n, edges, 4, max_width=8)
+    assert ei.value.code == qtgb.QT_EWIDTH
+
+
+def test_arena_cap():
+    n, edges = 30, synth.random_regular_graph(30, 1000)
+    with pytest.raises(qtgb.QTError) as ei:
+        host_plan(n, edges, 4, arena_bytes=1 << 20)
+    assert ei.value.code == qtgb.QT_ENOMEM
+
+
+def test_host_only_plan_refuses_evaluation():
+    n, edges = 10, synth.random_regular_graph(10, 1)
+    with host_plan(n, edges, 1) as pl:
+        with pytest.raises(qtgb.QTError) as ei:
+            pl.energy([0.1], [0.2])
+        assert ei.value.code == qtgb.QT_ESTATE
+
+
+def test_library_exports_every_declared_symbol():
+    header = (ROOT / "include/qt.h").read_text()
+    declared = set(re.findall(r"^\s*(?:int|void|const char \*)\s*(qt_\w+)\s*\(", header, flags=re.M))
+    assert declared, "no declarations parsed"
+    assert declared == set(qtgb.EXPORTS)
+    L = qtgb.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert "sm_103a" in qtgb.version()
