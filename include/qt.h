@@ -212,6 +212,11 @@ const char *qt_error_string(int code);
 /* Library version string. */
 const char *qt_version(void);
 
+/* Text describing the last QT_ECUDA / QT_ENOMEM failure on the calling thread
+ * (the failing CUDA call and its error name); empty if none. Owned by the
+ * library; valid until the next call on this thread. */
+const char *qt_last_error_detail(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,13 +17,6 @@ namespace {
 
 constexpr int kRing = 512;  // event pairs for per-launch kernel timing
 
-struct DeviceBuffer {
-    void* p = nullptr;
-    ~DeviceBuffer() {
-        if (p) cudaFree(p);
-    }
-};
-
 }  // namespace
 
 struct qt_plan_s {
@@ -81,12 +74,18 @@ struct qt_plan_s {
 
 namespace {
 
-#define QT_CUDA(call)                                  \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) {                       \
-            return e_ == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA; \
-        }                                              \
+thread_local char g_detail[512] = "";
+
+int cuda_fail(cudaError_t e, const char* what, int line) {
+    std::snprintf(g_detail, sizeof(g_detail), "%s failed at capi.cu:%d: %s (%s)", what, line, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA;
+}
+
+#define QT_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call, __LINE__); \
     } while (0)
 
 bool is_host_ptr(const void* p) {
@@ -196,9 +195,9 @@ int enqueue_eval(qt_plan_t P, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     QT_CUDA(qt::launch_leaf_fill(P->dtype, P->d_angles, (int)hp.graphs.size(), hp.cfg.p, P->d_arena, s));
     if (P->sched == QT_SCHED_PERSISTENT) {
         QT_CUDA(cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, s));
-        QT_CUDA(cudaEventRecord(e0, s));
+        QT_CUDA(cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal));
         QT_CUDA(qt::launch_persistent(P->dtype, P->grid, P->dp, s));
-        QT_CUDA(cudaEventRecord(e1, s));
+        QT_CUDA(cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal));
     } else {
         QT_CUDA(cudaEventRecord(e0, s));
         for (size_t b = 0; b < hp.buckets.size(); ++b)
@@ -220,7 +219,7 @@ int ensure_graph(qt_plan_t P) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
-    if (ce != cudaSuccess) return QT_ECUDA;
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture", __LINE__);
     P->graph = g;
     size_t n = 0;
     QT_CUDA(cudaGraphGetNodes(g, nullptr, &n));
@@ -235,7 +234,10 @@ int ensure_graph(qt_plan_t P) {
         if (ev == P->cap_ev[0]) P->ev_nodes[0] = nd;
         if (ev == P->cap_ev[1]) P->ev_nodes[1] = nd;
     }
-    if (!P->ev_nodes[0] || !P->ev_nodes[1]) return QT_ECUDA;
+    if (!P->ev_nodes[0] || !P->ev_nodes[1]) {
+        std::snprintf(g_detail, sizeof(g_detail), "timing event nodes not found in the captured graph");
+        return QT_ECUDA;
+    }
     QT_CUDA(cudaGraphInstantiate(&P->exec, g, 0));
     return QT_OK;
 }
@@ -528,5 +530,7 @@ const char* qt_error_string(int code) {
 }
 
 const char* qt_version(void) { return "qtgb 0.1 sm_103a"; }
+
+const char* qt_last_error_detail(void) { return g_detail; }
 
 }  // extern "C"

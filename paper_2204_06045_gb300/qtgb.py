@@ -22,12 +22,15 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 # every symbol include/qt.h declares
 EXPORTS = ("qt_plan", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-           "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version")
+           "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail")
 
 
 class QTError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {error_string(code)} ({code})")
+        detail = ""
+        if code in (QT_ECUDA, QT_ENOMEM):
+            detail = lib().qt_last_error_detail().decode()
+        super().__init__(f"{what}: {error_string(code)} ({code})" + (f" [{detail}]" if detail else ""))
         self.code = code
 
 
@@ -81,6 +84,7 @@ def lib():
         L.qt_error_string.argtypes = [ctypes.c_int]
         L.qt_error_string.restype = ctypes.c_char_p
         L.qt_version.restype = ctypes.c_char_p
+        L.qt_last_error_detail.restype = ctypes.c_char_p
         for name in ("qt_plan", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket"):
