@@ -205,6 +205,32 @@ def ncu_traffic(kernel_tag: str):
         return None
 
 
+def golden_c2():
+    """Per-edge <Z_jZ_k> and E of the default workload from the stored 2^30 state-vector values."""
+    f = ROOT / "tests" / "golden" / "c2_n30_p4_statevector.txt"
+    if not f.exists():
+        return None, None
+    zz, E = [], None
+    for line in f.read_text().splitlines():
+        parts = line.split()
+        if parts and parts[0] == "edge":
+            zz.append(float(parts[4]))
+        elif parts and parts[0] == "energy":
+            E = float(parts[1])
+    return np.array(zz), E
+
+
+def accuracy(zz, E, ref_zz, ref_E):
+    if ref_zz is None:
+        return {"reference": "unavailable"}
+    d = np.abs(np.asarray(zz) - ref_zz)
+    return {"reference": "2^30 complex128 state vector (oracle, stored)",
+            "max_abs_err_zz": float(d.max()),
+            "max_rel_err_zz": float(np.max(d / np.abs(ref_zz))),
+            "max_rel_err_edge_energy": float(np.max(d / np.abs(1.0 - ref_zz))),
+            "rel_err_energy": float(abs(E - ref_E) / abs(ref_E))}
+
+
 def time_device(pl, gd, bd, zz, E, steps, warmup, dist, torch):
     s = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -265,6 +291,7 @@ def run_ours(args, rank, world, local_rank):
     n, p, edges, g, b = workload_inputs()
     m = edges.shape[0]
     peak, peak_kind = measured_peaks()
+    ref_zz, ref_E = golden_c2()
     results = {}
     for dtype in ("c64", "c128"):
         pl = qtgb.plan(n, edges, p, dtype=dtype)
@@ -293,7 +320,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "plan": {"buckets": st["n_buckets"], "max_width": st["max_width"], "sum_2w": st["sum_2w"],
                      "tasks": st["n_tasks"], "plan_seconds": st["plan_seconds"]},
-            "check": {"energy": float(E.item())},
+            "check": dict(energy=float(E.item()), **accuracy(zz.cpu().numpy(), float(E.item()), ref_zz, ref_E)),
         }
         pl.close()
     if rank != 0:

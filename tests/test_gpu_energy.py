@@ -1,8 +1,11 @@
 """GPU parity: qt_energy / qt_energy_batch through the C ABI against the oracle.
 
-Tolerance per edge: |x - ref| <= tol * max(|ref|, 1e-2), with tol = 1e-10 for
-complex128 and 1e-5 for complex64 (FP32 arithmetic); the floor keeps the test
-meaningful where an edge value is near zero. |Im| of every network value must
+Per edge, two measures must stay within tol (1e-10 for complex128, 1e-5 for
+complex64 with FP32 arithmetic):
+* the relative error of the per-edge energy <C_jk> = (1 - e_jk)/2, the edge's
+  term in E = sum_jk (1 - e_jk)/2 (§II-B edge decomposition);
+* the absolute error of e_jk = <Z_jZ_k>, a quantity bounded by 1.
+The energy E must match to tol relative, and |Im| of every network value must
 stay within 10 * tol.
 """
 from pathlib import Path
@@ -21,8 +24,10 @@ TOL = {"c128": 1e-10, "c64": 1e-5}
 
 
 def scaled_err(x, ref):
-    x, ref = np.asarray(x), np.asarray(ref)
-    return float(np.max(np.abs(x - ref) / np.maximum(np.abs(ref), 1e-2)))
+    """Larger of: relative error of (1 - e)/2 per edge, absolute error of e per edge."""
+    x, ref = np.asarray(x, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    d = np.abs(x - ref)
+    return float(max(np.max(d / np.abs(1.0 - ref)), np.max(d)))
 
 
 @pytest.fixture(scope="module", autouse=True)
