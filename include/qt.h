@@ -41,7 +41,7 @@ extern "C" {
 /* ---- error codes ---------------------------------------------------------- */
 #define QT_OK 0
 #define QT_EINVAL -1   /* bad argument: null pointer, self-loop, duplicate edge, vertex out of range, p < 1 */
-#define QT_EWIDTH -2   /* a bucket is wider than qt_plan_opts.max_width */
+#define QT_EWIDTH -2   /* a bucket is wider than qt_plan_opts.max_width, or has more than 16 operands */
 #define QT_ENOMEM -3   /* host or device allocation failed, or over qt_plan_opts.arena_bytes */
 #define QT_ECUDA -4    /* a CUDA runtime call failed (no device, launch failure, ...) */
 #define QT_ETIMEOUT -5 /* a kernel's bounded wait on a bucket dependency ran out */
@@ -92,7 +92,7 @@ typedef struct {
                                once plus every output written once, at the plan's dtype */
     double flops;           /* complex multiply-adds of one evaluation x 8 real flops */
     int64_t arena_bytes;    /* device bytes of the tensor arena */
-    int64_t n_tasks;        /* persistent-kernel tasks (bucket tiles) */
+    int64_t n_tasks;        /* output tiles over all buckets */
     int64_t n_items;        /* persistent-kernel work items (claims) */
     int32_t n_levels;       /* longest dependency chain, in buckets */
     int32_t dtype;
@@ -200,9 +200,10 @@ int qt_sync(qt_plan_t plan, void *cuda_stream);
  * *launches receives the count. reset != 0 clears the counters. */
 int qt_kernel_time(qt_plan_t plan, double *avg_ms, int64_t *launches, int32_t reset);
 
-/* Fault injection for tests: add one to the dependency count of bucket
- * `bucket` on the device so that no producer can ever satisfy it; the next
- * persistent run must end with QT_ETIMEOUT rather than wait forever. */
+/* Fault injection for tests: on the device, raise the number of output tiles
+ * bucket `bucket` must complete by one, so the bucket consuming its result can
+ * never start. The next persistent run must end with QT_ETIMEOUT (its bounded
+ * wait runs out) rather than wait forever. Use a plan that is then freed. */
 int qt_debug_stall_bucket(qt_plan_t plan, int64_t bucket);
 
 void qt_plan_free(qt_plan_t plan);

@@ -122,8 +122,8 @@ int upload(qt_plan_t P) {
     };
     std::vector<Piece> pieces = {
         {hp.buckets.data(), bytes_of(hp.buckets), 0},         {hp.operands.data(), bytes_of(hp.operands), 0},
-        {hp.item_begin.data(), bytes_of(hp.item_begin), 0},   {hp.tasks_bucket.data(), bytes_of(hp.tasks_bucket), 0},
-        {hp.tasks_chunk.data(), bytes_of(hp.tasks_chunk), 0}, {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
+        {hp.item_begin.data(), bytes_of(hp.item_begin), 0},   {hp.runs.data(), bytes_of(hp.runs), 0},
+        {nullptr, 0, 0},                                       {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
     };
     size_t total = 0;
@@ -139,7 +139,7 @@ int upload(qt_plan_t P) {
     char* base = static_cast<char*>(P->d_static);
 
     const uint32_t nb = (uint32_t)hp.buckets.size();
-    P->counters_bytes = (size_t)2 * nb * sizeof(uint32_t) + sizeof(qt::DControl);
+    P->counters_bytes = (size_t)nb * sizeof(uint32_t) + sizeof(qt::DControl);
     P->counters_bytes = (P->counters_bytes + 255) / 256 * 256;
     QT_CUDA(cudaMalloc(&P->d_counters, P->counters_bytes));
     QT_CUDA(cudaMemset(P->d_counters, 0, P->counters_bytes));
@@ -155,13 +155,11 @@ int upload(qt_plan_t P) {
     dp.buckets = reinterpret_cast<const qt::DBucket*>(base + pieces[0].off);
     dp.ops = reinterpret_cast<const qt::DOperand*>(base + pieces[1].off);
     dp.item_begin = reinterpret_cast<const uint32_t*>(base + pieces[2].off);
-    dp.task_bucket = reinterpret_cast<const uint32_t*>(base + pieces[3].off);
-    dp.task_chunk = reinterpret_cast<const uint32_t*>(base + pieces[4].off);
+    dp.runs = reinterpret_cast<const qt::DRun*>(base + pieces[3].off);
     dp.n_items = (uint32_t)(hp.item_begin.size() - 1);
     dp.n_buckets = nb;
     dp.chunks_done = static_cast<uint32_t*>(P->d_counters);
-    dp.deps_done = dp.chunks_done + nb;
-    dp.ctl = reinterpret_cast<qt::DControl*>(dp.deps_done + nb);
+    dp.ctl = reinterpret_cast<qt::DControl*>(dp.chunks_done + nb);
     dp.arena = P->d_arena;
     dp.spin_limit = P->spin_limit;
 
@@ -178,7 +176,13 @@ int upload(qt_plan_t P) {
 
     int sms = 0;
     QT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
-    P->grid = sms * qt::persistent_blocks_per_sm(P->dtype);
+    const int per_sm = qt::persistent_blocks_per_sm(P->dtype);
+    if (per_sm <= 0) {
+        std::snprintf(g_detail, sizeof(g_detail), "persistent kernel does not fit an SM (%zu bytes of shared memory)",
+                      qt::persistent_smem_bytes(P->dtype));
+        return QT_ECUDA;
+    }
+    P->grid = sms * per_sm;
     QT_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
     QT_CUDA(cudaEventCreate(&P->cap_ev[0]));
     QT_CUDA(cudaEventCreate(&P->cap_ev[1]));
@@ -398,7 +402,7 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->alg_bytes = hp.alg_bytes;
     out->flops = hp.flops;
     out->arena_bytes = (int64_t)P->arena_bytes;  // what the device arena takes (or would take)
-    out->n_tasks = (int64_t)hp.tasks_bucket.size();
+    out->n_tasks = (int64_t)hp.n_tiles;
     out->n_items = (int64_t)hp.item_begin.size() - 1;
     out->n_levels = hp.n_levels;
     out->dtype = P->dtype;
@@ -500,7 +504,7 @@ int qt_debug_stall_bucket(qt_plan_t P, int64_t bucket) {
     if (!P || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
     qt::DBucket d = P->hp.buckets[bucket];
-    d.n_deps += 1;
+    d.n_tasks += 1;  // one tile more than will ever be written
     QT_CUDA(cudaSetDevice(P->device));
     QT_CUDA(cudaMemcpy((void*)(P->dp.buckets + bucket), &d, sizeof(d), cudaMemcpyHostToDevice));
     return QT_OK;

@@ -12,13 +12,11 @@ namespace qt {
 struct DevPlan {
     const DBucket* buckets;
     const DOperand* ops;
-    const uint32_t* item_begin;
-    const uint32_t* task_bucket;
-    const uint32_t* task_chunk;
+    const uint32_t* item_begin;  // n_items + 1, into runs
+    const DRun* runs;
     uint32_t n_items;
     uint32_t n_buckets;
-    uint32_t* chunks_done;  // n_buckets
-    uint32_t* deps_done;    // n_buckets
+    uint32_t* chunks_done;  // n_buckets: tiles written so far
     DControl* ctl;
     void* arena;            // complex64 or complex128 elements
     uint64_t spin_limit;
@@ -42,6 +40,7 @@ cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream
 cudaError_t launch_per_bucket(int dtype, uint32_t bucket, uint32_t n_tasks, const DevPlan& dp, cudaStream_t s);
 cudaError_t launch_epilogue(int dtype, const DevEpilogue& de, cudaStream_t s);
 int persistent_blocks_per_sm(int dtype);
-constexpr int kPersistentThreads = 256;
+constexpr int kPersistentThreads = 128;  // 4 warps; each warp owns its shared-memory stages
+size_t persistent_smem_bytes(int dtype);
 
 }  // namespace qt

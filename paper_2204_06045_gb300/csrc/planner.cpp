@@ -294,10 +294,36 @@ static int make_buckets(const Network& net, const std::vector<int>& order, int m
     return QT_OK;
 }
 
-static int default_chunk_bits(int n_out) {
-    // Outputs per persistent task, by output size. Small buckets run whole;
-    // wide ones are cut into 4096-output tiles so all SMs share them.
-    return std::min(n_out, 12);
+// Tile size of a bucket: the largest 2^cb outputs (cb <= cap) for which the
+// footprints of the staged operands fit one shared-memory stage. Within an
+// aligned tile an operand with mask M touches the contiguous block of
+// 2^(popc(M & (2^cb - 1)) + 1) elements starting at 2 * pext(o0, M). Gate
+// tensors are folded into one per-tile table when their tile bits number at
+// most kLeafBits; otherwise they are staged like the others.
+static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_elems, int* cb_out, bool* fold_out) {
+    (void)net;
+    const int n_out = B.width - 1;
+    for (int cb = std::min(n_out, cap); cb >= 0; --cb) {
+        const uint32_t low = cb >= 32 ? 0xffffffffu : ((1u << cb) - 1u);
+        uint32_t U = 0;
+        int nleaf = 0;
+        for (const HOperand& op : B.ops)
+            if (op.src < 0) {
+                U |= op.mask & low;
+                nleaf++;
+            }
+        const bool fold = nleaf > 0 && nleaf <= kMaxFoldLeaves && __builtin_popcount(U) <= kLeafBits;
+        long foot = 0;
+        for (const HOperand& op : B.ops)
+            if (!(fold && op.src < 0)) foot += 2l << __builtin_popcount(op.mask & low);
+        if (foot <= stage_elems) {
+            *cb_out = cb;
+            *fold_out = fold;
+            return;
+        }
+    }
+    *cb_out = 0;
+    *fold_out = false;
 }
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -389,10 +415,14 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             const HBucket& B = np.buckets[lb];
             DBucket d{};
             d.op_begin = (uint32_t)hp->operands.size();
-            d.n_ops = (uint16_t)B.ops.size();
+            d.n_ops = (uint8_t)B.ops.size();
             d.n_out = (uint8_t)(B.width - 1);
-            int cb = cfg.chunk_log2 > 0 ? std::min<int>(d.n_out, cfg.chunk_log2) : default_chunk_bits(d.n_out);
+            int cb = 0;
+            bool fold = false;
+            pick_tile(B, net, cfg.chunk_log2 > 0 ? cfg.chunk_log2 : 30,
+                      cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, &cb, &fold);
             d.chunk_bits = (uint8_t)cb;
+            d.flags = fold ? kBucketFoldLeaves : 0;
             d.parent = B.parent >= 0 ? base + (uint32_t)B.parent : kNone;
             d.n_deps = (uint32_t)B.n_deps;
             d.n_tasks = 1u << (d.n_out - cb);
@@ -432,9 +462,12 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
         hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());
         hp->net_first_root.push_back((uint32_t)hp->root_bucket.size());
     }
-    // intermediate operands point at their producer's result
+    // intermediate operands point at their producer's result and name it
     for (size_t o = 0; o < hp->operands.size(); ++o)
-        if (hp->op_src[o] >= 0) hp->operands[o].off = hp->buckets[hp->op_src[o]].out_off;
+        if (hp->op_src[o] >= 0) {
+            hp->operands[o].off = hp->buckets[hp->op_src[o]].out_off;
+            hp->operands[o].flags = (uint32_t)hp->op_src[o] << 1;
+        }
     hp->arena_elems = off;
     hp->cot_off = 0;
     hp->total_elems = off;
@@ -447,38 +480,46 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     const uint32_t nb = (uint32_t)hp->buckets.size();
     hp->by_level.resize(nb);
     for (uint32_t b = 0; b < nb; ++b) hp->by_level[b] = b;
-    std::stable_sort(hp->by_level.begin(), hp->by_level.end(),
-                     [&](uint32_t a, uint32_t b) { return hp->bucket_level[a] < hp->bucket_level[b]; });
+    // level order (a topological order); within a level the largest buckets
+    // first, so that a level ends on small tasks
+    std::stable_sort(hp->by_level.begin(), hp->by_level.end(), [&](uint32_t a, uint32_t b) {
+        if (hp->bucket_level[a] != hp->bucket_level[b]) return hp->bucket_level[a] < hp->bucket_level[b];
+        return hp->buckets[a].n_out > hp->buckets[b].n_out;
+    });
     hp->level_first_bucket.assign(hp->n_levels + 1, 0);
     for (uint32_t b : hp->by_level) hp->level_first_bucket[hp->bucket_level[b] + 1]++;
     for (int l = 0; l < hp->n_levels; ++l) hp->level_first_bucket[l + 1] += hp->level_first_bucket[l];
-    hp->tasks_bucket.clear();
-    hp->tasks_chunk.clear();
+    hp->runs.clear();
     hp->item_begin.assign(1, 0);
-    const uint64_t item_outputs = 1u << 10;
-    const uint32_t item_max_tasks = 32;
-    uint64_t cur_out = 0;
-    uint32_t cur_tasks = 0;
+    hp->n_tiles = 0;
+    // A work item is what one claim hands a warp: one run of up to kRunTiles
+    // tiles of a wide bucket, or up to 32 single-tile buckets of one level
+    // (none of which depends on another).
+    const uint32_t item_max_runs = 32;
+    uint32_t cur_runs = 0;
     int cur_level = -1;
+    auto close_item = [&]() {
+        if (cur_runs > 0) hp->item_begin.push_back((uint32_t)hp->runs.size());
+        cur_runs = 0;
+    };
     for (uint32_t b : hp->by_level) {
         const DBucket& d = hp->buckets[b];
-        const uint64_t per_task = 1ull << d.chunk_bits;
-        for (uint32_t c = 0; c < d.n_tasks; ++c) {
-            bool start_new = cur_tasks > 0 && (hp->bucket_level[b] != cur_level || cur_out + per_task > item_outputs ||
-                                                cur_tasks >= item_max_tasks);
-            if (start_new) {
-                hp->item_begin.push_back((uint32_t)hp->tasks_bucket.size());
-                cur_out = 0;
-                cur_tasks = 0;
+        hp->n_tiles += d.n_tasks;
+        if (d.n_tasks > 1) {
+            close_item();
+            for (uint32_t c = 0; c < d.n_tasks; c += kRunTiles) {
+                hp->runs.push_back(DRun{b, c, std::min<uint32_t>(kRunTiles, d.n_tasks - c), 0});
+                cur_runs = 1;
+                close_item();
             }
-            hp->tasks_bucket.push_back(b);
-            hp->tasks_chunk.push_back(c);
-            cur_out += per_task;
-            cur_tasks++;
-            cur_level = hp->bucket_level[b];
+            continue;
         }
+        if (cur_runs > 0 && (hp->bucket_level[b] != cur_level || cur_runs >= item_max_runs)) close_item();
+        hp->runs.push_back(DRun{b, 0, 1, 0});
+        cur_runs++;
+        cur_level = hp->bucket_level[b];
     }
-    if (cur_tasks > 0) hp->item_begin.push_back((uint32_t)hp->tasks_bucket.size());
+    close_item();
     hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return QT_OK;
 }

@@ -80,9 +80,9 @@ struct HostPlan {
     std::vector<int32_t> op_rank;
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
-    std::vector<uint32_t> tasks_bucket; // tasks in claim order
-    std::vector<uint32_t> tasks_chunk;
-    std::vector<uint32_t> item_begin;   // n_items + 1, into the task arrays
+    std::vector<DRun> runs;             // runs of tiles in claim order
+    std::vector<uint32_t> item_begin;   // n_items + 1, into the run array
+    uint64_t n_tiles = 0;
     std::vector<uint32_t> root_bucket;  // every root bucket (scalar result)
     std::vector<uint32_t> net_first_root;  // n_nets + 1 into root_bucket
     std::vector<uint32_t> level_first_bucket;  // buckets sorted by level (for the adjoint)

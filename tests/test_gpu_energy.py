@@ -203,7 +203,7 @@ def test_stalled_dependency_times_out_and_context_survives():
     g, b = synth.angles(p, 3)
     with qtgb.plan(n, edges, p, dtype="c64", spin_limit=2000) as pl:
         B, _ = pl.export()
-        victim = int(np.nonzero(B["n_deps"] > 0)[0][-1])
+        victim = int(np.nonzero(B["parent"] >= 0)[0][-1])  # a producer: its consumer can never start
         pl.debug_stall_bucket(victim)
         with pytest.raises(qtgb.QTError) as ei:
             pl.energy(g, b)
