@@ -73,9 +73,13 @@ typedef struct {
     int32_t with_grad;     /* nonzero: also allocate what qt_energy_grad needs */
     uint64_t spin_limit;   /* polls of a dependency counter before a kernel gives up with
                               QT_ETIMEOUT (default 2^23, each poll sleeps ~0.1-1 us) */
-    int32_t chunk_log2;    /* outputs per persistent-kernel task, log2 (default 0: per-width table) */
+    int32_t chunk_log2;    /* most outputs per tile, log2 (default 0: 8, i.e. 256 outputs); smaller
+                              when a bucket's operand footprints do not fit the 8 KB stage */
     int32_t host_only;     /* nonzero: plan on the host only (statistics, export); no device
                               memory is touched and every evaluation call returns QT_ESTATE */
+    int32_t run_tiles;     /* most tiles of one bucket handed out per claim (default 0: 16) */
+    int32_t trace;         /* nonzero: run the instrumented persistent kernel, which counts
+                              per-warp cycles by phase (read with qt_trace_counters) */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -93,7 +97,7 @@ typedef struct {
     double flops;           /* complex multiply-adds of one evaluation x 8 real flops */
     int64_t arena_bytes;    /* device bytes of the tensor arena */
     int64_t n_tasks;        /* output tiles over all buckets */
-    int64_t n_items;        /* persistent-kernel work items (claims) */
+    int64_t n_items;        /* persistent-kernel work groups (ready-queue entries, one claim each) */
     int32_t n_levels;       /* longest dependency chain, in buckets */
     int32_t dtype;
     int64_t width_hist[64]; /* buckets per width */
@@ -140,6 +144,16 @@ typedef struct {
  */
 int qt_plan(int32_t n_vertices, int32_t n_edges, const int32_t *edges, int32_t p,
             const qt_plan_opts *opts, qt_plan_t *out);
+
+/*
+ * A plan for the networks of selected edges only: `sel` (host, n_sel indices
+ * into `edges`, any order, no repeats needed) picks the lightcones to plan.
+ * qt_energy then reports edge_zz in selection order and, as energy, the
+ * selected edges' share of <C>: n_sel/2 - 1/2 sum_sel e_jk. The lightcones
+ * still see the whole graph.
+ */
+int qt_plan_subset(int32_t n_vertices, int32_t n_edges, const int32_t *edges, int32_t p, int32_t n_sel,
+                   const int32_t *sel, const qt_plan_opts *opts, qt_plan_t *out);
 
 /*
  * One plan over several graphs, evaluated together by qt_energy_batch.
@@ -199,6 +213,15 @@ int qt_sync(qt_plan_t plan, void *cuda_stream);
  * since the last reset, measured with CUDA events on the launch stream.
  * *launches receives the count. reset != 0 clears the counters. */
 int qt_kernel_time(qt_plan_t plan, double *avg_ms, int64_t *launches, int32_t reset);
+
+/* Phase counters of the last persistent run of a plan built with opts.trace,
+ * summed over warps: totals[0..6] = cycles spent claiming work (and the
+ * kernel's tail), reading run descriptors, checking and waiting for producers,
+ * starting bulk copies, waiting for copies to land, contracting tiles, and
+ * publishing finished runs; totals[7] = tiles, totals[8] = runs, totals[9]
+ * unused. *n_warps receives the number of warps launched. Host call; waits
+ * for the plan's work to finish. QT_ESTATE if the plan was built without trace. */
+int qt_trace_counters(qt_plan_t plan, uint64_t *totals, int64_t *n_warps);
 
 /* Fault injection for tests: on the device, raise the number of output tiles
  * bucket `bucket` must complete by one, so the bucket consuming its result can

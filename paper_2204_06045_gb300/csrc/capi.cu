@@ -53,6 +53,8 @@ struct qt_plan_s {
     int64_t timed = 0;
     bool err_pending = false;
     bool host_only = false;
+    bool trace = false;
+    uint64_t* d_trace = nullptr;
 
     ~qt_plan_s() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -69,6 +71,7 @@ struct qt_plan_s {
         if (d_angles) cudaFree(d_angles);
         if (d_out) cudaFree(d_out);
         if (h_err) cudaFreeHost(h_err);
+        if (d_trace) cudaFree(d_trace);
     }
 };
 
@@ -115,14 +118,17 @@ int upload(qt_plan_t P) {
 
     // static plan arrays, one allocation, 256-byte aligned pieces
     std::vector<uint32_t> u_graph_first_net(hp.graph_first_net.begin(), hp.graph_first_net.end());
+    // operand array padded so a warp may read kMaxOps entries from any bucket's first operand
+    std::vector<qt::DOperand> ops_padded(hp.operands);
+    ops_padded.resize(hp.operands.size() + qt::kMaxOps, qt::DOperand{});
     struct Piece {
         const void* src;
         size_t bytes;
         size_t off;
     };
     std::vector<Piece> pieces = {
-        {hp.buckets.data(), bytes_of(hp.buckets), 0},         {hp.operands.data(), bytes_of(hp.operands), 0},
-        {hp.item_begin.data(), bytes_of(hp.item_begin), 0},   {hp.runs.data(), bytes_of(hp.runs), 0},
+        {hp.buckets.data(), bytes_of(hp.buckets), 0},         {ops_padded.data(), bytes_of(ops_padded), 0},
+        {nullptr, 0, 0},                                       {hp.runs.data(), bytes_of(hp.runs), 0},
         {nullptr, 0, 0},                                       {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
     };
@@ -138,9 +144,13 @@ int upload(qt_plan_t P) {
     QT_CUDA(cudaMemcpy(P->d_static, staging.data(), total, cudaMemcpyHostToDevice));
     char* base = static_cast<char*>(P->d_static);
 
+    // zeroed before every persistent run: control word, per-bucket tile and
+    // producer counters, and the published part of the ready queue
     const uint32_t nb = (uint32_t)hp.buckets.size();
-    P->counters_bytes = (size_t)nb * sizeof(uint32_t) + sizeof(qt::DControl);
-    P->counters_bytes = (P->counters_bytes + 255) / 256 * 256;
+    const uint64_t n_dyn = hp.n_groups - hp.runs.size();
+    const size_t ctl_bytes = 256;
+    const size_t cnt_bytes = ((size_t)2 * nb * sizeof(uint32_t) + 255) / 256 * 256;
+    P->counters_bytes = ctl_bytes + cnt_bytes + (size_t)n_dyn * sizeof(qt::DSlot);
     QT_CUDA(cudaMalloc(&P->d_counters, P->counters_bytes));
     QT_CUDA(cudaMemset(P->d_counters, 0, P->counters_bytes));
 
@@ -154,12 +164,15 @@ int upload(qt_plan_t P) {
     qt::DevPlan& dp = P->dp;
     dp.buckets = reinterpret_cast<const qt::DBucket*>(base + pieces[0].off);
     dp.ops = reinterpret_cast<const qt::DOperand*>(base + pieces[1].off);
-    dp.item_begin = reinterpret_cast<const uint32_t*>(base + pieces[2].off);
     dp.runs = reinterpret_cast<const qt::DRun*>(base + pieces[3].off);
-    dp.n_items = (uint32_t)(hp.item_begin.size() - 1);
+    dp.n_static = (uint32_t)hp.runs.size();
+    dp.n_groups = (uint32_t)hp.n_groups;
     dp.n_buckets = nb;
-    dp.chunks_done = static_cast<uint32_t*>(P->d_counters);
-    dp.ctl = reinterpret_cast<qt::DControl*>(dp.chunks_done + nb);
+    char* cbase = static_cast<char*>(P->d_counters);
+    dp.ctl = reinterpret_cast<qt::DControl*>(cbase);
+    dp.tiles_done = reinterpret_cast<uint32_t*>(cbase + ctl_bytes);
+    dp.prod_done = dp.tiles_done + nb;
+    dp.slots = reinterpret_cast<qt::DSlot*>(cbase + ctl_bytes + cnt_bytes);
     dp.arena = P->d_arena;
     dp.spin_limit = P->spin_limit;
 
@@ -183,6 +196,14 @@ int upload(qt_plan_t P) {
         return QT_ECUDA;
     }
     P->grid = sms * per_sm;
+    if (P->trace) {
+        const size_t tb = (size_t)P->grid * (qt::kPersistentThreads / 32) * qt::kTraceSlots * sizeof(uint64_t);
+        QT_CUDA(cudaMalloc((void**)&P->d_trace, tb));
+        QT_CUDA(cudaMemset(P->d_trace, 0, tb));
+        P->dp.trace = P->d_trace;
+    } else {
+        P->dp.trace = nullptr;
+    }
     QT_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
     QT_CUDA(cudaEventCreate(&P->cap_ev[0]));
     QT_CUDA(cudaEventCreate(&P->cap_ev[1]));
@@ -334,6 +355,8 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     cfg.seed = o.order_seed;
     cfg.max_width = o.max_width > 0 ? o.max_width : 31;
     cfg.chunk_log2 = o.chunk_log2;
+    cfg.run_tiles = o.run_tiles;
+    if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
     if (cfg.chunk_log2 < 0 || cfg.chunk_log2 > 24) return QT_EINVAL;
     std::unique_ptr<qt_plan_s> P(new (std::nothrow) qt_plan_s());
@@ -354,6 +377,7 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     if (o.arena_bytes && (size_t)P->hp.total_elems * P->esize > o.arena_bytes) return QT_ENOMEM;
     P->arena_bytes = (size_t)P->hp.total_elems * P->esize;
     P->host_only = o.host_only != 0;
+    P->trace = o.trace != 0;
     if (!P->host_only) {
         rc = upload(P.get());
         if (rc != QT_OK) return rc;
@@ -372,6 +396,16 @@ int qt_plan(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int32_t p
     std::vector<qt::GraphIn> gs(1);
     gs[0].n = n_vertices;
     for (int e = 0; e < n_edges; ++e) gs[0].edges.emplace_back(edges[2 * e], edges[2 * e + 1]);
+    return make_plan(gs, p, opts, out);
+}
+
+int qt_plan_subset(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int32_t p, int32_t n_sel,
+                   const int32_t* sel, const qt_plan_opts* opts, qt_plan_t* out) {
+    if (!edges || n_edges < 1 || n_vertices < 2 || n_sel < 1 || !sel) return QT_EINVAL;
+    std::vector<qt::GraphIn> gs(1);
+    gs[0].n = n_vertices;
+    for (int e = 0; e < n_edges; ++e) gs[0].edges.emplace_back(edges[2 * e], edges[2 * e + 1]);
+    gs[0].sel.assign(sel, sel + n_sel);
     return make_plan(gs, p, opts, out);
 }
 
@@ -403,7 +437,7 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->flops = hp.flops;
     out->arena_bytes = (int64_t)P->arena_bytes;  // what the device arena takes (or would take)
     out->n_tasks = (int64_t)hp.n_tiles;
-    out->n_items = (int64_t)hp.item_begin.size() - 1;
+    out->n_items = (int64_t)hp.n_groups;
     out->n_levels = hp.n_levels;
     out->dtype = P->dtype;
     std::memcpy(out->width_hist, hp.width_hist, sizeof(out->width_hist));
@@ -500,12 +534,28 @@ int qt_kernel_time(qt_plan_t P, double* avg_ms, int64_t* launches, int32_t reset
     return QT_OK;
 }
 
+int qt_trace_counters(qt_plan_t P, uint64_t* totals, int64_t* n_warps) {
+    if (!P || !totals) return QT_EINVAL;
+    if (P->host_only || !P->trace) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    QT_CUDA(cudaDeviceSynchronize());
+    const size_t nw = (size_t)P->grid * (qt::kPersistentThreads / 32);
+    std::vector<uint64_t> buf(nw * qt::kTraceSlots);
+    QT_CUDA(cudaMemcpy(buf.data(), P->d_trace, buf.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < qt::kTraceSlots; ++i) totals[i] = 0;
+    for (size_t w = 0; w < nw; ++w)
+        for (int i = 0; i < qt::kTraceSlots; ++i) totals[i] += buf[w * qt::kTraceSlots + i];
+    if (n_warps) *n_warps = (int64_t)nw;
+    return QT_OK;
+}
+
 int qt_debug_stall_bucket(qt_plan_t P, int64_t bucket) {
     if (!P || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    // the bucket then never counts as complete, so its consumer is never queued
     qt::DBucket d = P->hp.buckets[bucket];
     d.n_tasks += 1;  // one tile more than will ever be written
-    QT_CUDA(cudaSetDevice(P->device));
     QT_CUDA(cudaMemcpy((void*)(P->dp.buckets + bucket), &d, sizeof(d), cudaMemcpyHostToDevice));
     return QT_OK;
 }

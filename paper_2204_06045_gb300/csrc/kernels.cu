@@ -228,6 +228,7 @@ struct RunSlot {
     uint32_t lmask[kMaxFoldLeaves];
     typename CT<R>::c lval[kMaxFoldLeaves][kLeafSlots];  // the folded gate tensors
     uint32_t bucket, chunk_begin, n_chunks;
+    uint32_t parent, n_tasks;
     uint32_t leaf_u;      // folded gate masks within the tile
     uint32_t leaf_hi;     // nonzero if a folded gate mask has bits above the tile
     uint32_t total_foot;  // staged elements per tile
@@ -268,10 +269,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Bits of j deposited at the set bits of m (parallel bit deposit).
 __device__ __forceinline__ uint32_t pdep_u32(uint32_t j, uint32_t m) {
@@ -284,148 +281,166 @@ __device__ __forceinline__ uint32_t pdep_u32(uint32_t j, uint32_t m) {
     return r;
 }
 
-// Exclusive prefix sum over the warp.
-__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane, uint32_t* total) {
-    uint32_t x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
-    }
-    *total = __shfl_sync(kFull, x, 31);
-    return x - v;
-}
-
-// The claimed work of one warp, walked tile by tile. The next item is
-// claimed as soon as the current one is taken, so the claim's round trip
+// Queue positions are claimed with one atomic each; lane 0 claims the next
+// position as soon as it takes the current one, so the claim's round trip
 // overlaps the work.
 struct Cursor {
-    uint32_t r = 0, r_end = 0;  // runs of the current item
-    uint32_t c = 0;             // tiles handed out from run r
-    uint32_t reserved = 0;      // next item (lane 0), claimed ahead
-    bool have_reserved = false;
-
+    uint32_t reserved = 0;
     __device__ uint32_t claim(const DevPlan& dp, int lane) {
-        uint32_t item = 0;
-        if (lane == 0) item = ld_volatile(&dp.ctl->error) != 0 ? dp.n_items : atomicAdd(&dp.ctl->next_item, 1u);
-        return item;
+        uint32_t q = 0;
+        if (lane == 0) q = ld_volatile(&dp.ctl->error) != 0 ? dp.n_groups : atomicAdd(&dp.ctl->next_item, 1u);
+        return q;
     }
-    // Advance to the next run; false when the warp's work is done.
-    __device__ bool next_run(const DevPlan& dp, int lane) {
-        ++r;
-        c = 0;
-        if (r < r_end) return true;
-        uint32_t item = have_reserved ? reserved : claim(dp, lane);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= dp.n_items) return false;
+    __device__ uint32_t start(const DevPlan& dp, int lane) {
+        const uint32_t q = claim(dp, lane);
         reserved = claim(dp, lane);
-        have_reserved = true;
-        r = dp.item_begin[item];
-        r_end = dp.item_begin[item + 1];
-        return true;
+        return __shfl_sync(kFull, q, 0);
     }
-    __device__ bool start(const DevPlan& dp, int lane) {
-        r = 0xffffffffu;  // next_run() wraps it to 0 >= r_end and claims an item
-        r_end = 0;
-        return next_run(dp, lane);
+    __device__ uint32_t next(const DevPlan& dp, int lane) {
+        const uint32_t q = reserved;
+        reserved = claim(dp, lane);
+        return __shfl_sync(kFull, q, 0);
     }
 };
 
-// Read run `ri` into slot `sl`: bucket, operands, folded gate values. Each
-// lane returns the producer it must wait for (kNone if none) and that
-// producer's tile count.
+// The group at queue position q, if it has been published (non-blocking).
+__device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
+    uint32_t ok = 1;
+    DRun r{};
+    if (q < dp.n_static) {
+        r = dp.runs[q];
+    } else {
+        if (lane == 0) {
+            const DSlot* sl = dp.slots + (q - dp.n_static);
+            const uint32_t n = ld_acquire(&sl->n_chunks);
+            ok = n != 0;
+            if (ok) r = DRun{sl->bucket, sl->chunk_begin, n, sl->op_begin};
+        }
+        ok = __shfl_sync(kFull, ok, 0);
+        r.bucket = __shfl_sync(kFull, r.bucket, 0);
+        r.chunk_begin = __shfl_sync(kFull, r.chunk_begin, 0);
+        r.n_chunks = __shfl_sync(kFull, r.n_chunks, 0);
+        r.op_begin = __shfl_sync(kFull, r.op_begin, 0);
+    }
+    *out = r;
+    return ok != 0;
+}
+
+// Bounded wait until position q is published; records QT_ETIMEOUT on expiry.
+__device__ bool wait_group(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
+    uint64_t polls = 0;
+    while (!group_at(dp, q, out, lane)) {
+        const bool err = ld_volatile(&dp.ctl->error) != 0;
+        if (__any_sync(kFull, err)) return false;
+        if (++polls > dp.spin_limit) {
+            if (lane == 0 && atomicCAS(&dp.ctl->error, 0, QT_ETIMEOUT) == 0) dp.ctl->err_bucket = q;
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// Read group `run` into slot `sl`: bucket header, staged operands, folded gate
+// values (all laid out by the planner). Lane t < n_staged also gets the
+// compressed index of the group's first tile in its operand's bits above the
+// tile (pext(o0, M) is that index shifted left by the operand's tile bits).
 template <typename R>
-__device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, uint32_t ri, int lane, uint32_t* dep_b,
-                         uint32_t* dep_need) {
+__device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun& run, int lane, uint32_t* cbase) {
     using C = typename CT<R>::c;
-    const DRun run = dp.runs[ri];
+    DOperand op{};
+    if (lane < kMaxOps) op = dp.ops[run.op_begin + lane];  // the operand array is padded by kMaxOps
     const DBucket B = dp.buckets[run.bucket];
     RunSlot<R>& rs = ws.slot[sl];
-    const int cb = B.chunk_bits;
-    const uint32_t low = (1u << cb) - 1u;
-    const bool fold = (B.flags & kBucketFoldLeaves) != 0;
-    DOperand op{};
     const bool has = lane < B.n_ops;
-    if (has) op = dp.ops[B.op_begin + lane];
-    const bool leaf = has && (op.flags & kOpLeaf);
-    const bool folded = fold && leaf;
-    const bool staged = has && !folded;
-    const uint32_t foot = staged ? (2u << __popc(op.mask & low)) : 0u;
-    uint32_t total_foot, n_staged, n_leaves;
-    const uint32_t soff = warp_excl_scan(foot, lane, &total_foot);
-    const uint32_t spos = warp_excl_scan(staged ? 1u : 0u, lane, &n_staged);
-    const uint32_t lpos = warp_excl_scan(folded ? 1u : 0u, lane, &n_leaves);
-    const uint32_t leaf_u = __reduce_or_sync(kFull, folded ? (op.mask & low) : 0u);
-    const uint32_t leaf_hi = __reduce_or_sync(kFull, folded ? (op.mask & ~low) : 0u);
-    const bool fits = total_foot <= (uint32_t)StageCfg<R>::elems && n_leaves <= (uint32_t)kMaxFoldLeaves;
-    if (staged && fits) {
-        rs.goff[spos] = op.off;
-        rs.gmask[spos] = op.mask;
-        rs.soff[spos] = (uint16_t)soff;
-    }
-    if (folded && fits) {
-        rs.lmask[lpos] = op.mask;
-        const C* T = static_cast<const C*>(dp.arena) + op.off;
+    const bool fits = B.total_foot <= (uint32_t)StageCfg<R>::elems && B.n_leaves <= kMaxFoldLeaves;
+    if (has && fits) {
+        if (op.folded) {
+            rs.lmask[op.slot] = op.mask;
+            const C* T = static_cast<const C*>(dp.arena) + op.off;
 #pragma unroll
-        for (int i = 0; i < kLeafSlots; ++i) rs.lval[lpos][i] = T[i];
+            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = T[i];
+        } else {
+            rs.goff[op.slot] = op.off;
+            rs.gmask[op.slot] = op.mask;
+            rs.soff[op.slot] = op.soff;
+        }
     }
     if (lane == 0) {
         rs.out_off = B.out_off;
         rs.bucket = run.bucket;
         rs.chunk_begin = run.chunk_begin;
         rs.n_chunks = run.n_chunks;
-        rs.leaf_u = leaf_u;
-        rs.leaf_hi = leaf_hi;
-        rs.total_foot = total_foot;
+        rs.parent = B.parent;
+        rs.n_tasks = B.n_tasks;
+        rs.leaf_u = B.leaf_u;
+        rs.leaf_hi = B.leaf_hi;
+        rs.total_foot = B.total_foot;
         rs.n_out = B.n_out;
-        rs.cb = (uint8_t)cb;
-        rs.n_staged = (uint8_t)n_staged;
-        rs.n_leaves = (uint8_t)n_leaves;
+        rs.cb = B.chunk_bits;
+        rs.n_staged = B.n_staged;
+        rs.n_leaves = B.n_leaves;
         rs.bad = !fits;
         if (!fits && atomicCAS(&dp.ctl->error, 0, QT_EBOUNDS) == 0) dp.ctl->err_bucket = run.bucket;
     }
-    *dep_b = (has && !leaf) ? (op.flags >> 1) : kNone;
-    *dep_need = *dep_b != kNone ? dp.buckets[*dep_b].n_tasks : 0u;
     __syncwarp();
+    *cbase = 0;
+    if (lane < rs.n_staged) *cbase = pext_u32(run.chunk_begin, rs.gmask[lane] >> rs.cb);
 }
 
-// True once every producer has written all its tiles (one poll per lane).
-__device__ __forceinline__ bool deps_met(const DevPlan& dp, uint32_t dep_b, uint32_t need) {
-    const bool ok = dep_b == kNone || ld_acquire(&dp.chunks_done[dep_b]) >= need;
-    return __all_sync(kFull, ok);
-}
-
-// Bounded wait for the producers; on expiry records QT_ETIMEOUT.
-__device__ bool wait_deps_run(const DevPlan& dp, uint32_t dep_b, uint32_t need, uint32_t b, int lane) {
-    uint64_t polls = 0;
-    while (!deps_met(dp, dep_b, need)) {
-        const bool err = ld_volatile(&dp.ctl->error) != 0;
-        if (__any_sync(kFull, err)) return false;
-        if (++polls > dp.spin_limit) {
-            if (lane == 0 && atomicCAS(&dp.ctl->error, 0, QT_ETIMEOUT) == 0) dp.ctl->err_bucket = b;
-            return false;
+// Append every group of bucket p to the queue (its last producer just finished).
+__device__ void publish_bucket(const DevPlan& dp, uint32_t p, int lane) {
+    const DBucket& B = dp.buckets[p];
+    const uint32_t ng = B.n_groups, gt = B.group_tiles, nt = B.n_tasks, ob = B.op_begin;
+    uint32_t base = 0;
+    if (lane == 0) {
+        base = atomicAdd(&dp.ctl->next_free, ng);
+        if (base + ng > dp.n_groups - dp.n_static) {  // cannot happen with a consistent plan
+            if (atomicCAS(&dp.ctl->error, 0, QT_EBOUNDS) == 0) dp.ctl->err_bucket = p;
+            base = 0xffffffffu;
         }
-        __nanosleep(100);
     }
-    return true;
+    base = __shfl_sync(kFull, base, 0);
+    if (base == 0xffffffffu) return;
+    for (uint32_t k = lane; k < ng; k += 32) {
+        DSlot* sl = dp.slots + base + k;
+        sl->bucket = p;
+        sl->chunk_begin = k * gt;
+        sl->op_begin = ob;
+        const uint32_t n = min(gt, nt - k * gt);
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&sl->n_chunks), "r"(n) : "memory");
+    }
 }
 
-// Start the bulk copies of tile `chunk` of the run in slot `sl` into stage `st`.
+// Start the bulk copies of tile `chunk` of the group in slot `sl` into stage
+// `st`. Lane t < n_staged keeps in `cbase` the compressed index of the
+// current tile in its operand's bits above the tile; for the next tile of the
+// group it is advanced in place: going from chunk c-1 to c clears the trailing
+// ones of c-1 (their r operand bits below bit t = ctz(c) give back 2^r - 1)
+// and sets bit t (worth 2^r if the operand carries it).
 // Returns true if copies were issued (the stage's barrier will complete).
 template <typename R>
-__device__ __forceinline__ bool issue_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk, int lane) {
+__device__ __forceinline__ bool issue_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk,
+                                           bool first, int lane, uint32_t& cbase) {
     using C = typename CT<R>::c;
     const RunSlot<R>& rs = ws.slot[sl];
     if (rs.bad || rs.total_foot == 0) return false;
-    fence_proxy_async_smem();  // earlier reads of this stage come before the new copies
-    __syncwarp();
+    // The stage's previous contents were read into registers and consumed
+    // before the caller's __syncwarp, so the copies may overwrite it now.
     if (lane == 0) mbar_expect_tx(&ws.bar[st], rs.total_foot * (uint32_t)sizeof(C));
     __syncwarp();
     if (lane < rs.n_staged) {
         const uint32_t m = rs.gmask[lane];
-        const C* src = static_cast<const C*>(dp.arena) + rs.goff[lane] + 2ull * pext_u32(chunk << rs.cb, m);
-        const uint32_t foot = 2u << __popc(m & ((1u << rs.cb) - 1u));
-        bulk_g2s(&ws.stage[st][rs.soff[lane]], src, foot * (uint32_t)sizeof(C), &ws.bar[st]);
+        const uint32_t low = (1u << rs.cb) - 1u;
+        const uint32_t mh = m >> rs.cb;
+        if (!first) {
+            const uint32_t t = __ffs(chunk) - 1u;
+            const uint32_t r = __popc(mh & ((1u << t) - 1u));
+            cbase = cbase - ((1u << r) - 1u) + (((mh >> t) & 1u) << r);
+        }
+        const uint32_t plow = __popc(m & low);
+        const C* src = static_cast<const C*>(dp.arena) + rs.goff[lane] + 2ull * ((uint64_t)cbase << plow);
+        bulk_g2s(&ws.stage[st][rs.soff[lane]], src, (2u << plow) * (uint32_t)sizeof(C), &ws.bar[st]);
     }
     return true;
 }
@@ -554,6 +569,55 @@ __device__ void tile_from_smem_generic(const WarpSmem<R>& ws, int sl, int st, ty
     }
 }
 
+// The hot path for tiles of at least 64 outputs (cb = 6 + log2 NI): N
+// operands in shared memory, every loop fully unrolled. A lane owns outputs
+// 2*lane + {0,1} + 64*i; an operand's pair index for that output is its lane
+// part plus the iteration bits' deltas, all fixed before the loop.
+template <typename R, int N, int NI>
+__device__ __forceinline__ void tile_fast(const typename CT<R>::c* const (&base)[N], const uint32_t (&mask)[N],
+                                          typename CT<R>::c* out, int lane) {
+    using C = typename CT<R>::c;
+    constexpr int IB = NI == 1 ? 0 : NI == 2 ? 1 : NI == 4 ? 2 : NI == 8 ? 3 : 4;
+    uint32_t off0[N], second[N], d[N][IB > 0 ? IB : 1];
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        const uint32_t m = mask[t];
+        off0[t] = pext_u32((uint32_t)lane << 1, m & 63u);
+        second[t] = (m & 1u) ? 2u : 0u;  // element offset of the second output's pair
+#pragma unroll
+        for (int k = 0; k < IB; ++k) {
+            const int bit = 6 + k;
+            d[t][k] = ((m >> bit) & 1u) ? (1u << __popc(m & ((1u << bit) - 1u))) : 0u;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        C p00, p01, p10, p11;  // [output][x]
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            uint32_t o = off0[t];
+#pragma unroll
+            for (int k = 0; k < IB; ++k)
+                if ((i >> k) & 1) o += d[t][k];
+            const C* q = base[t] + 2u * o;
+            const Pair<C> a = ld_pair_smem(q);
+            const Pair<C> b = ld_pair_smem(q + second[t]);
+            if (t == 0) {
+                p00 = a.v0;
+                p01 = a.v1;
+                p10 = b.v0;
+                p11 = b.v1;
+            } else {
+                p00 = cmul(p00, a.v0);
+                p01 = cmul(p01, a.v1);
+                p10 = cmul(p10, b.v0);
+                p11 = cmul(p11, b.v1);
+            }
+        }
+        st_two(out, (uint64_t)(i * 64 + 2 * lane), cadd(p00, p01), cadd(p10, p11));
+    }
+}
+
 template <typename R, int N>
 __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st, typename CT<R>::c* out,
                                            uint32_t chunk, int lane) {
@@ -568,15 +632,21 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
         base[t] = is_tab ? ws.leaf_tab : ws.stage[st] + rs.soff[t];
         mask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
-    tile_from_smem<R, N>(base, mask, out, rs.cb, rs.n_out, chunk << rs.cb, lane);
+    C* tile_out = out + ((uint64_t)chunk << rs.cb);
+    switch (rs.cb) {
+        case 6: tile_fast<R, N, 1>(base, mask, tile_out, lane); break;
+        case 7: tile_fast<R, N, 2>(base, mask, tile_out, lane); break;
+        case 8: tile_fast<R, N, 4>(base, mask, tile_out, lane); break;
+        case 9: tile_fast<R, N, 8>(base, mask, tile_out, lane); break;
+        case 10: tile_fast<R, N, 16>(base, mask, tile_out, lane); break;
+        default: tile_from_smem<R, N>(base, mask, out, rs.cb, rs.n_out, chunk << rs.cb, lane); break;
+    }
 }
 
-// Wait for stage st, (re)build the gate table, contract tile `chunk` of the
-// run in slot sl. Returns false if the bounded wait ran out.
+// Wait (bounded) until the copies into stage st have landed. Returns false
+// if the wait ran out or the run cannot be computed.
 template <typename R>
-__device__ bool compute_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk, bool first_of_run,
-                             uint32_t& phase, int lane) {
-    using C = typename CT<R>::c;
+__device__ bool wait_stage(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t& phase, int lane) {
     const RunSlot<R>& rs = ws.slot[sl];
     if (rs.bad) return false;
     if (rs.total_foot > 0) {
@@ -590,18 +660,64 @@ __device__ bool compute_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st,
         }
         phase ^= 1u << st;
     }
-    const uint32_t o0 = chunk << rs.cb;
-    if (rs.n_leaves && (first_of_run || rs.leaf_hi)) {
-        const uint32_t nent = 2u << __popc(rs.leaf_u);
-        for (uint32_t e = lane; e < nent; e += 32) {
-            const uint32_t x = e & 1u;
-            const uint32_t o = o0 | pdep_u32(e >> 1, rs.leaf_u);
-            C v = rs.lval[0][2u * pext_u32(o, rs.lmask[0]) + x];
-            for (int l = 1; l < rs.n_leaves; ++l) v = cmul(v, rs.lval[l][2u * pext_u32(o, rs.lmask[l]) + x]);
-            ws.leaf_tab[e] = v;
+    return true;
+}
+
+// The folded gate table of a tile. Gate tensors whose output bit lies inside
+// the tile (and rank-1 ones) give a table over the tile bits that is the same
+// for every tile of a group: each lane keeps its two entries in `tlow`. Gate
+// tensors whose bit lies above the tile only select one of their two rows per
+// tile, so the table of a tile is tlow times that per-tile pair.
+template <typename R>
+__device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs, uint32_t chunk, bool first,
+                                           typename CT<R>::c (&tlow)[2], int lane) {
+    using C = typename CT<R>::c;
+    const uint32_t low = (1u << rs.cb) - 1u;
+    const uint32_t nent = 2u << __popc(rs.leaf_u);
+    if (first) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t e = (uint32_t)lane + 32u * h;
+            C v;
+            v.x = (R)1;
+            v.y = (R)0;
+            if (e < nent) {
+                const uint32_t x = e & 1u;
+                const uint32_t o = pdep_u32(e >> 1, rs.leaf_u);
+                for (int l = 0; l < rs.n_leaves; ++l)
+                    if ((rs.lmask[l] & ~low) == 0u) v = cmul(v, rs.lval[l][2u * pext_u32(o, rs.lmask[l]) + x]);
+            }
+            tlow[h] = v;
         }
-        __syncwarp();
     }
+    if (!first && !rs.leaf_hi) return;  // the table of the first tile still holds
+    C cp[2];
+    cp[0].x = cp[1].x = (R)1;
+    cp[0].y = cp[1].y = (R)0;
+    if (rs.leaf_hi) {
+        const uint32_t o0 = chunk << rs.cb;
+        for (int l = 0; l < rs.n_leaves; ++l)
+            if (rs.lmask[l] & ~low) {
+                const uint32_t y = (o0 & rs.lmask[l]) ? 1u : 0u;  // the gate's single output bit
+                cp[0] = cmul(cp[0], rs.lval[l][2u * y]);
+                cp[1] = cmul(cp[1], rs.lval[l][2u * y + 1u]);
+            }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t e = (uint32_t)lane + 32u * h;
+        if (e < nent) ws.leaf_tab[e] = cmul(tlow[h], cp[e & 1u]);
+    }
+    __syncwarp();
+}
+
+// Contract tile `chunk` of the group in slot sl from stage st.
+template <typename R>
+__device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk, bool first_of_run,
+                              typename CT<R>::c (&tlow)[2], int lane) {
+    using C = typename CT<R>::c;
+    const RunSlot<R>& rs = ws.slot[sl];
+    if (rs.n_leaves) gate_table<R>(ws, rs, chunk, first_of_run, tlow, lane);
     C* out = static_cast<C*>(dp.arena) + rs.out_off;
     const int n = rs.n_staged + (rs.n_leaves ? 1 : 0);
     switch (n) {
@@ -611,22 +727,72 @@ __device__ bool compute_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st,
         default: tile_from_smem_generic<R>(ws, sl, st, out, chunk, lane); break;
     }
     __syncwarp();
-    return true;
 }
 
-// A run's tiles are all written: publish them to consumers.
-__device__ __forceinline__ void finish_run(const DevPlan& dp, uint32_t bucket, uint32_t n_chunks, int lane) {
+// A group's tiles are all written. Count them; the warp that completes the
+// bucket counts one producer of the parent done, and the warp that completes
+// the parent's last producer publishes the parent's groups.
+template <typename R>
+__device__ __forceinline__ void finish_group(const DevPlan& dp, const RunSlot<R>& rs, int lane) {
     fence_proxy_async_global();  // results become visible to later bulk copies
     __syncwarp();
-    if (lane == 0) red_release_add(&dp.chunks_done[bucket], n_chunks);
+    uint32_t push = 0;
+    const uint32_t parent = rs.parent;
+    if (lane == 0) {
+        __threadfence();
+        const uint32_t done = atomicAdd(&dp.tiles_done[rs.bucket], rs.n_chunks) + rs.n_chunks;
+        if (done == rs.n_tasks && parent != kNone) {
+            __threadfence();
+            const uint32_t pd = atomicAdd(&dp.prod_done[parent], 1u) + 1u;
+            push = pd == dp.buckets[parent].n_deps;
+            if (push) __threadfence();
+        }
+    }
+    push = __shfl_sync(kFull, push, 0);
+    if (push) publish_bucket(dp, parent, lane);
     __syncwarp();
 }
 
-template <typename R>
+// Per-warp cycle counters of the kernel's phases (the traced instantiation
+// only; the plain one compiles every call away).
+template <bool On>
+struct PhaseClock {
+    uint64_t acc[kTraceSlots];
+    long long t0;
+    __device__ void begin() {
+        if (On) {
+#pragma unroll
+            for (int i = 0; i < kTraceSlots; ++i) acc[i] = 0;
+            t0 = clock64();
+        }
+    }
+    __device__ void lap(int phase) {
+        if (On) {
+            const long long t = clock64();
+            acc[phase] += (uint64_t)(t - t0);
+            t0 = t;
+        }
+    }
+    __device__ void count(int slot, uint32_t n) {
+        if (On) acc[slot] += n;
+    }
+    __device__ void store(const DevPlan& dp, int lane) {
+        if (On && lane == 0 && dp.trace) {
+            const uint32_t w = blockIdx.x * kPW + (threadIdx.x >> 5);
+#pragma unroll
+            for (int i = 0; i < kTraceSlots; ++i) dp.trace[(size_t)w * kTraceSlots + i] = acc[i];
+        }
+    }
+};
+
+template <typename R, bool Trace>
 __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp) {
+    using C = typename CT<R>::c;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<R>& ws = reinterpret_cast<WarpSmem<R>*>(smem_raw)[warp];
+    PhaseClock<Trace> clk;
+    clk.begin();
     if (lane == 0) {
         mbar_init(&ws.bar[0], 1);
         mbar_init(&ws.bar[1], 1);
@@ -636,50 +802,82 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp
     uint32_t phase = 0;
     bool pending[2] = {false, false};
     Cursor cur;
-    if (cur.start(dp, lane)) {
-        // tile A: being computed (slot sa, stage st); tile B: the next one
+    const uint32_t qa = cur.start(dp, lane);
+    clk.lap(kTrClaim);
+    if (qa < dp.n_groups) {
+        // tile A is contracted from stage st (group in slot sa) while the
+        // copies for tile B, the next one, are in flight
         int sa = 0, st = 0;
-        uint32_t dep_b, dep_need;
-        prep_run<R>(dp, ws, sa, cur.r, lane, &dep_b, &dep_need);
-        uint32_t a_chunk = ws.slot[sa].chunk_begin, a_left = ws.slot[sa].n_chunks;
-        bool a_first = true;
-        bool ok = wait_deps_run(dp, dep_b, dep_need, ws.slot[sa].bucket, lane);
+        uint32_t cbase = 0;
+        C tlow[2];
+        DRun ra;
+        bool ok = wait_group(dp, qa, &ra, lane);
+        clk.lap(kTrDeps);
         if (ok) {
-            if (lane == 0) fence_proxy_async_global();
+            prep_run<R>(dp, ws, sa, ra, lane, &cbase);
+            clk.lap(kTrPrep);
+            clk.count(kTrRuns, 1);
+            if (lane == 0) fence_proxy_async_global();  // producers' results before this warp's copies
             __syncwarp();
-            pending[st] = issue_tile<R>(dp, ws, sa, st, a_chunk, lane);
+            pending[st] = issue_tile<R>(dp, ws, sa, st, ra.chunk_begin, true, lane, cbase);
+            clk.lap(kTrIssue);
         }
+        uint32_t a_chunk = ra.chunk_begin, a_left = ra.n_chunks;
+        bool a_first = true;
         while (ok) {
-            // the next tile: same run, or the first tile of the next run
             int sb = sa;
-            uint32_t b_chunk = a_chunk + 1, b_left = a_left - 1;
+            uint32_t b_chunk = a_chunk + 1, b_left = a_left - 1, qb = 0;
             bool b_valid = true, b_first = false, b_issued = false;
-            uint32_t bdep = kNone, bneed = 0;
-            if (a_left == 1) {
-                b_valid = cur.next_run(dp, lane);
-                if (b_valid) {
+            DRun rb;
+            if (a_left > 1) {
+                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase);
+                b_issued = true;
+                clk.lap(kTrIssue);
+            } else {
+                qb = cur.next(dp, lane);
+                b_valid = qb < dp.n_groups;
+                clk.lap(kTrClaim);
+                if (b_valid && group_at(dp, qb, &rb, lane)) {
                     sb = sa ^ 1;
-                    prep_run<R>(dp, ws, sb, cur.r, lane, &bdep, &bneed);
-                    b_chunk = ws.slot[sb].chunk_begin;
-                    b_left = ws.slot[sb].n_chunks;
+                    prep_run<R>(dp, ws, sb, rb, lane, &cbase);
+                    clk.lap(kTrPrep);
+                    clk.count(kTrRuns, 1);
+                    if (lane == 0) fence_proxy_async_global();
+                    __syncwarp();
+                    pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase);
+                    b_issued = true;
+                    b_chunk = rb.chunk_begin;
+                    b_left = rb.n_chunks;
                     b_first = true;
+                    clk.lap(kTrIssue);
                 }
             }
-            if (b_valid && deps_met(dp, bdep, bneed)) {
-                if (b_first && lane == 0) fence_proxy_async_global();
-                __syncwarp();
-                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, lane);
-                b_issued = true;
-            }
-            if (!compute_tile<R>(dp, ws, sa, st, a_chunk, a_first, phase, lane)) break;
+            if (!wait_stage<R>(dp, ws, sa, st, phase, lane)) break;
+            clk.lap(kTrWait);
+            contract_tile<R>(dp, ws, sa, st, a_chunk, a_first, tlow, lane);
+            clk.lap(kTrCompute);
+            clk.count(kTrTiles, 1);
             pending[st] = false;
-            if (a_left == 1) finish_run(dp, ws.slot[sa].bucket, ws.slot[sa].n_chunks, lane);
+            if (a_left == 1) {
+                finish_group<R>(dp, ws.slot[sa], lane);
+                clk.lap(kTrFinish);
+            }
             if (!b_valid) break;
             if (!b_issued) {
-                if (!wait_deps_run(dp, bdep, bneed, ws.slot[sb].bucket, lane)) break;
+                // the next group was not yet published when looked at: wait for it now
+                if (!wait_group(dp, qb, &rb, lane)) break;
+                clk.lap(kTrDeps);
+                sb = sa ^ 1;
+                prep_run<R>(dp, ws, sb, rb, lane, &cbase);
+                clk.lap(kTrPrep);
+                clk.count(kTrRuns, 1);
                 if (lane == 0) fence_proxy_async_global();
                 __syncwarp();
-                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, lane);
+                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase);
+                b_chunk = rb.chunk_begin;
+                b_left = rb.n_chunks;
+                b_first = true;
+                clk.lap(kTrIssue);
             }
             sa = sb;
             a_chunk = b_chunk;
@@ -696,6 +894,8 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp
         for (uint64_t polls = 0; polls < dp.spin_limit && !mbar_try_wait(&ws.bar[s2], par); ++polls) {
         }
     }
+    clk.lap(kTrClaim);
+    clk.store(dp, lane);
 }
 
 template <typename R>
@@ -805,10 +1005,18 @@ size_t persistent_smem_bytes(int dtype) {
 
 cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream_t s) {
     const size_t smem = persistent_smem_bytes(dtype);
-    if (dtype == QT_C128)
-        k_persistent<double><<<grid, kPersistentThreads, smem, s>>>(dp);
-    else
-        k_persistent<float><<<grid, kPersistentThreads, smem, s>>>(dp);
+    const bool tr = dp.trace != nullptr;
+    if (dtype == QT_C128) {
+        if (tr)
+            k_persistent<double, true><<<grid, kPersistentThreads, smem, s>>>(dp);
+        else
+            k_persistent<double, false><<<grid, kPersistentThreads, smem, s>>>(dp);
+    } else {
+        if (tr)
+            k_persistent<float, true><<<grid, kPersistentThreads, smem, s>>>(dp);
+        else
+            k_persistent<float, false><<<grid, kPersistentThreads, smem, s>>>(dp);
+    }
     return cudaGetLastError();
 }
 
@@ -834,13 +1042,17 @@ int persistent_blocks_per_sm(int dtype) {
     int n = 0;
     cudaError_t e;
     if (dtype == QT_C128) {
-        e = cudaFuncSetAttribute(k_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_persistent<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<double>, kPersistentThreads, smem);
+            e = cudaFuncSetAttribute(k_persistent<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<double, false>, kPersistentThreads, smem);
     } else {
-        e = cudaFuncSetAttribute(k_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_persistent<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<float>, kPersistentThreads, smem);
+            e = cudaFuncSetAttribute(k_persistent<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<float, false>, kPersistentThreads, smem);
     }
     return e == cudaSuccess && n > 0 ? n : 0;
 }

@@ -12,14 +12,32 @@ namespace qt {
 struct DevPlan {
     const DBucket* buckets;
     const DOperand* ops;
-    const uint32_t* item_begin;  // n_items + 1, into runs
-    const DRun* runs;
-    uint32_t n_items;
+    const DRun* runs;       // the queue's first n_static positions: groups of buckets without producers
+    uint32_t n_static;
+    uint32_t n_groups;      // queue length
     uint32_t n_buckets;
-    uint32_t* chunks_done;  // n_buckets: tiles written so far
+    DSlot* slots;           // queue positions n_static.. n_groups-1, published at run time
+    uint32_t* tiles_done;   // n_buckets: tiles written so far
+    uint32_t* prod_done;    // n_buckets: producers finished so far
     DControl* ctl;
     void* arena;            // complex64 or complex128 elements
     uint64_t spin_limit;
+    uint64_t* trace;        // per-warp phase counters (kTraceSlots each), or null: untraced kernel
+};
+
+// Phase counters of the traced persistent kernel, per warp (cycles unless noted).
+constexpr int kTraceSlots = 10;
+enum : int {
+    kTrClaim = 0,   // claiming work items, and the kernel's tail
+    kTrPrep = 1,    // reading run descriptors and gate tensors
+    kTrDeps = 2,    // checking and waiting for producers
+    kTrIssue = 3,   // starting bulk copies
+    kTrWait = 4,    // waiting for bulk copies to land
+    kTrCompute = 5, // contracting tiles and storing results
+    kTrFinish = 6,  // publishing finished runs
+    kTrTiles = 7,   // count of tiles
+    kTrRuns = 8,    // count of runs
+    kTrSpare = 9
 };
 
 // Everything the epilogue reads and writes.

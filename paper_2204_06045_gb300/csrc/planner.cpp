@@ -343,11 +343,13 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             auto key = std::minmax(e.first, e.second);
             if (!seen.insert(key).second) return QT_EINVAL;
         }
+        for (int e : g.sel)
+            if (e < 0 || e >= (int)g.edges.size()) return QT_EINVAL;
     }
     // networks, one per edge of every graph
     hp->graph_first_net.assign(1, 0);
     for (size_t g = 0; g < graphs.size(); ++g)
-        hp->graph_first_net.push_back(hp->graph_first_net.back() + (int)graphs[g].edges.size());
+        hp->graph_first_net.push_back(hp->graph_first_net.back() + (int)graphs[g].n_nets());
     const int n_nets = hp->graph_first_net.back();
     hp->nets.assign(n_nets, Network());
     hp->nplans.assign(n_nets, NetPlan());
@@ -361,7 +363,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
                           hp->graph_first_net.begin()) - 1;
             Network& net = hp->nets[i];
             net.graph = g;
-            net.edge = i - hp->graph_first_net[g];
+            net.edge = graphs[g].edge_of((size_t)(i - hp->graph_first_net[g]));
             build_network(graphs[g], cfg.p, net.edge, &net);
             std::vector<int> best_order, ord;
             double best_cost = 0, c = 0;
@@ -419,10 +421,29 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             d.n_out = (uint8_t)(B.width - 1);
             int cb = 0;
             bool fold = false;
-            pick_tile(B, net, cfg.chunk_log2 > 0 ? cfg.chunk_log2 : 30,
+            pick_tile(B, net, cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
                       cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, &cb, &fold);
             d.chunk_bits = (uint8_t)cb;
             d.flags = fold ? kBucketFoldLeaves : 0;
+            {
+                const uint32_t low = (1u << cb) - 1u;
+                uint32_t foot = 0, ns = 0, nl = 0, lu = 0, lh = 0;
+                for (const HOperand& op : B.ops) {
+                    if (fold && op.src < 0) {
+                        nl++;
+                        lu |= op.mask & low;
+                        lh |= op.mask & ~low;
+                    } else {
+                        foot += 2u << __builtin_popcount(op.mask & low);
+                        ns++;
+                    }
+                }
+                d.total_foot = foot;
+                d.n_staged = (uint8_t)ns;
+                d.n_leaves = (uint8_t)nl;
+                d.leaf_u = lu;
+                d.leaf_hi = lh;
+            }
             d.parent = B.parent >= 0 ? base + (uint32_t)B.parent : kNone;
             d.n_deps = (uint32_t)B.n_deps;
             d.n_tasks = 1u << (d.n_out - cb);
@@ -430,9 +451,19 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             d.out_off = off;
             off += align_up(1ull << d.n_out, align);
             double opbytes = 0;
+            uint32_t next_soff = 0, next_staged = 0, next_leaf = 0;
             for (const HOperand& op : B.ops) {
                 DOperand o{};
                 o.mask = op.mask;
+                o.src = kNone;
+                o.folded = (d.flags & kBucketFoldLeaves) && op.src < 0;
+                if (o.folded) {
+                    o.slot = (uint8_t)next_leaf++;
+                } else {
+                    o.slot = (uint8_t)next_staged++;
+                    o.soff = (uint16_t)next_soff;
+                    next_soff += 2u << __builtin_popcount(op.mask & ((1u << d.chunk_bits) - 1u));
+                }
                 if (op.src >= 0) {
                     o.off = 0;  // set below, once every result has its offset
                     o.flags = 0;
@@ -465,8 +496,10 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     // intermediate operands point at their producer's result and name it
     for (size_t o = 0; o < hp->operands.size(); ++o)
         if (hp->op_src[o] >= 0) {
-            hp->operands[o].off = hp->buckets[hp->op_src[o]].out_off;
-            hp->operands[o].flags = (uint32_t)hp->op_src[o] << 1;
+            const DBucket& src = hp->buckets[hp->op_src[o]];
+            hp->operands[o].off = src.out_off;
+            hp->operands[o].src = (uint32_t)hp->op_src[o];
+            hp->operands[o].src_tiles = src.n_tasks;
         }
     hp->arena_elems = off;
     hp->cot_off = 0;
@@ -489,37 +522,24 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     hp->level_first_bucket.assign(hp->n_levels + 1, 0);
     for (uint32_t b : hp->by_level) hp->level_first_bucket[hp->bucket_level[b] + 1]++;
     for (int l = 0; l < hp->n_levels; ++l) hp->level_first_bucket[l + 1] += hp->level_first_bucket[l];
+    // Work groups: a bucket's tiles are handed out in groups of group_tiles
+    // consecutive tiles, so a warp reads the bucket's descriptors once per group. Groups of buckets without producers open the
+    // queue, in level order with the largest buckets first; every other bucket
+    // appends its groups when its last producer finishes.
     hp->runs.clear();
-    hp->item_begin.assign(1, 0);
     hp->n_tiles = 0;
-    // A work item is what one claim hands a warp: one run of up to kRunTiles
-    // tiles of a wide bucket, or up to 32 single-tile buckets of one level
-    // (none of which depends on another).
-    const uint32_t item_max_runs = 32;
-    uint32_t cur_runs = 0;
-    int cur_level = -1;
-    auto close_item = [&]() {
-        if (cur_runs > 0) hp->item_begin.push_back((uint32_t)hp->runs.size());
-        cur_runs = 0;
-    };
+    hp->n_groups = 0;
     for (uint32_t b : hp->by_level) {
-        const DBucket& d = hp->buckets[b];
+        DBucket& d = hp->buckets[b];
+        const uint32_t rt = cfg.run_tiles > 0 ? (uint32_t)cfg.run_tiles : (uint32_t)kRunTiles;
+        d.group_tiles = std::min(rt, d.n_tasks);
+        d.n_groups = (d.n_tasks + d.group_tiles - 1) / d.group_tiles;
         hp->n_tiles += d.n_tasks;
-        if (d.n_tasks > 1) {
-            close_item();
-            for (uint32_t c = 0; c < d.n_tasks; c += kRunTiles) {
-                hp->runs.push_back(DRun{b, c, std::min<uint32_t>(kRunTiles, d.n_tasks - c), 0});
-                cur_runs = 1;
-                close_item();
-            }
-            continue;
-        }
-        if (cur_runs > 0 && (hp->bucket_level[b] != cur_level || cur_runs >= item_max_runs)) close_item();
-        hp->runs.push_back(DRun{b, 0, 1, 0});
-        cur_runs++;
-        cur_level = hp->bucket_level[b];
+        hp->n_groups += d.n_groups;
+        if (d.n_deps == 0)
+            for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
+                hp->runs.push_back(DRun{b, c, std::min<uint32_t>(d.group_tiles, d.n_tasks - c), d.op_begin});
     }
-    close_item();
     hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return QT_OK;
 }

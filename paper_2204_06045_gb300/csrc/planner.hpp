@@ -51,6 +51,9 @@ struct NetPlan {
 struct GraphIn {
     int n = 0;
     std::vector<std::pair<int, int>> edges;
+    std::vector<int> sel;  // edges whose networks are planned; empty: every edge
+    size_t n_nets() const { return sel.empty() ? edges.size() : sel.size(); }
+    int edge_of(size_t i) const { return sel.empty() ? (int)i : sel[i]; }
 };
 
 struct PlanConfig {
@@ -60,6 +63,7 @@ struct PlanConfig {
     uint64_t seed = 0;
     int max_width = 31;
     int chunk_log2 = 0;
+    int run_tiles = 0;
     bool with_grad = false;
 };
 
@@ -80,9 +84,9 @@ struct HostPlan {
     std::vector<int32_t> op_rank;
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
-    std::vector<DRun> runs;             // runs of tiles in claim order
-    std::vector<uint32_t> item_begin;   // n_items + 1, into the run array
+    std::vector<DRun> runs;             // the queue's first entries: groups of buckets with no producer
     uint64_t n_tiles = 0;
+    uint64_t n_groups = 0;              // queue length: groups over all buckets
     std::vector<uint32_t> root_bucket;  // every root bucket (scalar result)
     std::vector<uint32_t> net_first_root;  // n_nets + 1 into root_bucket
     std::vector<uint32_t> level_first_bucket;  // buckets sorted by level (for the adjoint)

@@ -25,48 +25,75 @@ constexpr int kStageElemsC128 = 512;
 constexpr int kLeafBits = 5;
 constexpr int kMaxFoldLeaves = 8;
 constexpr uint8_t kBucketFoldLeaves = 1;
-constexpr int kRunTiles = 16;  // tiles of one bucket handed out per claim
+constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim (default)
+constexpr int kDefaultTileBits = 8;  // at most 256 outputs per tile (default); measured best on GB300
 
-// One bucket on the device. 32 bytes.
+// One bucket on the device. 64 bytes.
 struct DBucket {
     uint64_t out_off;   // element offset of the result in the arena
     uint32_t op_begin;  // first operand in the operand array
     uint8_t n_ops;      // operand count
     uint8_t flags;      // kBucketFoldLeaves: gate tensors go through the per-tile product table
     uint8_t n_out;      // output bits (width - 1)
-    uint8_t chunk_bits; // log2 of the outputs per task
+    uint8_t chunk_bits; // log2 of the outputs per tile
     uint32_t parent;    // consuming bucket, kNone for a root (scalar result)
     uint32_t n_deps;    // operands produced by earlier buckets
-    uint32_t n_tasks;   // tasks (output chunks) = 2^(n_out - chunk_bits)
+    uint32_t n_tasks;   // tiles = 2^(n_out - chunk_bits)
     uint32_t net;       // network index
+    // staging of one tile (persistent kernel), fixed by the planner
+    uint32_t total_foot;// staged elements per tile
+    uint8_t n_staged;   // operands copied into the stage buffer
+    uint8_t n_leaves;   // gate tensors folded into the product table
+    uint16_t pad0;
+    uint32_t leaf_u;    // folded gate masks within the tile
+    uint32_t leaf_hi;   // folded gate masks above the tile (nonzero: the table changes per tile)
+    uint32_t group_tiles; // tiles per work group (the unit a warp claims)
+    uint32_t n_groups;    // ceil(n_tasks / group_tiles)
+    uint32_t pad1[2];
 };
-static_assert(sizeof(DBucket) == 32, "DBucket layout");
+static_assert(sizeof(DBucket) == 64, "DBucket layout");
 
-// One operand on the device. 16 bytes.
+// One operand on the device. 32 bytes.
 struct DOperand {
-    uint64_t off;  // element offset of the operand's tensor in the arena
-    uint32_t mask; // output bits the operand carries
-    uint32_t flags;// bit 0 (kOpLeaf): a gate tensor; otherwise bits 1..31 hold the producing bucket
+    uint64_t off;      // element offset of the operand's tensor in the arena
+    uint32_t mask;     // output bits the operand carries
+    uint32_t flags;    // kOpLeaf: a gate tensor (written before the contraction starts)
+    uint32_t src;      // producing bucket, kNone for a gate tensor
+    uint32_t src_tiles;// the producer's tile count
+    uint16_t soff;     // staged: element offset of its tile footprint in the stage buffer
+    uint8_t slot;      // position among the staged operands, or among the folded gate tensors
+    uint8_t folded;    // 1: folded into the per-tile gate table
+    uint32_t pad;
 };
-static_assert(sizeof(DOperand) == 16, "DOperand layout");
+static_assert(sizeof(DOperand) == 32, "DOperand layout");
 constexpr uint32_t kOpLeaf = 1u;
 
-// A run of consecutive tiles of one bucket, the unit a persistent warp
-// prepares once (descriptors, gate values, dependency check). 16 bytes.
+// A group of consecutive tiles of one bucket: what one claim hands a warp,
+// which reads the bucket's descriptors once for all of them. 16 bytes.
 struct DRun {
     uint32_t bucket;
     uint32_t chunk_begin;
     uint32_t n_chunks;
-    uint32_t pad;
+    uint32_t op_begin;  // the bucket's first operand (saves a dependent load)
 };
 static_assert(sizeof(DRun) == 16, "DRun layout");
 
+// A published slot of the ready queue: a group whose bucket's producers have
+// all finished. 16 bytes.
+struct DSlot {
+    uint32_t bucket;
+    uint32_t chunk_begin;
+    uint32_t op_begin;
+    uint32_t n_chunks;  // written last (release); nonzero marks the slot as published
+};
+static_assert(sizeof(DSlot) == 16, "DSlot layout");
+
 // Counters the persistent kernel uses; zeroed before every run.
 struct DControl {
-    uint32_t next_item;  // next work item to claim
+    uint32_t next_item;  // next queue position to claim
     int32_t error;       // first kernel-side error (QT_E* code), 0 if none
     uint32_t err_bucket; // bucket at which the error was raised
-    uint32_t pad;
+    uint32_t next_free;  // next free slot of the dynamic part of the queue
 };
 
 }  // namespace qt

@@ -20,9 +20,9 @@ QT_SCHED_PERSISTENT, QT_SCHED_PER_BUCKET = 0, 1
 LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 
 # every symbol include/qt.h declares
-EXPORTS = ("qt_plan", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
+EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-           "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail")
+           "qt_trace_counters", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail")
 
 
 class QTError(RuntimeError):
@@ -38,7 +38,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("sched", ctypes.c_int), ("order_restarts", ctypes.c_int32),
                 ("order_seed", ctypes.c_uint64), ("max_width", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
                 ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
-                ("host_only", ctypes.c_int32)]
+                ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -69,6 +69,7 @@ def lib():
         i32p = ctypes.POINTER(ctypes.c_int32)
         L.qt_plan.argtypes = [i32, i32, i32p, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
         L.qt_plan_batch.argtypes = [i32, i32p, i32p, i32p, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+        L.qt_plan_subset.argtypes = [i32, i32, i32p, i32, i32, i32p, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
         L.qt_plan_stats_get.argtypes = [vp, ctypes.POINTER(PlanStats)]
         L.qt_plan_export.argtypes = [vp, vp, vp]
         L.qt_plan_network_wires.argtypes = [vp, i32, i32p]
@@ -79,15 +80,16 @@ def lib():
         L.qt_sync.argtypes = [vp, vp]
         L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
         L.qt_debug_stall_bucket.argtypes = [vp, i64]
+        L.qt_trace_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64)]
         L.qt_plan_free.argtypes = [vp]
         L.qt_plan_free.restype = None
         L.qt_error_string.argtypes = [ctypes.c_int]
         L.qt_error_string.restype = ctypes.c_char_p
         L.qt_version.restype = ctypes.c_char_p
         L.qt_last_error_detail.restype = ctypes.c_char_p
-        for name in ("qt_plan", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
+        for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-                     "qt_debug_stall_bucket"):
+                     "qt_debug_stall_bucket", "qt_trace_counters"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -146,7 +148,7 @@ class Plan:
     # -- construction -------------------------------------------------------------
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
-              with_grad=False, spin_limit=0, chunk_log2=0, host_only=False):
+              with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False):
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
         o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
@@ -158,6 +160,8 @@ class Plan:
         o.spin_limit = int(spin_limit)
         o.chunk_log2 = int(chunk_log2)
         o.host_only = int(bool(host_only))
+        o.run_tiles = int(run_tiles)
+        o.trace = int(bool(trace))
         return o
 
     @classmethod
@@ -168,6 +172,18 @@ class Plan:
         _check(lib().qt_plan(int(n), int(e.shape[0]), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(p),
                              ctypes.byref(o), ctypes.byref(h)), "qt_plan")
         return cls(h.value, [e.shape[0]], p, opts.get("dtype", "c64"), [n])
+
+    @classmethod
+    def create_subset(cls, n: int, edges, p: int, sel, **opts) -> "Plan":
+        """Plan only the lightcone networks of the edges listed in ``sel``."""
+        e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        sv = np.ascontiguousarray(sel, dtype=np.int32).ravel()
+        o = cls._opts(**opts)
+        h = ctypes.c_void_p()
+        ip = ctypes.POINTER(ctypes.c_int32)
+        _check(lib().qt_plan_subset(int(n), int(e.shape[0]), e.ctypes.data_as(ip), int(p), int(sv.size),
+                                    sv.ctypes.data_as(ip), ctypes.byref(o), ctypes.byref(h)), "qt_plan_subset")
+        return cls(h.value, [sv.size], p, opts.get("dtype", "c64"), [n])
 
     @classmethod
     def create_batch(cls, graphs, p: int, **opts) -> "Plan":
@@ -278,12 +294,27 @@ class Plan:
         _check(lib().qt_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n), int(reset)), "qt_kernel_time")
         return ms.value, n.value
 
+    TRACE_PHASES = ("claim", "prep", "deps", "issue", "wait", "compute", "finish")
+
+    def trace_counters(self) -> dict:
+        """Per-phase cycles summed over warps, tile and run counts, warps launched."""
+        buf = (ctypes.c_uint64 * 10)()
+        nw = ctypes.c_int64(0)
+        _check(lib().qt_trace_counters(self._h, buf, ctypes.byref(nw)), "qt_trace_counters")
+        d = {k: int(buf[i]) for i, k in enumerate(self.TRACE_PHASES)}
+        d.update(tiles=int(buf[7]), runs=int(buf[8]), warps=int(nw.value))
+        return d
+
     def debug_stall_bucket(self, bucket: int):
         _check(lib().qt_debug_stall_bucket(self._h, int(bucket)), "qt_debug_stall_bucket")
 
 
 def plan(n: int, edges, p: int, **opts) -> Plan:
     return Plan.create(n, edges, p, **opts)
+
+
+def plan_subset(n: int, edges, p: int, sel, **opts) -> Plan:
+    return Plan.create_subset(n, edges, p, sel, **opts)
 
 
 def plan_batch(graphs, p: int, **opts) -> Plan:
