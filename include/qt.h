@@ -73,13 +73,17 @@ typedef struct {
     int32_t with_grad;     /* nonzero: also allocate what qt_energy_grad needs */
     uint64_t spin_limit;   /* polls of a dependency counter before a kernel gives up with
                               QT_ETIMEOUT (default 2^23, each poll sleeps ~0.1-1 us) */
-    int32_t chunk_log2;    /* most outputs per tile, log2 (default 0: 8, i.e. 256 outputs); smaller
+    int32_t chunk_log2;    /* most outputs per tile, log2 (default 0: 9, i.e. 512 outputs); smaller
                               when a bucket's operand footprints do not fit the 8 KB stage */
     int32_t host_only;     /* nonzero: plan on the host only (statistics, export); no device
                               memory is touched and every evaluation call returns QT_ESTATE */
     int32_t run_tiles;     /* most tiles of one bucket handed out per claim (default 0: 16) */
     int32_t trace;         /* nonzero: run the instrumented persistent kernel, which counts
                               per-warp cycles by phase (read with qt_trace_counters) */
+    int32_t order;         /* claim order of the persistent kernel: 0 (default) the order of a
+                              critical-path list-scheduling simulation made at plan time, each
+                              group starting once its producers are done; 1 a device-side ready
+                              queue, first come first served */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -102,6 +106,7 @@ typedef struct {
     int32_t dtype;
     int64_t width_hist[64]; /* buckets per width */
     double plan_seconds;    /* host time spent building the plan */
+    double sim_seconds;     /* makespan predicted by the plan-time schedule simulation (0: none) */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */
@@ -214,14 +219,31 @@ int qt_sync(qt_plan_t plan, void *cuda_stream);
  * *launches receives the count. reset != 0 clears the counters. */
 int qt_kernel_time(qt_plan_t plan, double *avg_ms, int64_t *launches, int32_t reset);
 
+/*
+ * Time the persistent kernel on the tiles of one bucket alone (no other bucket
+ * runs, no consumer is notified): `reps` launches after one warm-up launch, on
+ * the plan's own stream, with CUDA events around each launch. *avg_ms receives
+ * the mean, *bytes (may be NULL) the bucket's algorithmic bytes (every operand
+ * read once, the result written once). The operands hold whatever the last
+ * evaluation left (run qt_energy first for meaningful data; the timing does
+ * not depend on the values). Persistent plans only; host call, synchronous.
+ */
+int qt_bucket_time(qt_plan_t plan, int64_t bucket, int32_t reps, double *avg_ms, double *bytes);
+
 /* Phase counters of the last persistent run of a plan built with opts.trace,
  * summed over warps: totals[0..6] = cycles spent claiming work (and the
  * kernel's tail), reading run descriptors, checking and waiting for producers,
  * starting bulk copies, waiting for copies to land, contracting tiles, and
- * publishing finished runs; totals[7] = tiles, totals[8] = runs, totals[9]
- * unused. *n_warps receives the number of warps launched. Host call; waits
+ * publishing finished runs; totals[7] = tiles, totals[8] = runs, totals[9] =
+ * cycles spent building the folded gate tables. *n_warps receives the number of warps launched. Host call; waits
  * for the plan's work to finish. QT_ESTATE if the plan was built without trace. */
 int qt_trace_counters(qt_plan_t plan, uint64_t *totals, int64_t *n_warps);
+
+/* Per-bucket timeline of the last persistent run of a traced plan:
+ * start_end_ns[2b] = %globaltimer (ns) when the first group of bucket b was
+ * taken up, start_end_ns[2b+1] = when its last group finished. Host, 2 *
+ * n_buckets entries; waits for the plan's work. QT_ESTATE without opts.trace. */
+int qt_trace_bucket_times(qt_plan_t plan, uint64_t *start_end_ns);
 
 /* Fault injection for tests: on the device, raise the number of output tiles
  * bucket `bucket` must complete by one, so the bucket consuming its result can

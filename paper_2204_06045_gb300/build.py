@@ -43,39 +43,43 @@ def up_to_date() -> bool:
     return all(d.stat().st_mtime <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> Path:
-    """Compile and link ``libqtgb.so``; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, defines=(), out: Path = None) -> Path:
+    """Compile and link ``libqtgb.so`` (or a variant with extra -D ``defines``
+    at ``out``); returns its path."""
+    lib = Path(out) if out else LIB
+    if not force and not defines and out is None and up_to_date():
         return LIB
-    BUILD.mkdir(exist_ok=True)
+    build_dir = BUILD if out is None else lib.parent / (lib.stem + "_obj")
+    build_dir.mkdir(parents=True, exist_ok=True)
+    dflags = [f"-D{d}" for d in defines]
     nvcc = _nvcc()
     procs = []
     objs = []
     for src in _sources():
-        obj = BUILD / (src.name + ".o")
+        obj = build_dir / (src.name + ".o")
         objs.append(obj)
         if src.suffix == ".cu":
-            cmd = [nvcc, *NVCC_FLAGS, *extra_nvcc, "-I", str(INCLUDE), "-c", str(src), "-o", str(obj)]
+            cmd = [nvcc, *NVCC_FLAGS, *dflags, "-I", str(INCLUDE), "-c", str(src), "-o", str(obj)]
         else:
-            cmd = ["g++", *CXX_FLAGS, "-I", str(INCLUDE), "-c", str(src), "-o", str(obj)]
+            cmd = ["g++", *CXX_FLAGS, *dflags, "-I", str(INCLUDE), "-c", str(src), "-o", str(obj)]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for cmd, pr in procs:
-        out, _ = pr.communicate()
+        log, _ = pr.communicate()
         if pr.returncode != 0:
-            failed.append((cmd, out.decode(errors="replace")))
-        elif verbose and out:
-            print(out.decode(errors="replace"), file=sys.stderr)
+            failed.append((cmd, log.decode(errors="replace")))
+        elif verbose and log:
+            print(log.decode(errors="replace"), file=sys.stderr)
     if failed:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError(f"libqtgb build failed:\n{msg}")
-    tmp = LIB.with_suffix(f".{os.getpid()}.tmp.so")
+    tmp = lib.with_suffix(f".{os.getpid()}.tmp.so")
     link = [nvcc, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lpthread"]
     subprocess.run(link, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -55,6 +56,7 @@ struct qt_plan_s {
     bool host_only = false;
     bool trace = false;
     uint64_t* d_trace = nullptr;
+    unsigned long long* d_btimes = nullptr;
 
     ~qt_plan_s() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -72,6 +74,7 @@ struct qt_plan_s {
         if (d_out) cudaFree(d_out);
         if (h_err) cudaFreeHost(h_err);
         if (d_trace) cudaFree(d_trace);
+        if (d_btimes) cudaFree(d_btimes);
     }
 };
 
@@ -201,8 +204,11 @@ int upload(qt_plan_t P) {
         QT_CUDA(cudaMalloc((void**)&P->d_trace, tb));
         QT_CUDA(cudaMemset(P->d_trace, 0, tb));
         P->dp.trace = P->d_trace;
+        QT_CUDA(cudaMalloc((void**)&P->d_btimes, hp.buckets.size() * 2 * sizeof(unsigned long long)));
+        P->dp.bucket_times = P->d_btimes;
     } else {
         P->dp.trace = nullptr;
+        P->dp.bucket_times = nullptr;
     }
     QT_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
     QT_CUDA(cudaEventCreate(&P->cap_ev[0]));
@@ -220,6 +226,10 @@ int enqueue_eval(qt_plan_t P, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     QT_CUDA(qt::launch_leaf_fill(P->dtype, P->d_angles, (int)hp.graphs.size(), hp.cfg.p, P->d_arena, s));
     if (P->sched == QT_SCHED_PERSISTENT) {
         QT_CUDA(cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, s));
+        if (P->d_btimes) {  // starts to all ones (min), ends to zero (max)
+            QT_CUDA(cudaMemsetAsync(P->d_btimes, 0xff, hp.buckets.size() * 2 * sizeof(unsigned long long), s));
+            QT_CUDA(qt::launch_clear_ends(P->d_btimes, hp.buckets.size(), s));
+        }
         QT_CUDA(cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal));
         QT_CUDA(qt::launch_persistent(P->dtype, P->grid, P->dp, s));
         QT_CUDA(cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal));
@@ -356,6 +366,8 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     cfg.max_width = o.max_width > 0 ? o.max_width : 31;
     cfg.chunk_log2 = o.chunk_log2;
     cfg.run_tiles = o.run_tiles;
+    cfg.order = o.order;
+    if (o.order < 0 || o.order > 1) return QT_EINVAL;
     if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
     if (cfg.chunk_log2 < 0 || cfg.chunk_log2 > 24) return QT_EINVAL;
@@ -442,6 +454,7 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->dtype = P->dtype;
     std::memcpy(out->width_hist, hp.width_hist, sizeof(out->width_hist));
     out->plan_seconds = hp.plan_seconds;
+    out->sim_seconds = hp.sim_seconds;
     return QT_OK;
 }
 
@@ -534,6 +547,47 @@ int qt_kernel_time(qt_plan_t P, double* avg_ms, int64_t* launches, int32_t reset
     return QT_OK;
 }
 
+int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, double* bytes) {
+    if (!P || !avg_ms || reps < 1 || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
+    if (P->host_only || P->sched != QT_SCHED_PERSISTENT) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    const qt::DBucket& d = P->hp.buckets[bucket];
+    std::vector<qt::DRun> groups;
+    for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
+        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, {0, 0, 0}});
+    qt::DRun* d_groups = nullptr;
+    QT_CUDA(cudaMalloc((void**)&d_groups, groups.size() * sizeof(qt::DRun)));
+    cudaError_t e = cudaMemcpy(d_groups, groups.data(), groups.size() * sizeof(qt::DRun), cudaMemcpyHostToDevice);
+    qt::DevPlan dp = P->dp;
+    dp.runs = d_groups;
+    dp.n_static = dp.n_groups = (uint32_t)groups.size();
+    dp.isolated = 1;
+    cudaEvent_t e0 = P->cap_ev[0], e1 = P->cap_ev[1];
+    float total = 0;
+    for (int r = 0; r < reps + 1 && e == cudaSuccess; ++r) {
+        e = cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, P->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+        if (e == cudaSuccess) e = qt::launch_persistent(P->dtype, P->grid, dp, P->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) total += ms;  // the first launch warms up
+    }
+    int32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, &P->dp.ctl->error, sizeof(err), cudaMemcpyDeviceToHost);
+    cudaFree(d_groups);
+    if (e != cudaSuccess) return cuda_fail(e, "qt_bucket_time", __LINE__);
+    if (err != 0) return err;
+    *avg_ms = total / reps;
+    if (bytes) {
+        double b = (double)(1ull << d.n_out);
+        for (uint32_t o = d.op_begin; o < d.op_begin + d.n_ops; ++o) b += std::ldexp(1.0, P->hp.op_rank[o]);
+        *bytes = b * (double)P->esize;
+    }
+    return QT_OK;
+}
+
 int qt_trace_counters(qt_plan_t P, uint64_t* totals, int64_t* n_warps) {
     if (!P || !totals) return QT_EINVAL;
     if (P->host_only || !P->trace) return QT_ESTATE;
@@ -546,6 +600,15 @@ int qt_trace_counters(qt_plan_t P, uint64_t* totals, int64_t* n_warps) {
     for (size_t w = 0; w < nw; ++w)
         for (int i = 0; i < qt::kTraceSlots; ++i) totals[i] += buf[w * qt::kTraceSlots + i];
     if (n_warps) *n_warps = (int64_t)nw;
+    return QT_OK;
+}
+
+int qt_trace_bucket_times(qt_plan_t P, uint64_t* start_end_ns) {
+    if (!P || !start_end_ns) return QT_EINVAL;
+    if (P->host_only || !P->trace) return QT_ESTATE;
+    QT_CUDA(cudaSetDevice(P->device));
+    QT_CUDA(cudaDeviceSynchronize());
+    QT_CUDA(cudaMemcpy(start_end_ns, P->d_btimes, P->hp.buckets.size() * 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     return QT_OK;
 }
 

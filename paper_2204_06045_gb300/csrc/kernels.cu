@@ -72,6 +72,9 @@ __device__ __forceinline__ Pair<float2> ld_pair_smem(const float2* p) {
 }
 __device__ __forceinline__ Pair<double2> ld_pair_smem(const double2* p) { return {p[0], p[1]}; }
 
+__device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldcg_c(const double2* p) { return __ldcg(p); }
+
 __device__ __forceinline__ void st_two(float2* out, uint64_t o, float2 a, float2 b) {
     *reinterpret_cast<float4*>(out + o) = make_float4(a.x, a.y, b.x, b.y);
 }
@@ -185,6 +188,12 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 
 __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *reinterpret_cast<const volatile int32_t*>(p); }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // Persistent kernel with shared-memory staging (Blackwell bulk copies).
 //
@@ -206,6 +215,7 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *reint
 constexpr int kPW = kPersistentThreads / 32;  // warps per block
 constexpr int kLeafTab = 2 << kLeafBits;       // entries of the folded gate table
 constexpr int kUnrollS = 2;                    // 64-output iterations in flight when reading shared memory
+constexpr int kFast = 4;                       // most operands of the unrolled tile loop
 
 template <typename R>
 struct StageCfg;
@@ -234,6 +244,14 @@ struct RunSlot {
     uint32_t total_foot;  // staged elements per tile
     uint8_t n_out, cb, n_staged, n_leaves;
     uint32_t bad;         // the plan's footprint exceeds the stage: not computed
+    // per-group constants of the unrolled tile loop, for the staged operands
+    // and the gate table (at most kFast of them)
+    uint8_t n_fast;                  // operands of the tile loop; 0: the generic loop
+    uint8_t loff[kFast][32];         // each lane's pair index within the footprint
+    uint16_t dstep[kFast][5];        // pair-index step of tile bits 6..10
+    uint8_t n_hi;                    // folded tensors whose output bit lies above the tile
+    uint8_t hi_idx[kMaxFoldLeaves];  // their slots
+    uint8_t hi_shift[kMaxFoldLeaves];// position of that bit within the chunk index
 };
 
 template <typename R>
@@ -303,18 +321,24 @@ struct Cursor {
     }
 };
 
-// The group at queue position q, if it has been published (non-blocking).
+// The group at queue position q, if it may start (non-blocking): a position of
+// the static order once its bucket's producers have all finished, a position
+// of the ready queue once it has been published.
 __device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
     uint32_t ok = 1;
     DRun r{};
     if (q < dp.n_static) {
         r = dp.runs[q];
+        if (r.n_deps) {
+            if (lane == 0) ok = ld_acquire(&dp.prod_done[r.bucket]) >= r.n_deps;
+            ok = __shfl_sync(kFull, ok, 0);
+        }
     } else {
         if (lane == 0) {
             const DSlot* sl = dp.slots + (q - dp.n_static);
             const uint32_t n = ld_acquire(&sl->n_chunks);
             ok = n != 0;
-            if (ok) r = DRun{sl->bucket, sl->chunk_begin, n, sl->op_begin};
+            if (ok) r = DRun{sl->bucket, sl->chunk_begin, n, sl->op_begin, 0u, {0u, 0u, 0u}};
         }
         ok = __shfl_sync(kFull, ok, 0);
         r.bucket = __shfl_sync(kFull, r.bucket, 0);
@@ -356,10 +380,13 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
     const bool fits = B.total_foot <= (uint32_t)StageCfg<R>::elems && B.n_leaves <= kMaxFoldLeaves;
     if (has && fits) {
         if (op.folded) {
+            // a gate tensor (4 slots) or an earlier result of rank <= 2, which
+            // this launch wrote from another SM: read that one at L2; its
+            // allocation is 128-byte aligned, so 4 entries stay inside it
             rs.lmask[op.slot] = op.mask;
             const C* T = static_cast<const C*>(dp.arena) + op.off;
 #pragma unroll
-            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = T[i];
+            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = (op.flags & kOpLeaf) ? T[i] : ldcg_c(T + i);
         } else {
             rs.goff[op.slot] = op.off;
             rs.gmask[op.slot] = op.mask;
@@ -386,6 +413,31 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
     __syncwarp();
     *cbase = 0;
     if (lane < rs.n_staged) *cbase = pext_u32(run.chunk_begin, rs.gmask[lane] >> rs.cb);
+    // constants of the unrolled tile loop: lane offsets, iteration steps, and
+    // the folded tensors whose single output bit lies above the tile
+    const uint32_t low = (1u << rs.cb) - 1u;
+    const int nf = rs.n_staged + (rs.n_leaves ? 1 : 0);
+    const bool fast = !rs.bad && rs.cb >= 6 && rs.cb <= 11 && nf <= kFast;
+    for (int t = 0; t < nf && fast; ++t) {
+        const uint32_t m = t < rs.n_staged ? (rs.gmask[t] & low) : rs.leaf_u;
+        rs.loff[t][lane] = (uint8_t)pext_u32((uint32_t)lane << 1, m & 63u);
+        if (lane < 5) {
+            const int bit = 6 + lane;
+            rs.dstep[t][lane] = ((m >> bit) & 1u) ? (uint16_t)(1u << __popc(m & ((1u << bit) - 1u))) : (uint16_t)0;
+        }
+    }
+    if (lane == 0) {
+        rs.n_fast = fast ? (uint8_t)nf : (uint8_t)0;
+        uint8_t nh = 0;
+        for (int l = 0; l < rs.n_leaves; ++l)
+            if (rs.lmask[l] & ~low) {
+                rs.hi_idx[nh] = (uint8_t)l;
+                rs.hi_shift[nh] = (uint8_t)(31 - __clz(rs.lmask[l]) - rs.cb);
+                ++nh;
+            }
+        rs.n_hi = nh;
+    }
+    __syncwarp();
 }
 
 // Append every group of bucket p to the queue (its last producer just finished).
@@ -569,39 +621,64 @@ __device__ void tile_from_smem_generic(const WarpSmem<R>& ws, int sl, int st, ty
     }
 }
 
+// Shared-memory reads of the tile loop use 32-bit shared addresses. The loads
+// are ordinary (non-volatile) asm so the compiler may schedule them freely;
+// each address carries `tok`, an opaque zero produced after the last wait or
+// barrier, so no load can be hoisted above the point its data became valid.
+__device__ __forceinline__ uint32_t opaque_zero() {
+    uint32_t z;
+    asm volatile("mov.u32 %0, 0;" : "=r"(z));
+    return z;
+}
+__device__ __forceinline__ Pair<float2> lds_pair(uint32_t a, const float2*) {
+    float4 v;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ Pair<double2> lds_pair(uint32_t a, const double2*) {
+    double2 u, w;
+    asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(u.x), "=d"(u.y) : "r"(a));
+    asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w.x), "=d"(w.y) : "r"(a + 16u));
+    return {u, w};
+}
+__device__ __forceinline__ void stg_two(float2* p, float2 a, float2 b) {
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+}
+__device__ __forceinline__ void stg_two(double2* p, double2 a, double2 b) {
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(a.x), "d"(a.y));
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p + 1), "d"(b.x), "d"(b.y));
+}
+
 // The hot path for tiles of at least 64 outputs (cb = 6 + log2 NI): N
 // operands in shared memory, every loop fully unrolled. A lane owns outputs
-// 2*lane + {0,1} + 64*i; an operand's pair index for that output is its lane
-// part plus the iteration bits' deltas, all fixed before the loop.
+// 2*lane + {0,1} + 64*i; an operand's pair for such an output sits at the
+// lane's offset plus the steps of the iteration's bits, all fixed per group.
 template <typename R, int N, int NI>
-__device__ __forceinline__ void tile_fast(const typename CT<R>::c* const (&base)[N], const uint32_t (&mask)[N],
-                                          typename CT<R>::c* out, int lane) {
+__device__ __forceinline__ void tile_fast(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
+                                          const RunSlot<R>& rs, typename CT<R>::c* out, int lane) {
     using C = typename CT<R>::c;
-    constexpr int IB = NI == 1 ? 0 : NI == 2 ? 1 : NI == 4 ? 2 : NI == 8 ? 3 : 4;
-    uint32_t off0[N], second[N], d[N][IB > 0 ? IB : 1];
+    constexpr uint32_t PB = 2 * sizeof(C);  // bytes of one (x=0, x=1) pair
+    constexpr int IB = NI == 1 ? 0 : NI == 2 ? 1 : NI == 4 ? 2 : NI == 8 ? 3 : NI == 16 ? 4 : 5;
+    uint32_t a0[N], second[N], d[N][IB > 0 ? IB : 1];
 #pragma unroll
     for (int t = 0; t < N; ++t) {
-        const uint32_t m = mask[t];
-        off0[t] = pext_u32((uint32_t)lane << 1, m & 63u);
-        second[t] = (m & 1u) ? 2u : 0u;  // element offset of the second output's pair
+        a0[t] = sbase[t] + PB * rs.loff[t][lane];
+        second[t] = (smask[t] & 1u) ? PB : 0u;  // the lane's second output uses the next pair
 #pragma unroll
-        for (int k = 0; k < IB; ++k) {
-            const int bit = 6 + k;
-            d[t][k] = ((m >> bit) & 1u) ? (1u << __popc(m & ((1u << bit) - 1u))) : 0u;
-        }
+        for (int k = 0; k < IB; ++k) d[t][k] = PB * rs.dstep[t][k];
     }
+    const C* tag = nullptr;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
         C p00, p01, p10, p11;  // [output][x]
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            uint32_t o = off0[t];
+            uint32_t q = a0[t];
 #pragma unroll
             for (int k = 0; k < IB; ++k)
-                if ((i >> k) & 1) o += d[t][k];
-            const C* q = base[t] + 2u * o;
-            const Pair<C> a = ld_pair_smem(q);
-            const Pair<C> b = ld_pair_smem(q + second[t]);
+                if ((i >> k) & 1) q += d[t][k];
+            const Pair<C> a = lds_pair(q, tag);
+            const Pair<C> b = lds_pair(q + second[t], tag);
             if (t == 0) {
                 p00 = a.v0;
                 p01 = a.v1;
@@ -614,7 +691,7 @@ __device__ __forceinline__ void tile_fast(const typename CT<R>::c* const (&base)
                 p11 = cmul(p11, b.v1);
             }
         }
-        st_two(out, (uint64_t)(i * 64 + 2 * lane), cadd(p00, p01), cadd(p10, p11));
+        stg_two(out + (i * 64 + 2 * lane), cadd(p00, p01), cadd(p10, p11));
     }
 }
 
@@ -624,22 +701,22 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
     using C = typename CT<R>::c;
     const RunSlot<R>& rs = ws.slot[sl];
     const uint32_t low = (1u << rs.cb) - 1u;
-    const C* base[N];
-    uint32_t mask[N];
+    const uint32_t tok = opaque_zero();  // after the stage wait and the gate table's barrier
+    uint32_t sbase[N], smask[N];
 #pragma unroll
     for (int t = 0; t < N; ++t) {
         const bool is_tab = t == rs.n_staged;
-        base[t] = is_tab ? ws.leaf_tab : ws.stage[st] + rs.soff[t];
-        mask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
+        sbase[t] = tok + (is_tab ? smem_u32(ws.leaf_tab) : smem_u32(ws.stage[st] + rs.soff[t]));
+        smask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
     C* tile_out = out + ((uint64_t)chunk << rs.cb);
     switch (rs.cb) {
-        case 6: tile_fast<R, N, 1>(base, mask, tile_out, lane); break;
-        case 7: tile_fast<R, N, 2>(base, mask, tile_out, lane); break;
-        case 8: tile_fast<R, N, 4>(base, mask, tile_out, lane); break;
-        case 9: tile_fast<R, N, 8>(base, mask, tile_out, lane); break;
-        case 10: tile_fast<R, N, 16>(base, mask, tile_out, lane); break;
-        default: tile_from_smem<R, N>(base, mask, out, rs.cb, rs.n_out, chunk << rs.cb, lane); break;
+        case 6: tile_fast<R, N, 1>(sbase, smask, rs, tile_out, lane); break;
+        case 7: tile_fast<R, N, 2>(sbase, smask, rs, tile_out, lane); break;
+        case 8: tile_fast<R, N, 4>(sbase, smask, rs, tile_out, lane); break;
+        case 9: tile_fast<R, N, 8>(sbase, smask, rs, tile_out, lane); break;
+        case 10: tile_fast<R, N, 16>(sbase, smask, rs, tile_out, lane); break;
+        default: tile_fast<R, N, 32>(sbase, smask, rs, tile_out, lane); break;
     }
 }
 
@@ -670,7 +747,7 @@ __device__ bool wait_stage(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, u
 // tile, so the table of a tile is tlow times that per-tile pair.
 template <typename R>
 __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs, uint32_t chunk, bool first,
-                                           typename CT<R>::c (&tlow)[2], int lane) {
+                                           typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane) {
     using C = typename CT<R>::c;
     const uint32_t low = (1u << rs.cb) - 1u;
     const uint32_t nent = 2u << __popc(rs.leaf_u);
@@ -690,18 +767,19 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
             tlow[h] = v;
         }
     }
-    if (!first && !rs.leaf_hi) return;  // the table of the first tile still holds
+    // the table changes only when one of the high output bits changes
+    uint32_t key = 0;
+    for (int h = 0; h < rs.n_hi; ++h) key |= ((chunk >> rs.hi_shift[h]) & 1u) << h;
+    if (!first && key == hi_key) return;
+    hi_key = key;
     C cp[2];
     cp[0].x = cp[1].x = (R)1;
     cp[0].y = cp[1].y = (R)0;
-    if (rs.leaf_hi) {
-        const uint32_t o0 = chunk << rs.cb;
-        for (int l = 0; l < rs.n_leaves; ++l)
-            if (rs.lmask[l] & ~low) {
-                const uint32_t y = (o0 & rs.lmask[l]) ? 1u : 0u;  // the gate's single output bit
-                cp[0] = cmul(cp[0], rs.lval[l][2u * y]);
-                cp[1] = cmul(cp[1], rs.lval[l][2u * y + 1u]);
-            }
+    for (int h = 0; h < rs.n_hi; ++h) {
+        const int l = rs.hi_idx[h];
+        const uint32_t y = (key >> h) & 1u;  // the tensor's single output bit
+        cp[0] = cmul(cp[0], rs.lval[l][2u * y]);
+        cp[1] = cmul(cp[1], rs.lval[l][2u * y + 1u]);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -712,18 +790,19 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
 }
 
 // Contract tile `chunk` of the group in slot sl from stage st.
-template <typename R>
+template <typename R, typename Clock>
 __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk, bool first_of_run,
-                              typename CT<R>::c (&tlow)[2], int lane) {
+                              typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane, Clock& clk) {
     using C = typename CT<R>::c;
     const RunSlot<R>& rs = ws.slot[sl];
-    if (rs.n_leaves) gate_table<R>(ws, rs, chunk, first_of_run, tlow, lane);
+    if (rs.n_leaves) gate_table<R>(ws, rs, chunk, first_of_run, tlow, hi_key, lane);
+    clk.lap(kTrGate);
     C* out = static_cast<C*>(dp.arena) + rs.out_off;
-    const int n = rs.n_staged + (rs.n_leaves ? 1 : 0);
-    switch (n) {
+    switch (rs.n_fast) {
         case 1: run_tile_n<R, 1>(ws, sl, st, out, chunk, lane); break;
         case 2: run_tile_n<R, 2>(ws, sl, st, out, chunk, lane); break;
         case 3: run_tile_n<R, 3>(ws, sl, st, out, chunk, lane); break;
+        case 4: run_tile_n<R, 4>(ws, sl, st, out, chunk, lane); break;
         default: tile_from_smem_generic<R>(ws, sl, st, out, chunk, lane); break;
     }
     __syncwarp();
@@ -738,6 +817,7 @@ __device__ __forceinline__ void finish_group(const DevPlan& dp, const RunSlot<R>
     __syncwarp();
     uint32_t push = 0;
     const uint32_t parent = rs.parent;
+    if (dp.isolated) return;
     if (lane == 0) {
         __threadfence();
         const uint32_t done = atomicAdd(&dp.tiles_done[rs.bucket], rs.n_chunks) + rs.n_chunks;
@@ -749,7 +829,7 @@ __device__ __forceinline__ void finish_group(const DevPlan& dp, const RunSlot<R>
         }
     }
     push = __shfl_sync(kFull, push, 0);
-    if (push) publish_bucket(dp, parent, lane);
+    if (push && dp.n_static < dp.n_groups) publish_bucket(dp, parent, lane);  // ready-queue order only
     __syncwarp();
 }
 
@@ -785,8 +865,24 @@ struct PhaseClock {
     }
 };
 
+#ifndef QT_PERSISTENT_MIN_BLOCKS
+#define QT_PERSISTENT_MIN_BLOCKS 3
+#endif
+
+// Traced runs: each bucket's earliest group start and latest group end.
+template <bool On>
+__device__ __forceinline__ void mark_bucket(const DevPlan& dp, uint32_t b, bool end, int lane) {
+    if (On && lane == 0 && dp.bucket_times) {
+        const unsigned long long t = globaltimer_ns();
+        if (end)
+            atomicMax(&dp.bucket_times[2 * b + 1], t);
+        else
+            atomicMin(&dp.bucket_times[2 * b], t);
+    }
+}
+
 template <typename R, bool Trace>
-__global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp) {
+__global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) k_persistent(DevPlan dp) {
     using C = typename CT<R>::c;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -808,13 +904,14 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp
         // tile A is contracted from stage st (group in slot sa) while the
         // copies for tile B, the next one, are in flight
         int sa = 0, st = 0;
-        uint32_t cbase = 0;
+        uint32_t cbase = 0, hi_key = 0;
         C tlow[2];
         DRun ra;
         bool ok = wait_group(dp, qa, &ra, lane);
         clk.lap(kTrDeps);
         if (ok) {
             prep_run<R>(dp, ws, sa, ra, lane, &cbase);
+            mark_bucket<Trace>(dp, ra.bucket, false, lane);
             clk.lap(kTrPrep);
             clk.count(kTrRuns, 1);
             if (lane == 0) fence_proxy_async_global();  // producers' results before this warp's copies
@@ -840,6 +937,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp
                 if (b_valid && group_at(dp, qb, &rb, lane)) {
                     sb = sa ^ 1;
                     prep_run<R>(dp, ws, sb, rb, lane, &cbase);
+                    mark_bucket<Trace>(dp, rb.bucket, false, lane);
                     clk.lap(kTrPrep);
                     clk.count(kTrRuns, 1);
                     if (lane == 0) fence_proxy_async_global();
@@ -854,11 +952,12 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp
             }
             if (!wait_stage<R>(dp, ws, sa, st, phase, lane)) break;
             clk.lap(kTrWait);
-            contract_tile<R>(dp, ws, sa, st, a_chunk, a_first, tlow, lane);
+            contract_tile<R>(dp, ws, sa, st, a_chunk, a_first, tlow, hi_key, lane, clk);
             clk.lap(kTrCompute);
             clk.count(kTrTiles, 1);
             pending[st] = false;
             if (a_left == 1) {
+                mark_bucket<Trace>(dp, ws.slot[sa].bucket, true, lane);
                 finish_group<R>(dp, ws.slot[sa], lane);
                 clk.lap(kTrFinish);
             }
@@ -869,6 +968,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) k_persistent(DevPlan dp
                 clk.lap(kTrDeps);
                 sb = sa ^ 1;
                 prep_run<R>(dp, ws, sb, rb, lane, &cbase);
+                mark_bucket<Trace>(dp, rb.bucket, false, lane);
                 clk.lap(kTrPrep);
                 clk.count(kTrRuns, 1);
                 if (lane == 0) fence_proxy_async_global();
@@ -996,6 +1096,17 @@ cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int 
         k_leaf_fill<double><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<double2*>(arena));
     else
         k_leaf_fill<float><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<float2*>(arena));
+    return cudaGetLastError();
+}
+
+__global__ void k_clear_ends(unsigned long long* t, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) t[2 * i + 1] = 0ull;
+}
+
+cudaError_t launch_clear_ends(unsigned long long* t, size_t n, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_clear_ends<<<blocks, 256, 0, s>>>(t, n);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@ struct DevPlan {
     void* arena;            // complex64 or complex128 elements
     uint64_t spin_limit;
     uint64_t* trace;        // per-warp phase counters (kTraceSlots each), or null: untraced kernel
+    uint32_t isolated;      // nonzero: run only the groups in `runs` and notify no consumer
+    unsigned long long* bucket_times;  // traced runs: per bucket, first group start and last group end (ns)
 };
 
 // Phase counters of the traced persistent kernel, per warp (cycles unless noted).
@@ -37,7 +39,7 @@ enum : int {
     kTrFinish = 6,  // publishing finished runs
     kTrTiles = 7,   // count of tiles
     kTrRuns = 8,    // count of runs
-    kTrSpare = 9
+    kTrGate = 9     // building the folded gate table of a tile
 };
 
 // Everything the epilogue reads and writes.
@@ -58,6 +60,7 @@ cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream
 cudaError_t launch_per_bucket(int dtype, uint32_t bucket, uint32_t n_tasks, const DevPlan& dp, cudaStream_t s);
 cudaError_t launch_epilogue(int dtype, const DevEpilogue& de, cudaStream_t s);
 int persistent_blocks_per_sm(int dtype);
+cudaError_t launch_clear_ends(unsigned long long* t, size_t n, cudaStream_t s);
 constexpr int kPersistentThreads = 128;  // 4 warps; each warp owns its shared-memory stages
 size_t persistent_smem_bytes(int dtype);
 

@@ -294,6 +294,10 @@ static int make_buckets(const Network& net, const std::vector<int>& order, int m
     return QT_OK;
 }
 
+// Operands of rank <= 2 (gate tensors, and results of 4 entries or fewer) may
+// be folded into the per-tile product table.
+static bool foldable(const HOperand& op) { return op.rank <= 2; }
+
 // Tile size of a bucket: the largest 2^cb outputs (cb <= cap) for which the
 // footprints of the staged operands fit one shared-memory stage. Within an
 // aligned tile an operand with mask M touches the contiguous block of
@@ -308,14 +312,14 @@ static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_e
         uint32_t U = 0;
         int nleaf = 0;
         for (const HOperand& op : B.ops)
-            if (op.src < 0) {
+            if (foldable(op)) {
                 U |= op.mask & low;
                 nleaf++;
             }
         const bool fold = nleaf > 0 && nleaf <= kMaxFoldLeaves && __builtin_popcount(U) <= kLeafBits;
         long foot = 0;
         for (const HOperand& op : B.ops)
-            if (!(fold && op.src < 0)) foot += 2l << __builtin_popcount(op.mask & low);
+            if (!(fold && foldable(op))) foot += 2l << __builtin_popcount(op.mask & low);
         if (foot <= stage_elems) {
             *cb_out = cb;
             *fold_out = fold;
@@ -327,6 +331,84 @@ static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_e
 }
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Claim order by list scheduling on the host. Each of W simulated warps takes,
+// whenever it is free, the ready group whose bucket has the longest remaining
+// path to its network's result (the sum, along the path, of the time each
+// bucket takes with the whole GPU); a bucket's groups become ready when its
+// last producer finishes. A group's time is its bytes at one warp's share of
+// the memory bandwidth plus fixed per-tile and per-group costs. The order in
+// which the simulated warps start groups is the claim order used on the
+// device: it is topological (a group starts after its producers finish), and
+// it front-loads the critical path instead of serving buckets first come,
+// first served.
+static void simulate_order(HostPlan* hp) {
+    const PlanConfig& cfg = hp->cfg;
+    const size_t nb = hp->buckets.size();
+    const double esize = cfg.dtype == 1 ? 16.0 : 8.0;
+    const double W = std::max(1, cfg.sim_workers);
+    const double bw = 6.5e12;                  // bytes per second, whole GPU
+    const double t_tile = 0.3e-6, t_group = 1.5e-6;
+    std::vector<double> tile_s(nb), whole_s(nb), prio(nb, 0.0);
+    for (size_t b = 0; b < nb; ++b) {
+        const DBucket& d = hp->buckets[b];
+        const double tile_bytes = ((double)d.total_foot + std::ldexp(1.0, d.chunk_bits)) * esize;
+        tile_s[b] = tile_bytes / (bw / W) + t_tile;
+        const double groups_in_parallel = std::min<double>(W, d.n_groups);
+        whole_s[b] = std::max(tile_s[b] * d.n_tasks / groups_in_parallel, tile_s[b] * d.group_tiles) + t_group;
+    }
+    // buckets of a network are in elimination order, so parents come after children
+    for (size_t i = nb; i-- > 0;) {
+        const DBucket& d = hp->buckets[i];
+        prio[i] = whole_s[i] + (d.parent != kNone ? prio[d.parent] : 0.0);
+    }
+    // event simulation
+    std::vector<uint32_t> deps_left(nb);
+    for (size_t b = 0; b < nb; ++b) deps_left[b] = hp->buckets[b].n_deps;
+    std::vector<uint32_t> groups_left(nb);
+    for (size_t b = 0; b < nb; ++b) groups_left[b] = hp->buckets[b].n_groups;
+    struct Ready {
+        double prio;
+        uint32_t bucket, next_group;
+        bool operator<(const Ready& o) const { return prio < o.prio || (prio == o.prio && bucket > o.bucket); }
+    };
+    std::priority_queue<Ready> ready;  // buckets with unstarted groups, highest priority first
+    for (size_t b = 0; b < nb; ++b)
+        if (deps_left[b] == 0) ready.push(Ready{prio[b], (uint32_t)b, 0});
+    using Ev = std::pair<double, uint32_t>;  // (finish time, bucket)
+    std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
+    double now = 0.0;
+    uint64_t free_workers = (uint64_t)W;
+    hp->runs.clear();
+    hp->runs.reserve(hp->n_groups);
+    while (hp->runs.size() < hp->n_groups) {
+        while (free_workers > 0 && !ready.empty()) {
+            Ready r = ready.top();
+            ready.pop();
+            const DBucket& d = hp->buckets[r.bucket];
+            const uint32_t c = r.next_group * d.group_tiles;
+            const uint32_t n = std::min(d.group_tiles, d.n_tasks - c);
+            hp->runs.push_back(DRun{r.bucket, c, n, d.op_begin, d.n_deps, {0, 0, 0}});
+            running.push(Ev{now + tile_s[r.bucket] * n + t_group, r.bucket});
+            --free_workers;
+            if (++r.next_group < d.n_groups) ready.push(r);
+        }
+        if (running.empty()) break;  // cannot happen with a consistent plan
+        const Ev e = running.top();
+        running.pop();
+        now = e.first;
+        ++free_workers;
+        if (--groups_left[e.second] == 0) {
+            const uint32_t par = hp->buckets[e.second].parent;
+            if (par != kNone && --deps_left[par] == 0) ready.push(Ready{prio[par], par, 0});
+        }
+    }
+    while (!running.empty()) {
+        now = std::max(now, running.top().first);
+        running.pop();
+    }
+    hp->sim_seconds = now;
+}
 
 int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, HostPlan* hp) {
     auto t0 = std::chrono::steady_clock::now();
@@ -429,7 +511,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
                 const uint32_t low = (1u << cb) - 1u;
                 uint32_t foot = 0, ns = 0, nl = 0, lu = 0, lh = 0;
                 for (const HOperand& op : B.ops) {
-                    if (fold && op.src < 0) {
+                    if (fold && foldable(op)) {
                         nl++;
                         lu |= op.mask & low;
                         lh |= op.mask & ~low;
@@ -456,7 +538,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
                 DOperand o{};
                 o.mask = op.mask;
                 o.src = kNone;
-                o.folded = (d.flags & kBucketFoldLeaves) && op.src < 0;
+                o.folded = (d.flags & kBucketFoldLeaves) && foldable(op);
                 if (o.folded) {
                     o.slot = (uint8_t)next_leaf++;
                 } else {
@@ -523,22 +605,36 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     for (uint32_t b : hp->by_level) hp->level_first_bucket[hp->bucket_level[b] + 1]++;
     for (int l = 0; l < hp->n_levels; ++l) hp->level_first_bucket[l + 1] += hp->level_first_bucket[l];
     // Work groups: a bucket's tiles are handed out in groups of group_tiles
-    // consecutive tiles, so a warp reads the bucket's descriptors once per group. Groups of buckets without producers open the
-    // queue, in level order with the largest buckets first; every other bucket
-    // appends its groups when its last producer finishes.
+    // consecutive tiles, so a warp reads the bucket's descriptors once per group.
     hp->runs.clear();
     hp->n_tiles = 0;
     hp->n_groups = 0;
     for (uint32_t b : hp->by_level) {
         DBucket& d = hp->buckets[b];
-        const uint32_t rt = cfg.run_tiles > 0 ? (uint32_t)cfg.run_tiles : (uint32_t)kRunTiles;
+#ifndef QT_GROUP_DIV
+#define QT_GROUP_DIV 0
+#endif
+        // QT_GROUP_DIV > 0: groups of n_tasks / QT_GROUP_DIV tiles, within [1, kRunTiles]
+        const uint32_t rt = cfg.run_tiles > 0 ? (uint32_t)cfg.run_tiles
+                            : QT_GROUP_DIV > 0 ? std::max<uint32_t>(1, std::min<uint32_t>(kRunTiles, d.n_tasks / QT_GROUP_DIV))
+                                               : (uint32_t)kRunTiles;
         d.group_tiles = std::min(rt, d.n_tasks);
         d.n_groups = (d.n_tasks + d.group_tiles - 1) / d.group_tiles;
         hp->n_tiles += d.n_tasks;
         hp->n_groups += d.n_groups;
-        if (d.n_deps == 0)
-            for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-                hp->runs.push_back(DRun{b, c, std::min<uint32_t>(d.group_tiles, d.n_tasks - c), d.op_begin});
+    }
+    if (cfg.order == 1) {
+        // ready queue: groups of buckets without producers open it, in level
+        // order with the largest buckets first; every other bucket appends its
+        // groups when its last producer finishes
+        for (uint32_t b : hp->by_level) {
+            const DBucket& d = hp->buckets[b];
+            if (d.n_deps == 0)
+                for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
+                    hp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, {0, 0, 0}});
+        }
+    } else {
+        simulate_order(hp);
     }
     hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return QT_OK;

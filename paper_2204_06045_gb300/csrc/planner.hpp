@@ -64,6 +64,8 @@ struct PlanConfig {
     int max_width = 31;
     int chunk_log2 = 0;
     int run_tiles = 0;
+    int order = 0;        // 0: claim order from a critical-path list-scheduling simulation; 1: ready queue
+    int sim_workers = 1824;  // warps assumed by the simulation
     bool with_grad = false;
 };
 
@@ -84,9 +86,10 @@ struct HostPlan {
     std::vector<int32_t> op_rank;
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
-    std::vector<DRun> runs;             // the queue's first entries: groups of buckets with no producer
+    std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
     uint64_t n_tiles = 0;
     uint64_t n_groups = 0;              // queue length: groups over all buckets
+    double sim_seconds = 0;             // makespan of the host simulation (0 if not simulated)
     std::vector<uint32_t> root_bucket;  // every root bucket (scalar result)
     std::vector<uint32_t> net_first_root;  // n_nets + 1 into root_bucket
     std::vector<uint32_t> level_first_bucket;  // buckets sorted by level (for the adjoint)

@@ -18,15 +18,18 @@ constexpr int kMaxOps = 16;      // operands per bucket
 constexpr int kLeafSlots = 4;    // every leaf tensor occupies 4 elements
 // Persistent kernel staging: every operand's footprint in one output tile is a
 // contiguous block, copied into a per-warp shared-memory stage of this many
-// elements (8 KB for both element types). Gate tensors whose tile bits number
+// elements (QT_STAGE_BYTES, 8 KB by default, for both element types). Gate tensors whose tile bits number
 // at most kLeafBits are folded into one product table instead.
-constexpr int kStageElemsC64 = 1024;
-constexpr int kStageElemsC128 = 512;
+#ifndef QT_STAGE_BYTES
+#define QT_STAGE_BYTES 8192
+#endif
+constexpr int kStageElemsC64 = QT_STAGE_BYTES / 8;
+constexpr int kStageElemsC128 = QT_STAGE_BYTES / 16;
 constexpr int kLeafBits = 5;
 constexpr int kMaxFoldLeaves = 8;
 constexpr uint8_t kBucketFoldLeaves = 1;
 constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim (default)
-constexpr int kDefaultTileBits = 8;  // at most 256 outputs per tile (default); measured best on GB300
+constexpr int kDefaultTileBits = 9;  // at most 512 outputs per tile (default); measured best on GB300
 
 // One bucket on the device. 64 bytes.
 struct DBucket {
@@ -69,14 +72,16 @@ static_assert(sizeof(DOperand) == 32, "DOperand layout");
 constexpr uint32_t kOpLeaf = 1u;
 
 // A group of consecutive tiles of one bucket: what one claim hands a warp,
-// which reads the bucket's descriptors once for all of them. 16 bytes.
+// which reads the bucket's descriptors once for all of them. 32 bytes.
 struct DRun {
     uint32_t bucket;
     uint32_t chunk_begin;
     uint32_t n_chunks;
     uint32_t op_begin;  // the bucket's first operand (saves a dependent load)
+    uint32_t n_deps;    // producers that must finish before the group may start
+    uint32_t pad[3];
 };
-static_assert(sizeof(DRun) == 16, "DRun layout");
+static_assert(sizeof(DRun) == 32, "DRun layout");
 
 // A published slot of the ready queue: a group whose bucket's producers have
 // all finished. 16 bytes.

@@ -22,7 +22,7 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 # every symbol include/qt.h declares
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-           "qt_trace_counters", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail")
+           "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail")
 
 
 class QTError(RuntimeError):
@@ -38,7 +38,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("sched", ctypes.c_int), ("order_restarts", ctypes.c_int32),
                 ("order_seed", ctypes.c_uint64), ("max_width", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
                 ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
-                ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32)]
+                ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
+                ("order", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -47,7 +48,7 @@ class PlanStats(ctypes.Structure):
                 ("sum_2w", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("flops", ctypes.c_double),
                 ("arena_bytes", ctypes.c_int64), ("n_tasks", ctypes.c_int64), ("n_items", ctypes.c_int64),
                 ("n_levels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("width_hist", ctypes.c_int64 * 64),
-                ("plan_seconds", ctypes.c_double)]
+                ("plan_seconds", ctypes.c_double), ("sim_seconds", ctypes.c_double)]
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
@@ -56,6 +57,14 @@ OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_lay
                           ("mask", np.uint32), ("rank", np.int32), ("pad", np.int32)])
 
 _lib = None
+
+
+def use_library(path) -> None:
+    """Load the library from ``path`` instead (a tuning variant); before first use."""
+    global LIB_PATH, _lib
+    if _lib is not None:
+        raise RuntimeError("libqtgb is already loaded")
+    LIB_PATH = Path(path)
 
 
 def lib():
@@ -81,6 +90,8 @@ def lib():
         L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
         L.qt_debug_stall_bucket.argtypes = [vp, i64]
         L.qt_trace_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i64)]
+        L.qt_bucket_time.argtypes = [vp, i64, i32, dp, dp]
+        L.qt_trace_bucket_times.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.qt_plan_free.argtypes = [vp]
         L.qt_plan_free.restype = None
         L.qt_error_string.argtypes = [ctypes.c_int]
@@ -89,7 +100,7 @@ def lib():
         L.qt_last_error_detail.restype = ctypes.c_char_p
         for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-                     "qt_debug_stall_bucket", "qt_trace_counters"):
+                     "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -148,7 +159,8 @@ class Plan:
     # -- construction -------------------------------------------------------------
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
-              with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False):
+              with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
+              order="simulated"):
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
         o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
@@ -162,6 +174,7 @@ class Plan:
         o.host_only = int(bool(host_only))
         o.run_tiles = int(run_tiles)
         o.trace = int(bool(trace))
+        o.order = {"simulated": 0, "ready_queue": 1}[order]
         return o
 
     @classmethod
@@ -294,14 +307,31 @@ class Plan:
         _check(lib().qt_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n), int(reset)), "qt_kernel_time")
         return ms.value, n.value
 
-    TRACE_PHASES = ("claim", "prep", "deps", "issue", "wait", "compute", "finish")
+    def bucket_time(self, bucket: int, reps: int = 5):
+        """(mean ms, algorithmic bytes) of the persistent kernel on one bucket alone."""
+        ms = ctypes.c_double(0)
+        by = ctypes.c_double(0)
+        _check(lib().qt_bucket_time(self._h, int(bucket), int(reps), ctypes.byref(ms), ctypes.byref(by)),
+               "qt_bucket_time")
+        return ms.value, by.value
+
+    def trace_bucket_times(self) -> np.ndarray:
+        """(n_buckets, 2) array of start and end times (ns) of the last traced run."""
+        nb = self.stats()["n_buckets"]
+        out = np.zeros(2 * nb, dtype=np.uint64)
+        _check(lib().qt_trace_bucket_times(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+               "qt_trace_bucket_times")
+        return out.reshape(nb, 2)
+
+    TRACE_PHASES = ("claim", "prep", "deps", "issue", "wait", "compute", "finish", "gate")
 
     def trace_counters(self) -> dict:
         """Per-phase cycles summed over warps, tile and run counts, warps launched."""
         buf = (ctypes.c_uint64 * 10)()
         nw = ctypes.c_int64(0)
         _check(lib().qt_trace_counters(self._h, buf, ctypes.byref(nw)), "qt_trace_counters")
-        d = {k: int(buf[i]) for i, k in enumerate(self.TRACE_PHASES)}
+        d = {k: int(buf[i]) for i, k in enumerate(self.TRACE_PHASES[:7])}
+        d["gate"] = int(buf[9])
         d.update(tiles=int(buf[7]), runs=int(buf[8]), warps=int(nw.value))
         return d
 

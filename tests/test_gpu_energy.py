@@ -120,8 +120,9 @@ def _golden_edges(name):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("sched", ["persistent", "per_bucket"])
-def test_c2_n30_p4_matches_statevector_golden(dtype, sched):
+@pytest.mark.parametrize("sched,order", [("persistent", "simulated"), ("persistent", "ready_queue"),
+                                         ("per_bucket", "simulated")])
+def test_c2_n30_p4_matches_statevector_golden(dtype, sched, order):
     if not (GOLDEN / "c2_n30_p4_statevector.txt").exists():
         pytest.skip("golden not generated")
     rows, ref = _golden_edges("c2_n30_p4_statevector.txt")
@@ -129,7 +130,7 @@ def test_c2_n30_p4_matches_statevector_golden(dtype, sched):
     edges = synth.random_regular_graph(n, 1000)
     g, b = np.array(rows["gamma"]), np.array(rows["beta"])
     np.testing.assert_array_equal((g, b), synth.angles(p, 1000))
-    with qtgb.plan(n, edges, p, dtype=dtype, sched=sched) as pl:
+    with qtgb.plan(n, edges, p, dtype=dtype, sched=sched, order=order) as pl:
         zz, E = pl.energy(g, b)
         im = pl.last_imag()
     assert scaled_err(zz, ref) <= TOL[dtype]
@@ -151,10 +152,11 @@ def test_c5_n50_p4_matches_bucket_golden(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_batch_of_graphs_matches_oracle(dtype):
+@pytest.mark.parametrize("order", ["simulated", "ready_queue"])
+def test_batch_of_graphs_matches_oracle(dtype, order):
     p = 3
     graphs = synth.batch(6, p, lo=50, hi=120, base_seed=1000)
-    with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], p, dtype=dtype) as pl:
+    with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], p, dtype=dtype, order=order) as pl:
         G = np.array([gg for _, _, gg, _ in graphs])
         B = np.array([bb for _, _, _, bb in graphs])
         energies, zz = pl.energy_batch(G, B)
