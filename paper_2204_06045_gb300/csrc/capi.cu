@@ -57,6 +57,10 @@ struct qt_plan_s {
     bool trace = false;
     uint64_t* d_trace = nullptr;
     unsigned long long* d_btimes = nullptr;
+    // gradient plans
+    void* d_bwd = nullptr;       // op_param | net_graph | backward task arrays
+    double* d_grad = nullptr;    // n_graphs x 2p accumulators, then dgamma | dbeta
+    qt::DevBwd db{};
 
     ~qt_plan_s() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -75,6 +79,8 @@ struct qt_plan_s {
         if (h_err) cudaFreeHost(h_err);
         if (d_trace) cudaFree(d_trace);
         if (d_btimes) cudaFree(d_btimes);
+        if (d_bwd) cudaFree(d_bwd);
+        if (d_grad) cudaFree(d_grad);
     }
 };
 
@@ -217,13 +223,40 @@ int upload(qt_plan_t P) {
         QT_CUDA(cudaEventCreate(&r[0]));
         QT_CUDA(cudaEventCreate(&r[1]));
     }
+    if (hp.cfg.with_grad) {
+        const size_t b0 = (bytes_of(hp.op_param) + 255) / 256 * 256;
+        const size_t b1 = (bytes_of(hp.net_graph) + 255) / 256 * 256;
+        const size_t b2 = (bytes_of(hp.bwd_bucket) + 255) / 256 * 256;
+        const size_t b3 = (bytes_of(hp.bwd_tile) + 255) / 256 * 256;
+        QT_CUDA(cudaMalloc(&P->d_bwd, std::max<size_t>(b0 + b1 + b2 + b3, 256)));
+        char* q = static_cast<char*>(P->d_bwd);
+        if (!hp.op_param.empty()) QT_CUDA(cudaMemcpy(q, hp.op_param.data(), bytes_of(hp.op_param), cudaMemcpyHostToDevice));
+        QT_CUDA(cudaMemcpy(q + b0, hp.net_graph.data(), bytes_of(hp.net_graph), cudaMemcpyHostToDevice));
+        if (!hp.bwd_bucket.empty()) {
+            QT_CUDA(cudaMemcpy(q + b0 + b1, hp.bwd_bucket.data(), bytes_of(hp.bwd_bucket), cudaMemcpyHostToDevice));
+            QT_CUDA(cudaMemcpy(q + b0 + b1 + b2, hp.bwd_tile.data(), bytes_of(hp.bwd_tile), cudaMemcpyHostToDevice));
+        }
+        QT_CUDA(cudaMalloc((void**)&P->d_grad, sizeof(double) * 4 * n_graphs * hp.cfg.p));
+        qt::DevBwd& db = P->db;
+        db.buckets = dp.buckets;
+        db.ops = dp.ops;
+        db.op_param = reinterpret_cast<const int8_t*>(q);
+        db.net_graph = reinterpret_cast<const uint32_t*>(q + b0);
+        db.task_bucket = reinterpret_cast<const uint32_t*>(q + b0 + b1);
+        db.task_tile = reinterpret_cast<const uint32_t*>(q + b0 + b1 + b2);
+        db.p = hp.cfg.p;
+        db.arena = P->d_arena;
+        db.cot_delta = hp.cot_off - hp.leaf_elems;
+        db.dleaf_delta = hp.dleaf_off;
+        db.grad = P->d_grad;
+    }
     return QT_OK;
 }
 
 // Everything one evaluation runs after the angles are in place, on stream s.
 int enqueue_eval(qt_plan_t P, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     qt::HostPlan& hp = P->hp;
-    QT_CUDA(qt::launch_leaf_fill(P->dtype, P->d_angles, (int)hp.graphs.size(), hp.cfg.p, P->d_arena, s));
+    QT_CUDA(qt::launch_leaf_fill(P->dtype, P->d_angles, (int)hp.graphs.size(), hp.cfg.p, P->d_arena, hp.dleaf_off, s));
     if (P->sched == QT_SCHED_PERSISTENT) {
         QT_CUDA(cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, s));
         if (P->d_btimes) {  // starts to all ones (min), ends to zero (max)
@@ -509,9 +542,51 @@ int qt_energy_batch(qt_plan_t P, const double* gammas, const double* betas, doub
     return run_eval(P, gammas, betas, cuda_stream, edge_zz, energies, true);
 }
 
-int qt_energy_grad(qt_plan_t P, const double*, const double*, double*, double*, double*, void*) {
+int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, double* energy, double* dE_dgamma,
+                   double* dE_dbeta, void* cuda_stream) {
     if (!P) return QT_EINVAL;
-    return QT_ESTATE;
+    if (P->host_only || !P->hp.cfg.with_grad) return QT_ESTATE;
+    const qt::HostPlan& hp = P->hp;
+    const int G = (int)hp.graphs.size(), p = hp.cfg.p;
+    // forward pass: every result stays in the arena
+    int rc = run_eval(P, gammas, betas, cuda_stream, nullptr, nullptr, true);
+    if (rc != QT_OK) return rc;
+    cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : P->stream;
+    // reverse sweep
+    QT_CUDA(cudaMemsetAsync(static_cast<char*>(P->d_arena) + hp.cot_off * P->esize, 0,
+                            (hp.total_elems - hp.cot_off) * P->esize, s));
+    QT_CUDA(cudaMemsetAsync(P->d_grad, 0, sizeof(double) * 2 * G * p, s));
+    QT_CUDA(qt::launch_seed_roots(P->dtype, P->de, (int)hp.nets.size(), P->db.cot_delta, s));
+    for (int lv = hp.n_levels - 1; lv >= 0; --lv) {
+        qt::DevBwd db = P->db;
+        db.task_bucket += hp.bwd_level_begin[lv];
+        db.task_tile += hp.bwd_level_begin[lv];
+        db.n_tasks = hp.bwd_level_begin[lv + 1] - hp.bwd_level_begin[lv];
+        QT_CUDA(qt::launch_backward(P->dtype, db, s));
+    }
+    double* d_dg = P->d_grad + 2 * G * p;
+    double* d_db = d_dg + G * p;
+    QT_CUDA(qt::launch_grad_final(P->d_grad, G, p, d_dg, d_db, s));
+    QT_CUDA(cudaMemcpyAsync(P->h_err, &P->dp.ctl->error, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    bool host_out = false;
+    if (energy) {
+        QT_CUDA(cudaMemcpyAsync(energy, P->de.energies, sizeof(double) * G, cudaMemcpyDefault, s));
+        host_out |= is_host_ptr(energy);
+    }
+    if (dE_dgamma) {
+        QT_CUDA(cudaMemcpyAsync(dE_dgamma, d_dg, sizeof(double) * G * p, cudaMemcpyDefault, s));
+        host_out |= is_host_ptr(dE_dgamma);
+    }
+    if (dE_dbeta) {
+        QT_CUDA(cudaMemcpyAsync(dE_dbeta, d_db, sizeof(double) * G * p, cudaMemcpyDefault, s));
+        host_out |= is_host_ptr(dE_dbeta);
+    }
+    if (host_out || !cuda_stream) {
+        QT_CUDA(cudaStreamSynchronize(s));
+        P->err_pending = false;
+        return check_error_word(P);
+    }
+    return QT_OK;
 }
 
 int qt_last_imag(qt_plan_t P, double* edge_imag) {

@@ -1016,7 +1016,7 @@ __global__ void __launch_bounds__(kPersistentThreads) k_per_bucket(DevPlan dp, u
 // the mixer exp(-i beta_l X), its conjugate. Entry x + 2y: x is the bit of the
 // tensor's earlier variable. Both rank-2 kinds are symmetric in (x, y).
 template <typename R>
-__global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename CT<R>::c* arena) {
+__global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename CT<R>::c* arena, uint64_t dleaf_off) {
     using C = typename CT<R>::c;
     const int L = 2 + 4 * p;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1025,6 +1025,7 @@ __global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename 
     const double* gam = angles + (size_t)g * p;                      // all gammas first,
     const double* bet = angles + (size_t)n_graphs * p + (size_t)g * p;  // then all betas
     double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+    double dre[4] = {0, 0, 0, 0}, dim[4] = {0, 0, 0, 0};  // d/dgamma_l or d/dbeta_l of the same entries
     if (s == 0) {
         re[0] = re[1] = 0.70710678118654752440;
     } else if (s == 1) {
@@ -1036,16 +1037,22 @@ __global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename 
         for (int y = 0; y < 2; ++y)
             for (int x = 0; x < 2; ++x) {
                 if (k < 2) {
+                    // exp(-/+ i g a), a = s_x s_y; its derivative is -/+ i a times itself
                     const double ss = (1 - 2 * x) * (1 - 2 * y);
                     double sn, cs;
                     sincos(gam[l] * ss, &sn, &cs);
                     re[x + 2 * y] = cs;
                     im[x + 2 * y] = -sign * sn;
+                    dre[x + 2 * y] = -ss * sn;
+                    dim[x + 2 * y] = -sign * ss * cs;
                 } else {
+                    // [[c, -/+ i s], [-/+ i s, c]]; derivative [[-s, -/+ i c], [-/+ i c, -s]]
                     double sn, cs;
                     sincos(bet[l], &sn, &cs);
                     re[x + 2 * y] = x == y ? cs : 0.0;
                     im[x + 2 * y] = x == y ? 0.0 : -sign * sn;
+                    dre[x + 2 * y] = x == y ? -sn : 0.0;
+                    dim[x + 2 * y] = x == y ? 0.0 : -sign * cs;
                 }
             }
     }
@@ -1055,6 +1062,15 @@ __global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename 
         v.x = (R)re[i];
         v.y = (R)im[i];
         T[i] = v;
+    }
+    if (dleaf_off) {
+        C* D = T + dleaf_off;
+        for (int i = 0; i < 4; ++i) {
+            C v;
+            v.x = (R)dre[i];
+            v.y = (R)dim[i];
+            D[i] = v;
+        }
     }
 }
 
@@ -1089,13 +1105,192 @@ __global__ void k_epilogue(DevEpilogue de) {
 
 }  // namespace
 
-cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, cudaStream_t s) {
+cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, uint64_t dleaf_off,
+                             cudaStream_t s) {
     const int total = n_graphs * (2 + 4 * p);
     const int threads = 128, blocks = (total + threads - 1) / threads;
     if (dtype == QT_C128)
-        k_leaf_fill<double><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<double2*>(arena));
+        k_leaf_fill<double><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<double2*>(arena), dleaf_off);
     else
-        k_leaf_fill<float><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<float2*>(arena));
+        k_leaf_fill<float><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<float2*>(arena), dleaf_off);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reverse sweep (the adjoint of bucket elimination).
+//
+// A network's value V is a polynomial in the gate entries, so dV/dtheta =
+// sum over gate tensors g and entries i of (dV/dT_g[i]) (dT_g[i]/dtheta). The
+// cotangent of bucket b's result, Rbar, is complete once b's consumer has
+// been swept; the cotangent contribution to operand s from output o and
+// summed value x is Rbar[o] * prod_{t != s} T_t[2 pext(o, M_t) + x]. Results
+// of earlier buckets receive these contributions in their cotangent buffers
+// (atomically, since several outputs may share an entry); gate tensors turn
+// them at once into Re(contribution * dT_g/dtheta), summed per parameter.
+// E = |E|/2 - 1/2 sum Re V, so dE/dtheta = -1/2 times those sums.
+// ---------------------------------------------------------------------------
+
+// Each root's cotangent is the product of its network's other roots (1 when,
+// as usual, the network is connected).
+template <typename R>
+__global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
+    using C = typename CT<R>::c;
+    C* arena = static_cast<C*>(const_cast<void*>(de.arena));
+    const int net = blockIdx.x * blockDim.x + threadIdx.x;
+    if (net >= n_nets) return;
+    for (uint32_t r = de.net_first_root[net]; r < de.net_first_root[net + 1]; ++r) {
+        double vr = 1.0, vi = 0.0;
+        for (uint32_t q = de.net_first_root[net]; q < de.net_first_root[net + 1]; ++q) {
+            if (q == r) continue;
+            const C v = arena[de.buckets[de.root_bucket[q]].out_off];
+            const double nr = vr * (double)v.x - vi * (double)v.y, ni = vr * (double)v.y + vi * (double)v.x;
+            vr = nr;
+            vi = ni;
+        }
+        C c;
+        c.x = (R)vr;
+        c.y = (R)vi;
+        arena[de.buckets[de.root_bucket[r]].out_off + cot_delta] = c;
+    }
+}
+
+__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+// One tile (up to 2^kBwdTileBits outputs) of one bucket's reverse sweep, by one warp.
+template <typename R, int NMAX>
+__device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane) {
+    using C = typename CT<R>::c;
+    C* arena = static_cast<C*>(db.arena);
+    const DBucket B = db.buckets[b];
+    const int n = B.n_ops;
+    uint64_t off[NMAX];
+    uint32_t mask[NMAX];
+    bool leaf[NMAX];
+    int prm[NMAX];
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) {
+        if (t < n) {
+            const DOperand o = db.ops[B.op_begin + t];
+            off[t] = o.off;
+            mask[t] = o.mask;
+            leaf[t] = (o.flags & kOpLeaf) != 0u;
+            prm[t] = db.op_param[B.op_begin + t];
+        } else {
+            off[t] = 0;
+            mask[t] = 0;
+            leaf[t] = true;
+            prm[t] = -1;
+        }
+    }
+    R acc[NMAX], comp[NMAX];  // per-lane compensated (Kahan) sums of Re(c dT)
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) acc[t] = comp[t] = (R)0;
+    const int tb = min((int)B.n_out, kBwdTileBits);
+    const uint32_t obase = tile << tb;
+    for (uint32_t j = lane; j < (1u << tb); j += 32) {
+        const uint32_t o = obase + j;
+        const C r = __ldcg(arena + B.out_off + db.cot_delta + o);
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            C P[NMAX], S[NMAX];
+            uint32_t idx[NMAX];
+#pragma unroll
+            for (int t = 0; t < NMAX; ++t) {
+                idx[t] = 2u * pext_u32(o, mask[t]) + (uint32_t)x;
+                if (t < n) P[t] = __ldcg(arena + off[t] + idx[t]);
+            }
+            // suffix products S[t] = prod_{u > t} P[u]
+            C acc_s;
+            acc_s.x = (R)1;
+            acc_s.y = (R)0;
+#pragma unroll
+            for (int t = NMAX - 1; t >= 0; --t) {
+                if (t < n) {
+                    S[t] = acc_s;
+                    acc_s = cmul(acc_s, P[t]);
+                }
+            }
+            C pre = r;
+#pragma unroll
+            for (int t = 0; t < NMAX; ++t) {
+                if (t < n) {
+                    const C c = cmul(pre, S[t]);  // Rbar[o] * prod_{u != t} P[u]
+                    if (leaf[t]) {
+                        if (prm[t] >= 0) {
+                            const C d = __ldcg(arena + off[t] + db.dleaf_delta + idx[t]);
+                            const R v = c.x * d.x - c.y * d.y;
+                            const R y = v - comp[t];
+                            const R s2 = acc[t] + y;
+                            comp[t] = (s2 - acc[t]) - y;
+                            acc[t] = s2;
+                        }
+                    } else {
+                        atomic_add_c(arena + off[t] + db.cot_delta + idx[t], c);
+                    }
+                    pre = cmul(pre, P[t]);
+                }
+            }
+        }
+    }
+    const uint32_t g = db.net_graph[B.net];
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) {
+        if (t < n && prm[t] >= 0) {
+            double v = (double)acc[t];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+            if (lane == 0) atomicAdd(&db.grad[(size_t)g * 2 * db.p + prm[t]], v);
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_backward(DevBwd db) {
+    const uint32_t w = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= db.n_tasks) return;
+    const uint32_t b = db.task_bucket[w];
+    const uint32_t tile = db.task_tile[w];
+    if (db.buckets[b].n_ops <= 8)
+        bwd_tile<R, 8>(db, b, tile, lane);
+    else
+        bwd_tile<R, kMaxOps>(db, b, tile, lane);
+}
+
+__global__ void k_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_graphs * p) return;
+    const int g = i / p, k = i % p;
+    dgamma[i] = -0.5 * grad[(size_t)g * 2 * p + k];
+    dbeta[i] = -0.5 * grad[(size_t)g * 2 * p + p + k];
+}
+
+cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s) {
+    const int blocks = (n_nets + 127) / 128;
+    if (dtype == QT_C128)
+        k_seed_roots<double><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);
+    else
+        k_seed_roots<float><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(int dtype, const DevBwd& db, cudaStream_t s) {
+    if (db.n_tasks == 0) return cudaSuccess;
+    const uint32_t blocks = (db.n_tasks + 7) / 8;
+    if (dtype == QT_C128)
+        k_backward<double><<<blocks, 256, 0, s>>>(db);
+    else
+        k_backward<float><<<blocks, 256, 0, s>>>(db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta, cudaStream_t s) {
+    const int n = n_graphs * p;
+    k_grad_final<<<(n + 127) / 128, 128, 0, s>>>(grad, n_graphs, p, dgamma, dbeta);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,27 @@ struct DevEpilogue {
     double* energies;  // n_graphs
 };
 
-cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, cudaStream_t s);
+// Everything the reverse sweep reads and writes.
+struct DevBwd {
+    const DBucket* buckets;
+    const DOperand* ops;
+    const int8_t* op_param;     // per operand: gate parameter (k: gamma_k, p+k: beta_k), -1 none
+    const uint32_t* net_graph;  // graph of each network
+    const uint32_t* task_bucket;// tasks of one level: (bucket, tile)
+    const uint32_t* task_tile;
+    uint32_t n_tasks;
+    int32_t p;
+    void* arena;
+    uint64_t cot_delta;         // cotangent of the result at offset X lives at X + cot_delta
+    uint64_t dleaf_delta;       // derivative of the gate tensor at offset X lives at X + dleaf_delta
+    double* grad;               // n_graphs x 2p accumulators: sum Re <cotangent, dT/dtheta>
+};
+
+cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, uint64_t dleaf_off,
+                             cudaStream_t s);
+cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s);
+cudaError_t launch_backward(int dtype, const DevBwd& db, cudaStream_t s);
+cudaError_t launch_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta, cudaStream_t s);
 cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream_t s);
 cudaError_t launch_per_bucket(int dtype, uint32_t bucket, uint32_t n_tasks, const DevPlan& dp, cudaStream_t s);
 cudaError_t launch_epilogue(int dtype, const DevEpilogue& de, cudaStream_t s);

@@ -481,7 +481,11 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     const uint64_t esize = cfg.dtype == 1 ? 16 : 8;
     const uint64_t align = 128 / esize;
     const int L = leaf_slots_per_graph(cfg.p);
-    hp->leaf_elems = align_up((uint64_t)graphs.size() * L * kLeafSlots, align);
+    const uint64_t leaf_vals = (uint64_t)graphs.size() * L * kLeafSlots;
+    hp->dleaf_off = cfg.with_grad ? leaf_vals : 0;
+    hp->leaf_elems = align_up(cfg.with_grad ? 2 * leaf_vals : leaf_vals, align);
+    hp->op_param.clear();
+    hp->net_graph.clear();
     uint64_t off = hp->leaf_elems;
     hp->net_first_bucket.assign(1, 0);
     hp->net_first_root.assign(1, 0);
@@ -559,6 +563,15 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
                 hp->op_leaf_kind.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].kind);
                 hp->op_leaf_layer.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].layer);
                 hp->op_rank.push_back(op.rank);
+                {
+                    int8_t prm = -1;
+                    if (op.src < 0) {
+                        const Leaf& lf = net.leaves[op.leaf];
+                        if (lf.kind == QT_LEAF_ZZ || lf.kind == QT_LEAF_ZZ_CONJ) prm = (int8_t)lf.layer;
+                        if (lf.kind == QT_LEAF_RX || lf.kind == QT_LEAF_RX_CONJ) prm = (int8_t)(cfg.p + lf.layer);
+                    }
+                    hp->op_param.push_back(prm);
+                }
                 opbytes += std::ldexp(1.0, op.rank);
             }
             hp->buckets.push_back(d);
@@ -574,6 +587,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
         }
         hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());
         hp->net_first_root.push_back((uint32_t)hp->root_bucket.size());
+        hp->net_graph.push_back((uint32_t)net.graph);
     }
     // intermediate operands point at their producer's result and name it
     for (size_t o = 0; o < hp->operands.size(); ++o)
@@ -635,6 +649,24 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
         }
     } else {
         simulate_order(hp);
+    }
+    // reverse sweep: tiles of every bucket, level by level (a bucket's result
+    // cotangent is complete once its consumer, at a higher level, is done)
+    hp->bwd_bucket.clear();
+    hp->bwd_tile.clear();
+    hp->bwd_level_begin.assign(1, 0);
+    if (cfg.with_grad) {
+        for (int lv = 0; lv < hp->n_levels; ++lv) {
+            for (uint32_t i = hp->level_first_bucket[lv]; i < hp->level_first_bucket[lv + 1]; ++i) {
+                const uint32_t b = hp->by_level[i];
+                const int tb = std::min<int>(hp->buckets[b].n_out, kBwdTileBits);
+                for (uint32_t t = 0; t < (1u << (hp->buckets[b].n_out - tb)); ++t) {
+                    hp->bwd_bucket.push_back(b);
+                    hp->bwd_tile.push_back(t);
+                }
+            }
+            hp->bwd_level_begin.push_back((uint32_t)hp->bwd_bucket.size());
+        }
     }
     hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return QT_OK;

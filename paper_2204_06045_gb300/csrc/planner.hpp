@@ -95,7 +95,13 @@ struct HostPlan {
     std::vector<uint32_t> level_first_bucket;  // buckets sorted by level (for the adjoint)
     std::vector<uint32_t> by_level;
 
-    uint64_t leaf_elems = 0;   // leaf table size in elements
+    uint64_t leaf_elems = 0;   // leaf table size in elements (gate values, then their derivatives with_grad)
+    uint64_t dleaf_off = 0;    // element offset of the derivative table (gradient plans)
+    std::vector<int8_t> op_param;        // per operand: parameter of a gate tensor (k: gamma_k, p+k: beta_k), -1 none
+    std::vector<uint32_t> net_graph;     // graph of each network
+    std::vector<uint32_t> bwd_bucket;    // reverse sweep: (bucket, tile) tasks, deepest level last
+    std::vector<uint32_t> bwd_tile;
+    std::vector<uint32_t> bwd_level_begin;  // n_levels + 1 offsets into the task arrays, by level
     uint64_t arena_elems = 0;  // leaf table + results
     uint64_t cot_off = 0;      // start of the cotangent region (gradient plans)
     uint64_t total_elems = 0;

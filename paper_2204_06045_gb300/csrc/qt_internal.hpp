@@ -29,6 +29,7 @@ constexpr int kLeafBits = 5;
 constexpr int kMaxFoldLeaves = 8;
 constexpr uint8_t kBucketFoldLeaves = 1;
 constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim (default)
+constexpr int kBwdTileBits = 9;      // outputs per reverse-sweep tile, log2
 constexpr int kDefaultTileBits = 9;  // at most 512 outputs per tile (default); measured best on GB300
 
 // One bucket on the device. 64 bytes.

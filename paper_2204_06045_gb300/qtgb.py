@@ -349,3 +349,38 @@ def plan_subset(n: int, edges, p: int, sel, **opts) -> Plan:
 
 def plan_batch(graphs, p: int, **opts) -> Plan:
     return Plan.create_batch(graphs, p, **opts)
+
+
+def _autograd_function():
+    import torch
+
+    class QAOAEnergy(torch.autograd.Function):
+        """E(gamma, beta) of a single-graph gradient plan as a differentiable torch op.
+
+        forward runs qt_energy_grad (the energy and its adjoint in one call) and
+        keeps the gradient; backward scales it by the incoming gradient.
+        ``gammas`` and ``betas`` are float64 tensors of length p (CPU or CUDA).
+        """
+
+        @staticmethod
+        def forward(ctx, plan, gammas, betas):
+            g = gammas.detach().to(torch.float64).contiguous()
+            b = betas.detach().to(torch.float64).contiguous()
+            if g.is_cuda:
+                torch.cuda.current_stream().synchronize()
+            E, dg, db = plan.energy_grad(g.cpu().numpy(), b.cpu().numpy())
+            ctx.save_for_backward(torch.as_tensor(dg, dtype=torch.float64, device=gammas.device),
+                                  torch.as_tensor(db, dtype=torch.float64, device=betas.device))
+            return torch.as_tensor(E[0], dtype=torch.float64, device=gammas.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dg, db = ctx.saved_tensors
+            return None, grad_out * dg, grad_out * db
+
+    return QAOAEnergy
+
+
+def qaoa_energy(plan: "Plan", gammas, betas):
+    """Differentiable energy: ``qaoa_energy(plan, gammas, betas).backward()`` fills the angle gradients."""
+    return _autograd_function().apply(plan, gammas, betas)

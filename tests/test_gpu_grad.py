@@ -1,0 +1,142 @@
+"""GPU parity of the adjoint: qt_energy_grad through the C ABI.
+
+References: the published p=1 closed form's derivative, the oracle's exact
+parameter-shift gradient on a 2^20 state vector (stored values), central
+finite differences of the complex128 energy (h = 1e-5), and the oracle's
+parameter shift on small graphs. Gradients of the complex128 path must match
+to 1e-6 absolute (1e-8 against exact references), those of the complex64
+path to 1e-4 relative to the largest component.
+"""
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_06045_gb300 import qtgb, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLDEN = Path(__file__).parent / "golden"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_06045_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def grad_plan(n, edges, p, dtype="c128", **kw):
+    return qtgb.plan(n, edges, p, dtype=dtype, with_grad=True, **kw)
+
+
+@pytest.mark.parametrize("name,n,edges", [("petersen", 10, synth.petersen_graph()), ("prism", 6, synth.prism_graph()),
+                                          ("K4", 4, synth.complete_graph(4))])
+def test_p1_matches_closed_form_derivative(name, n, edges):
+    for g, b in [(0.3, 0.7), (1.9, 0.2)]:
+        with grad_plan(n, edges, 1) as pl:
+            E, dg, db = pl.energy_grad([g], [b])
+        cg, cb = oracle.p1_closed_form_grad(n, edges, g, b)
+        assert abs(dg[0] - cg) < 1e-9 and abs(db[0] - cb) < 1e-9
+        assert abs(E[0] - oracle.energy_from_zz(oracle.p1_closed_form(n, edges, g, b))) < 1e-10
+
+
+def _golden_grad():
+    rows = {}
+    for line in (GOLDEN / "c5_n20_p4_gradient.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            rows[k] = np.array([float(x) for x in v])
+    return rows
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-8), ("c64", 1e-4)])
+@pytest.mark.parametrize("sched", ["persistent", "per_bucket"])
+def test_n20_p4_matches_parameter_shift_golden(dtype, tol, sched):
+    rows = _golden_grad()
+    n, p = 20, 4
+    edges = synth.random_regular_graph(n, 1020)
+    with grad_plan(n, edges, p, dtype=dtype, sched=sched) as pl:
+        E, dg, db = pl.energy_grad(rows["gamma"], rows["beta"])
+    ref = np.concatenate([rows["dE_dgamma"], rows["dE_dbeta"]])
+    got = np.concatenate([dg, db])
+    scale = 1.0 if dtype == "c128" else np.abs(ref).max()
+    assert np.abs(got - ref).max() <= tol * scale, (got, ref)
+    assert abs(E[0] - rows["energy"][0]) <= (1e-10 if dtype == "c128" else 1e-5) * abs(E[0])
+
+
+def test_c5_n50_p4_matches_finite_differences():
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    with grad_plan(n, edges, p) as pl, qtgb.plan(n, edges, p, dtype="c128") as pe:
+        E, dg, db = pl.energy_grad(g, b)
+        fd = oracle.grad_fd(lambda G, B: pe.energy(G, B)[1], g, b, h=1e-5)
+        _, E2 = pe.energy(g, b)
+    np.testing.assert_allclose(dg, fd[0], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(db, fd[1], rtol=0, atol=1e-6)
+    assert abs(E[0] - E2) < 1e-10 * abs(E2)
+
+
+def test_c5_c64_gradient_close_to_c128():
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    with grad_plan(n, edges, p, dtype="c128") as a, grad_plan(n, edges, p, dtype="c64") as c:
+        _, dg1, db1 = a.energy_grad(g, b)
+        _, dg2, db2 = c.energy_grad(g, b)
+    ref = np.concatenate([dg1, db1])
+    assert np.abs(np.concatenate([dg2, db2]) - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("order", ["simulated", "ready_queue"])
+def test_batch_gradient_matches_parameter_shift(order):
+    p = 2
+    graphs = [(8, synth.random_regular_graph(8, 3)), (10, synth.random_regular_graph(10, 4)),
+              (12, synth.random_regular_graph(12, 5))]
+    G = np.array([synth.angles(p, s)[0] for s in (3, 4, 5)])
+    B = np.array([synth.angles(p, s)[1] for s in (3, 4, 5)])
+    with qtgb.plan_batch(graphs, p, dtype="c128", with_grad=True, order=order) as pl:
+        E, dg, db = pl.energy_grad(G, B)
+    for i, (n, e) in enumerate(graphs):
+        ps = oracle.grad_param_shift(n, e, G[i], B[i])
+        np.testing.assert_allclose(dg[i * p:(i + 1) * p], ps[0], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(db[i * p:(i + 1) * p], ps[1], rtol=0, atol=1e-9)
+        assert abs(E[i] - oracle.sv_energy(n, e, G[i], B[i])) < 1e-10
+
+
+def test_zero_angles_give_zero_gradient_and_half_edges():
+    n, p = 16, 3
+    edges = synth.random_regular_graph(n, 6)
+    with grad_plan(n, edges, p) as pl:
+        E, dg, db = pl.energy_grad(np.zeros(p), np.zeros(p))
+    assert abs(E[0] - edges.shape[0] / 2) < 1e-12
+    # at gamma = beta = 0 the first-order change in beta still moves E, in gamma it does not
+    assert np.abs(dg).max() < 1e-12
+
+
+def test_torch_autograd_function():
+    n, p = 12, 2
+    edges = synth.random_regular_graph(n, 9)
+    g0, b0 = synth.angles(p, 9)
+    with grad_plan(n, edges, p) as pl:
+        g = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
+        b = torch.tensor(b0, dtype=torch.float64, requires_grad=True)
+        E = qtgb.qaoa_energy(pl, g, b)
+        (2.0 * E).backward()
+    ps = oracle.grad_param_shift(n, edges, g0, b0)
+    np.testing.assert_allclose(g.grad.numpy(), 2 * ps[0], atol=1e-9)
+    np.testing.assert_allclose(b.grad.numpy(), 2 * ps[1], atol=1e-9)
+    assert abs(E.item() - oracle.sv_energy(n, edges, g0, b0)) < 1e-10
+
+
+def test_energy_only_plan_refuses_gradient():
+    n, p = 10, 1
+    edges = synth.random_regular_graph(n, 1)
+    with qtgb.plan(n, edges, p) as pl:
+        with pytest.raises(qtgb.QTError) as ei:
+            pl.energy_grad([0.1], [0.2])
+        assert ei.value.code == qtgb.QT_ESTATE
