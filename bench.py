@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--workload", choices=["c2", "c3", "c5"], default="c2",
+                    help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5); "
+                         "c3: 64-graph batch; c5: gradients on N=50 p=4")
+    ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
     return ap.parse_args()
 
 
@@ -231,6 +235,42 @@ def accuracy(zz, E, ref_zz, ref_E):
             "rel_err_energy": float(abs(E - ref_E) / abs(ref_E))}
 
 
+def wide_buckets(peak, torch):
+    """HBM GB/s of the persistent kernel on every bucket of width >= 24, each run alone.
+
+    Workload: random 3-regular N=1000 (seed 1000), p=5; the lightcone networks
+    of the edges whose plain greedy order reaches a maximum bucket width of
+    26..28 (chosen on a host-only plan of every edge)."""
+    from paper_2204_06045_gb300 import qtgb, synth
+    n, p, seed = 1000, 5, 1000
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, host_only=True) as hp:
+        B, _ = hp.export()
+    mw = np.zeros(edges.shape[0], dtype=np.int64)
+    np.maximum.at(mw, B["network"], B["width"])
+    sel = np.nonzero((mw >= 26) & (mw <= 28))[0]
+    out = {"workload": f"3-regular N={n} seed {seed}, p={p}: {sel.size} lightcone networks with greedy max width "
+                       f"26..28; every bucket of width >= 24, timed alone (mean of 3 launches after 1)",
+           "edges": sel.tolist()}
+    for dtype in ("c64", "c128"):
+        with qtgb.plan_subset(n, edges, p, sel, dtype=dtype) as pl:
+            pl.energy(g, b)  # leaves real data in every operand
+            Bs, _ = pl.export()
+            tot_b = tot_ms = 0.0
+            per = []
+            for bk in np.nonzero(Bs["width"] >= 24)[0]:
+                ms, by = pl.bucket_time(int(bk), reps=3)
+                tot_b += by
+                tot_ms += ms
+                per.append(by / ms / 1e6)
+        agg = tot_b / tot_ms / 1e6
+        out[dtype] = {"buckets": len(per), "agg_gbs": agg, "median_gbs": float(np.median(per)),
+                      "max_gbs": float(np.max(per)), "min_gbs": float(np.min(per)), "frac_of_peak": agg / peak,
+                      "bytes": tot_b, "ms": tot_ms}
+    return out
+
+
 def time_device(pl, gd, bd, zz, E, steps, warmup, dist, torch):
     s = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -339,11 +379,89 @@ def run_ours(args, rank, world, local_rank):
         "plan": main["plan"], "check": main["check"],
         "c128": {k: results["c128"][k] for k in ("value", "ms_per_step", "e2e", "roofline", "clocks", "plan", "check")},
     }
+    if world == 1 and not args.no_buckets:
+        line["bucket_gbs"] = wide_buckets(peak, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_c3(args, world, local_rank):
+    """64 seeded graphs, N ~ U{50..1000} even, p=3, per-graph angles: one persistent launch per batch."""
+    import torch
+    from paper_2204_06045_gb300 import build, qtgb, synth
+    torch.cuda.set_device(local_rank)
+    build.build()
+    graphs = synth.batch(64, 3, lo=50, hi=1000, base_seed=1000)
+    G = np.array([g for _, _, g, _ in graphs])
+    Bt = np.array([b for _, _, _, b in graphs])
+    res = {}
+    for dtype, sched, steps in (("c64", "persistent", args.steps), ("c128", "persistent", args.steps),
+                                ("c128", "per_bucket", 1)):
+        with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], 3, dtype=dtype, sched=sched) as pl:
+            st = pl.stats()
+            gd = torch.tensor(G.ravel(), dtype=torch.float64, device="cuda")
+            bd = torch.tensor(Bt.ravel(), dtype=torch.float64, device="cuda")
+            en = torch.zeros(64, dtype=torch.float64, device="cuda")
+            s = torch.cuda.current_stream()
+            for _ in range(1 if sched == "per_bucket" else args.warmup):
+                pl.energy_batch(gd, bd, energies=en, stream=s)
+            pl.sync(s)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                pl.energy_batch(gd, bd, energies=en, stream=s)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[f"{dtype}_{sched}"] = {"ms_per_step": ms, "graph_evals_per_s": 64 / (ms * 1e-3), "steps": steps,
+                                       "buckets": st["n_buckets"], "alg_bytes": st["alg_bytes"]}
+    main = res["c64_persistent"]
+    line = {"metric": "batched QAOA graph-evaluations/s (64 graphs, N in [50,1000], p=3)",
+            "value": main["graph_evals_per_s"], "unit": "graph-evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "64 seeded random 3-regular graphs, N uniform even in [50,1000] (synth.batch), "
+                                   "p=3, per-graph angles; every edge's lightcone network in one persistent launch"},
+            "plain_c128_per_bucket": res["c128_per_bucket"], "c128_persistent": res["c128_persistent"],
+            "speedup_vs_plain_c128": res["c128_per_bucket"]["ms_per_step"] / main["ms_per_step"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_c5(args, world, local_rank):
+    """dE/dgamma_k, dE/dbeta_k on the seeded random 3-regular N=50 (seed 1000), p=4."""
+    import torch
+    from paper_2204_06045_gb300 import build, qtgb, synth
+    torch.cuda.set_device(local_rank)
+    build.build()
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    res = {}
+    for dtype in ("c64", "c128"):
+        with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True) as pl:
+            for _ in range(args.warmup):
+                pl.energy_grad(g, b)
+            steps = max(1, min(args.steps, 20))
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                E, dg, db = pl.energy_grad(g, b)
+            dt = (time.perf_counter() - t0) / steps
+            res[dtype] = {"ms_per_step": dt * 1e3, "grad_evals_per_s": 1 / dt, "steps": steps,
+                          "dE_dgamma": dg.tolist(), "dE_dbeta": db.tolist(), "energy": float(E[0])}
+    line = {"metric": "QAOA energy+gradient evals/s (3-reg N=50 p=4)", "value": res["c64"]["grad_evals_per_s"],
+            "unit": "grad-evals/s", "n_gpus": world, "steps": res["c64"]["steps"], "warmup": args.warmup,
+            "ms_per_step": res["c64"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "random 3-regular N=50 seed 1000, p=4: energy and its 2p angle derivatives by "
+                                   "the adjoint of the bucket elimination (host arrays in and out)"},
+            "c128": res["c128"],
+            "c64_vs_c128_max_abs_diff": float(np.max(np.abs(np.array(res["c64"]["dE_dgamma"] + res["c64"]["dE_dbeta"])
+                                                          - np.array(res["c128"]["dE_dgamma"] + res["c128"]["dE_dbeta"]))))}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -353,6 +471,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "c3":
+        if rank == 0:
+            run_c3(args, world, local_rank)
+    elif args.workload == "c5":
+        if rank == 0:
+            run_c5(args, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
