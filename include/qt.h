@@ -251,6 +251,42 @@ int qt_trace_bucket_times(qt_plan_t plan, uint64_t *start_end_ns);
  * wait runs out) rather than wait forever. Use a plan that is then freed. */
 int qt_debug_stall_bucket(qt_plan_t plan, int64_t bucket);
 
+/*
+ * Energy without any device allocation. The paper has no counterpart: this
+ * entry point serves callers that must not allocate device memory during the
+ * call, e.g. code running inside a custom allocator or memory pool, or a host
+ * that fixes its device-memory footprint at start-up and forbids cudaMalloc
+ * afterwards. qt_energy's plans own device memory made by qt_plan; this call
+ * instead runs the same persistent kernel with all of its device memory (plan
+ * arrays, counters, queue, gate tables and intermediate results) inside one
+ * static device array of QT_NOALLOC_SCRATCH_BYTES, built into the library.
+ *
+ *  - plan: any plan, typically one made with opts.host_only = 1 (no device
+ *    memory at all). Single-graph or batch plans; the plan's dtype is used, its
+ *    schedule option is not (the persistent kernel always runs).
+ *  - gammas/betas: n_graphs*p doubles each (graph-major), host or device.
+ *  - energies: n_graphs doubles, edge_zz: the per-edge values of every graph
+ *    back to back; host or device, either may be NULL. Written only on success.
+ *  - cuda_stream: the work is queued there (NULL: the default stream); the call
+ *    waits for it to finish before returning, so it is synchronous.
+ * Returns QT_ENOMEM (with qt_last_error_detail() naming both sizes) if the plan
+ * needs more than QT_NOALLOC_SCRATCH_BYTES, checked before any CUDA call, and
+ * QT_ETIMEOUT / QT_EBOUNDS as qt_energy does. It calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the array's device address with cudaGetSymbolAddress and sets the kernel's
+ * shared-memory attribute; make that first call before any stream capture.
+ * From then on the array stays resident on every device that made a call,
+ * until the process exits.
+ * Every call, from every thread and plan, shares the one array and leaves its
+ * contents behind; each call resets what must start at zero. Calls whose GPU
+ * work overlaps (concurrent host threads, or different streams) race on the
+ * array and give wrong results: serialise them.
+ */
+#define QT_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20) /* 64 MiB of device memory */
+int qt_energy_noalloc(qt_plan_t plan, const double *gammas, const double *betas, double *energies,
+                      double *edge_zz, void *cuda_stream);
+
 void qt_plan_free(qt_plan_t plan);
 
 const char *qt_error_string(int code);

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -724,5 +725,181 @@ const char* qt_error_string(int code) {
 const char* qt_version(void) { return "qtgb 0.1 sm_103a"; }
 
 const char* qt_last_error_detail(void) { return g_detail; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// qt_energy_noalloc: the persistent-kernel evaluation with every piece of
+// device memory it needs (plan arrays, counters, intermediate results) taken
+// from one statically sized array, so the call itself allocates nothing.
+
+// The only device memory qt_energy_noalloc uses. In host code this name
+// denotes a host-side stand-in, not the device array: host code gets the
+// device address from cudaGetSymbolAddress (per device, in scratch_setup).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxScratchDevices = 64;
+struct ScratchDevice {
+    void* base = nullptr;  // device address of g_noalloc_scratch on this device
+    int grid[2] = {0, 0};  // persistent grid for complex64 / complex128 (0: not yet set up)
+};
+std::mutex g_scratch_mu;
+ScratchDevice g_scratch_dev[kMaxScratchDevices];
+
+size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Byte offsets of every piece inside the scratch array.
+struct ScratchLayout {
+    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net;
+    size_t counters, counters_bytes, ctl_bytes, cnt_bytes;
+    size_t angles, out, arena, total;
+};
+
+ScratchLayout scratch_layout(const qt::HostPlan& hp, size_t esize) {
+    ScratchLayout L{};
+    size_t at = 0;
+    auto take = [&at](size_t bytes) {
+        const size_t off = at;
+        at += pad256(bytes);
+        return off;
+    };
+    const size_t nb = hp.buckets.size();
+    L.buckets = take(nb * sizeof(qt::DBucket));
+    L.ops = take((hp.operands.size() + qt::kMaxOps) * sizeof(qt::DOperand));
+    L.runs = take(hp.runs.size() * sizeof(qt::DRun));
+    L.net_first_root = take(hp.net_first_root.size() * sizeof(uint32_t));
+    L.root_bucket = take(hp.root_bucket.size() * sizeof(uint32_t));
+    L.graph_first_net = take(hp.graph_first_net.size() * sizeof(int32_t));
+    L.ctl_bytes = 256;
+    L.cnt_bytes = pad256(2 * nb * sizeof(uint32_t));
+    L.counters_bytes = L.ctl_bytes + L.cnt_bytes + (size_t)(hp.n_groups - hp.runs.size()) * sizeof(qt::DSlot);
+    L.counters = take(L.counters_bytes);
+    L.angles = take(sizeof(double) * 2 * hp.graphs.size() * hp.cfg.p);
+    L.out = take(sizeof(double) * (2 * hp.nets.size() + hp.graphs.size()));
+    L.arena = take((size_t)hp.total_elems * esize);
+    L.total = at;
+    return L;
+}
+
+// Once per device (under a lock, with that device current): the device
+// address of the scratch array, and the persistent kernel's shared-memory
+// attribute and grid for `dtype`.
+int scratch_setup(int dtype, void** base, int* grid) {
+    int dev = 0;
+    QT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxScratchDevices) {
+        std::snprintf(g_detail, sizeof(g_detail), "device %d is beyond the %d devices qt_energy_noalloc supports", dev,
+                      kMaxScratchDevices);
+        return QT_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    ScratchDevice& sd = g_scratch_dev[dev];
+    if (!sd.base) {
+        void* ptr = nullptr;
+        QT_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        sd.base = ptr;
+    }
+    const int di = dtype == QT_C128 ? 1 : 0;
+    if (!sd.grid[di]) {
+        int sms = 0;
+        QT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int per_sm = qt::persistent_blocks_per_sm(dtype);
+        if (per_sm <= 0) {
+            std::snprintf(g_detail, sizeof(g_detail), "persistent kernel does not fit an SM (%zu bytes of shared memory)",
+                          qt::persistent_smem_bytes(dtype));
+            return QT_ECUDA;
+        }
+        sd.grid[di] = sms * per_sm;
+    }
+    *base = sd.base;
+    *grid = sd.grid[di];
+    return QT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, double* energies, double* edge_zz,
+                      void* cuda_stream) {
+    if (!P || !gammas || !betas) return QT_EINVAL;
+    const qt::HostPlan& hp = P->hp;
+    const ScratchLayout L = scratch_layout(hp, P->esize);
+    if (L.total > (size_t)QT_NOALLOC_SCRATCH_BYTES) {
+        std::snprintf(g_detail, sizeof(g_detail),
+                      "qt_energy_noalloc: the plan needs %zu bytes of device scratch; the static scratch holds %zu",
+                      L.total, (size_t)QT_NOALLOC_SCRATCH_BYTES);
+        return QT_ENOMEM;
+    }
+    void* base_v = nullptr;
+    int grid = 0;
+    int rc = scratch_setup(P->dtype, &base_v, &grid);
+    if (rc != QT_OK) return rc;
+    char* base = static_cast<char*>(base_v);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int G = (int)hp.graphs.size(), p = hp.cfg.p;
+    const size_t n_nets = hp.nets.size();
+
+    // plan arrays (the operand array keeps kMaxOps zeroed entries past its end)
+    QT_CUDA(cudaMemcpyAsync(base + L.buckets, hp.buckets.data(), bytes_of(hp.buckets), cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemcpyAsync(base + L.ops, hp.operands.data(), bytes_of(hp.operands), cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemsetAsync(base + L.ops + bytes_of(hp.operands), 0, qt::kMaxOps * sizeof(qt::DOperand), s));
+    if (!hp.runs.empty())
+        QT_CUDA(cudaMemcpyAsync(base + L.runs, hp.runs.data(), bytes_of(hp.runs), cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemcpyAsync(base + L.net_first_root, hp.net_first_root.data(), bytes_of(hp.net_first_root),
+                            cudaMemcpyHostToDevice, s));
+    if (!hp.root_bucket.empty())
+        QT_CUDA(cudaMemcpyAsync(base + L.root_bucket, hp.root_bucket.data(), bytes_of(hp.root_bucket),
+                                cudaMemcpyHostToDevice, s));
+    static_assert(sizeof(int) == sizeof(int32_t), "graph_first_net is copied as int32");
+    QT_CUDA(cudaMemcpyAsync(base + L.graph_first_net, hp.graph_first_net.data(), bytes_of(hp.graph_first_net),
+                            cudaMemcpyHostToDevice, s));
+    // the array keeps the previous call's contents: counters and the queue start at zero
+    QT_CUDA(cudaMemsetAsync(base + L.counters, 0, L.counters_bytes, s));
+    double* d_angles = reinterpret_cast<double*>(base + L.angles);
+    QT_CUDA(cudaMemcpyAsync(d_angles, gammas, sizeof(double) * G * p, cudaMemcpyDefault, s));
+    QT_CUDA(cudaMemcpyAsync(d_angles + (size_t)G * p, betas, sizeof(double) * G * p, cudaMemcpyDefault, s));
+
+    qt::DevPlan dp{};
+    dp.buckets = reinterpret_cast<const qt::DBucket*>(base + L.buckets);
+    dp.ops = reinterpret_cast<const qt::DOperand*>(base + L.ops);
+    dp.runs = reinterpret_cast<const qt::DRun*>(base + L.runs);
+    dp.n_static = (uint32_t)hp.runs.size();
+    dp.n_groups = (uint32_t)hp.n_groups;
+    dp.n_buckets = (uint32_t)hp.buckets.size();
+    char* cbase = base + L.counters;
+    dp.ctl = reinterpret_cast<qt::DControl*>(cbase);
+    dp.tiles_done = reinterpret_cast<uint32_t*>(cbase + L.ctl_bytes);
+    dp.prod_done = dp.tiles_done + hp.buckets.size();
+    dp.slots = reinterpret_cast<qt::DSlot*>(cbase + L.ctl_bytes + L.cnt_bytes);
+    dp.arena = base + L.arena;
+    dp.spin_limit = P->spin_limit;
+
+    qt::DevEpilogue de{};
+    de.buckets = dp.buckets;
+    de.net_first_root = reinterpret_cast<const uint32_t*>(base + L.net_first_root);
+    de.root_bucket = reinterpret_cast<const uint32_t*>(base + L.root_bucket);
+    de.graph_first_net = reinterpret_cast<const int32_t*>(base + L.graph_first_net);
+    de.n_graphs = G;
+    de.arena = dp.arena;
+    double* d_out = reinterpret_cast<double*>(base + L.out);
+    de.zz = d_out;
+    de.zz_imag = d_out + n_nets;
+    de.energies = d_out + 2 * n_nets;
+
+    QT_CUDA(qt::launch_leaf_fill(P->dtype, d_angles, G, p, dp.arena, hp.dleaf_off, s));
+    QT_CUDA(qt::launch_persistent(P->dtype, grid, dp, s));
+    QT_CUDA(qt::launch_epilogue(P->dtype, de, s));
+    int32_t err[2] = {0, 0};
+    QT_CUDA(cudaMemcpyAsync(err, &dp.ctl->error, sizeof(err), cudaMemcpyDeviceToHost, s));
+    QT_CUDA(cudaStreamSynchronize(s));
+    if (err[0] != 0) return err[0];
+    if (energies) QT_CUDA(cudaMemcpyAsync(energies, de.energies, sizeof(double) * G, cudaMemcpyDefault, s));
+    if (edge_zz) QT_CUDA(cudaMemcpyAsync(edge_zz, de.zz, sizeof(double) * n_nets, cudaMemcpyDefault, s));
+    QT_CUDA(cudaStreamSynchronize(s));
+    return QT_OK;
+}
 
 }  // extern "C"

@@ -22,7 +22,8 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 # every symbol include/qt.h declares
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-           "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail")
+           "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
+           "qt_energy_noalloc")
 
 
 class QTError(RuntimeError):
@@ -85,6 +86,7 @@ def lib():
         L.qt_energy.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_energy_batch.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_energy_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.qt_energy_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_last_imag.argtypes = [vp, dp]
         L.qt_sync.argtypes = [vp, vp]
         L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
@@ -100,7 +102,8 @@ def lib():
         L.qt_last_error_detail.restype = ctypes.c_char_p
         for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
-                     "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times"):
+                     "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
+                     "qt_energy_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -278,6 +281,18 @@ class Plan:
             edge_zz = np.zeros(self.n_networks, dtype=np.float64)
         _check(lib().qt_energy_batch(self._h, _ptr(g), _ptr(b), _ptr(energies), _ptr(edge_zz), _stream_ptr(stream)),
                "qt_energy_batch")
+        return energies, edge_zz
+
+    def energy_noalloc(self, gammas, betas, energies=None, edge_zz=None, stream=None):
+        """Energies through ``qt_energy_noalloc``: the persistent kernel run in the
+        library's static device scratch, with no device allocation by the call.
+        Works on host-only plans. Returns ``(energies, edge_zz)``; synchronous."""
+        g, b = _f64_in(gammas), _f64_in(betas)
+        if energies is None and edge_zz is None:
+            energies = np.zeros(len(self.n_edges), dtype=np.float64)
+            edge_zz = np.zeros(self.n_networks, dtype=np.float64)
+        _check(lib().qt_energy_noalloc(self._h, _ptr(g), _ptr(b), _ptr(energies), _ptr(edge_zz),
+                                       _stream_ptr(stream)), "qt_energy_noalloc")
         return energies, edge_zz
 
     def energy_grad(self, gammas, betas, energy=None, dgamma=None, dbeta=None, stream=None):
