@@ -235,6 +235,23 @@ def accuracy(zz, E, ref_zz, ref_E):
             "rel_err_energy": float(abs(E - ref_E) / abs(ref_E))}
 
 
+def roofline(dtype, st, kms, launches, achieved_gbs, peak_gbs, peak_kind, fma_tflops, traffic):
+    """complex64: HBM-bound (FP32 arithmetic is ~1-3 flop/byte, far below the ridge). complex128:
+    FP64 arithmetic bound on GB300 (its FP64 rate is below 1 flop per byte of HBM bandwidth), so the
+    line reports flops against the measured FP64 FMA rate and keeps the HBM figures beside it."""
+    tflops = st["flops"] / (kms * 1e-3) / 1e12 if kms > 0 else None
+    common = {"kernel": "k_persistent", "kernel_ms": kms, "kernel_launches": launches,
+              "alg_bytes_per_launch": st["alg_bytes"], "flops_per_launch": st["flops"]}
+    hbm = {"achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+           "frac": achieved_gbs / peak_gbs if achieved_gbs else None, "peak_source": peak_kind}
+    alu = {"achieved": tflops, "peak": fma_tflops, "unit": "TFLOP/s",
+           "frac": tflops / fma_tflops if tflops else None,
+           "peak_source": f"measured {'FP64' if dtype == 'c128' else 'FP32'} FMA rate (qt_fma_peak)"}
+    if dtype == "c128":
+        return {"bound": "alu", **alu, "traffic": traffic, "hbm": hbm, **common}
+    return {"bound": "hbm", **hbm, "traffic": traffic, "alu": alu, **common}
+
+
 def wide_buckets(peak, torch):
     """HBM GB/s of the persistent kernel on every bucket of width >= 24, each run alone.
 
@@ -332,6 +349,7 @@ def run_ours(args, rank, world, local_rank):
     m = edges.shape[0]
     peak, peak_kind = measured_peaks()
     ref_zz, ref_E = golden_c2()
+    fma_tflops = {"c64": qtgb.fma_peak("c64"), "c128": qtgb.fma_peak("c128")}
     results = {}
     for dtype in ("c64", "c128"):
         pl = qtgb.plan(n, edges, p, dtype=dtype)
@@ -352,11 +370,8 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step": ms / args.steps,
             "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s",
                     "h2d_bytes_per_step": 2 * p * 8, "d2h_bytes_per_step": (m + 1) * 8},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None, "traffic": ncu_traffic(tag),
-                         "peak_source": peak_kind,
-                         "kernel": "k_persistent", "kernel_ms": kms, "kernel_launches": launches,
-                         "alg_bytes_per_launch": st["alg_bytes"]},
+            "roofline": roofline(dtype, st, kms, launches, achieved, peak, peak_kind, fma_tflops[dtype],
+                                 ncu_traffic(tag)),
             "clocks": clk.summary(),
             "plan": {"buckets": st["n_buckets"], "max_width": st["max_width"], "sum_2w": st["sum_2w"],
                      "tasks": st["n_tasks"], "plan_seconds": st["plan_seconds"]},

@@ -287,6 +287,17 @@ int qt_debug_stall_bucket(qt_plan_t plan, int64_t bucket);
 int qt_energy_noalloc(qt_plan_t plan, const double *gammas, const double *betas, double *energies,
                       double *edge_zz, void *cuda_stream);
 
+/*
+ * Measured FMA throughput of the current device's CUDA cores, in TFLOP/s
+ * (an FMA counts 2 flops): FP32 for QT_C64, FP64 for QT_C128. Independent
+ * FMA chains on every SM, timed with CUDA events after a warm-up launch; a
+ * few milliseconds of GPU time. This is the arithmetic roofline of the
+ * contraction kernels (the paper has no counterpart: it reports flops
+ * against its V100's datasheet peak, §III-C). Allocates and frees a small
+ * buffer; synchronous.
+ */
+int qt_fma_peak(int32_t dtype, double *tflops);
+
 void qt_plan_free(qt_plan_t plan);
 
 const char *qt_error_string(int code);

@@ -23,7 +23,7 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
-           "qt_energy_noalloc")
+           "qt_energy_noalloc", "qt_fma_peak")
 
 
 class QTError(RuntimeError):
@@ -87,6 +87,7 @@ def lib():
         L.qt_energy_batch.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_energy_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.qt_energy_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.qt_fma_peak.argtypes = [i32, dp]
         L.qt_last_imag.argtypes = [vp, dp]
         L.qt_sync.argtypes = [vp, vp]
         L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
@@ -103,10 +104,17 @@ def lib():
         for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
-                     "qt_energy_noalloc"):
+                     "qt_energy_noalloc", "qt_fma_peak"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def fma_peak(dtype: str = "c128") -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device: FP64 for c128, FP32 for c64."""
+    out = ctypes.c_double(0.0)
+    _check(lib().qt_fma_peak({"c64": QT_C64, "c128": QT_C128}[dtype], ctypes.byref(out)), "qt_fma_peak")
+    return out.value
 
 
 def error_string(code: int) -> str:
