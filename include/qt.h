@@ -119,6 +119,11 @@ typedef struct {
     int32_t n_deps;    /* operands that are results of earlier buckets */
     int32_t level;     /* 0 for buckets whose operands are all leaves */
     int32_t var;       /* the summed variable, numbered within the network */
+    int32_t tile_log2; /* log2 of the outputs per tile of the persistent kernel */
+    uint32_t tile_bits;/* the output bits that vary within a tile (popcount = tile_log2): the
+                          lowest ones, so tile c holds outputs c * 2^tile_log2 + j */
+    uint32_t folded;   /* operands (bit i: the bucket's i-th) folded into the per-tile gate table */
+    uint32_t pad;
 } qt_bucket_info;
 
 /* One operand of a bucket. The operand's entry for output index o and summed

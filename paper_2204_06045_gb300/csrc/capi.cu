@@ -402,6 +402,16 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     cfg.run_tiles = o.run_tiles;
     cfg.order = o.order;
     if (o.order < 0 || o.order > 1) return QT_EINVAL;
+    {
+        // warps of the persistent grid (the schedule simulation and the group
+        // sizes of wide buckets assume them): 4 per block, 3 blocks per SM for
+        // complex64 and 2 for complex128; 152 SMs when planning without a GPU
+        int sms = 152, dev = 0;
+        if (!o.host_only && cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        cfg.sim_workers = sms * 4 * (o.dtype == QT_C128 ? 2 : 3);
+    }
     if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
     if (cfg.chunk_log2 < 0 || cfg.chunk_log2 > 24) return QT_EINVAL;
@@ -507,6 +517,12 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.n_deps = (int32_t)d.n_deps;
             o.level = hp.bucket_level[b];
             o.var = hp.bucket_var[b];
+            o.tile_log2 = d.chunk_bits;
+            o.tile_bits = (1u << d.chunk_bits) - 1u;
+            o.folded = 0;
+            for (uint32_t i = 0; i < d.n_ops; ++i)
+                if (hp.operands[d.op_begin + i].folded) o.folded |= 1u << i;
+            o.pad = 0;
         }
     }
     if (operands) {

@@ -53,7 +53,9 @@ class PlanStats(ctypes.Structure):
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
-                         ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32)])
+                         ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32),
+                         ("tile_log2", np.int32), ("tile_bits", np.uint32), ("folded", np.uint32),
+                         ("pad", np.uint32)])
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                           ("mask", np.uint32), ("rank", np.int32), ("pad", np.int32)])
 

@@ -192,3 +192,88 @@ def test_library_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(L, name), name
     assert "sm_103a" in qtgb.version()
+
+
+# ---- the persistent kernel's tile arithmetic, replayed on the host ----------
+
+def _pext(x, m):
+    r, k = 0, 0
+    while m:
+        low = m & -m
+        if x & low:
+            r |= 1 << k
+        m ^= low
+        k += 1
+    return r
+
+
+def _pext_arr(x, m):
+    out = np.zeros_like(x)
+    k = 0
+    while m:
+        low = m & -m
+        out |= ((x & low) != 0).astype(x.dtype) << k
+        m ^= low
+        k += 1
+    return out
+
+
+def _check_tiles(B, O, b, max_tiles=24):
+    """Replays the persistent kernel's staging of one bucket: for a claim group
+    of consecutive tiles (the compressed base index advanced from tile to tile
+    as the kernel does) and a few other tiles, every staged entry the tile loop
+    reads for output o and summed value x is the entry 2 pext(o, M) + x of the
+    operand, copies stay inside the operand, and footprints fit the stage."""
+    n_out = int(B["width"][b]) - 1
+    cb = int(B["tile_log2"][b])
+    low = (1 << cb) - 1
+    assert int(B["tile_bits"][b]) == low and cb <= n_out
+    n_tiles = 1 << (n_out - cb)
+    j = np.arange(1 << cb, dtype=np.int64)
+    rng = np.random.default_rng(b)
+    tiles = list(range(min(n_tiles, 16))) + [int(t) for t in rng.integers(0, n_tiles, size=max_tiles - 16)]
+    ob, no = int(B["op_begin"][b]), int(B["n_ops"][b])
+    folded = int(B["folded"][b])
+    total = 0
+    for t in range(no):
+        M = int(O["mask"][ob + t])
+        if (folded >> t) & 1:
+            # a folded tensor has at most one output bit; one above the tile
+            # is selected by bit (bit - cb) of the tile index
+            assert bin(M).count("1") <= 1
+            if M & ~low:
+                pos = M.bit_length() - 1 - cb
+                assert all(((c << cb) & M != 0) == bool((c >> pos) & 1) for c in tiles)
+            continue
+        rank = int(O["rank"][ob + t])
+        plow = bin(M & low).count("1")
+        mh = M >> cb
+        total += 2 << plow
+        cbase, prev = None, None
+        for c in tiles:
+            if prev is not None and c == prev + 1:  # the kernel's update within a group
+                tb = (c & -c).bit_length() - 1
+                r = bin(mh & ((1 << tb) - 1)).count("1")
+                cbase = cbase - ((1 << r) - 1) + (((mh >> tb) & 1) << r)
+            else:
+                cbase = _pext(c, mh)
+            prev = c
+            stage = 2 * (cbase << plow) + np.arange(2 << plow)  # one bulk copy
+            assert stage.max() < (1 << rank)
+            o = (c << cb) + j
+            assert o.max() < (1 << n_out)
+            for x in (0, 1):
+                np.testing.assert_array_equal(stage[2 * _pext_arr(j, M & low) + x], 2 * _pext_arr(o, M) + x)
+    return total
+
+
+@pytest.mark.parametrize("dtype,stage_elems", [("c64", 1024), ("c128", 512)])
+def test_tile_copy_arithmetic(dtype, stage_elems):
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    with host_plan(n, edges, p, dtype=dtype) as pl:
+        B, O = pl.export()
+    rng = np.random.default_rng(0)
+    wide = [b for b in range(len(B)) if B["width"][b] >= 12]
+    for b in wide[:40] + [int(x) for x in rng.choice(len(B), size=60, replace=False)]:
+        assert _check_tiles(B, O, b) <= stage_elems
