@@ -61,6 +61,8 @@ struct qt_plan_s {
     // gradient plans
     void* d_bwd = nullptr;       // op_param | net_graph | backward task arrays
     double* d_grad = nullptr;    // n_graphs x 2p accumulators, then dgamma | dbeta
+    const uint64_t* d_zero = nullptr;  // cotangent pieces zeroed before each reverse sweep (inside d_bwd)
+    uint32_t n_zero = 0;
     qt::DevBwd db{};
 
     ~qt_plan_s() {
@@ -225,18 +227,26 @@ int upload(qt_plan_t P) {
         QT_CUDA(cudaEventCreate(&r[1]));
     }
     if (hp.cfg.with_grad) {
-        const size_t b0 = (bytes_of(hp.op_param) + 255) / 256 * 256;
-        const size_t b1 = (bytes_of(hp.net_graph) + 255) / 256 * 256;
-        const size_t b2 = (bytes_of(hp.bwd_bucket) + 255) / 256 * 256;
-        const size_t b3 = (bytes_of(hp.bwd_tile) + 255) / 256 * 256;
-        QT_CUDA(cudaMalloc(&P->d_bwd, std::max<size_t>(b0 + b1 + b2 + b3, 256)));
-        char* q = static_cast<char*>(P->d_bwd);
-        if (!hp.op_param.empty()) QT_CUDA(cudaMemcpy(q, hp.op_param.data(), bytes_of(hp.op_param), cudaMemcpyHostToDevice));
-        QT_CUDA(cudaMemcpy(q + b0, hp.net_graph.data(), bytes_of(hp.net_graph), cudaMemcpyHostToDevice));
-        if (!hp.bwd_bucket.empty()) {
-            QT_CUDA(cudaMemcpy(q + b0 + b1, hp.bwd_bucket.data(), bytes_of(hp.bwd_bucket), cudaMemcpyHostToDevice));
-            QT_CUDA(cudaMemcpy(q + b0 + b1 + b2, hp.bwd_tile.data(), bytes_of(hp.bwd_tile), cudaMemcpyHostToDevice));
+        // op_param | net_graph | task buckets | task tiles | op_bwd | op_roff | zero ranges
+        struct Piece {
+            const void* src;
+            size_t bytes;
+            size_t off;
+        };
+        Piece pc[7] = {{hp.op_param.data(), bytes_of(hp.op_param), 0},   {hp.net_graph.data(), bytes_of(hp.net_graph), 0},
+                       {hp.bwd_bucket.data(), bytes_of(hp.bwd_bucket), 0}, {hp.bwd_tile.data(), bytes_of(hp.bwd_tile), 0},
+                       {hp.op_bwd.data(), bytes_of(hp.op_bwd), 0},         {hp.op_roff.data(), bytes_of(hp.op_roff), 0},
+                       {hp.bwd_zero.data(), bytes_of(hp.bwd_zero), 0}};
+        size_t tot = 0;
+        for (auto& x : pc) {
+            x.off = tot;
+            tot += (x.bytes + 255) / 256 * 256;
         }
+        QT_CUDA(cudaMalloc(&P->d_bwd, std::max<size_t>(tot, 256)));
+        char* q = static_cast<char*>(P->d_bwd);
+        for (auto& x : pc)
+            if (x.bytes) QT_CUDA(cudaMemcpy(q + x.off, x.src, x.bytes, cudaMemcpyHostToDevice));
+        const size_t b0 = pc[1].off, b1 = pc[2].off - pc[1].off, b2 = pc[3].off - pc[2].off;
         QT_CUDA(cudaMalloc((void**)&P->d_grad, sizeof(double) * 4 * n_graphs * hp.cfg.p));
         qt::DevBwd& db = P->db;
         db.buckets = dp.buckets;
@@ -245,6 +255,10 @@ int upload(qt_plan_t P) {
         db.net_graph = reinterpret_cast<const uint32_t*>(q + b0);
         db.task_bucket = reinterpret_cast<const uint32_t*>(q + b0 + b1);
         db.task_tile = reinterpret_cast<const uint32_t*>(q + b0 + b1 + b2);
+        db.op_bwd = reinterpret_cast<const int8_t*>(q + pc[4].off);
+        db.op_roff = reinterpret_cast<const uint16_t*>(q + pc[5].off);
+        P->d_zero = reinterpret_cast<const uint64_t*>(q + pc[6].off);
+        P->n_zero = (uint32_t)(hp.bwd_zero.size() / 2);
         db.p = hp.cfg.p;
         db.arena = P->d_arena;
         db.cot_delta = hp.cot_off - hp.leaf_elems;
@@ -570,16 +584,19 @@ int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, doubl
     if (rc != QT_OK) return rc;
     cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : P->stream;
     // reverse sweep
-    QT_CUDA(cudaMemsetAsync(static_cast<char*>(P->d_arena) + hp.cot_off * P->esize, 0,
-                            (hp.total_elems - hp.cot_off) * P->esize, s));
+    QT_CUDA(qt::launch_zero_ranges(P->dtype, P->d_arena, P->d_zero, P->n_zero, s));
     QT_CUDA(cudaMemsetAsync(P->d_grad, 0, sizeof(double) * 2 * G * p, s));
     QT_CUDA(qt::launch_seed_roots(P->dtype, P->de, (int)hp.nets.size(), P->db.cot_delta, s));
     for (int lv = hp.n_levels - 1; lv >= 0; --lv) {
-        qt::DevBwd db = P->db;
-        db.task_bucket += hp.bwd_level_begin[lv];
-        db.task_tile += hp.bwd_level_begin[lv];
-        db.n_tasks = hp.bwd_level_begin[lv + 1] - hp.bwd_level_begin[lv];
-        QT_CUDA(qt::launch_backward(P->dtype, db, s));
+        for (int cls = 0; cls < qt::kBwdClasses; ++cls) {
+            const uint32_t i0 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls];
+            const uint32_t i1 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls + 1];
+            qt::DevBwd db = P->db;
+            db.task_bucket += i0;
+            db.task_tile += i0;
+            db.n_tasks = i1 - i0;
+            QT_CUDA(qt::launch_backward(P->dtype, cls, db, s));
+        }
     }
     double* d_dg = P->d_grad + 2 * G * p;
     double* d_db = d_dg + G * p;

@@ -60,6 +60,8 @@ struct DevBwd {
     const DBucket* buckets;
     const DOperand* ops;
     const int8_t* op_param;     // per operand: gate parameter (k: gamma_k, p+k: beta_k), -1 none
+    const int8_t* op_bwd;       // per operand: kBwd* treatment
+    const uint16_t* op_roff;    // per operand: offset of its in-tile sum in the warp's shared memory
     const uint32_t* net_graph;  // graph of each network
     const uint32_t* task_bucket;// tasks of one level: (bucket, tile)
     const uint32_t* task_tile;
@@ -74,7 +76,10 @@ struct DevBwd {
 cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, uint64_t dleaf_off,
                              cudaStream_t s);
 cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s);
-cudaError_t launch_backward(int dtype, const DevBwd& db, cudaStream_t s);
+// op_class: the level's tasks of buckets with at most 4 (0), 8 (1) or 16 (2) operands
+cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s);
+
+cudaError_t launch_zero_ranges(int dtype, void* arena, const uint64_t* ranges, uint32_t n_ranges, cudaStream_t s);
 cudaError_t launch_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta, cudaStream_t s);
 cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream_t s);
 cudaError_t launch_per_bucket(int dtype, uint32_t bucket, uint32_t n_tasks, const DevPlan& dp, cudaStream_t s);

@@ -655,14 +655,64 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     hp->bwd_bucket.clear();
     hp->bwd_tile.clear();
     hp->bwd_level_begin.assign(1, 0);
+    hp->op_bwd.assign(hp->operands.size(), kBwdNone);
+    hp->op_roff.assign(hp->operands.size(), 0);
+    hp->bwd_zero.clear();
     if (cfg.with_grad) {
+        // Each result has one consumer, so its cotangent comes from one bucket:
+        // entries are stored once where the operand carries every output bit,
+        // or summed in shared memory over the tile's bits it lacks; only
+        // operands lacking bits above the tile take atomic adds (and a zeroed
+        // cotangent).
+        const uint64_t cot_delta = hp->cot_off - hp->leaf_elems;
+        for (uint32_t b = 0; b < nb; ++b) {
+            const DBucket& d = hp->buckets[b];
+            const uint32_t outm = d.n_out ? ((1u << d.n_out) - 1u) : 0u;
+            const int tb = std::min<int>(d.n_out, kBwdTileBits);
+            const uint32_t low = (1u << tb) - 1u;
+            uint32_t used = 0;
+            for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) {
+                const DOperand& o = hp->operands[i];
+                int8_t mode;
+                if (o.flags & kOpLeaf) {
+                    mode = hp->op_param[i] >= 0 ? kBwdGate : kBwdNone;
+                } else if (o.mask == outm) {
+                    mode = kBwdDirect;
+                } else {
+                    const uint32_t fp = 2u << __builtin_popcount(o.mask & low);
+                    const bool hi_free = (outm & ~low & ~o.mask) != 0u;
+                    if (used + fp <= (uint32_t)kBwdRedElems) {
+                        mode = hi_free ? kBwdRedAtomic : kBwdRedStore;
+                        hp->op_roff[i] = (uint16_t)used;
+                        used += fp;
+                    } else {
+                        mode = kBwdAtomic;
+                    }
+                    if (mode != kBwdRedStore) {
+                        const DBucket& src = hp->buckets[o.src];
+                        const uint64_t n = 1ull << src.n_out;
+                        for (uint64_t c = 0; c < n; c += kZeroChunk) {
+                            hp->bwd_zero.push_back(src.out_off + cot_delta + c);
+                            hp->bwd_zero.push_back(std::min<uint64_t>(kZeroChunk, n - c));
+                        }
+                    }
+                }
+                hp->op_bwd[i] = mode;
+            }
+        }
+        // tasks by level, and within a level by operand-count class (one
+        // launch each): bwd_level_begin[kBwdClasses * lv + c] starts class c
         for (int lv = 0; lv < hp->n_levels; ++lv) {
-            for (uint32_t i = hp->level_first_bucket[lv]; i < hp->level_first_bucket[lv + 1]; ++i) {
-                const uint32_t b = hp->by_level[i];
-                const int tb = std::min<int>(hp->buckets[b].n_out, kBwdTileBits);
-                for (uint32_t t = 0; t < (1u << (hp->buckets[b].n_out - tb)); ++t) {
-                    hp->bwd_bucket.push_back(b);
-                    hp->bwd_tile.push_back(t);
+            for (int cls = 0; cls < kBwdClasses; ++cls) {
+                if (cls > 0) hp->bwd_level_begin.push_back((uint32_t)hp->bwd_bucket.size());
+                for (uint32_t i = hp->level_first_bucket[lv]; i < hp->level_first_bucket[lv + 1]; ++i) {
+                    const uint32_t b = hp->by_level[i];
+                    if (bwd_op_class(hp->buckets[b].n_ops) != cls) continue;
+                    const int tb = std::min<int>(hp->buckets[b].n_out, kBwdTileBits);
+                    for (uint32_t t = 0; t < (1u << (hp->buckets[b].n_out - tb)); ++t) {
+                        hp->bwd_bucket.push_back(b);
+                        hp->bwd_tile.push_back(t);
+                    }
                 }
             }
             hp->bwd_level_begin.push_back((uint32_t)hp->bwd_bucket.size());

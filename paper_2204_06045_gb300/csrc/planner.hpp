@@ -98,10 +98,14 @@ struct HostPlan {
     uint64_t leaf_elems = 0;   // leaf table size in elements (gate values, then their derivatives with_grad)
     uint64_t dleaf_off = 0;    // element offset of the derivative table (gradient plans)
     std::vector<int8_t> op_param;        // per operand: parameter of a gate tensor (k: gamma_k, p+k: beta_k), -1 none
+    std::vector<int8_t> op_bwd;          // per operand: kBwd* treatment in the reverse sweep
+    std::vector<uint16_t> op_roff;       // per operand: offset of its in-tile sum in the warp's shared memory
+    std::vector<uint64_t> bwd_zero;      // cotangent pieces to zero before the sweep: (element offset, count) pairs
     std::vector<uint32_t> net_graph;     // graph of each network
     std::vector<uint32_t> bwd_bucket;    // reverse sweep: (bucket, tile) tasks, deepest level last
     std::vector<uint32_t> bwd_tile;
-    std::vector<uint32_t> bwd_level_begin;  // n_levels + 1 offsets into the task arrays, by level
+    std::vector<uint32_t> bwd_level_begin;  // kBwdClasses * n_levels + 1 offsets into the task arrays:
+                                            // level lv, operand-count class c starts at kBwdClasses * lv + c
     uint64_t arena_elems = 0;  // leaf table + results
     uint64_t cot_off = 0;      // start of the cotangent region (gradient plans)
     uint64_t total_elems = 0;

@@ -29,7 +29,21 @@ constexpr int kLeafBits = 5;
 constexpr int kMaxFoldLeaves = 8;
 constexpr uint8_t kBucketFoldLeaves = 1;
 constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim (default)
-constexpr int kBwdTileBits = 9;      // outputs per reverse-sweep tile, log2
+constexpr int kBwdTileBits = 8;      // outputs per reverse-sweep tile, log2
+constexpr int kBwdRedElems = 1024;   // per-warp shared-memory elements for in-tile cotangent sums
+constexpr uint32_t kZeroChunk = 1u << 16;  // elements per block of the cotangent zeroing kernel
+// Reverse-sweep launches per level: buckets of at most 4, 8 or 16 operands.
+constexpr int kBwdClasses = 3;
+constexpr int bwd_op_class(int n_ops) { return n_ops <= 4 ? 0 : n_ops <= 8 ? 1 : 2; }
+// How the reverse sweep treats an operand (per operand, fixed at plan time).
+enum : int8_t {
+    kBwdNone = 0,       // a gate tensor without an angle (|+>, Z)
+    kBwdGate = 1,       // a gate tensor of an angle: Re <cotangent, dT/dangle> summed per angle
+    kBwdDirect = 2,     // a result carrying every output bit: each cotangent entry stored once
+    kBwdRedStore = 3,   // summed over the tile's missing bits in shared memory, then stored
+    kBwdRedAtomic = 4,  // as 3, but other tiles add to the same entries: atomic adds
+    kBwdAtomic = 5      // no room in shared memory: atomic adds per output (zeroed first)
+};
 constexpr int kDefaultTileBits = 9;  // at most 512 outputs per tile (default); measured best on GB300
 
 // One bucket on the device. 64 bytes.
