@@ -322,11 +322,20 @@ def time_e2e(pl, g, b, steps, dist, torch):
 
 
 def max_over_ranks(x, dist, torch):
+    """The slowest rank's value (the whole job's time): an all-reduce MAX over
+    the process group (NCCL on GPUs, gloo on CPU)."""
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Weak scaling: every rank processes its own units; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 def run_ours(args, rank, world, local_rank):
@@ -366,9 +375,9 @@ def run_ours(args, rank, world, local_rank):
         achieved = st["alg_bytes"] / (kms * 1e-3) / 1e9 if kms > 0 else None
         tag = f"k_persistent_{dtype}_n30_p4"
         results[dtype] = {
-            "value": world * args.steps / (ms * 1e-3),
+            "value": job_throughput(world, args.steps, ms * 1e-3),
             "ms_per_step": ms / args.steps,
-            "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s",
+            "e2e": {"value": job_throughput(world, args.steps, e2e_s), "unit": "evals/s",
                     "h2d_bytes_per_step": 2 * p * 8, "d2h_bytes_per_step": (m + 1) * 8},
             "roofline": roofline(dtype, st, kms, launches, achieved, peak, peak_kind, fma_tflops[dtype],
                                  ncu_traffic(tag)),

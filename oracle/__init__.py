@@ -65,10 +65,12 @@ def _load():
         lib.oracle_bucket_zz.argtypes = [c_int, c_int, i32p, c_int, dp, dp, u64, c_int, dp, ip]
         lib.oracle_edge_brute.argtypes = [c_int, c_int, i32p, c_int, dp, dp, c_int, dp]
         lib.oracle_edge_network_shape.argtypes = [c_int, c_int, i32p, c_int, c_int, ip, ip, ip]
+        lib.oracle_edge_bucket_order.argtypes = [c_int, c_int, i32p, c_int, dp, dp, c_int, c_int, u64, c_int, dp, ip]
         lib.oracle_set_threads.argtypes = [c_int]
         lib.oracle_get_threads.restype = c_int
         for f in (lib.oracle_sv_zz, lib.oracle_sv_zz_gates, lib.oracle_edge_bucket,
-                  lib.oracle_bucket_zz, lib.oracle_edge_brute, lib.oracle_edge_network_shape):
+                  lib.oracle_bucket_zz, lib.oracle_edge_brute, lib.oracle_edge_network_shape,
+                  lib.oracle_edge_bucket_order):
             f.restype = c_int
         _lib = lib
     return _lib
@@ -142,6 +144,22 @@ def edge_bucket(n: int, edges, gammas, betas, eidx: int, seed: int = 0, max_widt
     _check(lib.oracle_edge_bucket(n, e.shape[0], ep, g.size, gp, bp, int(eidx), int(seed), int(max_width),
                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(w)),
            "edge_bucket")
+    return complex(out[0], out[1]), int(w.value)
+
+
+def edge_bucket_min_fill(n: int, edges, gammas, betas, eidx: int, seed: int = 0, max_width: int = 30):
+    """(value, max bucket width) of edge ``eidx``'s network, eliminated in a greedy
+    min-fill order with random ties (the oracle's own, for networks whose
+    min-degree orders are too wide)."""
+    lib = _load()
+    e, ep = _i32(edges)
+    g, gp = _f64(gammas)
+    b, bp = _f64(betas)
+    out = np.zeros(2, dtype=np.float64)
+    w = ctypes.c_int(0)
+    _check(lib.oracle_edge_bucket_order(n, e.shape[0], ep, g.size, gp, bp, int(eidx), 1, int(seed), int(max_width),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(w)),
+           "edge_bucket_min_fill")
     return complex(out[0], out[1]), int(w.value)
 
 

@@ -22,7 +22,9 @@
  *   1. state vector over all 2^N amplitudes           (oracle_sv_*)
  *   2. bucket elimination of each edge's lightcone      (oracle_bucket_*)
  *      tensor network, with this file's own network
- *      builder and its own min-degree order
+ *      builder and its own min-degree order (or, for
+ *      the large N=1000 p=5 networks, its own greedy
+ *      min-fill order; both break ties at random)
  *   3. brute-force sum over every variable assignment   (oracle_edge_brute)
  *      of one lightcone network
  */
@@ -445,6 +447,59 @@ static int min_degree_order(const network_t *net, uint64_t seed, int *order) {
     return OR_OK;
 }
 
+/*
+ * Greedy min-fill order (§II-D leaves the ordering heuristic open): at each
+ * step eliminate a variable whose neighbours in the interaction graph need
+ * the fewest new edges to become a clique; ties are broken at random
+ * (splitmix64 seeded by `seed`). Eliminating v joins its neighbours.
+ */
+static int min_fill_order(const network_t *net, uint64_t seed, int *order) {
+    const int V = net->nvars;
+    unsigned char *adj = (unsigned char *)calloc((size_t)V * V, 1);
+    unsigned char *done = (unsigned char *)calloc((size_t)V, 1);
+    int *cand = (int *)malloc(sizeof(int) * (size_t)V);
+    int *nb = (int *)malloc(sizeof(int) * (size_t)V);
+    if (!adj || !done || !cand || !nb) {
+        free(adj); free(done); free(cand); free(nb);
+        return OR_ENOMEM;
+    }
+#define ADJ(a, b) adj[(size_t)(a) * V + (b)]
+    for (int t = 0; t < net->ntens; ++t) {
+        if (net->t[t].rank != 2) continue;
+        int a = net->t[t].vars[0], b = net->t[t].vars[1];
+        if (a != b) ADJ(a, b) = ADJ(b, a) = 1;
+    }
+    uint64_t rng = seed;
+    for (int step = 0; step < V; ++step) {
+        long best = -1;
+        int nc = 0;
+        for (int v = 0; v < V; ++v) {
+            if (done[v]) continue;
+            int nn = 0;
+            for (int a = 0; a < V; ++a)
+                if (ADJ(v, a)) nb[nn++] = a;
+            long fill = 0;
+            for (int i = 0; i < nn; ++i)
+                for (int j2 = i + 1; j2 < nn; ++j2)
+                    if (!ADJ(nb[i], nb[j2])) fill++;
+            if (best < 0 || fill < best) { best = fill; nc = 0; }
+            if (fill == best) cand[nc++] = v;
+        }
+        int v = cand[splitmix64(&rng) % (uint64_t)nc];
+        order[step] = v;
+        done[v] = 1;
+        int nn = 0;
+        for (int a = 0; a < V; ++a)
+            if (ADJ(v, a)) nb[nn++] = a;
+        for (int i = 0; i < nn; ++i) ADJ(v, nb[i]) = ADJ(nb[i], v) = 0;
+        for (int i = 0; i < nn; ++i)
+            for (int j2 = i + 1; j2 < nn; ++j2) ADJ(nb[i], nb[j2]) = ADJ(nb[j2], nb[i]) = 1;
+    }
+#undef ADJ
+    free(adj); free(done); free(cand); free(nb);
+    return OR_OK;
+}
+
 /* A dense tensor over binary variables: bit i of an entry's index is the
  * value of vars[i]. rank 0 is a scalar. */
 typedef struct {
@@ -611,6 +666,31 @@ int oracle_edge_bucket(int n, int m, const int32_t *edges, int p, const double *
     if (rc != OR_OK) return rc;
     int *order = (int *)malloc(sizeof(int) * (size_t)net.nvars);
     rc = order ? min_degree_order(&net, seed, order) : OR_ENOMEM;
+    cplx v = 0.0;
+    int w = 0;
+    if (rc == OR_OK) rc = eliminate(&net, order, max_width, &v, &w);
+    free(order);
+    net_free(&net);
+    if (rc != OR_OK) return rc;
+    out_re_im[0] = creal(v);
+    out_re_im[1] = cimag(v);
+    if (max_w) *max_w = w;
+    return OR_OK;
+}
+
+/* As oracle_edge_bucket, with the order chosen by `order_kind`: 0 min-degree,
+ * 1 greedy min-fill (both with random ties drawn from `seed`). */
+int oracle_edge_bucket_order(int n, int m, const int32_t *edges, int p, const double *gammas,
+                             const double *betas, int eidx, int order_kind, uint64_t seed, int max_width,
+                             double *out_re_im, int *max_w) {
+    if (check_graph(n, m, edges) != OR_OK || p < 1 || eidx < 0 || eidx >= m) return OR_EINVAL;
+    if (order_kind != 0 && order_kind != 1) return OR_EINVAL;
+    network_t net;
+    int rc = build_network(n, m, edges, p, gammas, betas, eidx, &net);
+    if (rc != OR_OK) return rc;
+    int *order = (int *)malloc(sizeof(int) * (size_t)net.nvars);
+    if (!order) rc = OR_ENOMEM;
+    else rc = order_kind == 1 ? min_fill_order(&net, seed, order) : min_degree_order(&net, seed, order);
     cplx v = 0.0;
     int w = 0;
     if (rc == OR_OK) rc = eliminate(&net, order, max_width, &v, &w);

