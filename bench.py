@@ -189,19 +189,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+FORWARD_SOURCES = ("kernels.cu", "device_common.cuh", "kernels.hpp", "qt_internal.hpp")
+
+
+def forward_source_sha() -> str:
+    """Hash of the sources the forward kernels are built from (a profile summary
+    records it; its DRAM figures are used only while the sources match)."""
+    h = hashlib.sha256()
+    for name in FORWARD_SOURCES:
+        h.update((ROOT / "paper_2204_06045_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel_tag: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
     f = ROOT / "profiles" / f"{kernel_tag}.txt"
     if not f.exists():
         return None
-    src = (ROOT / "paper_2204_06045_gb300" / "csrc" / "kernels.cu").read_bytes()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = forward_source_sha()
     vals = {}
     for line in f.read_text().splitlines():
         parts = line.split()
         if len(parts) == 2 and not line.startswith("#"):
             vals[parts[0]] = parts[1]
-    if vals.get("kernels_cu_sha256_16") != sha:
+    if vals.get("forward_src_sha256_16") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

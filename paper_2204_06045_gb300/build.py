@@ -27,7 +27,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(CSRC.glob("*.hpp")) + sorted(INCLUDE.glob("*.h")) + [Path(__file__)]
+    return (_sources() + sorted(CSRC.glob("*.hpp")) + sorted(CSRC.glob("*.cuh")) + sorted(INCLUDE.glob("*.h"))
+            + [Path(__file__)])
 
 
 def _nvcc() -> str:

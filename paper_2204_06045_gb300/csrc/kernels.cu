@@ -16,39 +16,14 @@
 #include <cuda_runtime.h>
 
 #include "../../include/qt.h"
+#include "device_common.cuh"
 #include "kernels.hpp"
 
 namespace qt {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = kPersistentThreads / 32;
 constexpr int kUnroll = 4;  // iterations of 64 outputs in flight per warp
-
-template <typename R>
-struct CT;
-template <>
-struct CT<float> {
-    using c = float2;
-};
-template <>
-struct CT<double> {
-    using c = double2;
-};
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-
-template <typename C>
-struct Pair {
-    C v0, v1;
-};
 
 // The (x = 0, x = 1) entries at element e (even) of a tensor. Gate tensors are
 // written by an earlier kernel and read through the read-only path;
@@ -81,17 +56,6 @@ __device__ __forceinline__ void st_two(float2* out, uint64_t o, float2 a, float2
 __device__ __forceinline__ void st_two(double2* out, uint64_t o, double2 a, double2 b) {
     out[o] = a;
     out[o + 1] = b;
-}
-
-// Bits of x selected by m, packed to the low end (parallel bit extract).
-__device__ __forceinline__ uint32_t pext_u32(uint32_t x, uint32_t m) {
-    uint32_t r = 0, t = x & m;
-    while (t) {
-        uint32_t low = t & (0u - t);
-        r |= 1u << __popc(m & (low - 1u));
-        t ^= low;
-    }
-    return r;
 }
 
 struct OpStage {
@@ -1113,327 +1077,6 @@ cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int 
         k_leaf_fill<double><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<double2*>(arena), dleaf_off);
     else
         k_leaf_fill<float><<<blocks, threads, 0, s>>>(angles, n_graphs, p, static_cast<float2*>(arena), dleaf_off);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Reverse sweep (the adjoint of bucket elimination).
-//
-// A network's value V is a polynomial in the gate entries, so dV/dtheta =
-// sum over gate tensors g and entries i of (dV/dT_g[i]) (dT_g[i]/dtheta). The
-// cotangent of bucket b's result, Rbar, is complete once b's consumer has
-// been swept; the cotangent contribution to operand s from output o and
-// summed value x is Rbar[o] * prod_{t != s} T_t[2 pext(o, M_t) + x]. Results
-// of earlier buckets receive these contributions in their cotangent buffers
-// (atomically, since several outputs may share an entry); gate tensors turn
-// them at once into Re(contribution * dT_g/dtheta), summed per parameter.
-// E = |E|/2 - 1/2 sum Re V, so dE/dtheta = -1/2 times those sums.
-// ---------------------------------------------------------------------------
-
-// Each root's cotangent is the product of its network's other roots (1 when,
-// as usual, the network is connected).
-template <typename R>
-__global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
-    using C = typename CT<R>::c;
-    C* arena = static_cast<C*>(const_cast<void*>(de.arena));
-    const int net = blockIdx.x * blockDim.x + threadIdx.x;
-    if (net >= n_nets) return;
-    for (uint32_t r = de.net_first_root[net]; r < de.net_first_root[net + 1]; ++r) {
-        double vr = 1.0, vi = 0.0;
-        for (uint32_t q = de.net_first_root[net]; q < de.net_first_root[net + 1]; ++q) {
-            if (q == r) continue;
-            const C v = arena[de.buckets[de.root_bucket[q]].out_off];
-            const double nr = vr * (double)v.x - vi * (double)v.y, ni = vr * (double)v.y + vi * (double)v.x;
-            vr = nr;
-            vi = ni;
-        }
-        C c;
-        c.x = (R)vr;
-        c.y = (R)vi;
-        arena[de.buckets[de.root_bucket[r]].out_off + cot_delta] = c;
-    }
-}
-
-__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-
-// Pair (x = 0, x = 1) of an operand entry through the read-only path: every
-// value the reverse sweep reads was written by an earlier launch.
-__device__ __forceinline__ Pair<float2> ldg_pair(const float2* p) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
-}
-__device__ __forceinline__ Pair<double2> ldg_pair(const double2* p) {
-    return {__ldg(p), __ldg(p + 1)};
-}
-__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
-    p[0] = a;
-    p[1] = b;
-}
-__device__ __forceinline__ void smem_add(float2* p, float2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-__device__ __forceinline__ void smem_add(double2* p, double2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-
-constexpr int kBwdWarps = 4;  // warps per block of the reverse sweep, one (bucket, tile) task each
-
-// One tile (2^tb outputs, tb = min(n_out, kBwdTileBits)) of one bucket's
-// reverse sweep, by one warp. Lane l takes outputs o = obase + l + 32 k. For
-// each output and x it forms c_s = Rbar[o] prod_{t != s} T_t[2 pext(o, M_t) + x]
-// (prefix and suffix products) and hands it to operand s by its mode. An
-// operand's pair index pext(o, M) is split, as in the forward tile loop, into
-// the tile's part (once per task), the lane's part and the steps of the
-// iteration bits, so no output pays for a bit-by-bit extract.
-template <typename R, int NMAX>
-__device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, typename CT<R>::c* red) {
-    using C = typename CT<R>::c;
-    constexpr int KB = kBwdTileBits - 5;  // iteration bits at most
-    C* arena = static_cast<C*>(db.arena);
-    const DBucket B = db.buckets[b];
-    const int n = B.n_ops;
-    const int tb = min((int)B.n_out, kBwdTileBits);
-    const int kb = tb > 5 ? tb - 5 : 0;
-    const uint32_t low = (1u << tb) - 1u;
-    const uint32_t lmask = low & 31u;
-    const bool active = ((uint32_t)lane & ~lmask) == 0u;
-    const uint32_t obase = tile << tb;
-    const C* rbar = arena + B.out_off + db.cot_delta;
-    uint64_t off[NMAX];
-    uint32_t mask[NMAX], base[NMAX], lo[NMAX], step[NMAX][KB];
-    int mode[NMAX], prm[NMAX];
-    uint32_t roff[NMAX];
-    uint32_t red_elems = 0;
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) {
-        off[t] = 0;
-        mask[t] = 0;
-        mode[t] = kBwdNone;
-        prm[t] = -1;
-        roff[t] = 0;
-        base[t] = lo[t] = 0;
-#pragma unroll
-        for (int k = 0; k < KB; ++k) step[t][k] = 0;
-        if (t < n) {
-            const uint32_t i = B.op_begin + t;
-            const DOperand o = db.ops[i];
-            off[t] = o.off;
-            mask[t] = o.mask;
-            mode[t] = db.op_bwd[i];
-            prm[t] = db.op_param[i];
-            roff[t] = db.op_roff[i];
-            base[t] = pext_u32(obase, o.mask);
-            lo[t] = pext_u32((uint32_t)lane & lmask, o.mask & lmask);
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                const int bit = 5 + k;
-                step[t][k] = (k < kb && ((o.mask >> bit) & 1u)) ? (1u << __popc(o.mask & ((1u << bit) - 1u))) : 0u;
-            }
-            if (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)
-                red_elems = max(red_elems, roff[t] + (2u << __popc(o.mask & low)));
-        }
-    }
-    for (uint32_t e = lane; e < red_elems; e += 32) red[e] = C{};
-    __syncwarp();
-    R acc[NMAX], comp[NMAX];  // per-lane compensated (Kahan) sums of Re(c dT)
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) acc[t] = comp[t] = (R)0;
-    // every lane runs the loop (the in-tile sums shuffle across lanes); lanes
-    // beyond a tile of fewer than 32 outputs carry a zero cotangent and store nothing
-    for (uint32_t k = 0; k < (1u << kb); ++k) {
-        const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
-        C r = C{};
-        if (active) r = __ldg(rbar + o);
-        Pair<C> P[NMAX];
-        uint32_t li[NMAX];  // pair index within the tile's block of the operand
-#pragma unroll
-        for (int t = 0; t < NMAX; ++t) {
-            uint32_t q = lo[t];
-#pragma unroll
-            for (int kk = 0; kk < KB; ++kk)
-                if ((k >> kk) & 1u) q += step[t][kk];
-            li[t] = q;
-            if (t < n) P[t] = ldg_pair(arena + off[t] + 2u * (base[t] + q));
-        }
-        C cd[NMAX][2];  // contributions of this output to direct operands
-#pragma unroll
-        for (int x = 0; x < 2; ++x) {
-            C S[NMAX];  // suffix products S[t] = prod_{u > t} P[u]
-            C acc_s;
-            acc_s.x = (R)1;
-            acc_s.y = (R)0;
-#pragma unroll
-            for (int t = NMAX - 1; t >= 0; --t) {
-                if (t < n) {
-                    S[t] = acc_s;
-                    acc_s = cmul(acc_s, x ? P[t].v1 : P[t].v0);
-                }
-            }
-            C pre = r;
-#pragma unroll
-            for (int t = 0; t < NMAX; ++t) {
-                if (t < n && mode[t] != kBwdNone) {
-                    const C c = cmul(pre, S[t]);  // Rbar[o] * prod_{u != t} P[u]
-                    switch (mode[t]) {
-                        case kBwdGate: {
-                            const C d = __ldg(arena + off[t] + db.dleaf_delta + 2u * (base[t] + li[t]) + x);
-                            const R v = c.x * d.x - c.y * d.y;
-                            const R y = v - comp[t];
-                            const R s2 = acc[t] + y;
-                            comp[t] = (s2 - acc[t]) - y;
-                            acc[t] = s2;
-                            break;
-                        }
-                        case kBwdDirect:
-                            cd[t][x] = c;
-                            break;
-                        case kBwdRedStore:
-                        case kBwdRedAtomic: {
-                            // lanes that differ only in bits the operand lacks
-                            // add to the same entry: sum them by shuffles first
-                            C v = c;
-                            const uint32_t miss = lmask & ~mask[t];
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) {
-                                if ((miss >> i) & 1u) {
-                                    v.x += __shfl_xor_sync(kFull, v.x, 1 << i);
-                                    v.y += __shfl_xor_sync(kFull, v.y, 1 << i);
-                                }
-                            }
-                            if (active && ((uint32_t)lane & miss) == 0u) smem_add(red + roff[t] + 2u * li[t] + x, v);
-                            break;
-                        }
-                        case kBwdAtomic:
-                            if (active) atomic_add_c(arena + off[t] + db.cot_delta + 2u * (base[t] + li[t]) + x, c);
-                            break;
-                        default:
-                            break;
-                    }
-                }
-                if (t < n) pre = cmul(pre, x ? P[t].v1 : P[t].v0);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < NMAX; ++t)
-            if (active && t < n && mode[t] == kBwdDirect)
-                st_pair(arena + off[t] + db.cot_delta + 2u * o, cd[t][0], cd[t][1]);
-    }
-    __syncwarp();
-    // in-tile sums: the operand's entries for this tile are one contiguous block
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) {
-        if (t < n && (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)) {
-            const uint32_t fp = 2u << __popc(mask[t] & low);
-            C* dst = arena + off[t] + db.cot_delta + 2u * base[t];
-            for (uint32_t e = lane; e < fp; e += 32) {
-                if (mode[t] == kBwdRedStore)
-                    dst[e] = red[roff[t] + e];
-                else
-                    atomic_add_c(dst + e, red[roff[t] + e]);
-            }
-        }
-    }
-    const uint32_t g = db.net_graph[B.net];
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) {
-        if (t < n && mode[t] == kBwdGate) {
-            double v = (double)acc[t];
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-            if (lane == 0) atomicAdd(&db.grad[(size_t)g * 2 * db.p + prm[t]], v);
-        }
-    }
-}
-
-// One launch per level and operand-count class (buckets of at most NMAX
-// operands), so that each instantiation keeps its own register budget.
-template <typename R, int NMAX>
-__global__ void __launch_bounds__(kBwdWarps * 32, NMAX <= 4 ? 4 : 2) k_backward(DevBwd db) {
-    using C = typename CT<R>::c;
-    extern __shared__ __align__(16) unsigned char bwd_smem[];
-    C* red = reinterpret_cast<C*>(bwd_smem) + (threadIdx.x >> 5) * kBwdRedElems;
-    const uint32_t w = blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= db.n_tasks) return;
-    bwd_tile<R, NMAX>(db, db.task_bucket[w], db.task_tile[w], lane, red);
-}
-
-// Zero the cotangent pieces that receive atomic adds: (offset, count) pairs,
-// one block per piece (pieces are at most kZeroChunk elements).
-template <typename R>
-__global__ void k_zero_ranges(typename CT<R>::c* arena, const uint64_t* ranges, uint32_t n) {
-    using C = typename CT<R>::c;
-    for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
-        C* p = arena + ranges[2 * r];
-        const uint32_t cnt = (uint32_t)ranges[2 * r + 1];
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) p[i] = C{};
-    }
-}
-
-__global__ void k_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_graphs * p) return;
-    const int g = i / p, k = i % p;
-    dgamma[i] = -0.5 * grad[(size_t)g * 2 * p + k];
-    dbeta[i] = -0.5 * grad[(size_t)g * 2 * p + p + k];
-}
-
-cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s) {
-    const int blocks = (n_nets + 127) / 128;
-    if (dtype == QT_C128)
-        k_seed_roots<double><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);
-    else
-        k_seed_roots<float><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);
-    return cudaGetLastError();
-}
-
-template <typename R, int NMAX>
-static cudaError_t launch_bwd(const DevBwd& db, cudaStream_t s) {
-    const uint32_t blocks = (db.n_tasks + kBwdWarps - 1) / kBwdWarps;
-    const size_t smem = (size_t)kBwdWarps * kBwdRedElems * sizeof(typename CT<R>::c);
-    if (smem > 48 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_backward<R, NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_backward<R, NMAX><<<blocks, kBwdWarps * 32, smem, s>>>(db);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s) {
-    if (db.n_tasks == 0) return cudaSuccess;
-    if (dtype == QT_C128) {
-        if (op_class == 0) return launch_bwd<double, 4>(db, s);
-        if (op_class == 1) return launch_bwd<double, 8>(db, s);
-        return launch_bwd<double, kMaxOps>(db, s);
-    }
-    if (op_class == 0) return launch_bwd<float, 4>(db, s);
-    if (op_class == 1) return launch_bwd<float, 8>(db, s);
-    return launch_bwd<float, kMaxOps>(db, s);
-}
-
-cudaError_t launch_zero_ranges(int dtype, void* arena, const uint64_t* ranges, uint32_t n_ranges, cudaStream_t s) {
-    if (n_ranges == 0) return cudaSuccess;
-    const uint32_t blocks = n_ranges < 65535u ? n_ranges : 65535u;
-    if (dtype == QT_C128)
-        k_zero_ranges<double><<<blocks, 256, 0, s>>>(static_cast<double2*>(arena), ranges, n_ranges);
-    else
-        k_zero_ranges<float><<<blocks, 256, 0, s>>>(static_cast<float2*>(arena), ranges, n_ranges);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta, cudaStream_t s) {
-    const int n = n_graphs * p;
-    k_grad_final<<<(n + 127) / 128, 128, 0, s>>>(grad, n_graphs, p, dgamma, dbeta);
     return cudaGetLastError();
 }
 
