@@ -220,6 +220,19 @@ def ncu_traffic(kernel_tag: str):
         return None
 
 
+def golden_c4():
+    """Per-edge <Z_jZ_k> of the N=1000 p=5 graph from the stored oracle values (dict edge -> value)."""
+    f = ROOT / "tests" / "golden" / "c4_n1000_p5_bucket.txt"
+    if not f.exists():
+        return None
+    ref = {}
+    for line in f.read_text().splitlines():
+        parts = line.split()
+        if parts and parts[0] == "edge":
+            ref[int(parts[1])] = float(parts[4])
+    return ref
+
+
 def golden_c2():
     """Per-edge <Z_jZ_k> and E of the default workload from the stored 2^30 state-vector values."""
     f = ROOT / "tests" / "golden" / "c2_n30_p4_statevector.txt"
@@ -281,9 +294,17 @@ def wide_buckets(peak, torch):
     out = {"workload": f"3-regular N={n} seed {seed}, p={p}: {sel.size} lightcone networks with greedy max width "
                        f"26..28; every bucket of width >= 24, timed alone (mean of 3 launches after 1)",
            "edges": sel.tolist()}
+    ref = golden_c4()
     for dtype in ("c64", "c128"):
         with qtgb.plan_subset(n, edges, p, sel, dtype=dtype) as pl:
-            pl.energy(g, b)  # leaves real data in every operand
+            zz, _ = pl.energy(g, b)  # also leaves real data in every operand
+            if ref is not None:
+                want = np.array([ref[int(e)] for e in sel])
+                d = np.abs(zz - want)
+                out.setdefault("check", {})[dtype] = {
+                    "reference": "oracle complex128 bucket elimination, min-fill order (stored)",
+                    "max_abs_err_zz": float(d.max()), "max_rel_err_zz": float((d / np.abs(want)).max()),
+                    "max_rel_err_edge_energy": float((d / np.abs(1.0 - want)).max())}
             Bs, _ = pl.export()
             tot_b = tot_ms = 0.0
             per = []

@@ -138,6 +138,65 @@ def test_c2_n30_p4_matches_statevector_golden(dtype, sched, order):
     assert np.abs(im).max() <= 10 * TOL[dtype]
 
 
+def _c4_golden():
+    rows, ref = {}, {}
+    with open(GOLDEN / "c4_n1000_p5_bucket.txt") as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if parts[0] == "edge":
+                ref[int(parts[1])] = (float(parts[4]), float(parts[5]))
+            else:
+                rows[parts[0]] = [float(x) for x in parts[1:]]
+    return rows, ref
+
+
+def _c4_inputs():
+    n, p = 1000, 5
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    return n, p, edges, g, b
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_c4_wide_networks_match_min_fill_golden(dtype):
+    """The networks whose greedy order reaches width 26..28 (buckets of up to
+    2^27 outputs) against the oracle's complex128 elimination in its own
+    min-fill order."""
+    if not (GOLDEN / "c4_n1000_p5_bucket.txt").exists():
+        pytest.skip("golden not generated")
+    rows, ref = _c4_golden()
+    n, p, edges, g, b = _c4_inputs()
+    np.testing.assert_array_equal((g, b), (np.array(rows["gamma"]), np.array(rows["beta"])))
+    with qtgb.plan(n, edges, p, host_only=True) as hp:
+        B, _ = hp.export()
+    mw = np.zeros(edges.shape[0], dtype=np.int64)
+    np.maximum.at(mw, B["network"], B["width"])
+    sel = np.nonzero((mw >= 26) & (mw <= 28))[0]
+    assert sel.size == 15
+    with qtgb.plan_subset(n, edges, p, sel, dtype=dtype) as pl:
+        zz, _ = pl.energy(g, b)
+        im = pl.last_imag()
+    want = np.array([ref[int(e)][0] for e in sel])
+    assert scaled_err(zz, want) <= TOL[dtype]
+    assert np.abs(im).max() <= 10 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_c4_whole_graph_energy_matches_golden(dtype):
+    """All 1500 lightcone networks of the N=1000 p=5 graph in one launch."""
+    if not (GOLDEN / "c4_n1000_p5_bucket.txt").exists():
+        pytest.skip("golden not generated")
+    rows, ref = _c4_golden()
+    n, p, edges, g, b = _c4_inputs()
+    with qtgb.plan(n, edges, p, dtype=dtype) as pl:
+        zz, E = pl.energy(g, b)
+    want = np.array([ref[e][0] for e in range(edges.shape[0])])
+    assert scaled_err(zz, want) <= TOL[dtype]
+    assert abs(E - rows["energy"][0]) <= TOL[dtype] * abs(E)
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_c5_n50_p4_matches_bucket_golden(dtype):
     if not (GOLDEN / "c5_n50_p4_bucket.txt").exists():
