@@ -84,6 +84,9 @@ typedef struct {
                               critical-path list-scheduling simulation made at plan time, each
                               group starting once its producers are done; 1 a device-side ready
                               queue, first come first served */
+    int32_t no_fuse;       /* nonzero: no fused units (by default, subtrees of small buckets, at most
+                              256 outputs each, run as one work group contracted in a warp's shared
+                              memory; never for gradient plans or the per-bucket schedule) */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -107,6 +110,8 @@ typedef struct {
     int64_t width_hist[64]; /* buckets per width */
     double plan_seconds;    /* host time spent building the plan */
     double sim_seconds;     /* makespan predicted by the plan-time schedule simulation (0: none) */
+    int64_t n_units;        /* fused units (small subtrees run as one work group) */
+    int64_t n_fused;        /* buckets inside fused units, their roots included */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */
@@ -123,7 +128,7 @@ typedef struct {
     uint32_t tile_bits;/* the output bits that vary within a tile (popcount = tile_log2): the
                           lowest ones, so tile c holds outputs c * 2^tile_log2 + j */
     uint32_t folded;   /* operands (bit i: the bucket's i-th) folded into the per-tile gate table */
-    uint32_t pad;
+    uint32_t unit_role;/* 0: scheduled on its own; 1: inside a fused unit; 2: the root of a fused unit */
 } qt_bucket_info;
 
 /* One operand of a bucket. The operand's entry for output index o and summed

@@ -143,6 +143,7 @@ int upload(qt_plan_t P) {
         {nullptr, 0, 0},                                       {hp.runs.data(), bytes_of(hp.runs), 0},
         {nullptr, 0, 0},                                       {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
+        {hp.unit_list.data(), bytes_of(hp.unit_list), 0},
     };
     size_t total = 0;
     for (auto& pc : pieces) {
@@ -177,6 +178,8 @@ int upload(qt_plan_t P) {
     dp.buckets = reinterpret_cast<const qt::DBucket*>(base + pieces[0].off);
     dp.ops = reinterpret_cast<const qt::DOperand*>(base + pieces[1].off);
     dp.runs = reinterpret_cast<const qt::DRun*>(base + pieces[3].off);
+    dp.unit_list = reinterpret_cast<const uint32_t*>(base + pieces[8].off);
+    dp.has_units = hp.n_units > 0 ? 1u : 0u;
     dp.n_static = (uint32_t)hp.runs.size();
     dp.n_groups = (uint32_t)hp.n_groups;
     dp.n_buckets = nb;
@@ -428,6 +431,7 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     }
     if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
+    cfg.fuse = o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad && o.no_fuse == 0;
     if (cfg.chunk_log2 < 0 || cfg.chunk_log2 > 24) return QT_EINVAL;
     std::unique_ptr<qt_plan_s> P(new (std::nothrow) qt_plan_s());
     if (!P) return QT_ENOMEM;
@@ -513,6 +517,8 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     std::memcpy(out->width_hist, hp.width_hist, sizeof(out->width_hist));
     out->plan_seconds = hp.plan_seconds;
     out->sim_seconds = hp.sim_seconds;
+    out->n_units = (int64_t)hp.n_units;
+    out->n_fused = (int64_t)hp.n_fused;
     return QT_OK;
 }
 
@@ -536,7 +542,7 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.folded = 0;
             for (uint32_t i = 0; i < d.n_ops; ++i)
                 if (hp.operands[d.op_begin + i].folded) o.folded |= 1u << i;
-            o.pad = 0;
+            o.unit_role = (d.flags & qt::kBucketInUnit) ? 1u : (d.flags & qt::kBucketUnitRoot) ? 2u : 0u;
         }
     }
     if (operands) {
@@ -663,7 +669,7 @@ int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, do
     const qt::DBucket& d = P->hp.buckets[bucket];
     std::vector<qt::DRun> groups;
     for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, {0, 0, 0}});
+        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, 0});
     qt::DRun* d_groups = nullptr;
     QT_CUDA(cudaMalloc((void**)&d_groups, groups.size() * sizeof(qt::DRun)));
     cudaError_t e = cudaMemcpy(d_groups, groups.data(), groups.size() * sizeof(qt::DRun), cudaMemcpyHostToDevice);
@@ -785,7 +791,7 @@ size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Byte offsets of every piece inside the scratch array.
 struct ScratchLayout {
-    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net;
+    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net, unit_list;
     size_t counters, counters_bytes, ctl_bytes, cnt_bytes;
     size_t angles, out, arena, total;
 };
@@ -805,6 +811,7 @@ ScratchLayout scratch_layout(const qt::HostPlan& hp, size_t esize) {
     L.net_first_root = take(hp.net_first_root.size() * sizeof(uint32_t));
     L.root_bucket = take(hp.root_bucket.size() * sizeof(uint32_t));
     L.graph_first_net = take(hp.graph_first_net.size() * sizeof(int32_t));
+    L.unit_list = take(hp.unit_list.size() * sizeof(uint32_t));
     L.ctl_bytes = 256;
     L.cnt_bytes = pad256(2 * nb * sizeof(uint32_t));
     L.counters_bytes = L.ctl_bytes + L.cnt_bytes + (size_t)(hp.n_groups - hp.runs.size()) * sizeof(qt::DSlot);
@@ -889,6 +896,9 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     static_assert(sizeof(int) == sizeof(int32_t), "graph_first_net is copied as int32");
     QT_CUDA(cudaMemcpyAsync(base + L.graph_first_net, hp.graph_first_net.data(), bytes_of(hp.graph_first_net),
                             cudaMemcpyHostToDevice, s));
+    if (!hp.unit_list.empty())
+        QT_CUDA(cudaMemcpyAsync(base + L.unit_list, hp.unit_list.data(), bytes_of(hp.unit_list),
+                                cudaMemcpyHostToDevice, s));
     // the array keeps the previous call's contents: counters and the queue start at zero
     QT_CUDA(cudaMemsetAsync(base + L.counters, 0, L.counters_bytes, s));
     double* d_angles = reinterpret_cast<double*>(base + L.angles);
@@ -899,6 +909,8 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     dp.buckets = reinterpret_cast<const qt::DBucket*>(base + L.buckets);
     dp.ops = reinterpret_cast<const qt::DOperand*>(base + L.ops);
     dp.runs = reinterpret_cast<const qt::DRun*>(base + L.runs);
+    dp.unit_list = reinterpret_cast<const uint32_t*>(base + L.unit_list);
+    dp.has_units = hp.n_units > 0 ? 1u : 0u;
     dp.n_static = (uint32_t)hp.runs.size();
     dp.n_groups = (uint32_t)hp.n_groups;
     dp.n_buckets = (uint32_t)hp.buckets.size();

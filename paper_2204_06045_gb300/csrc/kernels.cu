@@ -216,6 +216,8 @@ struct RunSlot {
     uint8_t n_hi;                    // folded tensors whose output bit lies above the tile
     uint8_t hi_idx[kMaxFoldLeaves];  // their slots
     uint8_t hi_shift[kMaxFoldLeaves];// position of that bit within the chunk index
+    uint32_t unit_begin;             // a fused unit: 1 + its first entry in the unit list (0: none)
+    uint32_t unit_count;
 };
 
 template <typename R>
@@ -225,6 +227,11 @@ struct alignas(128) WarpSmem {
     RunSlot<R> slot[2];
     unsigned long long bar[2];
 };
+
+// Three blocks of the complex64 kernel per SM (228 KB of shared memory per
+// SM, 1 KB of it reserved per block), two of the complex128 one.
+static_assert(sizeof(WarpSmem<float>) * kPW + 1024 <= 233472 / 3, "complex64 persistent kernel: 3 blocks per SM");
+static_assert(sizeof(WarpSmem<double>) * kPW + 1024 <= 233472 / 2, "complex128 persistent kernel: 2 blocks per SM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -302,7 +309,7 @@ __device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* ou
             const DSlot* sl = dp.slots + (q - dp.n_static);
             const uint32_t n = ld_acquire(&sl->n_chunks);
             ok = n != 0;
-            if (ok) r = DRun{sl->bucket, sl->chunk_begin, n, sl->op_begin, 0u, {0u, 0u, 0u}};
+            if (ok) r = DRun{sl->bucket, sl->chunk_begin, n, sl->op_begin, 0u, 0u, 0u, 0u};
         }
         ok = __shfl_sync(kFull, ok, 0);
         r.bucket = __shfl_sync(kFull, r.bucket, 0);
@@ -333,9 +340,36 @@ __device__ bool wait_group(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
 // values (all laid out by the planner). Lane t < n_staged also gets the
 // compressed index of the group's first tile in its operand's bits above the
 // tile (pext(o0, M) is that index shifted left by the operand's tile bits).
-template <typename R>
+template <typename R, bool Units>
 __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun& run, int lane, uint32_t* cbase) {
     using C = typename CT<R>::c;
+    if (Units && run.unit_begin) {  // a fused unit: nothing to stage, no gate table
+        RunSlot<R>& us = ws.slot[sl];
+        if (lane == 0) {
+            const DBucket B = dp.buckets[run.bucket];
+            us.out_off = B.out_off;
+            us.bucket = run.bucket;
+            us.chunk_begin = 0;
+            us.n_chunks = 1;  // the whole unit is one "tile" of its root
+            us.parent = B.parent;
+            us.n_tasks = 1;
+            us.leaf_u = 0;
+            us.leaf_hi = 0;
+            us.total_foot = 0;
+            us.n_out = B.n_out;
+            us.cb = B.n_out;
+            us.n_staged = 0;
+            us.n_leaves = 0;
+            us.bad = 0;
+            us.n_fast = 0;
+            us.n_hi = 0;
+            us.unit_begin = run.unit_begin;
+            us.unit_count = run.unit_count;
+        }
+        __syncwarp();
+        *cbase = 0;
+        return;
+    }
     DOperand op{};
     if (lane < kMaxOps) op = dp.ops[run.op_begin + lane];  // the operand array is padded by kMaxOps
     const DBucket B = dp.buckets[run.bucket];
@@ -371,6 +405,8 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
         rs.cb = B.chunk_bits;
         rs.n_staged = B.n_staged;
         rs.n_leaves = B.n_leaves;
+        rs.unit_begin = 0;
+        rs.unit_count = 0;
         rs.bad = !fits;
         if (!fits && atomicCAS(&dp.ctl->error, 0, QT_EBOUNDS) == 0) dp.ctl->err_bucket = run.bucket;
     }
@@ -753,12 +789,69 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
     __syncwarp();
 }
 
+// A fused unit: its buckets in elimination order, one output per lane at a
+// time, intermediates in stage st (free: a unit stages nothing), the root's
+// result to the arena. Each bucket's operand descriptors are first copied to
+// the warp's gate-table area (unused by units).
+template <typename R>
+__device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int lane) {
+    using C = typename CT<R>::c;
+    struct UOp {
+        uint32_t mask;
+        uint32_t in_stage;  // 1: an intermediate of the unit (stage offset), 0: a gate tensor (arena offset)
+        uint64_t off;
+    };
+    static_assert(sizeof(UOp) * kMaxOps <= sizeof(ws.leaf_tab), "unit operand descriptors");
+    UOp* uops = reinterpret_cast<UOp*>(ws.leaf_tab);
+    const RunSlot<R>& rs = ws.slot[sl];
+    C* scr = ws.stage[st];
+    C* arena = static_cast<C*>(dp.arena);
+    const uint32_t first = rs.unit_begin - 1u, count = rs.unit_count;
+    for (uint32_t k = 0; k < count; ++k) {
+        const uint32_t u = dp.unit_list[first + k];
+        const DBucket B = dp.buckets[u];
+        if (lane < B.n_ops) {
+            const DOperand op = dp.ops[B.op_begin + lane];
+            UOp d;
+            d.mask = op.mask;
+            d.in_stage = (op.flags & kOpLeaf) ? 0u : 1u;
+            d.off = (op.flags & kOpLeaf) ? op.off : (uint64_t)dp.buckets[op.src].scr_off;
+            uops[lane] = d;
+        }
+        __syncwarp();
+        C* dst = k + 1 == count ? arena + B.out_off : scr + B.scr_off;
+        const uint32_t n_out = 1u << B.n_out;
+        for (uint32_t o = lane; o < n_out; o += 32) {
+            C a0, a1;
+            a0.x = a1.x = (R)1;
+            a0.y = a1.y = (R)0;
+            for (int t = 0; t < B.n_ops; ++t) {
+                const UOp d = uops[t];
+                const uint32_t e = 2u * pext_u32(o, d.mask);
+                const C* src = d.in_stage ? scr + d.off : arena + d.off;
+                a0 = cmul(a0, src[e]);
+                a1 = cmul(a1, src[e + 1]);
+            }
+            dst[o] = cadd(a0, a1);
+        }
+        __syncwarp();
+    }
+    // the stage will be a bulk-copy target again: order these generic writes
+    // before later async-proxy writes to it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+}
+
 // Contract tile `chunk` of the group in slot sl from stage st.
-template <typename R, typename Clock>
+template <typename R, bool Units, typename Clock>
 __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk, bool first_of_run,
                               typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane, Clock& clk) {
     using C = typename CT<R>::c;
     const RunSlot<R>& rs = ws.slot[sl];
+    if (Units && rs.unit_begin) {
+        run_unit<R>(dp, ws, sl, st, lane);
+        return;
+    }
     if (rs.n_leaves) gate_table<R>(ws, rs, chunk, first_of_run, tlow, hi_key, lane);
     clk.lap(kTrGate);
     C* out = static_cast<C*>(dp.arena) + rs.out_off;
@@ -845,7 +938,9 @@ __device__ __forceinline__ void mark_bucket(const DevPlan& dp, uint32_t b, bool 
     }
 }
 
-template <typename R, bool Trace>
+// Units: the plan has fused units (a separate instantiation, so that plans
+// without them run the tile loop alone).
+template <typename R, bool Trace, bool Units>
 __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) k_persistent(DevPlan dp) {
     using C = typename CT<R>::c;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -874,7 +969,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
         bool ok = wait_group(dp, qa, &ra, lane);
         clk.lap(kTrDeps);
         if (ok) {
-            prep_run<R>(dp, ws, sa, ra, lane, &cbase);
+            prep_run<R, Units>(dp, ws, sa, ra, lane, &cbase);
             mark_bucket<Trace>(dp, ra.bucket, false, lane);
             clk.lap(kTrPrep);
             clk.count(kTrRuns, 1);
@@ -900,7 +995,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                 clk.lap(kTrClaim);
                 if (b_valid && group_at(dp, qb, &rb, lane)) {
                     sb = sa ^ 1;
-                    prep_run<R>(dp, ws, sb, rb, lane, &cbase);
+                    prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
                     mark_bucket<Trace>(dp, rb.bucket, false, lane);
                     clk.lap(kTrPrep);
                     clk.count(kTrRuns, 1);
@@ -916,7 +1011,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             }
             if (!wait_stage<R>(dp, ws, sa, st, phase, lane)) break;
             clk.lap(kTrWait);
-            contract_tile<R>(dp, ws, sa, st, a_chunk, a_first, tlow, hi_key, lane, clk);
+            contract_tile<R, Units>(dp, ws, sa, st, a_chunk, a_first, tlow, hi_key, lane, clk);
             clk.lap(kTrCompute);
             clk.count(kTrTiles, 1);
             pending[st] = false;
@@ -931,7 +1026,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                 if (!wait_group(dp, qb, &rb, lane)) break;
                 clk.lap(kTrDeps);
                 sb = sa ^ 1;
-                prep_run<R>(dp, ws, sb, rb, lane, &cbase);
+                prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
                 mark_bucket<Trace>(dp, rb.bucket, false, lane);
                 clk.lap(kTrPrep);
                 clk.count(kTrRuns, 1);
@@ -1095,20 +1190,26 @@ size_t persistent_smem_bytes(int dtype) {
     return dtype == QT_C128 ? sizeof(WarpSmem<double>) * kPW : sizeof(WarpSmem<float>) * kPW;
 }
 
+template <typename R, bool Trace, bool Units>
+static void launch_k(int grid, size_t smem, const DevPlan& dp, cudaStream_t s) {
+    k_persistent<R, Trace, Units><<<grid, kPersistentThreads, smem, s>>>(dp);
+}
+
+template <typename R>
+static void launch_k(int grid, size_t smem, const DevPlan& dp, cudaStream_t s) {
+    const bool tr = dp.trace != nullptr, un = dp.has_units != 0;
+    if (tr)
+        un ? launch_k<R, true, true>(grid, smem, dp, s) : launch_k<R, true, false>(grid, smem, dp, s);
+    else
+        un ? launch_k<R, false, true>(grid, smem, dp, s) : launch_k<R, false, false>(grid, smem, dp, s);
+}
+
 cudaError_t launch_persistent(int dtype, int grid, const DevPlan& dp, cudaStream_t s) {
     const size_t smem = persistent_smem_bytes(dtype);
-    const bool tr = dp.trace != nullptr;
-    if (dtype == QT_C128) {
-        if (tr)
-            k_persistent<double, true><<<grid, kPersistentThreads, smem, s>>>(dp);
-        else
-            k_persistent<double, false><<<grid, kPersistentThreads, smem, s>>>(dp);
-    } else {
-        if (tr)
-            k_persistent<float, true><<<grid, kPersistentThreads, smem, s>>>(dp);
-        else
-            k_persistent<float, false><<<grid, kPersistentThreads, smem, s>>>(dp);
-    }
+    if (dtype == QT_C128)
+        launch_k<double>(grid, smem, dp, s);
+    else
+        launch_k<float>(grid, smem, dp, s);
     return cudaGetLastError();
 }
 
@@ -1129,23 +1230,34 @@ cudaError_t launch_epilogue(int dtype, const DevEpilogue& de, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename R>
+static cudaError_t set_smem_attributes(int smem) {
+    const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_persistent<R, false, false>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_persistent<R, false, true>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_persistent<R, true, false>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_persistent<R, true, true>, a, smem);
+    return e;
+}
+
 int persistent_blocks_per_sm(int dtype) {
     const size_t smem = persistent_smem_bytes(dtype);
-    int n = 0;
+    int n = 0, n2 = 0;
     cudaError_t e;
     if (dtype == QT_C128) {
-        e = cudaFuncSetAttribute(k_persistent<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = set_smem_attributes<double>((int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_persistent<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<double, false, false>, kPersistentThreads, smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<double, false>, kPersistentThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_persistent<double, false, true>, kPersistentThreads, smem);
     } else {
-        e = cudaFuncSetAttribute(k_persistent<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = set_smem_attributes<float>((int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_persistent<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<float, false, false>, kPersistentThreads, smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persistent<float, false>, kPersistentThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_persistent<float, false, true>, kPersistentThreads, smem);
     }
+    n = n < n2 ? n : n2;  // one grid size serves every instantiation
     return e == cudaSuccess && n > 0 ? n : 0;
 }
 

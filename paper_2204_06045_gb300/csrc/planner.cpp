@@ -332,6 +332,122 @@ static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_e
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Fused units (§III-A and §III-C: small buckets dominate GPU time). A bucket
+// whose subtree (it and every bucket producing, directly or not, one of its
+// operands) holds only small buckets can run as one work group without waiting
+// for any other: a warp contracts the subtree's buckets in elimination order,
+// each intermediate in its shared-memory stage, and writes only the root's
+// result. Units are the maximal such subtrees whose intermediates, placed
+// first-fit by lifetime (a result is freed once its consumer is done), fit the
+// stage; a subtree that does not fit is split at its root.
+static void form_units(HostPlan* hp, int stage_elems) {
+    hp->unit_list.clear();
+    hp->n_units = 0;
+    hp->n_fused = 0;
+    if (!hp->cfg.fuse) return;
+    const uint32_t nb = (uint32_t)hp->buckets.size();
+    std::vector<uint8_t> ok(nb, 0);  // the bucket's whole subtree is small
+    std::vector<std::vector<uint32_t>> kids(nb);
+    for (uint32_t b = 0; b < nb; ++b) {
+        const DBucket& d = hp->buckets[b];
+        bool good = d.n_out <= kFuseOutBits;
+        for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) {
+            const int32_t src = hp->op_src[i];
+            if (src >= 0) {
+                kids[b].push_back((uint32_t)src);
+                good = good && ok[src];  // producers precede their consumer
+            }
+        }
+        ok[b] = good;
+    }
+    // first-fit placement of a subtree's intermediates; false if it overflows
+    auto place = [&](const std::vector<uint32_t>& members, uint32_t root) {
+        std::vector<std::pair<uint32_t, uint32_t>> used;  // (offset, size), sorted by offset
+        std::vector<uint32_t> off(members.size(), 0);
+        for (size_t k = 0; k < members.size(); ++k) {
+            const uint32_t u = members[k];
+            if (u != root) {
+                const uint32_t sz = 1u << hp->buckets[u].n_out;
+                uint32_t at = 0;
+                for (auto& iv : used) {
+                    if (at + sz <= iv.first) break;
+                    at = std::max(at, iv.first + iv.second);
+                }
+                if (at + sz > (uint32_t)stage_elems) return false;
+                used.insert(std::upper_bound(used.begin(), used.end(), std::make_pair(at, 0u)), {at, sz});
+                off[k] = at;
+            }
+            // u's producers are consumed now: free their space
+            for (uint32_t c : kids[u]) {
+                const uint32_t co = hp->buckets[c].scr_off, cs = 1u << hp->buckets[c].n_out;
+                auto it = std::find(used.begin(), used.end(), std::make_pair(co, cs));
+                if (it != used.end()) used.erase(it);
+            }
+            if (u != root) hp->buckets[u].scr_off = (uint16_t)off[k];
+        }
+        return true;
+    };
+    std::vector<uint32_t> stack, members;
+    for (uint32_t r = nb; r-- > 0;) {  // parents before producers: maximal subtrees first
+        const DBucket& d = hp->buckets[r];
+        if (!ok[r] || (d.flags & kBucketInUnit)) continue;
+        if (d.parent != kNone && ok[d.parent]) continue;  // part of a larger candidate
+        stack.assign(1, r);
+        while (!stack.empty()) {
+            const uint32_t root = stack.back();
+            stack.pop_back();
+            members.clear();
+            std::vector<uint32_t> todo(1, root);
+            while (!todo.empty()) {
+                const uint32_t u = todo.back();
+                todo.pop_back();
+                members.push_back(u);
+                for (uint32_t c : kids[u]) todo.push_back(c);
+            }
+            std::sort(members.begin(), members.end());  // elimination order
+            if (place(members, root)) {
+                hp->buckets[root].flags |= kBucketUnitRoot;
+                for (uint32_t u : members)
+                    if (u != root) hp->buckets[u].flags |= kBucketInUnit;
+                hp->buckets[root].unit_begin = (uint32_t)hp->unit_list.size() + 1u;
+                hp->buckets[root].unit_count = (uint32_t)members.size();
+                hp->unit_list.insert(hp->unit_list.end(), members.begin(), members.end());
+                hp->n_units++;
+                hp->n_fused += members.size();
+            } else {
+                for (uint32_t c : kids[root]) stack.push_back(c);  // split at the root
+            }
+        }
+    }
+    // Units pay when they remove more work groups than the GPU has warps to
+    // run them; otherwise (few small buckets, as in a single graph's networks)
+    // the plan keeps every bucket on its own and the kernel without unit code.
+    if (hp->n_fused - hp->n_units <= 2ull * (uint64_t)std::max(1, hp->cfg.sim_workers)) {
+        for (uint32_t b = 0; b < nb; ++b) {
+            DBucket& d = hp->buckets[b];
+            d.flags &= (uint8_t)~(kBucketInUnit | kBucketUnitRoot);
+            d.unit_begin = d.unit_count = 0;
+            d.scr_off = 0;
+        }
+        hp->unit_list.clear();
+        hp->n_units = hp->n_fused = 0;
+        return;
+    }
+    // a unit is one group; its members are never claimed on their own
+    hp->n_groups = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        DBucket& d = hp->buckets[b];
+        if (d.flags & kBucketInUnit) d.n_groups = 0;
+        else if (d.flags & kBucketUnitRoot) d.n_groups = 1;
+        hp->n_groups += d.n_groups;
+    }
+}
+
+static DRun unit_run(const HostPlan& hp, uint32_t root) {
+    const DBucket& d = hp.buckets[root];
+    return DRun{root, 0, 1, d.op_begin, 0, d.unit_begin, d.unit_count, 0};  // one "tile": the whole unit
+}
+
 // Claim order by list scheduling on the host. Each of W simulated warps takes,
 // whenever it is free, the ready group whose bucket has the longest remaining
 // path to its network's result (the sum, along the path, of the time each
@@ -350,11 +466,17 @@ static void simulate_order(HostPlan* hp) {
     const double bw = 6.5e12;                  // bytes per second, whole GPU
     const double t_tile = 0.3e-6, t_group = 1.5e-6;
     std::vector<double> tile_s(nb), whole_s(nb), prio(nb, 0.0);
+    const double t_unit_bucket = 0.15e-6;  // one small bucket inside a fused unit
     for (size_t b = 0; b < nb; ++b) {
         const DBucket& d = hp->buckets[b];
         const double tile_bytes = ((double)d.total_foot + std::ldexp(1.0, d.chunk_bits)) * esize;
         tile_s[b] = tile_bytes / (bw / W) + t_tile;
-        const double groups_in_parallel = std::min<double>(W, d.n_groups);
+        if (d.flags & kBucketUnitRoot) {  // the whole unit, as one group of one "tile"
+            tile_s[b] = t_unit_bucket * d.unit_count;
+            whole_s[b] = tile_s[b] + t_group;
+            continue;
+        }
+        const double groups_in_parallel = std::min<double>(W, std::max<uint32_t>(1, d.n_groups));
         whole_s[b] = std::max(tile_s[b] * d.n_tasks / groups_in_parallel, tile_s[b] * d.group_tiles) + t_group;
     }
     // buckets of a network are in elimination order, so parents come after children
@@ -364,7 +486,11 @@ static void simulate_order(HostPlan* hp) {
     }
     // event simulation
     std::vector<uint32_t> deps_left(nb);
-    for (size_t b = 0; b < nb; ++b) deps_left[b] = hp->buckets[b].n_deps;
+    for (size_t b = 0; b < nb; ++b) {
+        const DBucket& d = hp->buckets[b];
+        // a fused unit waits for nothing; its members never run on their own
+        deps_left[b] = (d.flags & kBucketUnitRoot) ? 0u : (d.flags & kBucketInUnit) ? 1u : d.n_deps;
+    }
     std::vector<uint32_t> groups_left(nb);
     for (size_t b = 0; b < nb; ++b) groups_left[b] = hp->buckets[b].n_groups;
     struct Ready {
@@ -386,9 +512,15 @@ static void simulate_order(HostPlan* hp) {
             Ready r = ready.top();
             ready.pop();
             const DBucket& d = hp->buckets[r.bucket];
+            if (d.flags & kBucketUnitRoot) {
+                hp->runs.push_back(unit_run(*hp, r.bucket));
+                running.push(Ev{now + tile_s[r.bucket] + t_group, r.bucket});
+                --free_workers;
+                continue;
+            }
             const uint32_t c = r.next_group * d.group_tiles;
             const uint32_t n = std::min(d.group_tiles, d.n_tasks - c);
-            hp->runs.push_back(DRun{r.bucket, c, n, d.op_begin, d.n_deps, {0, 0, 0}});
+            hp->runs.push_back(DRun{r.bucket, c, n, d.op_begin, d.n_deps, 0, 0, 0});
             running.push(Ev{now + tile_s[r.bucket] * n + t_group, r.bucket});
             --free_workers;
             if (++r.next_group < d.n_groups) ready.push(r);
@@ -637,15 +769,20 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
         hp->n_tiles += d.n_tasks;
         hp->n_groups += d.n_groups;
     }
+    form_units(hp, cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64);
     if (cfg.order == 1) {
-        // ready queue: groups of buckets without producers open it, in level
-        // order with the largest buckets first; every other bucket appends its
-        // groups when its last producer finishes
+        // ready queue: groups of buckets without producers open it (fused units
+        // among them), in level order with the largest buckets first; every
+        // other bucket appends its groups when its last producer finishes
         for (uint32_t b : hp->by_level) {
             const DBucket& d = hp->buckets[b];
-            if (d.n_deps == 0)
+            if (d.flags & kBucketInUnit) continue;
+            if (d.flags & kBucketUnitRoot) {
+                hp->runs.push_back(unit_run(*hp, b));
+            } else if (d.n_deps == 0) {
                 for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-                    hp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, {0, 0, 0}});
+                    hp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, 0});
+            }
         }
     } else {
         simulate_order(hp);

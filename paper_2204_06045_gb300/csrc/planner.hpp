@@ -67,6 +67,7 @@ struct PlanConfig {
     int order = 0;        // 0: claim order from a critical-path list-scheduling simulation; 1: ready queue
     int sim_workers = 1824;  // warps assumed by the simulation
     bool with_grad = false;
+    bool fuse = false;       // form fused units of small subtrees (persistent energy plans)
 };
 
 // The flat plan: what gets uploaded plus host-side bookkeeping.
@@ -87,6 +88,9 @@ struct HostPlan {
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
+    std::vector<uint32_t> unit_list;    // fused units' buckets, unit by unit, each in elimination order
+    uint64_t n_units = 0;
+    uint64_t n_fused = 0;               // buckets inside fused units (roots included)
     uint64_t n_tiles = 0;
     uint64_t n_groups = 0;              // queue length: groups over all buckets
     double sim_seconds = 0;             // makespan of the host simulation (0 if not simulated)

@@ -28,6 +28,16 @@ constexpr int kStageElemsC128 = QT_STAGE_BYTES / 16;
 constexpr int kLeafBits = 5;
 constexpr int kMaxFoldLeaves = 8;
 constexpr uint8_t kBucketFoldLeaves = 1;
+constexpr uint8_t kBucketInUnit = 2;    // inside a fused unit, not its root: never claimed on its own
+constexpr uint8_t kBucketUnitRoot = 4;  // the root (last bucket) of a fused unit
+// Fused units: a subtree of small buckets (every output count at most
+// 2^kFuseOutBits, every non-gate operand produced inside the subtree) is one
+// work group; one warp contracts its buckets in elimination order with the
+// intermediates in its shared-memory stage and writes only the root's result.
+#ifndef QT_FUSE_OUT_BITS
+#define QT_FUSE_OUT_BITS 8
+#endif
+constexpr int kFuseOutBits = QT_FUSE_OUT_BITS;
 constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim (default)
 constexpr int kBwdTileBits = 8;      // outputs per reverse-sweep tile, log2
 constexpr int kBwdRedElems = 1024;   // per-warp shared-memory elements for in-tile cotangent sums
@@ -62,12 +72,13 @@ struct DBucket {
     uint32_t total_foot;// staged elements per tile
     uint8_t n_staged;   // operands copied into the stage buffer
     uint8_t n_leaves;   // gate tensors folded into the product table
-    uint16_t pad0;
+    uint16_t scr_off;   // kBucketInUnit: element offset of its result in the warp's stage
     uint32_t leaf_u;    // folded gate masks within the tile
     uint32_t leaf_hi;   // folded gate masks above the tile (nonzero: the table changes per tile)
     uint32_t group_tiles; // tiles per work group (the unit a warp claims)
-    uint32_t n_groups;    // ceil(n_tasks / group_tiles)
-    uint32_t pad1[2];
+    uint32_t n_groups;    // ceil(n_tasks / group_tiles); 1 for a unit root, 0 inside a unit
+    uint32_t unit_begin;  // kBucketUnitRoot: 1 + the unit's first entry in the unit list
+    uint32_t unit_count;  // kBucketUnitRoot: the unit's buckets (the root last)
 };
 static_assert(sizeof(DBucket) == 64, "DBucket layout");
 
@@ -94,7 +105,9 @@ struct DRun {
     uint32_t n_chunks;
     uint32_t op_begin;  // the bucket's first operand (saves a dependent load)
     uint32_t n_deps;    // producers that must finish before the group may start
-    uint32_t pad[3];
+    uint32_t unit_begin;// fused unit: 1 + its first entry in the unit list (0: an ordinary group)
+    uint32_t unit_count;// fused unit: its buckets (the root last)
+    uint32_t pad;
 };
 static_assert(sizeof(DRun) == 32, "DRun layout");
 

@@ -40,7 +40,7 @@ class PlanOpts(ctypes.Structure):
                 ("order_seed", ctypes.c_uint64), ("max_width", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
                 ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
-                ("order", ctypes.c_int32)]
+                ("order", ctypes.c_int32), ("no_fuse", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -49,13 +49,14 @@ class PlanStats(ctypes.Structure):
                 ("sum_2w", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("flops", ctypes.c_double),
                 ("arena_bytes", ctypes.c_int64), ("n_tasks", ctypes.c_int64), ("n_items", ctypes.c_int64),
                 ("n_levels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("width_hist", ctypes.c_int64 * 64),
-                ("plan_seconds", ctypes.c_double), ("sim_seconds", ctypes.c_double)]
+                ("plan_seconds", ctypes.c_double), ("sim_seconds", ctypes.c_double),
+                ("n_units", ctypes.c_int64), ("n_fused", ctypes.c_int64)]
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
                          ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32),
                          ("tile_log2", np.int32), ("tile_bits", np.uint32), ("folded", np.uint32),
-                         ("pad", np.uint32)])
+                         ("unit_role", np.uint32)])
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                           ("mask", np.uint32), ("rank", np.int32), ("pad", np.int32)])
 
@@ -173,7 +174,7 @@ class Plan:
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
-              order="simulated"):
+              order="simulated", fuse=True):
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
         o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
@@ -188,6 +189,7 @@ class Plan:
         o.run_tiles = int(run_tiles)
         o.trace = int(bool(trace))
         o.order = {"simulated": 0, "ready_queue": 1}[order]
+        o.no_fuse = 0 if fuse else 1
         return o
 
     @classmethod

@@ -212,6 +212,32 @@ def test_c5_n50_p4_matches_bucket_golden(dtype):
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("order", ["simulated", "ready_queue"])
+def test_fused_units_match_unfused_and_oracle(dtype, order):
+    """A batch with enough small buckets to form fused units (subtrees run in
+    one warp's shared memory) against the same plan without units and the
+    oracle's bucket elimination."""
+    p = 3
+    graphs = synth.batch(12, p, lo=50, hi=300, base_seed=2000)
+    spec = [(n, e) for n, e, _, _ in graphs]
+    G = np.array([gg for _, _, gg, _ in graphs])
+    Bt = np.array([bb for _, _, _, bb in graphs])
+    with qtgb.plan_batch(spec, p, dtype=dtype, order=order) as pl:
+        assert pl.stats()["n_units"] > 0
+        e_f, zz_f = pl.energy_batch(G, Bt)
+    with qtgb.plan_batch(spec, p, dtype=dtype, order=order, fuse=False) as pl:
+        assert pl.stats()["n_units"] == 0
+        e_u, zz_u = pl.energy_batch(G, Bt)
+    assert scaled_err(zz_f, zz_u) <= TOL[dtype]
+    first = 0
+    for gi, (n, e, gg, bb) in enumerate(graphs[:3]):
+        ref, _ = oracle.bucket_zz(n, e, gg, bb, seed=1)
+        m = e.shape[0]
+        assert scaled_err(zz_f[first:first + m], ref.real) <= TOL[dtype]
+        first += m
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("order", ["simulated", "ready_queue"])
 def test_batch_of_graphs_matches_oracle(dtype, order):
     p = 3
     graphs = synth.batch(6, p, lo=50, hi=120, base_seed=1000)
@@ -262,7 +288,8 @@ def test_stalled_dependency_times_out_and_context_survives():
     n, p = 12, 2
     edges = synth.random_regular_graph(n, 3)
     g, b = synth.angles(p, 3)
-    with qtgb.plan(n, edges, p, dtype="c64", spin_limit=2000) as pl:
+    # without fused units every bucket waits on its producers' counters
+    with qtgb.plan(n, edges, p, dtype="c64", spin_limit=2000, fuse=False) as pl:
         B, _ = pl.export()
         victim = int(np.nonzero(B["parent"] >= 0)[0][-1])  # a producer: its consumer can never start
         pl.debug_stall_bucket(victim)

@@ -277,3 +277,42 @@ def test_tile_copy_arithmetic(dtype, stage_elems):
     wide = [b for b in range(len(B)) if B["width"][b] >= 12]
     for b in wide[:40] + [int(x) for x in rng.choice(len(B), size=60, replace=False)]:
         assert _check_tiles(B, O, b) <= stage_elems
+
+
+def test_fused_units_are_closed_small_subtrees():
+    """Fused units: every member has at most 2^8 outputs; a member's consumer is
+    in its unit (a member or the root); a root's consumer is outside; every
+    operand of a member or root that is an earlier result comes from the same
+    unit. Gradient plans and the per-bucket schedule form no units."""
+    graphs = [(n, e) for n, e, _, _ in synth.batch(4, 3, lo=50, hi=200, base_seed=1000)]
+    with qtgb.plan_batch(graphs, 3, host_only=True) as pl:
+        B, O = pl.export()
+        st = pl.stats()
+    role = B["unit_role"]
+    assert st["n_units"] == int((role == 2).sum()) > 0
+    assert st["n_fused"] == int((role > 0).sum())
+    # unit of each bucket: walk up through members to the root
+    unit = np.full(len(B), -1)
+    for b in range(len(B)):
+        if role[b] == 0:
+            continue
+        r = b
+        while role[r] == 1:
+            r = B["parent"][r]
+            assert r >= 0 and role[r] > 0
+        unit[b] = r
+    for b in np.nonzero(role > 0)[0]:
+        assert B["width"][b] - 1 <= 8
+        ob, no = B["op_begin"][b], B["n_ops"][b]
+        for src in O["src"][ob:ob + no]:
+            if src >= 0:
+                assert unit[src] == unit[b] and role[src] == 1
+    for b in np.nonzero(role == 2)[0]:
+        par = B["parent"][b]
+        assert par < 0 or unit[par] != unit[b]
+    with qtgb.plan_batch(graphs, 3, host_only=True, with_grad=True) as pl:
+        assert pl.stats()["n_units"] == 0
+    with qtgb.plan_batch(graphs, 3, host_only=True, sched="per_bucket") as pl:
+        assert pl.stats()["n_units"] == 0
+    with qtgb.plan_batch(graphs, 3, host_only=True, fuse=False) as pl:
+        assert pl.stats()["n_units"] == 0
