@@ -143,7 +143,7 @@ int upload(qt_plan_t P) {
         {nullptr, 0, 0},                                       {hp.runs.data(), bytes_of(hp.runs), 0},
         {nullptr, 0, 0},                                       {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
-        {hp.unit_list.data(), bytes_of(hp.unit_list), 0},
+        {hp.unit_prog.data(), bytes_of(hp.unit_prog), 0},
     };
     size_t total = 0;
     for (auto& pc : pieces) {
@@ -178,7 +178,7 @@ int upload(qt_plan_t P) {
     dp.buckets = reinterpret_cast<const qt::DBucket*>(base + pieces[0].off);
     dp.ops = reinterpret_cast<const qt::DOperand*>(base + pieces[1].off);
     dp.runs = reinterpret_cast<const qt::DRun*>(base + pieces[3].off);
-    dp.unit_list = reinterpret_cast<const uint32_t*>(base + pieces[8].off);
+    dp.unit_prog = reinterpret_cast<const qt::URec*>(base + pieces[8].off);
     dp.has_units = hp.n_units > 0 ? 1u : 0u;
     dp.n_static = (uint32_t)hp.runs.size();
     dp.n_groups = (uint32_t)hp.n_groups;
@@ -811,7 +811,7 @@ ScratchLayout scratch_layout(const qt::HostPlan& hp, size_t esize) {
     L.net_first_root = take(hp.net_first_root.size() * sizeof(uint32_t));
     L.root_bucket = take(hp.root_bucket.size() * sizeof(uint32_t));
     L.graph_first_net = take(hp.graph_first_net.size() * sizeof(int32_t));
-    L.unit_list = take(hp.unit_list.size() * sizeof(uint32_t));
+    L.unit_list = take(hp.unit_prog.size() * sizeof(qt::URec));
     L.ctl_bytes = 256;
     L.cnt_bytes = pad256(2 * nb * sizeof(uint32_t));
     L.counters_bytes = L.ctl_bytes + L.cnt_bytes + (size_t)(hp.n_groups - hp.runs.size()) * sizeof(qt::DSlot);
@@ -896,8 +896,8 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     static_assert(sizeof(int) == sizeof(int32_t), "graph_first_net is copied as int32");
     QT_CUDA(cudaMemcpyAsync(base + L.graph_first_net, hp.graph_first_net.data(), bytes_of(hp.graph_first_net),
                             cudaMemcpyHostToDevice, s));
-    if (!hp.unit_list.empty())
-        QT_CUDA(cudaMemcpyAsync(base + L.unit_list, hp.unit_list.data(), bytes_of(hp.unit_list),
+    if (!hp.unit_prog.empty())
+        QT_CUDA(cudaMemcpyAsync(base + L.unit_list, hp.unit_prog.data(), bytes_of(hp.unit_prog),
                                 cudaMemcpyHostToDevice, s));
     // the array keeps the previous call's contents: counters and the queue start at zero
     QT_CUDA(cudaMemsetAsync(base + L.counters, 0, L.counters_bytes, s));
@@ -909,7 +909,7 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     dp.buckets = reinterpret_cast<const qt::DBucket*>(base + L.buckets);
     dp.ops = reinterpret_cast<const qt::DOperand*>(base + L.ops);
     dp.runs = reinterpret_cast<const qt::DRun*>(base + L.runs);
-    dp.unit_list = reinterpret_cast<const uint32_t*>(base + L.unit_list);
+    dp.unit_prog = reinterpret_cast<const qt::URec*>(base + L.unit_list);
     dp.has_units = hp.n_units > 0 ? 1u : 0u;
     dp.n_static = (uint32_t)hp.runs.size();
     dp.n_groups = (uint32_t)hp.n_groups;

@@ -791,44 +791,51 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
 
 // A fused unit: its buckets in elimination order, one output per lane at a
 // time, intermediates in stage st (free: a unit stages nothing), the root's
-// result to the arena. Each bucket's operand descriptors are first copied to
-// the warp's gate-table area (unused by units).
+// result to the arena. The unit's program is read kURecWindow records at a
+// time, one per lane, with one coalesced load; each bucket's operand records
+// go to the warp's gate-table area (unused by units) for the output loop.
+__device__ __forceinline__ URec shfl_rec(const URec& r, int src) {
+    URec o;
+    o.a = __shfl_sync(kFull, r.a, src);
+    o.b = __shfl_sync(kFull, r.b, src);
+    o.off = __shfl_sync(kFull, r.off, src);
+    return o;
+}
+
 template <typename R>
 __device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int lane) {
     using C = typename CT<R>::c;
-    struct UOp {
-        uint32_t mask;
-        uint32_t in_stage;  // 1: an intermediate of the unit (stage offset), 0: a gate tensor (arena offset)
-        uint64_t off;
-    };
-    static_assert(sizeof(UOp) * kMaxOps <= sizeof(ws.leaf_tab), "unit operand descriptors");
-    UOp* uops = reinterpret_cast<UOp*>(ws.leaf_tab);
+    static_assert(sizeof(URec) * kMaxOps <= sizeof(ws.leaf_tab), "unit operand records");
+    static_assert(kURecWindow == 32 && kMaxOps + 1 <= kURecWindow, "one bucket's records fit the window");
+    URec* uops = reinterpret_cast<URec*>(ws.leaf_tab);
     const RunSlot<R>& rs = ws.slot[sl];
     C* scr = ws.stage[st];
     C* arena = static_cast<C*>(dp.arena);
-    const uint32_t first = rs.unit_begin - 1u, count = rs.unit_count;
-    for (uint32_t k = 0; k < count; ++k) {
-        const uint32_t u = dp.unit_list[first + k];
-        const DBucket B = dp.buckets[u];
-        if (lane < B.n_ops) {
-            const DOperand op = dp.ops[B.op_begin + lane];
-            UOp d;
-            d.mask = op.mask;
-            d.in_stage = (op.flags & kOpLeaf) ? 0u : 1u;
-            d.off = (op.flags & kOpLeaf) ? op.off : (uint64_t)dp.buckets[op.src].scr_off;
-            uops[lane] = d;
+    const URec* prog = dp.unit_prog + (rs.unit_begin - 1u);
+    uint32_t pos = 0, base = 0;  // next record; first record held in the window
+    URec mine = prog[lane];
+    for (uint32_t k = 0; k < rs.unit_count; ++k) {
+        if (pos + 1u + kMaxOps > base + kURecWindow) {  // refill: the bucket's records all in the window
+            base = pos;
+            mine = prog[base + lane];
         }
+        const URec h = shfl_rec(mine, (int)(pos - base));
+        const uint32_t n_out = h.a & 0xffu, n_ops = (h.a >> 8) & 0xffu;
+        const bool root = (h.a >> 16) & 1u;
+        const int first_op = (int)(pos + 1u - base);
+        const URec r = shfl_rec(mine, (first_op + lane) & (kURecWindow - 1));  // lane t: operand t
+        if (lane < (int)n_ops) uops[lane] = r;
+        pos += 1u + n_ops;
         __syncwarp();
-        C* dst = k + 1 == count ? arena + B.out_off : scr + B.scr_off;
-        const uint32_t n_out = 1u << B.n_out;
-        for (uint32_t o = lane; o < n_out; o += 32) {
+        C* dst = root ? arena + rs.out_off : scr + h.b;
+        for (uint32_t o = lane; o < (1u << n_out); o += 32) {
             C a0, a1;
             a0.x = a1.x = (R)1;
             a0.y = a1.y = (R)0;
-            for (int t = 0; t < B.n_ops; ++t) {
-                const UOp d = uops[t];
-                const uint32_t e = 2u * pext_u32(o, d.mask);
-                const C* src = d.in_stage ? scr + d.off : arena + d.off;
+            for (uint32_t t = 0; t < n_ops; ++t) {
+                const URec d = uops[t];
+                const uint32_t e = 2u * pext_u32(o, d.a);
+                const C* src = d.b ? scr + d.off : arena + d.off;
                 a0 = cmul(a0, src[e]);
                 a1 = cmul(a1, src[e + 1]);
             }

@@ -25,7 +25,7 @@ struct DevPlan {
     uint64_t* trace;        // per-warp phase counters (kTraceSlots each), or null: untraced kernel
     uint32_t isolated;      // nonzero: run only the groups in `runs` and notify no consumer
     unsigned long long* bucket_times;  // traced runs: per bucket, first group start and last group end (ns)
-    const uint32_t* unit_list;  // fused units' buckets (DRun.unit_begin - 1 indexes it)
+    const URec* unit_prog;      // fused units' programs (DRun.unit_begin - 1 indexes them)
     uint32_t has_units;         // nonzero: the plan has fused units (the kernel variant that runs them)
 };
 

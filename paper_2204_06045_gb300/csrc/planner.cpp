@@ -341,7 +341,7 @@ static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 // first-fit by lifetime (a result is freed once its consumer is done), fit the
 // stage; a subtree that does not fit is split at its root.
 static void form_units(HostPlan* hp, int stage_elems) {
-    hp->unit_list.clear();
+    hp->unit_prog.clear();
     hp->n_units = 0;
     hp->n_fused = 0;
     if (!hp->cfg.fuse) return;
@@ -409,9 +409,19 @@ static void form_units(HostPlan* hp, int stage_elems) {
                 hp->buckets[root].flags |= kBucketUnitRoot;
                 for (uint32_t u : members)
                     if (u != root) hp->buckets[u].flags |= kBucketInUnit;
-                hp->buckets[root].unit_begin = (uint32_t)hp->unit_list.size() + 1u;
+                hp->buckets[root].unit_begin = (uint32_t)hp->unit_prog.size() + 1u;
                 hp->buckets[root].unit_count = (uint32_t)members.size();
-                hp->unit_list.insert(hp->unit_list.end(), members.begin(), members.end());
+                for (uint32_t u : members) {
+                    const DBucket& m = hp->buckets[u];
+                    hp->unit_prog.push_back(URec{(uint32_t)m.n_out | ((uint32_t)m.n_ops << 8) | (u == root ? 1u << 16 : 0u),
+                                                 u == root ? 0u : (uint32_t)m.scr_off, 0});
+                    for (uint32_t i = m.op_begin; i < m.op_begin + m.n_ops; ++i) {
+                        const DOperand& o = hp->operands[i];
+                        const bool leaf = (o.flags & kOpLeaf) != 0;
+                        hp->unit_prog.push_back(
+                            URec{o.mask, leaf ? 0u : 1u, leaf ? o.off : (uint64_t)hp->buckets[hp->op_src[i]].scr_off});
+                    }
+                }
                 hp->n_units++;
                 hp->n_fused += members.size();
             } else {
@@ -429,10 +439,11 @@ static void form_units(HostPlan* hp, int stage_elems) {
             d.unit_begin = d.unit_count = 0;
             d.scr_off = 0;
         }
-        hp->unit_list.clear();
+        hp->unit_prog.clear();
         hp->n_units = hp->n_fused = 0;
         return;
     }
+    hp->unit_prog.resize(hp->unit_prog.size() + kURecWindow, URec{0, 0, 0});  // window reads past the last unit
     // a unit is one group; its members are never claimed on their own
     hp->n_groups = 0;
     for (uint32_t b = 0; b < nb; ++b) {

@@ -88,7 +88,7 @@ struct HostPlan {
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
-    std::vector<uint32_t> unit_list;    // fused units' buckets, unit by unit, each in elimination order
+    std::vector<URec> unit_prog;        // fused units' programs, unit by unit (padded by kURecWindow records)
     uint64_t n_units = 0;
     uint64_t n_fused = 0;               // buckets inside fused units (roots included)
     uint64_t n_tiles = 0;

@@ -77,7 +77,7 @@ struct DBucket {
     uint32_t leaf_hi;   // folded gate masks above the tile (nonzero: the table changes per tile)
     uint32_t group_tiles; // tiles per work group (the unit a warp claims)
     uint32_t n_groups;    // ceil(n_tasks / group_tiles); 1 for a unit root, 0 inside a unit
-    uint32_t unit_begin;  // kBucketUnitRoot: 1 + the unit's first entry in the unit list
+    uint32_t unit_begin;  // kBucketUnitRoot: 1 + the unit's first record in the unit programs
     uint32_t unit_count;  // kBucketUnitRoot: the unit's buckets (the root last)
 };
 static_assert(sizeof(DBucket) == 64, "DBucket layout");
@@ -105,7 +105,7 @@ struct DRun {
     uint32_t n_chunks;
     uint32_t op_begin;  // the bucket's first operand (saves a dependent load)
     uint32_t n_deps;    // producers that must finish before the group may start
-    uint32_t unit_begin;// fused unit: 1 + its first entry in the unit list (0: an ordinary group)
+    uint32_t unit_begin;// fused unit: 1 + its first record in the unit programs (0: an ordinary group)
     uint32_t unit_count;// fused unit: its buckets (the root last)
     uint32_t pad;
 };
@@ -120,6 +120,20 @@ struct DSlot {
     uint32_t n_chunks;  // written last (release); nonzero marks the slot as published
 };
 static_assert(sizeof(DSlot) == 16, "DSlot layout");
+
+// A fused unit's program: for each bucket, in elimination order, a header
+// record then one record per operand. 16 bytes.
+//   header:  a = n_out | n_ops << 8 | (1 << 16 if the unit's root), b = stage
+//            offset of the result (not the root), off unused
+//   operand: a = mask, b = 1 for an intermediate of the unit (off: its stage
+//            offset), 0 for a gate tensor (off: arena offset)
+struct URec {
+    uint32_t a;
+    uint32_t b;
+    uint64_t off;
+};
+static_assert(sizeof(URec) == 16, "URec layout");
+constexpr int kURecWindow = 32;  // records a warp holds at once (one per lane)
 
 // Counters the persistent kernel uses; zeroed before every run.
 struct DControl {
