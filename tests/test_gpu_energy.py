@@ -237,6 +237,26 @@ def test_fused_units_match_unfused_and_oracle(dtype, order):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_whole_networks_as_fused_units(dtype):
+    """p=1 networks are small enough that each network's whole bucket tree is
+    one fused unit, its root the network's scalar: energies against the p=1
+    closed form."""
+    graphs = synth.batch(200, 1, lo=20, hi=60, base_seed=4000)
+    spec = [(n, e) for n, e, _, _ in graphs]
+    with qtgb.plan_batch(spec, 1, dtype=dtype) as pl:
+        st = pl.stats()
+        assert st["n_units"] == st["n_networks"] and st["n_fused"] == st["n_buckets"]
+        G = np.array([gg for _, _, gg, _ in graphs])
+        Bt = np.array([bb for _, _, _, bb in graphs])
+        _, zz = pl.energy_batch(G, Bt)
+    first = 0
+    for n, e, gg, bb in graphs[:20]:
+        m = e.shape[0]
+        assert scaled_err(zz[first:first + m], oracle.p1_closed_form(n, e, gg[0], bb[0])) <= TOL[dtype]
+        first += m
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("order", ["simulated", "ready_queue"])
 def test_batch_of_graphs_matches_oracle(dtype, order):
     p = 3

@@ -119,3 +119,22 @@ def test_noalloc_device_buffers_on_a_stream():
             pl.energy_noalloc(gd, bd, energies=en, edge_zz=zz, stream=s)
             assert scaled_err(zz.cpu().numpy(), zz_ref) <= TOL["c64"]
             assert abs(float(en.cpu()[0]) - e_ref) <= TOL["c64"] * abs(e_ref)
+
+
+@pytest.mark.gpu
+def test_noalloc_batch_with_fused_units():
+    """A batch whose small buckets form fused units (their programs also live
+    in the static array) against qt_energy_batch, two calls in a row."""
+    _gpu_setup()
+    graphs = synth.batch(8, 2, lo=40, hi=120, base_seed=3000)
+    spec = [(n, e) for n, e, _, _ in graphs]
+    G = np.array([gg for _, _, gg, _ in graphs])
+    B = np.array([bb for _, _, _, bb in graphs])
+    with qtgb.plan_batch(spec, 2, dtype="c64") as ref_plan, qtgb.plan_batch(spec, 2, dtype="c64",
+                                                                           host_only=True) as pl:
+        assert pl.stats()["n_units"] > 0
+        e_ref, zz_ref = ref_plan.energy_batch(G, B)
+        for _ in range(2):
+            energies, zz = pl.energy_noalloc(G, B)
+            assert scaled_err(zz, zz_ref) <= TOL["c64"]
+            assert np.all(np.abs(energies - e_ref) <= TOL["c64"] * np.abs(e_ref))
