@@ -150,6 +150,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
     return v;
 }
 
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *reinterpret_cast<const volatile int32_t*>(p); }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -883,13 +888,13 @@ __device__ __forceinline__ void finish_group(const DevPlan& dp, const RunSlot<R>
     const uint32_t parent = rs.parent;
     if (dp.isolated) return;
     if (lane == 0) {
-        __threadfence();
-        const uint32_t done = atomicAdd(&dp.tiles_done[rs.bucket], rs.n_chunks) + rs.n_chunks;
+        // acquire-release adds: the group that completes the bucket has
+        // acquired the other groups' results before it releases them (with its
+        // own) to the consumer, whose dependency check is an acquire load
+        const uint32_t done = atom_add_acq_rel(&dp.tiles_done[rs.bucket], rs.n_chunks) + rs.n_chunks;
         if (done == rs.n_tasks && parent != kNone) {
-            __threadfence();
-            const uint32_t pd = atomicAdd(&dp.prod_done[parent], 1u) + 1u;
+            const uint32_t pd = atom_add_acq_rel(&dp.prod_done[parent], 1u) + 1u;
             push = pd == dp.buckets[parent].n_deps;
-            if (push) __threadfence();
         }
     }
     push = __shfl_sync(kFull, push, 0);
