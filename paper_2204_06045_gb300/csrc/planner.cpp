@@ -502,11 +502,14 @@ static void simulate_order(HostPlan* hp) {
         // a fused unit waits for nothing; its members never run on their own
         deps_left[b] = (d.flags & kBucketUnitRoot) ? 0u : (d.flags & kBucketInUnit) ? 1u : d.n_deps;
     }
-    std::vector<uint32_t> groups_left(nb);
-    for (size_t b = 0; b < nb; ++b) groups_left[b] = hp->buckets[b].n_groups;
+    std::vector<uint32_t> groups_left(nb), gsize(nb);
+    for (size_t b = 0; b < nb; ++b) {
+        groups_left[b] = hp->buckets[b].n_groups;
+        gsize[b] = hp->buckets[b].group_tiles;
+    }
     struct Ready {
         double prio;
-        uint32_t bucket, next_group;
+        uint32_t bucket, next_tile;
         bool operator<(const Ready& o) const { return prio < o.prio || (prio == o.prio && bucket > o.bucket); }
     };
     std::priority_queue<Ready> ready;  // buckets with unstarted groups, highest priority first
@@ -518,7 +521,7 @@ static void simulate_order(HostPlan* hp) {
     uint64_t free_workers = (uint64_t)W;
     hp->runs.clear();
     hp->runs.reserve(hp->n_groups);
-    while (hp->runs.size() < hp->n_groups) {
+    while (!ready.empty() || !running.empty()) {
         while (free_workers > 0 && !ready.empty()) {
             Ready r = ready.top();
             ready.pop();
@@ -529,12 +532,36 @@ static void simulate_order(HostPlan* hp) {
                 --free_workers;
                 continue;
             }
-            const uint32_t c = r.next_group * d.group_tiles;
-            const uint32_t n = std::min(d.group_tiles, d.n_tasks - c);
+            if (r.next_tile == 0 && cfg.run_tiles == 0) {
+                // Group size when the bucket starts: where the GPU is nearly
+                // idle (QT_SPLIT_SHARE free warps or more per ready bucket, as
+                // on the chains that end every network), the bucket spreads
+                // over its share of them, in groups of QT_MIN_GROUP tiles or
+                // more; elsewhere group_tiles. Measured on GB300: 64 and 8 gave
+                // the N=30 p=4 plan 4.5% over fixed groups of 16; smaller groups
+                // lost (each group costs a claim, descriptor reads and a copy
+                // round trip that the host model undercounts).
+#ifndef QT_SPLIT_SHARE
+#define QT_SPLIT_SHARE 64
+#endif
+#ifndef QT_MIN_GROUP
+#define QT_MIN_GROUP 8
+#endif
+                const double share = (double)free_workers / (double)(ready.size() + 1);
+                if (share >= QT_SPLIT_SHARE) {
+                    const double want = std::ceil((double)d.n_tasks / share);
+                    gsize[r.bucket] = (uint32_t)std::max<double>(std::min<double>(QT_MIN_GROUP, d.group_tiles),
+                                                                 std::min<double>(d.group_tiles, want));
+                }
+                groups_left[r.bucket] = (d.n_tasks + gsize[r.bucket] - 1) / gsize[r.bucket];
+            }
+            const uint32_t c = r.next_tile;
+            const uint32_t n = std::min(gsize[r.bucket], d.n_tasks - c);
             hp->runs.push_back(DRun{r.bucket, c, n, d.op_begin, d.n_deps, 0, 0, 0});
             running.push(Ev{now + tile_s[r.bucket] * n + t_group, r.bucket});
             --free_workers;
-            if (++r.next_group < d.n_groups) ready.push(r);
+            r.next_tile = c + n;
+            if (r.next_tile < d.n_tasks) ready.push(r);
         }
         if (running.empty()) break;  // cannot happen with a consistent plan
         const Ev e = running.top();
@@ -551,6 +578,7 @@ static void simulate_order(HostPlan* hp) {
         running.pop();
     }
     hp->sim_seconds = now;
+    hp->n_groups = hp->runs.size();  // the queue: every group, in claim order
 }
 
 int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, HostPlan* hp) {
