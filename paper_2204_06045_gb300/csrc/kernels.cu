@@ -212,6 +212,7 @@ struct RunSlot {
     uint32_t leaf_hi;     // nonzero if a folded gate mask has bits above the tile
     uint32_t total_foot;  // staged elements per tile
     uint8_t n_out, cb, n_staged, n_leaves;
+    uint8_t n_ops;
     uint32_t bad;         // the plan's footprint exceeds the stage: not computed
     // per-group constants of the unrolled tile loop, for the staged operands
     // and the gate table (at most kFast of them)
@@ -346,7 +347,8 @@ __device__ bool wait_group(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
 // compressed index of the group's first tile in its operand's bits above the
 // tile (pext(o0, M) is that index shifted left by the operand's tile bits).
 template <typename R, bool Units>
-__device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun& run, int lane, uint32_t* cbase) {
+__device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun& run, int lane, uint32_t* cbase,
+                         bool results_ready = true) {
     using C = typename CT<R>::c;
     if (Units && run.unit_begin) {  // a fused unit: nothing to stage, no gate table
         RunSlot<R>& us = ws.slot[sl];
@@ -388,8 +390,10 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             // allocation is 128-byte aligned, so 4 entries stay inside it
             rs.lmask[op.slot] = op.mask;
             const C* T = static_cast<const C*>(dp.arena) + op.off;
+            if ((op.flags & kOpLeaf) || results_ready) {
 #pragma unroll
-            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = (op.flags & kOpLeaf) ? T[i] : ldcg_c(T + i);
+                for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = (op.flags & kOpLeaf) ? T[i] : ldcg_c(T + i);
+            }
         } else {
             rs.goff[op.slot] = op.off;
             rs.gmask[op.slot] = op.mask;
@@ -410,6 +414,7 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
         rs.cb = B.chunk_bits;
         rs.n_staged = B.n_staged;
         rs.n_leaves = B.n_leaves;
+        rs.n_ops = B.n_ops;
         rs.unit_begin = 0;
         rs.unit_count = 0;
         rs.bad = !fits;
@@ -441,6 +446,22 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
                 ++nh;
             }
         rs.n_hi = nh;
+    }
+    __syncwarp();
+}
+
+// A group prepared before its producers finished: read the earlier results
+// folded into its gate table (rank <= 2, read at L2) now that they are done.
+template <typename R>
+__device__ void load_folded_results(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun& run, int lane) {
+    RunSlot<R>& rs = ws.slot[sl];
+    if (!rs.bad && lane < rs.n_ops) {
+        const DOperand op = dp.ops[run.op_begin + lane];
+        if (op.folded && !(op.flags & kOpLeaf)) {
+            const typename CT<R>::c* T = static_cast<const typename CT<R>::c*>(dp.arena) + op.off;
+#pragma unroll
+            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = ldcg_c(T + i);
+        }
     }
     __syncwarp();
 }
@@ -995,7 +1016,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
         while (ok) {
             int sb = sa;
             uint32_t b_chunk = a_chunk + 1, b_left = a_left - 1, qb = 0;
-            bool b_valid = true, b_first = false, b_issued = false;
+            bool b_valid = true, b_first = false, b_issued = false, b_prepped = false;
             DRun rb;
             if (a_left > 1) {
                 pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase);
@@ -1019,6 +1040,13 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                     b_left = rb.n_chunks;
                     b_first = true;
                     clk.lap(kTrIssue);
+                } else if (b_valid && qb < dp.n_static) {
+                    // not ready yet: prepare everything that does not depend
+                    // on its producers while tile A is contracted
+                    sb = sa ^ 1;
+                    prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase, false);
+                    b_prepped = true;
+                    clk.lap(kTrPrep);
                 }
             }
             if (!wait_stage<R>(dp, ws, sa, st, phase, lane)) break;
@@ -1038,7 +1066,10 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                 if (!wait_group(dp, qb, &rb, lane)) break;
                 clk.lap(kTrDeps);
                 sb = sa ^ 1;
-                prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
+                if (b_prepped)
+                    load_folded_results<R>(dp, ws, sb, rb, lane);
+                else
+                    prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
                 mark_bucket<Trace>(dp, rb.bucket, false, lane);
                 clk.lap(kTrPrep);
                 clk.count(kTrRuns, 1);
