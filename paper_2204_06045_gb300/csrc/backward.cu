@@ -88,13 +88,13 @@ constexpr int kBwdWarps = 4;  // warps per block of the reverse sweep, one (buck
 // operand's pair index pext(o, M) is split, as in the forward tile loop, into
 // the tile's part (once per task), the lane's part and the steps of the
 // iteration bits, so no output pays for a bit-by-bit extract.
-template <typename R, int NMAX>
+template <typename R, int NMAX, bool Exact>
 __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, typename CT<R>::c* red) {
     using C = typename CT<R>::c;
     constexpr int KB = kBwdTileBits - 5;  // iteration bits at most
     C* arena = static_cast<C*>(db.arena);
     const DBucket B = db.buckets[b];
-    const int n = B.n_ops;
+    const int n = Exact ? NMAX : (int)B.n_ops;  // Exact: every bucket of the launch has NMAX operands
     const int tb = min((int)B.n_out, kBwdTileBits);
     const int kb = tb > 5 ? tb - 5 : 0;
     const uint32_t low = (1u << tb) - 1u;
@@ -250,7 +250,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
 
 // One launch per level and operand-count class (buckets of at most NMAX
 // operands), so that each instantiation keeps its own register budget.
-template <typename R, int NMAX>
+template <typename R, int NMAX, bool Exact>
 __global__ void __launch_bounds__(kBwdWarps * 32, NMAX <= 4 ? 4 : 2) k_backward(DevBwd db) {
     using C = typename CT<R>::c;
     extern __shared__ __align__(16) unsigned char bwd_smem[];
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, NMAX <= 4 ? 4 : 2) k_backward(
     const uint32_t w = blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= db.n_tasks) return;
-    bwd_tile<R, NMAX>(db, db.task_bucket[w], db.task_tile[w], lane, red);
+    bwd_tile<R, NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
 }
 
 // Zero the cotangent pieces that receive atomic adds: (offset, count) pairs,
@@ -292,29 +292,34 @@ cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint
     return cudaGetLastError();
 }
 
-template <typename R, int NMAX>
+template <typename R, int NMAX, bool Exact>
 static cudaError_t launch_bwd(const DevBwd& db, cudaStream_t s) {
     const uint32_t blocks = (db.n_tasks + kBwdWarps - 1) / kBwdWarps;
     const size_t smem = (size_t)kBwdWarps * kBwdRedElems * sizeof(typename CT<R>::c);
     if (smem > 48 * 1024) {
         const cudaError_t e =
-            cudaFuncSetAttribute(k_backward<R, NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_backward<R, NMAX, Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_backward<R, NMAX><<<blocks, kBwdWarps * 32, smem, s>>>(db);
+    k_backward<R, NMAX, Exact><<<blocks, kBwdWarps * 32, smem, s>>>(db);
     return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_bwd_class(int op_class, const DevBwd& db, cudaStream_t s) {
+    switch (op_class) {
+        case 0: return launch_bwd<R, 1, true>(db, s);
+        case 1: return launch_bwd<R, 2, true>(db, s);
+        case 2: return launch_bwd<R, 3, true>(db, s);
+        case 3: return launch_bwd<R, 4, true>(db, s);
+        case 4: return launch_bwd<R, 8, false>(db, s);
+        default: return launch_bwd<R, kMaxOps, false>(db, s);
+    }
 }
 
 cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s) {
     if (db.n_tasks == 0) return cudaSuccess;
-    if (dtype == QT_C128) {
-        if (op_class == 0) return launch_bwd<double, 4>(db, s);
-        if (op_class == 1) return launch_bwd<double, 8>(db, s);
-        return launch_bwd<double, kMaxOps>(db, s);
-    }
-    if (op_class == 0) return launch_bwd<float, 4>(db, s);
-    if (op_class == 1) return launch_bwd<float, 8>(db, s);
-    return launch_bwd<float, kMaxOps>(db, s);
+    return dtype == QT_C128 ? launch_bwd_class<double>(op_class, db, s) : launch_bwd_class<float>(op_class, db, s);
 }
 
 cudaError_t launch_zero_ranges(int dtype, void* arena, const uint64_t* ranges, uint32_t n_ranges, cudaStream_t s) {

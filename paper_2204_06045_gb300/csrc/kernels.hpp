@@ -78,7 +78,7 @@ struct DevBwd {
 cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, uint64_t dleaf_off,
                              cudaStream_t s);
 cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s);
-// op_class: the level's tasks of buckets with at most 4 (0), 8 (1) or 16 (2) operands
+// op_class: the level's tasks of buckets with exactly 1..4 operands (0..3), at most 8 (4) or 16 (5)
 cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s);
 
 cudaError_t launch_zero_ranges(int dtype, void* arena, const uint64_t* ranges, uint32_t n_ranges, cudaStream_t s);

@@ -42,9 +42,10 @@ constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim
 constexpr int kBwdTileBits = 8;      // outputs per reverse-sweep tile, log2
 constexpr int kBwdRedElems = 1024;   // per-warp shared-memory elements for in-tile cotangent sums
 constexpr uint32_t kZeroChunk = 1u << 16;  // elements per block of the cotangent zeroing kernel
-// Reverse-sweep launches per level: buckets of at most 4, 8 or 16 operands.
-constexpr int kBwdClasses = 3;
-constexpr int bwd_op_class(int n_ops) { return n_ops <= 4 ? 0 : n_ops <= 8 ? 1 : 2; }
+// Reverse-sweep launches per level: buckets of exactly 1, 2, 3 or 4 operands
+// (compile-time counts), then at most 8, then at most 16.
+constexpr int kBwdClasses = 6;
+constexpr int bwd_op_class(int n_ops) { return n_ops <= 4 ? n_ops - 1 : n_ops <= 8 ? 4 : 5; }
 // How the reverse sweep treats an operand (per operand, fixed at plan time).
 enum : int8_t {
     kBwdNone = 0,       // a gate tensor without an angle (|+>, Z)
