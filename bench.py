@@ -317,6 +317,22 @@ def wide_buckets(peak, torch):
         out[dtype] = {"buckets": len(per), "agg_gbs": agg, "median_gbs": float(np.median(per)),
                       "max_gbs": float(np.max(per)), "min_gbs": float(np.min(per)), "frac_of_peak": agg / peak,
                       "bytes": tot_b, "ms": tot_ms}
+        # single-edge contraction: each network alone in its own plan, every bucket of it in one
+        # persistent launch; algorithmic bytes of the network over the kernel's time
+        nb = nm = 0.0
+        for e in sel:
+            with qtgb.plan_subset(n, edges, p, [int(e)], dtype=dtype) as one:
+                for _ in range(2):
+                    one.energy(g, b)
+                one.kernel_time(reset=True)
+                for _ in range(3):
+                    one.energy(g, b)
+                ms, _ = one.kernel_time(reset=True)
+                nb += one.stats()["alg_bytes"]
+                nm += ms
+        out[dtype]["networks"] = {"count": int(sel.size), "agg_gbs": nb / nm / 1e6, "frac_of_peak": nb / nm / 1e6 / peak,
+                                  "bytes": nb, "ms": nm,
+                                  "note": "each network alone: all its buckets in one persistent launch (mean of 3 after 2)"}
     return out
 
 
