@@ -189,6 +189,23 @@ int qt_plan_export(qt_plan_t plan, qt_bucket_info *buckets, qt_operand_info *ope
  * n_vertices of its graph entries; 0 for qubits outside the lightcone). */
 int qt_plan_network_wires(qt_plan_t plan, int32_t network, int32_t *vars_per_qubit);
 
+/* One work group of the persistent kernel's queue, as seen by host-side
+ * inspection (tests): tiles [first_tile, first_tile + n_tiles) of `bucket`,
+ * or, when unit_buckets > 0, a fused unit of that many buckets rooted at
+ * `bucket` (n_tiles 1). */
+typedef struct {
+    int32_t bucket;
+    int32_t first_tile;
+    int32_t n_tiles;
+    int32_t unit_buckets;
+} qt_group_info;
+
+/* The static part of the queue in claim order (qt_plan_stats.n_items groups
+ * with the default order; with the ready-queue order, only the groups of
+ * buckets without producers, the rest being published at run time). `groups`
+ * holds at least n_items entries; *n_out receives the count. */
+int qt_plan_export_groups(qt_plan_t plan, qt_group_info *groups, int64_t *n_out);
+
 /*
  * Energy of a single-graph plan: edge_zz[e] = e_jk of edge e (n_edges doubles,
  * host or device, may be NULL), *energy = |E|/2 - 1/2 sum e_jk (host or

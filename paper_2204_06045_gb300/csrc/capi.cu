@@ -559,6 +559,18 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
     return QT_OK;
 }
 
+int qt_plan_export_groups(qt_plan_t P, qt_group_info* groups, int64_t* n_out) {
+    if (!P || !groups || !n_out) return QT_EINVAL;
+    const qt::HostPlan& hp = P->hp;
+    for (size_t i = 0; i < hp.runs.size(); ++i) {
+        const qt::DRun& r = hp.runs[i];
+        groups[i] = qt_group_info{(int32_t)r.bucket, (int32_t)r.chunk_begin, (int32_t)r.n_chunks,
+                                  r.unit_begin ? (int32_t)r.unit_count : 0};
+    }
+    *n_out = (int64_t)hp.runs.size();
+    return QT_OK;
+}
+
 int qt_plan_network_wires(qt_plan_t P, int32_t network, int32_t* vars_per_qubit) {
     if (!P || !vars_per_qubit || network < 0 || network >= (int32_t)P->hp.nets.size()) return QT_EINVAL;
     const qt::Network& net = P->hp.nets[network];

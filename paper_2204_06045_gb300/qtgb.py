@@ -23,7 +23,7 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
-           "qt_energy_noalloc", "qt_fma_peak")
+           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups")
 
 
 class QTError(RuntimeError):
@@ -57,6 +57,8 @@ BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", n
                          ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32),
                          ("tile_log2", np.int32), ("tile_bits", np.uint32), ("folded", np.uint32),
                          ("unit_role", np.uint32)])
+GROUP_DTYPE = np.dtype([("bucket", np.int32), ("first_tile", np.int32), ("n_tiles", np.int32),
+                        ("unit_buckets", np.int32)])
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                           ("mask", np.uint32), ("rank", np.int32), ("pad", np.int32)])
 
@@ -91,6 +93,7 @@ def lib():
         L.qt_energy_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.qt_energy_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_fma_peak.argtypes = [i32, dp]
+        L.qt_plan_export_groups.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_last_imag.argtypes = [vp, dp]
         L.qt_sync.argtypes = [vp, vp]
         L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
@@ -107,7 +110,7 @@ def lib():
         for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
-                     "qt_energy_noalloc", "qt_fma_peak"):
+                     "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -269,6 +272,14 @@ class Plan:
     @property
     def n_networks(self) -> int:
         return int(sum(self.n_edges))
+
+    def export_groups(self) -> np.ndarray:
+        """The static work-group queue in claim order (bucket, first_tile, n_tiles, unit_buckets)."""
+        n = max(1, self.stats()["n_items"])
+        out = np.zeros(n, dtype=GROUP_DTYPE)
+        cnt = ctypes.c_int64(0)
+        _check(lib().qt_plan_export_groups(self._h, out.ctypes.data, ctypes.byref(cnt)), "qt_plan_export_groups")
+        return out[:cnt.value]
 
     def energy(self, gammas, betas, edge_zz=None, energy=None, stream=None):
         """One graph. With no output buffers given, returns ``(edge_zz, E)`` as host numpy/float.

@@ -316,3 +316,63 @@ def test_fused_units_are_closed_small_subtrees():
         assert pl.stats()["n_units"] == 0
     with qtgb.plan_batch(graphs, 3, host_only=True, fuse=False) as pl:
         assert pl.stats()["n_units"] == 0
+
+
+def _check_claim_order(B, O, G):
+    """Every tile of every bucket scheduled on its own appears in exactly one
+    group; a fused unit's root appears once; no bucket inside a unit appears;
+    every group comes after every group of each of its bucket's producers
+    (for a unit: after the producers outside it, of which there are none)."""
+    nb = len(B)
+    role = B["unit_role"]
+    covered = [[] for _ in range(nb)]
+    pos_last = np.full(nb, -1)
+    pos_first = np.full(nb, -1)
+    for i, gr in enumerate(G):
+        b = int(gr["bucket"])
+        assert role[b] != 1, "a bucket inside a unit was scheduled on its own"
+        if pos_first[b] < 0:
+            pos_first[b] = i
+        pos_last[b] = i
+        covered[b].append((int(gr["first_tile"]), int(gr["n_tiles"])))
+        assert (gr["unit_buckets"] > 0) == (role[b] == 2)
+    for b in range(nb):
+        if role[b] == 1:
+            assert not covered[b]
+            continue
+        n_tiles = 1 << (int(B["width"][b]) - 1 - int(B["tile_log2"][b]))
+        if role[b] == 2:
+            assert covered[b] == [(0, 1)]
+            continue
+        tiles = sorted(covered[b])
+        assert tiles[0][0] == 0 and sum(t[1] for t in tiles) == n_tiles
+        for (a, na), (c, _) in zip(tiles, tiles[1:]):
+            assert a + na == c
+        assert all(1 <= t[1] <= 16 for t in tiles)
+    for b in range(nb):
+        if role[b] != 0:
+            continue
+        ob, no = B["op_begin"][b], B["n_ops"][b]
+        for src in O["src"][ob:ob + no]:
+            if src >= 0:
+                assert pos_last[src] < pos_first[b], "a group precedes one of its producers"
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_claim_order_covers_every_tile_and_respects_dependencies(dtype):
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    with host_plan(n, edges, p, dtype=dtype) as pl:
+        B, O = pl.export()
+        G = pl.export_groups()
+        assert len(G) == pl.stats()["n_items"]
+    _check_claim_order(B, O, G)
+
+
+def test_claim_order_with_fused_units():
+    graphs = [(n, e) for n, e, _, _ in synth.batch(6, 3, lo=50, hi=300, base_seed=1000)]
+    with qtgb.plan_batch(graphs, 3, host_only=True) as pl:
+        B, O = pl.export()
+        G = pl.export_groups()
+        assert pl.stats()["n_units"] > 0
+    _check_claim_order(B, O, G)
