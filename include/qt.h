@@ -40,7 +40,8 @@ extern "C" {
 
 /* ---- error codes ---------------------------------------------------------- */
 #define QT_OK 0
-#define QT_EINVAL -1   /* bad argument: null pointer, self-loop, duplicate edge, vertex out of range, p < 1 */
+#define QT_EINVAL -1   /* bad argument: null pointer, self-loop, duplicate edge, vertex out of range, p < 1
+                          (a graph without edges is valid: no networks, energy 0) */
 #define QT_EWIDTH -2   /* a bucket is wider than qt_plan_opts.max_width, or has more than 16 operands */
 #define QT_ENOMEM -3   /* host or device allocation failed, or over qt_plan_opts.arena_bytes */
 #define QT_ECUDA -4    /* a CUDA runtime call failed (no device, launch failure, ...) */

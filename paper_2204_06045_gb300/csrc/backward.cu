@@ -284,6 +284,7 @@ __global__ void k_grad_final(const double* grad, int n_graphs, int p, double* dg
 }  // namespace
 
 cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s) {
+    if (n_nets == 0) return cudaSuccess;  // a plan of graphs without edges
     const int blocks = (n_nets + 127) / 128;
     if (dtype == QT_C128)
         k_seed_roots<double><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);

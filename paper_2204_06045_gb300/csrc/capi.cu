@@ -466,7 +466,7 @@ extern "C" {
 
 int qt_plan(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int32_t p, const qt_plan_opts* opts,
             qt_plan_t* out) {
-    if (!edges || n_edges < 1 || n_vertices < 2) return QT_EINVAL;
+    if (n_edges < 0 || (n_edges > 0 && !edges) || n_vertices < 1) return QT_EINVAL;
     std::vector<qt::GraphIn> gs(1);
     gs[0].n = n_vertices;
     for (int e = 0; e < n_edges; ++e) gs[0].edges.emplace_back(edges[2 * e], edges[2 * e + 1]);
@@ -485,11 +485,14 @@ int qt_plan_subset(int32_t n_vertices, int32_t n_edges, const int32_t* edges, in
 
 int qt_plan_batch(int32_t n_graphs, const int32_t* n_vertices, const int32_t* n_edges, const int32_t* edges,
                   int32_t p, const qt_plan_opts* opts, qt_plan_t* out) {
-    if (n_graphs < 1 || !n_vertices || !n_edges || !edges) return QT_EINVAL;
+    if (n_graphs < 1 || !n_vertices || !n_edges) return QT_EINVAL;
+    int64_t total_edges = 0;
+    for (int g = 0; g < n_graphs; ++g) total_edges += n_edges[g] > 0 ? n_edges[g] : 0;
+    if (total_edges > 0 && !edges) return QT_EINVAL;
     std::vector<qt::GraphIn> gs(n_graphs);
     size_t at = 0;
     for (int g = 0; g < n_graphs; ++g) {
-        if (n_edges[g] < 1 || n_vertices[g] < 2) return QT_EINVAL;
+        if (n_edges[g] < 0 || n_vertices[g] < 1) return QT_EINVAL;
         gs[g].n = n_vertices[g];
         for (int e = 0; e < n_edges[g]; ++e, ++at) gs[g].edges.emplace_back(edges[2 * at], edges[2 * at + 1]);
     }

@@ -237,6 +237,28 @@ def test_fused_units_match_unfused_and_oracle(dtype, order):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("sched", ["persistent", "per_bucket"])
+def test_graphs_without_edges(dtype, sched):
+    """An edgeless graph has energy 0 (no networks); in a batch it leaves the
+    other graphs' energies unchanged."""
+    empty = np.zeros((0, 2), dtype=np.int32)
+    g, b = synth.angles(2, 5)
+    with qtgb.plan(6, empty, 2, dtype=dtype, sched=sched) as pl:
+        zz, E = pl.energy(g, b)
+    assert zz.size == 0 and E == 0.0
+    n, edges = 10, synth.random_regular_graph(10, 1)
+    graphs = [(6, empty), (n, edges), (3, empty)]
+    G = np.tile(g, (3, 1))
+    Bt = np.tile(b, (3, 1))
+    with qtgb.plan_batch(graphs, 2, dtype=dtype, sched=sched) as pl:
+        energies, zz = pl.energy_batch(G, Bt)
+    ref = oracle.sv_zz(n, edges, g, b)
+    assert energies[0] == 0.0 and energies[2] == 0.0
+    assert scaled_err(zz, ref) <= TOL[dtype]
+    assert abs(energies[1] - oracle.energy_from_zz(ref)) <= TOL[dtype] * abs(energies[1])
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_whole_networks_as_fused_units(dtype):
     """p=1 networks are small enough that each network's whole bucket tree is
     one fused unit, its root the network's scalar: energies against the p=1

@@ -140,3 +140,11 @@ def test_energy_only_plan_refuses_gradient():
         with pytest.raises(qtgb.QTError) as ei:
             pl.energy_grad([0.1], [0.2])
         assert ei.value.code == qtgb.QT_ESTATE
+
+
+def test_gradient_of_a_graph_without_edges_is_zero():
+    empty = np.zeros((0, 2), dtype=np.int32)
+    g, b = synth.angles(3, 2)
+    with qtgb.plan(4, empty, 3, dtype="c64", with_grad=True) as pl:
+        E, dg, db = pl.energy_grad(g, b)
+    assert E[0] == 0.0 and not np.any(dg) and not np.any(db)

@@ -376,3 +376,19 @@ def test_claim_order_with_fused_units():
         G = pl.export_groups()
         assert pl.stats()["n_units"] > 0
     _check_claim_order(B, O, G)
+
+
+def test_graph_without_edges_plans_no_networks():
+    """C = 0 on a graph without edges: no networks, no buckets; in a batch such
+    a graph contributes nothing but keeps its place."""
+    empty = np.zeros((0, 2), dtype=np.int32)
+    with host_plan(5, empty, 2) as pl:
+        st = pl.stats()
+        assert st["n_networks"] == 0 and st["n_buckets"] == 0
+        assert len(pl.export_groups()) == 0
+    graphs = [(5, empty), (10, synth.random_regular_graph(10, 1)), (1, empty)]
+    with qtgb.plan_batch(graphs, 2, host_only=True) as pl:
+        st = pl.stats()
+        assert st["n_graphs"] == 3 and st["n_networks"] == 15
+    with pytest.raises(qtgb.QTError):
+        host_plan(0, empty, 2)
