@@ -210,6 +210,34 @@ def test_c5_n50_p4_matches_bucket_golden(dtype):
     assert scaled_err(zz, ref) <= TOL[dtype]
 
 
+def _c3_sample(graphs, n_sample, seed):
+    """(flat network index, graph, edge) of a seeded sample of the batch's edges."""
+    rng = np.random.default_rng(seed)
+    first = np.cumsum([0] + [e.shape[0] for _, e, _, _ in graphs])
+    flat = np.sort(rng.choice(first[-1], size=n_sample, replace=False))
+    gi = np.searchsorted(first, flat, side="right") - 1
+    return [(int(f), int(g), int(f - first[g])) for f, g in zip(flat, gi)]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_c3_full_batch_sampled_edges_match_oracle(dtype):
+    """The 64-graph, N in [50, 1000], p=3 batch at full size, in the persistent
+    launch with fused units that the benchmark times: 100 sampled edges against
+    the oracle's bucket elimination of their networks."""
+    p = 3
+    graphs = synth.batch(64, p, lo=50, hi=1000, base_seed=1000)
+    G = np.array([gg for _, _, gg, _ in graphs])
+    Bt = np.array([bb for _, _, _, bb in graphs])
+    with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], p, dtype=dtype) as pl:
+        assert pl.stats()["n_units"] > 0
+        energies, zz = pl.energy_batch(G, Bt)
+    for f, g, e in _c3_sample(graphs, 100, 7):
+        n, edges, gg, bb = graphs[g]
+        ref, _ = oracle.edge_bucket(n, edges, gg, bb, e, seed=f)
+        assert scaled_err([zz[f]], [ref.real]) <= TOL[dtype]
+        assert abs(ref.imag) < 1e-12
+
+
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("order", ["simulated", "ready_queue"])
 def test_fused_units_match_unfused_and_oracle(dtype, order):
