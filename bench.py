@@ -451,6 +451,18 @@ def run_ours(args, rank, world, local_rank):
         "plan": main["plan"], "check": main["check"],
         "c128": {k: results["c128"][k] for k in ("value", "ms_per_step", "e2e", "roofline", "clocks", "plan", "check")},
     }
+    if world == 1:
+        # the plan-time autotuner on the same workload: what it chooses and the kernel time it gets
+        t = time.perf_counter()
+        with qtgb.plan(n, edges, p, dtype="c64", autotune=3) as tp:
+            st = tp.stats()
+            tg = torch.tensor(g, dtype=torch.float64, device="cuda")
+            tb = torch.tensor(b, dtype=torch.float64, device="cuda")
+            _, kms_t, _ = time_device(tp, tg, tb, torch.zeros(m, dtype=torch.float64, device="cuda"),
+                                      torch.zeros(1, dtype=torch.float64, device="cuda"), 50, 3, None, torch)
+        line["autotune_c64"] = {"tile_cap_by_width_class": st["tile_cap"], "run_tiles": st["run_tiles"],
+                                "candidates": st["tune_candidates"], "plan_seconds": time.perf_counter() - t,
+                                "kernel_ms": kms_t, "default_kernel_ms": main["roofline"]["kernel_ms"]}
     if world == 1 and not args.no_buckets:
         line["bucket_gbs"] = wide_buckets(peak, torch)
     if world == 1 and not args.no_cpu_baseline:

@@ -88,6 +88,12 @@ typedef struct {
     int32_t no_fuse;       /* nonzero: no fused units (by default, subtrees of small buckets, at most
                               256 outputs each, run as one work group contracted in a warp's shared
                               memory; never for gradient plans or the per-bucket schedule) */
+    int32_t autotune;      /* > 0: autotune the tile shapes at plan time (persistent schedule, device
+                              plans): per bucket-width class (output bits <= 6, 7..10, 11..14, 15..19,
+                              >= 20) the most tile bits, then the group size, each candidate timed on
+                              the device over `autotune` evaluations; the choice is in qt_plan_stats */
+    int8_t tile_cap[8];    /* most tile bits (log2 outputs per tile, 1..11) per width class, 0: default
+                              (chunk_log2, else 9); the first 5 entries are used */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -113,6 +119,10 @@ typedef struct {
     double sim_seconds;     /* makespan predicted by the plan-time schedule simulation (0: none) */
     int64_t n_units;        /* fused units (small subtrees run as one work group) */
     int64_t n_fused;        /* buckets inside fused units, their roots included */
+    int32_t tile_cap[8];    /* most tile bits per width class in effect (5 used) */
+    int32_t run_tiles;      /* most tiles per work group in effect */
+    double tune_seconds;    /* host time spent autotuning (0 without opts.autotune) */
+    int32_t tune_candidates;/* configurations the autotuner laid out and timed */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -65,26 +66,48 @@ struct qt_plan_s {
     uint32_t n_zero = 0;
     qt::DevBwd db{};
 
-    ~qt_plan_s() {
+    // autotuning record
+    double tune_seconds = 0;
+    int32_t tune_candidates = 0;
+
+    // Free every device-side resource and forget it (the host plan stays).
+    void release_device() {
+        if (stream) cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        for (auto& e : cap_ev)
+        exec = nullptr;
+        graph = nullptr;
+        ev_nodes[0] = ev_nodes[1] = nullptr;
+        for (auto& e : cap_ev) {
             if (e) cudaEventDestroy(e);
-        for (auto& r : ring)
-            for (auto& e : r)
+            e = nullptr;
+        }
+        for (int i = 0; i < kRing; ++i) {
+            for (auto& e : ring[i]) {
                 if (e) cudaEventDestroy(e);
+                e = nullptr;
+            }
+            ring_pending[i] = false;
+        }
         if (stream) cudaStreamDestroy(stream);
-        if (d_arena) cudaFree(d_arena);
-        if (d_static) cudaFree(d_static);
-        if (d_counters) cudaFree(d_counters);
-        if (d_angles) cudaFree(d_angles);
-        if (d_out) cudaFree(d_out);
+        stream = nullptr;
+        void* dev[] = {d_arena, d_static, d_counters, d_angles, d_out, d_trace, d_btimes, d_bwd, d_grad};
+        for (void* q : dev)
+            if (q) cudaFree(q);
+        d_arena = d_static = d_counters = d_bwd = nullptr;
+        d_angles = d_out = d_grad = nullptr;
+        d_trace = nullptr;
+        d_btimes = nullptr;
+        d_zero = nullptr;
         if (h_err) cudaFreeHost(h_err);
-        if (d_trace) cudaFree(d_trace);
-        if (d_btimes) cudaFree(d_btimes);
-        if (d_bwd) cudaFree(d_bwd);
-        if (d_grad) cudaFree(d_grad);
+        h_err = nullptr;
+        calls = 0;
+        time_ms = 0;
+        timed = 0;
+        err_pending = false;
     }
+
+    ~qt_plan_s() { release_device(); }
 };
 
 namespace {
@@ -397,6 +420,92 @@ int run_eval(qt_plan_t P, const double* gammas, const double* betas, void* strea
     return QT_OK;
 }
 
+// Mean device time of the persistent kernel over `reps` evaluations (after
+// one warm-up) at fixed probe angles, on the plan as uploaded.
+int time_probe(qt_plan_t P, int reps, double* ms) {
+    const int G = (int)P->hp.graphs.size(), p = P->hp.cfg.p;
+    std::vector<double> g((size_t)G * p, 0.4), b((size_t)G * p, 0.3);
+    int rc = run_eval(P, g.data(), b.data(), nullptr, nullptr, nullptr, true);  // warm-up
+    if (rc != QT_OK) return rc;
+    for (int i = 0; i < kRing; ++i) harvest_slot(P, i);
+    P->time_ms = 0;
+    P->timed = 0;
+    for (int r = 0; r < reps; ++r) {
+        rc = run_eval(P, g.data(), b.data(), nullptr, nullptr, nullptr, true);
+        if (rc != QT_OK) return rc;
+    }
+    for (int i = 0; i < kRing; ++i) harvest_slot(P, i);
+    if (P->timed == 0) return QT_ECUDA;
+    *ms = P->time_ms / (double)P->timed;
+    return QT_OK;
+}
+
+// Autotuner of the tile shapes (§III-C: per-bucket kernel choices). For each
+// bucket-width class present, in turn, try every cap on the tile's outputs
+// (2^6 .. 2^11, within the class's widths) with the best settings so far,
+// then groups of 8 and 32 tiles; keep a change only if the probe time drops
+// by 1% or more. Each candidate is laid out, uploaded and timed on the
+// device; the plan ends uploaded with the best settings.
+int autotune(qt_plan_t P, int reps) {
+    auto t0 = std::chrono::steady_clock::now();
+    qt::HostPlan& hp = P->hp;
+    int max_out[qt::kWidthClasses] = {-1, -1, -1, -1, -1};
+    for (const auto& d : hp.buckets) {
+        const int c = qt::width_class(d.n_out);
+        max_out[c] = std::max(max_out[c], (int)d.n_out);
+    }
+    auto trial = [&](const qt::PlanConfig& cfg, double* ms) {
+        P->release_device();
+        hp.cfg = cfg;
+        int rc = qt::layout_plan(&hp);
+        if (rc == QT_OK) rc = upload(P);
+        if (rc == QT_OK) rc = time_probe(P, reps, ms);
+        P->tune_candidates++;
+        return rc;
+    };
+    qt::PlanConfig best = hp.cfg;
+    double best_ms = 0;
+    int rc = trial(best, &best_ms);
+    if (rc != QT_OK) return rc;
+    const int def_cap = best.chunk_log2 > 0 ? best.chunk_log2 : qt::kDefaultTileBits;
+    for (int c = 0; c < qt::kWidthClasses; ++c) {
+        if (max_out[c] <= 6) continue;  // tiles of 64 outputs or fewer: nothing to choose
+        const int cur = best.tile_cap[c] > 0 ? best.tile_cap[c] : def_cap;
+        for (int cap = 6; cap <= std::min(11, max_out[c]); ++cap) {
+            if (cap == cur) continue;
+            qt::PlanConfig cfg = best;
+            cfg.tile_cap[c] = cap;
+            double ms = 0;
+            rc = trial(cfg, &ms);
+            if (rc != QT_OK) return rc;
+            if (ms < 0.99 * best_ms) {
+                best_ms = ms;
+                best = cfg;
+            }
+        }
+    }
+    for (int rt : {8, 32}) {
+        qt::PlanConfig cfg = best;
+        cfg.run_tiles = rt;
+        double ms = 0;
+        rc = trial(cfg, &ms);
+        if (rc != QT_OK) return rc;
+        if (ms < 0.99 * best_ms) {
+            best_ms = ms;
+            best = cfg;
+        }
+    }
+    // the chosen settings, stated explicitly
+    for (int c = 0; c < qt::kWidthClasses; ++c)
+        if (best.tile_cap[c] == 0) best.tile_cap[c] = def_cap;
+    P->release_device();
+    hp.cfg = best;
+    rc = qt::layout_plan(&hp);
+    if (rc == QT_OK) rc = upload(P);
+    P->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
 qt_plan_opts default_opts() {
     qt_plan_opts o;
     std::memset(&o, 0, sizeof(o));
@@ -432,6 +541,11 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
     cfg.fuse = o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad && o.no_fuse == 0;
+    for (int c = 0; c < qt::kWidthClasses; ++c) {
+        if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
+        cfg.tile_cap[c] = o.tile_cap[c];
+    }
+    if (o.autotune < 0 || o.autotune > 1000 || (o.autotune > 0 && o.sched != QT_SCHED_PERSISTENT)) return QT_EINVAL;
     if (cfg.chunk_log2 < 0 || cfg.chunk_log2 > 24) return QT_EINVAL;
     std::unique_ptr<qt_plan_s> P(new (std::nothrow) qt_plan_s());
     if (!P) return QT_ENOMEM;
@@ -453,7 +567,7 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     P->host_only = o.host_only != 0;
     P->trace = o.trace != 0;
     if (!P->host_only) {
-        rc = upload(P.get());
+        rc = o.autotune > 0 ? autotune(P.get(), o.autotune) : upload(P.get());
         if (rc != QT_OK) return rc;
     }
     *out = P.release();
@@ -522,6 +636,12 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->sim_seconds = hp.sim_seconds;
     out->n_units = (int64_t)hp.n_units;
     out->n_fused = (int64_t)hp.n_fused;
+    const int def_cap = hp.cfg.chunk_log2 > 0 ? hp.cfg.chunk_log2 : qt::kDefaultTileBits;
+    for (int c = 0; c < 8; ++c)
+        out->tile_cap[c] = c < qt::kWidthClasses ? (hp.cfg.tile_cap[c] > 0 ? hp.cfg.tile_cap[c] : def_cap) : 0;
+    out->run_tiles = hp.cfg.run_tiles > 0 ? hp.cfg.run_tiles : qt::kRunTiles;
+    out->tune_seconds = P->tune_seconds;
+    out->tune_candidates = P->tune_candidates;
     return QT_OK;
 }
 

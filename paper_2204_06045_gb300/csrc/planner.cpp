@@ -647,6 +647,26 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     for (auto& th : pool) th.join();
     for (int s : status)
         if (s != QT_OK) return s;
+    const int rc = layout_plan(hp);
+    hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+// Everything after the networks, their orders and buckets: tile choice,
+// device layout, fused units, claim order, reverse-sweep tasks. Rerun by the
+// autotuner for each candidate configuration (hp->cfg).
+int layout_plan(HostPlan* hp) {
+    const PlanConfig& cfg = hp->cfg;
+    const std::vector<GraphIn>& graphs = hp->graphs;
+    const int n_nets = hp->graph_first_net.back();
+    hp->op_src.clear();
+    hp->op_leaf_kind.clear();
+    hp->op_leaf_layer.clear();
+    hp->op_rank.clear();
+    hp->bucket_level.clear();
+    hp->bucket_var.clear();
+    hp->root_bucket.clear();
+    hp->sim_seconds = 0;
 
     // ---- flatten ---------------------------------------------------------
     const uint64_t esize = cfg.dtype == 1 ? 16 : 8;
@@ -678,7 +698,8 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             d.n_out = (uint8_t)(B.width - 1);
             int cb = 0;
             bool fold = false;
-            pick_tile(B, net, cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
+            const int tcap = cfg.tile_cap[width_class(B.width - 1)];
+            pick_tile(B, net, tcap > 0 ? tcap : cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
                       cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, &cb, &fold);
             d.chunk_bits = (uint8_t)cb;
             d.flags = fold ? kBucketFoldLeaves : 0;
@@ -894,7 +915,6 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             hp->bwd_level_begin.push_back((uint32_t)hp->bwd_bucket.size());
         }
     }
-    hp->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return QT_OK;
 }
 

@@ -68,6 +68,7 @@ struct PlanConfig {
     int sim_workers = 1824;  // warps assumed by the simulation
     bool with_grad = false;
     bool fuse = false;       // form fused units of small subtrees (persistent energy plans)
+    int tile_cap[kWidthClasses] = {0, 0, 0, 0, 0};  // most tile bits per bucket-width class (0: chunk_log2 / default)
 };
 
 // The flat plan: what gets uploaded plus host-side bookkeeping.
@@ -122,6 +123,9 @@ struct HostPlan {
 
 // Returns QT_OK or a QT_E* code.
 int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, HostPlan* out);
+// Recompute the layout stages (tiles, device arrays, units, claim order) of a
+// plan whose networks are built, for the configuration in hp->cfg.
+int layout_plan(HostPlan* hp);
 
 int leaf_slots_per_graph(int p);
 int leaf_index(int kind, int layer);

@@ -56,6 +56,10 @@ enum : int8_t {
     kBwdAtomic = 5      // no room in shared memory: atomic adds per output (zeroed first)
 };
 constexpr int kDefaultTileBits = 9;  // at most 512 outputs per tile (default); measured best on GB300
+// Bucket-width classes of the tile autotuner, by output bits: <= 6, 7..10,
+// 11..14, 15..19, >= 20.
+constexpr int kWidthClasses = 5;
+constexpr int width_class(int n_out) { return n_out <= 6 ? 0 : n_out <= 10 ? 1 : n_out <= 14 ? 2 : n_out <= 19 ? 3 : 4; }
 
 // One bucket on the device. 64 bytes.
 struct DBucket {

@@ -138,6 +138,23 @@ def test_c2_n30_p4_matches_statevector_golden(dtype, sched, order):
     assert np.abs(im).max() <= 10 * TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_autotuned_plan_matches_state_vector(dtype):
+    """opts.autotune: every candidate layout is uploaded and timed; the plan
+    left behind must still give the oracle's values."""
+    n, p = 20, 4
+    edges = synth.random_regular_graph(n, 1020)
+    g, b = synth.angles(p, 1020)
+    with qtgb.plan(n, edges, p, dtype=dtype, autotune=2) as pl:
+        st = pl.stats()
+        zz, E = pl.energy(g, b)
+    assert st["tune_candidates"] > 1 and st["tune_seconds"] > 0
+    assert all(6 <= c <= 11 for c in st["tile_cap"]) and st["run_tiles"] in (8, 16, 32)
+    ref = oracle.sv_zz(n, edges, g, b)
+    assert scaled_err(zz, ref) <= TOL[dtype]
+    assert abs(E - oracle.energy_from_zz(ref)) <= TOL[dtype] * abs(E)
+
+
 def _c4_golden():
     rows, ref = {}, {}
     with open(GOLDEN / "c4_n1000_p5_bucket.txt") as f:

@@ -392,3 +392,24 @@ def test_graph_without_edges_plans_no_networks():
         assert st["n_graphs"] == 3 and st["n_networks"] == 15
     with pytest.raises(qtgb.QTError):
         host_plan(0, empty, 2)
+
+
+def test_tile_caps_per_width_class():
+    """opts.tile_cap bounds the tile of each bucket-width class (output bits
+    <= 6, 7..10, 11..14, 15..19, >= 20); 0 keeps the default (9)."""
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    cls = lambda n_out: 0 if n_out <= 6 else 1 if n_out <= 10 else 2 if n_out <= 14 else 3 if n_out <= 19 else 4
+    with host_plan(n, edges, p, tile_cap=[0, 7, 8, 0, 6]) as pl:
+        B, O = pl.export()
+        st = pl.stats()
+    assert st["tile_cap"] == [9, 7, 8, 9, 6]
+    caps = [9, 7, 8, 9, 6]
+    for b in range(len(B)):
+        n_out = int(B["width"][b]) - 1
+        assert B["tile_log2"][b] <= min(n_out, caps[cls(n_out)])
+    assert (B["tile_log2"][B["width"] - 1 >= 20] == 6).all()
+    for b in np.nonzero(B["width"] >= 12)[0][:30]:
+        _check_tiles(B, O, int(b))
+    with pytest.raises(qtgb.QTError):
+        host_plan(n, edges, p, tile_cap=[12, 0, 0, 0, 0])
