@@ -190,6 +190,23 @@ int qt_plan_batch(int32_t n_graphs, const int32_t *n_vertices, const int32_t *n_
                   const int32_t *edges, int32_t p, const qt_plan_opts *opts, qt_plan_t *out);
 
 /* Statistics of a plan (host only). */
+/*
+ * One rank's share of a graph's lightcone networks, for splitting one energy
+ * over `world` processes (one GPU each). Every network is planned on the host
+ * for its cost (sum over its buckets of 2^width); networks go to ranks by
+ * longest-processing-time-first (the costliest network to the least loaded
+ * rank). The plan holds the networks of rank `rank`: its qt_energy gives
+ * that rank's edge values and the partial energy sum over its edges of
+ * (1 - e_jk)/2, and its qt_energy_grad the partial gradient; the full E and
+ * gradient are the sums over ranks (one reduction of 2p + 1 doubles).
+ * shard_edges (may be NULL, else n_edges int32 of room) receives the rank's
+ * edges in increasing order, *n_shard their count. A rank with no network
+ * gets a plan of no networks (energy 0). Options as for qt_plan.
+ */
+int qt_plan_shard(int32_t n_vertices, int32_t n_edges, const int32_t *edges, int32_t p, int32_t world,
+                  int32_t rank, const qt_plan_opts *opts, qt_plan_t *out, int32_t *shard_edges,
+                  int32_t *n_shard);
+
 int qt_plan_stats_get(qt_plan_t plan, qt_plan_stats *out);
 
 /* Copy the schedule out for inspection (host only). `buckets` holds

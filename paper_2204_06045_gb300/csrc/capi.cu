@@ -597,6 +597,45 @@ int qt_plan_subset(int32_t n_vertices, int32_t n_edges, const int32_t* edges, in
     return make_plan(gs, p, opts, out);
 }
 
+int qt_plan_shard(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int32_t p, int32_t world, int32_t rank,
+                  const qt_plan_opts* opts, qt_plan_t* out, int32_t* shard_edges, int32_t* n_shard) {
+    if (!out || !n_shard || world < 1 || rank < 0 || rank >= world) return QT_EINVAL;
+    if (n_edges < 0 || (n_edges > 0 && !edges) || n_vertices < 1) return QT_EINVAL;
+    // every network planned on the host, for its cost (sum of 2^width)
+    qt_plan_opts ho = opts ? *opts : default_opts();
+    ho.host_only = 1;
+    ho.autotune = 0;
+    qt_plan_t full = nullptr;
+    int rc = qt_plan(n_vertices, n_edges, edges, p, &ho, &full);
+    if (rc != QT_OK) return rc;
+    std::vector<double> cost(n_edges);
+    for (int e = 0; e < n_edges; ++e) cost[e] = full->hp.nplans[e].cost;
+    qt_plan_free(full);
+    // LPT: the costliest network first (ties: lower edge), to the least loaded rank (ties: lower rank)
+    std::vector<int> idx(n_edges);
+    for (int e = 0; e < n_edges; ++e) idx[e] = e;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(world, 0.0);
+    std::vector<int> owner(n_edges, 0);
+    for (int e : idx) {
+        const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[e] = r;
+        load[r] += cost[e];
+    }
+    std::vector<int32_t> mine;
+    for (int e = 0; e < n_edges; ++e)
+        if (owner[e] == rank) mine.push_back(e);
+    *n_shard = (int32_t)mine.size();
+    if (shard_edges && !mine.empty()) std::memcpy(shard_edges, mine.data(), mine.size() * sizeof(int32_t));
+    std::vector<qt::GraphIn> gs(1);
+    gs[0].n = n_vertices;
+    if (!mine.empty()) {  // an empty shard is a graph without edges: no networks, energy 0
+        for (int e = 0; e < n_edges; ++e) gs[0].edges.emplace_back(edges[2 * e], edges[2 * e + 1]);
+        gs[0].sel = mine;
+    }
+    return make_plan(gs, p, opts, out);
+}
+
 int qt_plan_batch(int32_t n_graphs, const int32_t* n_vertices, const int32_t* n_edges, const int32_t* edges,
                   int32_t p, const qt_plan_opts* opts, qt_plan_t* out) {
     if (n_graphs < 1 || !n_vertices || !n_edges) return QT_EINVAL;

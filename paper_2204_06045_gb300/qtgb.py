@@ -23,7 +23,7 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
-           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups")
+           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard")
 
 
 class QTError(RuntimeError):
@@ -96,6 +96,8 @@ def lib():
         L.qt_energy_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_fma_peak.argtypes = [i32, dp]
         L.qt_plan_export_groups.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        L.qt_plan_shard.argtypes = [i32, i32, i32p, i32, i32, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp), i32p,
+                                    i32p]
         L.qt_last_imag.argtypes = [vp, dp]
         L.qt_sync.argtypes = [vp, vp]
         L.qt_kernel_time.argtypes = [vp, dp, ctypes.POINTER(i64), i32]
@@ -112,7 +114,7 @@ def lib():
         for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
-                     "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups"):
+                     "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -220,6 +222,23 @@ class Plan:
         _check(lib().qt_plan_subset(int(n), int(e.shape[0]), e.ctypes.data_as(ip), int(p), int(sv.size),
                                     sv.ctypes.data_as(ip), ctypes.byref(o), ctypes.byref(h)), "qt_plan_subset")
         return cls(h.value, [sv.size], p, opts.get("dtype", "c64"), [n])
+
+    @classmethod
+    def create_shard(cls, n: int, edges, p: int, world: int, rank: int, **opts) -> "Plan":
+        """Rank ``rank``'s share (by LPT on network cost) of the graph's networks;
+        ``plan.shard_edges`` lists its edges."""
+        e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        mine = np.zeros(max(1, e.shape[0]), dtype=np.int32)
+        cnt = ctypes.c_int32(0)
+        o = cls._opts(**opts)
+        h = ctypes.c_void_p()
+        ip = ctypes.POINTER(ctypes.c_int32)
+        _check(lib().qt_plan_shard(int(n), int(e.shape[0]), e.ctypes.data_as(ip), int(p), int(world), int(rank),
+                                   ctypes.byref(o), ctypes.byref(h), mine.ctypes.data_as(ip), ctypes.byref(cnt)),
+               "qt_plan_shard")
+        pl = cls(h.value, [int(cnt.value)], p, opts.get("dtype", "c64"), [n])
+        pl.shard_edges = mine[:cnt.value].copy()
+        return pl
 
     @classmethod
     def create_batch(cls, graphs, p: int, **opts) -> "Plan":
@@ -389,6 +408,10 @@ def plan(n: int, edges, p: int, **opts) -> Plan:
 
 def plan_subset(n: int, edges, p: int, sel, **opts) -> Plan:
     return Plan.create_subset(n, edges, p, sel, **opts)
+
+
+def plan_shard(n: int, edges, p: int, world: int, rank: int, **opts) -> Plan:
+    return Plan.create_shard(n, edges, p, world, rank, **opts)
 
 
 def plan_batch(graphs, p: int, **opts) -> Plan:

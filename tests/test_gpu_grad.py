@@ -148,3 +148,28 @@ def test_gradient_of_a_graph_without_edges_is_zero():
     with qtgb.plan(4, empty, 3, dtype="c64", with_grad=True) as pl:
         E, dg, db = pl.energy_grad(g, b)
     assert E[0] == 0.0 and not np.any(dg) and not np.any(db)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_sharded_energy_and_gradient_sum_to_the_whole(dtype):
+    """Three ranks' shards (LPT by network cost), run one after the other on
+    this GPU: their partial energies and gradients add up to the unsharded
+    plan's."""
+    n, p = 20, 3
+    edges = synth.random_regular_graph(n, 1020)
+    g, b = synth.angles(p, 1020)
+    with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True) as pl:
+        E, dg, db = pl.energy_grad(g, b)
+    tot_E, tot_g, tot_b, held = 0.0, np.zeros(p), np.zeros(p), []
+    for rank in range(3):
+        with qtgb.plan_shard(n, edges, p, 3, rank, dtype=dtype, with_grad=True) as sh:
+            e_r, g_r, b_r = sh.energy_grad(g, b)
+            held += sh.shard_edges.tolist()
+        tot_E += e_r[0]
+        tot_g += g_r
+        tot_b += b_r
+    assert sorted(held) == list(range(edges.shape[0]))
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    assert abs(tot_E - E[0]) <= tol * abs(E[0])
+    np.testing.assert_allclose(tot_g, dg, atol=tol * 10)
+    np.testing.assert_allclose(tot_b, db, atol=tol * 10)

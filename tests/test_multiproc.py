@@ -10,6 +10,7 @@ import socket
 import sys
 from pathlib import Path
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -61,3 +62,60 @@ def test_two_gloo_ranks_take_the_slowest_time_and_count_every_rank():
         assert job == pytest.approx(0.020)  # the slower rank's time, seen by both
         assert rate == pytest.approx(world * 5 / 0.020)
     assert res[0][3] == 45 and res[1][3] == 60  # each rank planned its own graph
+
+
+def _shard_rank(rank, world, port, out):
+    """One rank of a sharded energy: plan this rank's networks (LPT by cost),
+    contract them with the test-side numpy evaluator, reduce the partial
+    energies with one all-reduce."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, str(ROOT))
+    sys.path.insert(0, str(ROOT / "tests"))
+    from plan_eval import evaluate
+    from paper_2204_06045_gb300 import qtgb, synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n, p = 14, 2
+        edges = synth.random_regular_graph(n, 22)
+        g, b = synth.angles(p, 22)
+        with qtgb.plan_shard(n, edges, p, world, rank, host_only=True) as pl:
+            mine = pl.shard_edges
+            cost = float(pl.stats()["sum_2w"])
+            if mine.size:
+                B, O = pl.export()
+                zz = evaluate(B, O, g, b).real
+            else:
+                zz = np.zeros(0)
+        part = torch.tensor([0.5 * float(np.sum(1.0 - zz))], dtype=torch.float64)
+        dist.all_reduce(part, op=dist.ReduceOp.SUM)
+        out[rank] = (mine.tolist(), zz.tolist(), float(part.item()), cost)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_energy_over_gloo_ranks_matches_oracle():
+    """§8(e): one graph's networks split over ranks by LPT on their cost; the
+    ranks' partial energies sum to the oracle's energy, every edge is held by
+    exactly one rank, and the loads are balanced."""
+    import oracle
+    from paper_2204_06045_gb300 import build, synth
+    build.build()
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    n, p = 14, 2
+    edges = synth.random_regular_graph(n, 22)
+    g, b = synth.angles(p, 22)
+    held = sorted(e for r in range(world) for e in res[r][0])
+    assert held == list(range(edges.shape[0]))
+    E = res[0][2]
+    assert res[1][2] == pytest.approx(E, abs=1e-14)
+    assert E == pytest.approx(oracle.sv_energy(n, edges, g, b), abs=1e-10)
+    zz = oracle.sv_zz(n, edges, g, b)
+    for r in range(world):
+        np.testing.assert_allclose(res[r][1], zz[res[r][0]], atol=1e-12)
+    costs = [res[r][3] for r in range(world)]
+    assert max(costs) <= 1.5 * min(costs)
