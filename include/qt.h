@@ -94,6 +94,10 @@ typedef struct {
                               the device over `autotune` evaluations; the choice is in qt_plan_stats */
     int8_t tile_cap[8];    /* most tile bits (log2 outputs per tile, 1..11) per width class, 0: default
                               (chunk_log2, else 9); the first 5 entries are used */
+    size_t adjoint_budget_bytes; /* gradient plans (single graph): device bytes for results and their
+                              cotangents; a plan that needs more runs its networks in passes that fit
+                              (each pass saves its own results; energies and gradients are summed over
+                              passes); a network that alone exceeds it gives QT_ENOMEM. 0: no budget */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -123,6 +127,7 @@ typedef struct {
     int32_t run_tiles;      /* most tiles per work group in effect */
     double tune_seconds;    /* host time spent autotuning (0 without opts.autotune) */
     int32_t tune_candidates;/* configurations the autotuner laid out and timed */
+    int32_t n_passes;       /* gradient plans over opts.adjoint_budget_bytes: passes over the networks */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */

@@ -69,6 +69,12 @@ struct qt_plan_s {
     // autotuning record
     double tune_seconds = 0;
     int32_t tune_candidates = 0;
+    // gradient plans over a memory budget: the networks run in passes, each a
+    // plan of its own on one shared arena (owned here, d_arena of the parts)
+    std::vector<std::unique_ptr<qt_plan_s>> parts;
+    std::vector<std::vector<int32_t>> part_edges;
+    void* d_shared = nullptr;
+    bool arena_external = false;  // d_arena belongs to the plan that holds this one
 
     // Free every device-side resource and forget it (the host plan stays).
     void release_device() {
@@ -91,7 +97,8 @@ struct qt_plan_s {
         }
         if (stream) cudaStreamDestroy(stream);
         stream = nullptr;
-        void* dev[] = {d_arena, d_static, d_counters, d_angles, d_out, d_trace, d_btimes, d_bwd, d_grad};
+        void* dev[] = {arena_external ? nullptr : d_arena, d_static, d_counters, d_angles, d_out, d_trace, d_btimes,
+                       d_bwd, d_grad};
         for (void* q : dev)
             if (q) cudaFree(q);
         d_arena = d_static = d_counters = d_bwd = nullptr;
@@ -107,7 +114,11 @@ struct qt_plan_s {
         err_pending = false;
     }
 
-    ~qt_plan_s() { release_device(); }
+    ~qt_plan_s() {
+        parts.clear();  // before the arena they share
+        if (d_shared) cudaFree(d_shared);
+        release_device();
+    }
 };
 
 namespace {
@@ -146,10 +157,12 @@ int upload(qt_plan_t P) {
     QT_CUDA(cudaGetDevice(&P->device));
     // tensors
     P->arena_bytes = (size_t)hp.total_elems * P->esize;
-    size_t free_b = 0, total_b = 0;
-    QT_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    if (P->arena_bytes + (256u << 20) > free_b) return QT_ENOMEM;
-    QT_CUDA(cudaMalloc(&P->d_arena, std::max<size_t>(P->arena_bytes, 256)));
+    if (!P->arena_external) {
+        size_t free_b = 0, total_b = 0;
+        QT_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        if (P->arena_bytes + (256u << 20) > free_b) return QT_ENOMEM;
+        QT_CUDA(cudaMalloc(&P->d_arena, std::max<size_t>(P->arena_bytes, 256)));
+    }
 
     // static plan arrays, one allocation, 256-byte aligned pieces
     std::vector<uint32_t> u_graph_first_net(hp.graph_first_net.begin(), hp.graph_first_net.end());
@@ -512,6 +525,102 @@ qt_plan_opts default_opts() {
     return o;
 }
 
+int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_opts* opts_in, qt_plan_t* out);
+
+// A gradient plan over opts.adjoint_budget_bytes: its networks are packed, in
+// edge order, into passes whose saved results and cotangents fit the budget
+// (with the leaf tables); each pass is a plan of its own, all on one arena of
+// the largest pass's size. A network that alone exceeds the budget is refused
+// (QT_ENOMEM): networks are not split. Single-graph plans only.
+int make_passes(qt_plan_t P, const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_opts& o) {
+    const qt::HostPlan& hp = P->hp;
+    if (graphs.size() != 1) return QT_ESTATE;
+    const size_t leaf_bytes = (size_t)hp.leaf_elems * P->esize;
+    if (leaf_bytes >= o.adjoint_budget_bytes) return QT_ENOMEM;
+    const size_t room = o.adjoint_budget_bytes - leaf_bytes;
+    const qt::GraphIn& g0 = graphs[0];
+    std::vector<int32_t> cur;
+    size_t cur_bytes = 0;
+    for (size_t i = 0; i < hp.nets.size(); ++i) {
+        size_t nb = 0;  // results and their cotangents (128-byte aligned results)
+        for (uint32_t b = hp.net_first_bucket[i]; b < hp.net_first_bucket[i + 1]; ++b)
+            nb += 2 * (((size_t)1 << hp.buckets[b].n_out) * P->esize + 128);
+        if (nb > room) return QT_ENOMEM;
+        if (cur_bytes + nb > room && !cur.empty()) {
+            P->part_edges.push_back(cur);
+            cur.clear();
+            cur_bytes = 0;
+        }
+        cur.push_back((int32_t)g0.edge_of(i));
+        cur_bytes += nb;
+    }
+    if (!cur.empty()) P->part_edges.push_back(cur);
+    qt_plan_opts so = o;
+    so.adjoint_budget_bytes = 0;
+    so.host_only = 1;
+    so.autotune = 0;
+    size_t arena = 0;
+    for (const auto& pe : P->part_edges) {
+        std::vector<qt::GraphIn> gs(1);
+        gs[0].n = g0.n;
+        gs[0].edges = g0.edges;
+        gs[0].sel = pe;
+        qt_plan_t part = nullptr;
+        const int rc = make_plan(gs, p, &so, &part);
+        if (rc != QT_OK) return rc;
+        P->parts.emplace_back(part);
+        arena = std::max(arena, (size_t)part->hp.total_elems * P->esize);
+    }
+    if (o.host_only) return QT_OK;
+    size_t free_b = 0, total_b = 0;
+    QT_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (arena + (256u << 20) > free_b) return QT_ENOMEM;
+    QT_CUDA(cudaMalloc(&P->d_shared, std::max<size_t>(arena, 256)));
+    for (auto& part : P->parts) {
+        part->host_only = false;
+        part->arena_external = true;
+        part->d_arena = P->d_shared;
+        const int rc = upload(part.get());
+        if (rc != QT_OK) return rc;
+    }
+    return QT_OK;
+}
+
+// Energy (and gradient) of a plan that runs in passes: each pass in turn on
+// the shared arena; per-edge values scattered to the graph's edge order,
+// partial energies and gradients summed in FP64 on the host.
+int run_passes(qt_plan_t P, const double* gammas, const double* betas, double* edge_zz, double* energy,
+               double* dg, double* db, void* stream, bool grad) {
+    const int p = P->hp.cfg.p;
+    const size_t m = P->hp.graphs[0].edges.size();
+    std::vector<double> g(p), b(p), zz(m, 0.0), gs(p, 0.0), bs(p, 0.0);
+    QT_CUDA(cudaMemcpy(g.data(), gammas, sizeof(double) * p, cudaMemcpyDefault));
+    QT_CUDA(cudaMemcpy(b.data(), betas, sizeof(double) * p, cudaMemcpyDefault));
+    double E = 0.0;
+    for (size_t k = 0; k < P->parts.size(); ++k) {
+        qt_plan_t part = P->parts[k].get();
+        const auto& pe = P->part_edges[k];
+        std::vector<double> pz(pe.size()), pg(p), pb(p);
+        double pE = 0.0;
+        int rc = grad ? qt_energy_grad(part, g.data(), b.data(), &pE, pg.data(), pb.data(), stream)
+                      : qt_energy(part, g.data(), b.data(), pz.data(), &pE, stream);
+        if (rc != QT_OK) return rc;
+        if (grad) {
+            for (int i = 0; i < p; ++i) {
+                gs[i] += pg[i];
+                bs[i] += pb[i];
+            }
+        }
+        for (size_t i = 0; i < pe.size(); ++i) zz[pe[i]] = pz[i];
+        E += pE;
+    }
+    if (edge_zz) QT_CUDA(cudaMemcpy(edge_zz, zz.data(), sizeof(double) * m, cudaMemcpyDefault));
+    if (energy) QT_CUDA(cudaMemcpy(energy, &E, sizeof(double), cudaMemcpyDefault));
+    if (grad && dg) QT_CUDA(cudaMemcpy(dg, gs.data(), sizeof(double) * p, cudaMemcpyDefault));
+    if (grad && db) QT_CUDA(cudaMemcpy(db, bs.data(), sizeof(double) * p, cudaMemcpyDefault));
+    return QT_OK;
+}
+
 int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_opts* opts_in, qt_plan_t* out) {
     if (!out) return QT_EINVAL;
     *out = nullptr;
@@ -566,6 +675,12 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     P->arena_bytes = (size_t)P->hp.total_elems * P->esize;
     P->host_only = o.host_only != 0;
     P->trace = o.trace != 0;
+    if (cfg.with_grad && o.adjoint_budget_bytes > 0 && P->arena_bytes > o.adjoint_budget_bytes) {
+        rc = make_passes(P.get(), graphs, p, o);
+        if (rc != QT_OK) return rc;
+        *out = P.release();
+        return QT_OK;
+    }
     if (!P->host_only) {
         rc = o.autotune > 0 ? autotune(P.get(), o.autotune) : upload(P.get());
         if (rc != QT_OK) return rc;
@@ -681,6 +796,7 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->run_tiles = hp.cfg.run_tiles > 0 ? hp.cfg.run_tiles : qt::kRunTiles;
     out->tune_seconds = P->tune_seconds;
     out->tune_candidates = P->tune_candidates;
+    out->n_passes = P->parts.empty() ? 1 : (int32_t)P->parts.size();
     return QT_OK;
 }
 
@@ -743,12 +859,14 @@ int qt_plan_network_wires(qt_plan_t P, int32_t network, int32_t* vars_per_qubit)
 int qt_energy(qt_plan_t P, const double* gammas, const double* betas, double* edge_zz, double* energy,
               void* cuda_stream) {
     if (!P) return QT_EINVAL;
+    if (!P->parts.empty()) return run_passes(P, gammas, betas, edge_zz, energy, nullptr, nullptr, cuda_stream, false);
     if (P->hp.graphs.size() != 1) return QT_ESTATE;
     return run_eval(P, gammas, betas, cuda_stream, edge_zz, energy, false);
 }
 
 int qt_energy_batch(qt_plan_t P, const double* gammas, const double* betas, double* energies, double* edge_zz,
                     void* cuda_stream) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P) return QT_EINVAL;
     return run_eval(P, gammas, betas, cuda_stream, edge_zz, energies, true);
 }
@@ -756,6 +874,10 @@ int qt_energy_batch(qt_plan_t P, const double* gammas, const double* betas, doub
 int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, double* energy, double* dE_dgamma,
                    double* dE_dbeta, void* cuda_stream) {
     if (!P) return QT_EINVAL;
+    if (!P->parts.empty()) {
+        if (!gammas || !betas) return QT_EINVAL;
+        return run_passes(P, gammas, betas, nullptr, energy, dE_dgamma, dE_dbeta, cuda_stream, true);
+    }
     if (P->host_only || !P->hp.cfg.with_grad) return QT_ESTATE;
     const qt::HostPlan& hp = P->hp;
     const int G = (int)hp.graphs.size(), p = hp.cfg.p;
@@ -804,6 +926,7 @@ int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, doubl
 }
 
 int qt_last_imag(qt_plan_t P, double* edge_imag) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P || !edge_imag) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
@@ -814,6 +937,13 @@ int qt_last_imag(qt_plan_t P, double* edge_imag) {
 }
 
 int qt_sync(qt_plan_t P, void* cuda_stream) {
+    if (P && !P->parts.empty()) {
+        for (auto& part : P->parts) {
+            const int rc = qt_sync(part.get(), cuda_stream);
+            if (rc != QT_OK) return rc;
+        }
+        return QT_OK;
+    }
     if (!P) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
@@ -823,6 +953,7 @@ int qt_sync(qt_plan_t P, void* cuda_stream) {
 }
 
 int qt_kernel_time(qt_plan_t P, double* avg_ms, int64_t* launches, int32_t reset) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
@@ -837,6 +968,7 @@ int qt_kernel_time(qt_plan_t P, double* avg_ms, int64_t* launches, int32_t reset
 }
 
 int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, double* bytes) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P || !avg_ms || reps < 1 || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
     if (P->host_only || P->sched != QT_SCHED_PERSISTENT) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
@@ -878,6 +1010,7 @@ int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, do
 }
 
 int qt_trace_counters(qt_plan_t P, uint64_t* totals, int64_t* n_warps) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P || !totals) return QT_EINVAL;
     if (P->host_only || !P->trace) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
@@ -893,6 +1026,7 @@ int qt_trace_counters(qt_plan_t P, uint64_t* totals, int64_t* n_warps) {
 }
 
 int qt_trace_bucket_times(qt_plan_t P, uint64_t* start_end_ns) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P || !start_end_ns) return QT_EINVAL;
     if (P->host_only || !P->trace) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
@@ -902,6 +1036,7 @@ int qt_trace_bucket_times(qt_plan_t P, uint64_t* start_end_ns) {
 }
 
 int qt_debug_stall_bucket(qt_plan_t P, int64_t bucket) {
+    if (P && !P->parts.empty()) return QT_ESTATE;  // a plan that runs in passes: energy and gradient only
     if (!P || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));

@@ -41,7 +41,7 @@ class PlanOpts(ctypes.Structure):
                 ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("no_fuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("tile_cap", ctypes.c_int8 * 8)]
+                ("tile_cap", ctypes.c_int8 * 8), ("adjoint_budget_bytes", ctypes.c_size_t)]
 
 
 class PlanStats(ctypes.Structure):
@@ -52,7 +52,8 @@ class PlanStats(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("width_hist", ctypes.c_int64 * 64),
                 ("plan_seconds", ctypes.c_double), ("sim_seconds", ctypes.c_double),
                 ("n_units", ctypes.c_int64), ("n_fused", ctypes.c_int64), ("tile_cap", ctypes.c_int32 * 8),
-                ("run_tiles", ctypes.c_int32), ("tune_seconds", ctypes.c_double), ("tune_candidates", ctypes.c_int32)]
+                ("run_tiles", ctypes.c_int32), ("tune_seconds", ctypes.c_double), ("tune_candidates", ctypes.c_int32),
+                ("n_passes", ctypes.c_int32)]
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
@@ -181,7 +182,7 @@ class Plan:
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
-              order="simulated", fuse=True, autotune=0, tile_cap=None):
+              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0):
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
         o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
@@ -198,6 +199,7 @@ class Plan:
         o.order = {"simulated": 0, "ready_queue": 1}[order]
         o.no_fuse = 0 if fuse else 1
         o.autotune = int(autotune)
+        o.adjoint_budget_bytes = int(adjoint_budget_bytes)
         for i, c in enumerate(tile_cap or []):
             o.tile_cap[i] = int(c)
         return o

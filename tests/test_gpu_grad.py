@@ -173,3 +173,26 @@ def test_sharded_energy_and_gradient_sum_to_the_whole(dtype):
     assert abs(tot_E - E[0]) <= tol * abs(E[0])
     np.testing.assert_allclose(tot_g, dg, atol=tol * 10)
     np.testing.assert_allclose(tot_b, db, atol=tol * 10)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_gradient_under_a_memory_budget_matches_the_whole(dtype):
+    """opts.adjoint_budget_bytes at a quarter of what the plan would hold: the
+    networks run in passes on one shared arena; energy, edge values and
+    gradient equal the unbudgeted plan's."""
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True) as pl:
+        need = pl.stats()["arena_bytes"]
+        E, dg, db = pl.energy_grad(g, b)
+        zz, _ = pl.energy(g, b)
+    with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True, adjoint_budget_bytes=need // 4) as pl:
+        assert pl.stats()["n_passes"] >= 4
+        E2, dg2, db2 = pl.energy_grad(g, b)
+        zz2, E3 = pl.energy(g, b)
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    assert abs(E2[0] - E[0]) <= tol * abs(E[0]) and abs(E3 - E[0]) <= tol * abs(E[0])
+    np.testing.assert_allclose(zz2, zz, atol=tol)
+    np.testing.assert_allclose(dg2, dg, atol=10 * tol)
+    np.testing.assert_allclose(db2, db, atol=10 * tol)

@@ -413,3 +413,18 @@ def test_tile_caps_per_width_class():
         _check_tiles(B, O, int(b))
     with pytest.raises(qtgb.QTError):
         host_plan(n, edges, p, tile_cap=[12, 0, 0, 0, 0])
+
+
+def test_adjoint_budget_splits_networks_into_passes():
+    """A gradient plan over opts.adjoint_budget_bytes runs its networks in
+    passes that fit; a budget below the largest network is refused."""
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    with host_plan(n, edges, p, with_grad=True) as full:
+        need = full.stats()["arena_bytes"]
+        assert full.stats()["n_passes"] == 1
+    with host_plan(n, edges, p, with_grad=True, adjoint_budget_bytes=need // 3) as pl:
+        assert pl.stats()["n_passes"] >= 3
+    with pytest.raises(qtgb.QTError) as ei:
+        host_plan(n, edges, p, with_grad=True, adjoint_budget_bytes=1 << 20)
+    assert ei.value.code == qtgb.QT_ENOMEM
