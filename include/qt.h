@@ -94,6 +94,10 @@ typedef struct {
                               the device over `autotune` evaluations; the choice is in qt_plan_stats */
     int8_t tile_cap[8];    /* most tile bits (log2 outputs per tile, 1..11) per width class, 0: default
                               (chunk_log2, else 9); the first 5 entries are used */
+    int32_t no_merge;      /* nonzero: no merged eliminations. By default a bucket of 2^12 outputs or
+                              more and the consumer that only extends it become one bucket summing
+                              both variables, the intermediate never written (persistent-schedule
+                              plans without gradients; the others never merge) */
     size_t adjoint_budget_bytes; /* gradient plans (single graph): device bytes for results and their
                               cotangents; a plan that needs more runs its networks in passes that fit
                               (each pass saves its own results; energies and gradients are summed over
@@ -140,22 +144,26 @@ typedef struct {
     int32_t n_deps;    /* operands that are results of earlier buckets */
     int32_t level;     /* 0 for buckets whose operands are all leaves */
     int32_t var;       /* the summed variable, numbered within the network */
-    int32_t tile_log2; /* log2 of the outputs per tile of the persistent kernel */
+    int32_t tile_log2; /* log2 of the outputs per tile of the persistent kernel (a merged bucket's
+                          tiles run over pairs (o, s1), s1 lowest: 2^(tile_log2 - 1) results) */
     uint32_t tile_bits;/* the output bits that vary within a tile (popcount = tile_log2): the
                           lowest ones, so tile c holds outputs c * 2^tile_log2 + j */
     uint32_t folded;   /* operands (bit i: the bucket's i-th) folded into the per-tile gate table */
     uint32_t unit_role;/* 0: scheduled on its own; 1: inside a fused unit; 2: the root of a fused unit */
+    int32_t n_sum;     /* summed variables (more than 1: merged eliminations); outputs 2^(width - n_sum) */
+    int32_t var2;      /* a merged bucket's second summed variable (its consumer's), else -1 */
 } qt_bucket_info;
 
-/* One operand of a bucket. The operand's entry for output index o and summed
- * value x is at element 2*pext(o, mask) + x of its tensor. */
+/* One operand of a bucket. With one summed variable (smask = 1) the operand's
+ * entry for output index o and summed value x is at element 2*pext(o, mask) + x. */
 typedef struct {
     int32_t src;       /* producing bucket, or -1 for a leaf gate tensor */
     int32_t leaf_kind; /* for leaves: QT_LEAF_* below, else -1 */
     int32_t leaf_layer;/* for ZZ and mixer leaves: layer 0..p-1, else -1 */
     uint32_t mask;     /* output bits this operand carries */
-    int32_t rank;      /* index bits of the operand (summed bit included) */
-    int32_t pad;
+    int32_t rank;      /* index bits of the operand (summed bits included) */
+    uint32_t smask;    /* summed variables it carries; its entry for output o and summed values s is
+                          2^popc(smask) * pext(o, mask) + pext(s, smask) */
 } qt_operand_info;
 
 #define QT_LEAF_PLUS 0   /* [1, 1]/sqrt 2: |+> and <+| */

@@ -544,7 +544,7 @@ int make_passes(qt_plan_t P, const std::vector<qt::GraphIn>& graphs, int32_t p, 
     for (size_t i = 0; i < hp.nets.size(); ++i) {
         size_t nb = 0;  // results and their cotangents (128-byte aligned results)
         for (uint32_t b = hp.net_first_bucket[i]; b < hp.net_first_bucket[i + 1]; ++b)
-            nb += 2 * (((size_t)1 << hp.buckets[b].n_out) * P->esize + 128);
+            nb += 2 * (((size_t)1 << qt::result_bits(hp.buckets[b])) * P->esize + 128);
         if (nb > room) return QT_ENOMEM;
         if (cur_bytes + nb > room && !cur.empty()) {
             P->part_edges.push_back(cur);
@@ -650,6 +650,9 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
     cfg.fuse = o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad && o.no_fuse == 0;
+    // the reverse sweep, the per-bucket kernel and fused units sum one
+    // variable per bucket: merging is a forward, persistent-schedule option
+    cfg.merge = o.no_merge == 0 && o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad;
     for (int c = 0; c < qt::kWidthClasses; ++c) {
         if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
         cfg.tile_cap[c] = o.tile_cap[c];
@@ -821,6 +824,8 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             for (uint32_t i = 0; i < d.n_ops; ++i)
                 if (hp.operands[d.op_begin + i].folded) o.folded |= 1u << i;
             o.unit_role = (d.flags & qt::kBucketInUnit) ? 1u : (d.flags & qt::kBucketUnitRoot) ? 2u : 0u;
+            o.n_sum = qt::bucket_n_sum(d.flags);
+            o.var2 = hp.bucket_var2[b];
         }
     }
     if (operands) {
@@ -829,9 +834,14 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.src = hp.op_src[i];
             o.leaf_kind = hp.op_leaf_kind[i];
             o.leaf_layer = hp.op_leaf_layer[i];
-            o.mask = hp.operands[i].mask;
             o.rank = hp.op_rank[i];
-            o.pad = 0;
+            o.smask = hp.operands[i].smask;
+            o.mask = hp.operands[i].mask;
+        }
+        // a merged bucket's operands carry s1 as bit 0 of their device masks
+        for (const qt::DBucket& d : hp.buckets) {
+            if (qt::bucket_n_sum(d.flags) == 1) continue;
+            for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) operands[i].mask >>= 1;
         }
     }
     return QT_OK;
@@ -1002,7 +1012,7 @@ int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, do
     if (err != 0) return err;
     *avg_ms = total / reps;
     if (bytes) {
-        double b = (double)(1ull << d.n_out);
+        double b = (double)(1ull << qt::result_bits(d));
         for (uint32_t o = d.op_begin; o < d.op_begin + d.n_ops; ++o) b += std::ldexp(1.0, P->hp.op_rank[o]);
         *bytes = b * (double)P->esize;
     }

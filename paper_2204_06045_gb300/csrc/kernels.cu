@@ -205,6 +205,7 @@ struct RunSlot {
     uint32_t gmask[kMaxOps];   // staged operands: full masks
     uint16_t soff[kMaxOps];    // staged operands: element offset in the stage buffer
     uint32_t lmask[kMaxFoldLeaves];
+    uint8_t lx[kMaxFoldLeaves];  // 1: the folded tensor's entries pair over x; 0: it lacks x (merged buckets)
     typename CT<R>::c lval[kMaxFoldLeaves][kLeafSlots];  // the folded gate tensors
     uint32_t bucket, chunk_begin, n_chunks;
     uint32_t parent, n_tasks;
@@ -213,6 +214,7 @@ struct RunSlot {
     uint32_t total_foot;  // staged elements per tile
     uint8_t n_out, cb, n_staged, n_leaves;
     uint8_t n_ops;
+    uint8_t merged;       // merged eliminations: each lane's two outputs add into one result
     uint32_t bad;         // the plan's footprint exceeds the stage: not computed
     // per-group constants of the unrolled tile loop, for the staged operands
     // and the gate table (at most kFast of them)
@@ -370,6 +372,7 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             us.bad = 0;
             us.n_fast = 0;
             us.n_hi = 0;
+            us.merged = 0;
             us.unit_begin = run.unit_begin;
             us.unit_count = run.unit_count;
         }
@@ -382,13 +385,16 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
     const DBucket B = dp.buckets[run.bucket];
     RunSlot<R>& rs = ws.slot[sl];
     const bool has = lane < B.n_ops;
-    const bool fits = B.total_foot <= (uint32_t)StageCfg<R>::elems && B.n_leaves <= kMaxFoldLeaves;
+    // an operand without x (a merged bucket's consumer gates) is always folded
+    const bool fits = B.total_foot <= (uint32_t)StageCfg<R>::elems && B.n_leaves <= kMaxFoldLeaves &&
+                      __all_sync(kFull, !has || op.folded || (op.smask & 1u));
     if (has && fits) {
         if (op.folded) {
             // a gate tensor (4 slots) or an earlier result of rank <= 2, which
             // this launch wrote from another SM: read that one at L2; its
             // allocation is 128-byte aligned, so 4 entries stay inside it
             rs.lmask[op.slot] = op.mask;
+            rs.lx[op.slot] = op.smask & 1u;
             const C* T = static_cast<const C*>(dp.arena) + op.off;
             if ((op.flags & kOpLeaf) || results_ready) {
 #pragma unroll
@@ -415,6 +421,7 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
         rs.n_staged = B.n_staged;
         rs.n_leaves = B.n_leaves;
         rs.n_ops = B.n_ops;
+        rs.merged = bucket_n_sum(B.flags) > 1;
         rs.unit_begin = 0;
         rs.unit_count = 0;
         rs.bad = !fits;
@@ -640,6 +647,8 @@ __device__ void tile_from_smem_generic(const WarpSmem<R>& ws, int sl, int st, ty
                 const C r1 = cadd(acc[u][1][0], acc[u][1][1]);
                 if (rs.n_out == 0)
                     out[0] = r0;
+                else if (rs.merged)  // outputs (o, s1 = 0, 1) add into result o
+                    out[((uint64_t)o0 >> 1) + ((uint64_t)i << 5) + (uint64_t)lane] = cadd(r0, r1);
                 else
                     st_two(out, (uint64_t)o0 + ((uint64_t)i << 6) + ((uint64_t)lane << 1), r0, r1);
             }
@@ -674,11 +683,19 @@ __device__ __forceinline__ void stg_two(double2* p, double2 a, double2 b) {
     asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(a.x), "d"(a.y));
     asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p + 1), "d"(b.x), "d"(b.y));
 }
+__device__ __forceinline__ void stg_one(float2* p, float2 a) {
+    asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a.x), "f"(a.y));
+}
+__device__ __forceinline__ void stg_one(double2* p, double2 a) {
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(a.x), "d"(a.y));
+}
 
 // The hot path for tiles of at least 64 outputs (cb = 6 + log2 NI): N
 // operands in shared memory, every loop fully unrolled. A lane owns outputs
 // 2*lane + {0,1} + 64*i; an operand's pair for such an output sits at the
 // lane's offset plus the steps of the iteration's bits, all fixed per group.
+// In a merged bucket the two outputs are s1 = 0, 1 of result lane + 32*i:
+// the lane adds them.
 template <typename R, int N, int NI>
 __device__ __forceinline__ void tile_fast(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
                                           const RunSlot<R>& rs, typename CT<R>::c* out, int lane) {
@@ -717,7 +734,11 @@ __device__ __forceinline__ void tile_fast(const uint32_t (&sbase)[N], const uint
                 p11 = cmul(p11, b.v1);
             }
         }
-        stg_two(out + (i * 64 + 2 * lane), cadd(p00, p01), cadd(p10, p11));
+        const C r0 = cadd(p00, p01), r1 = cadd(p10, p11);
+        if (rs.merged)
+            stg_one(out + (i * 32 + lane), cadd(r0, r1));
+        else
+            stg_two(out + (i * 64 + 2 * lane), r0, r1);
     }
 }
 
@@ -735,7 +756,7 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
         sbase[t] = tok + (is_tab ? smem_u32(ws.leaf_tab) : smem_u32(ws.stage[st] + rs.soff[t]));
         smask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
-    C* tile_out = out + ((uint64_t)chunk << rs.cb);
+    C* tile_out = out + ((uint64_t)chunk << (rs.cb - rs.merged));
     switch (rs.cb) {
         case 6: tile_fast<R, N, 1>(sbase, smask, rs, tile_out, lane); break;
         case 7: tile_fast<R, N, 2>(sbase, smask, rs, tile_out, lane); break;
@@ -766,11 +787,16 @@ __device__ bool wait_stage(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, u
     return true;
 }
 
-// The folded gate table of a tile. Gate tensors whose output bit lies inside
-// the tile (and rank-1 ones) give a table over the tile bits that is the same
-// for every tile of a group: each lane keeps its two entries in `tlow`. Gate
-// tensors whose bit lies above the tile only select one of their two rows per
-// tile, so the table of a tile is tlow times that per-tile pair.
+// The folded gate table of a tile: entry 2j + x is the product of the folded
+// tensors at tile output pdep(j, leaf_u) and summed value x; a tensor without
+// x (a merged bucket's consumer gates) gives both x the same factor. Tensors
+// whose bits lie inside the tile give a table over the tile bits that is the
+// same for every tile of a group: each lane keeps its two entries in `tlow`.
+// A tensor with a bit above the tile (one at most: rank <= 2) takes one of two
+// values per tile. With x it depends on x alone within the tile; without x its
+// other bit is output bit 0, which is then in leaf_u, so that entry e sees it
+// as bit 1 of e. The table of a tile is tlow times one of four per-tile
+// factors, picked by e & 3; each lane computes its own.
 template <typename R>
 __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs, uint32_t chunk, bool first,
                                            typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane) {
@@ -788,7 +814,10 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
                 const uint32_t x = e & 1u;
                 const uint32_t o = pdep_u32(e >> 1, rs.leaf_u);
                 for (int l = 0; l < rs.n_leaves; ++l)
-                    if ((rs.lmask[l] & ~low) == 0u) v = cmul(v, rs.lval[l][2u * pext_u32(o, rs.lmask[l]) + x]);
+                    if ((rs.lmask[l] & ~low) == 0u) {
+                        const uint32_t jl = pext_u32(o, rs.lmask[l]);
+                        v = cmul(v, rs.lval[l][rs.lx[l] ? 2u * jl + x : jl]);
+                    }
             }
             tlow[h] = v;
         }
@@ -798,19 +827,20 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
     for (int h = 0; h < rs.n_hi; ++h) key |= ((chunk >> rs.hi_shift[h]) & 1u) << h;
     if (!first && key == hi_key) return;
     hi_key = key;
-    C cp[2];
-    cp[0].x = cp[1].x = (R)1;
-    cp[0].y = cp[1].y = (R)0;
+    // this lane's entries e = lane + 32h all have e & 3 = lane & 3
+    const uint32_t x = (uint32_t)lane & 1u, b0 = ((uint32_t)lane >> 1) & 1u;
+    C f;
+    f.x = (R)1;
+    f.y = (R)0;
     for (int h = 0; h < rs.n_hi; ++h) {
         const int l = rs.hi_idx[h];
-        const uint32_t y = (key >> h) & 1u;  // the tensor's single output bit
-        cp[0] = cmul(cp[0], rs.lval[l][2u * y]);
-        cp[1] = cmul(cp[1], rs.lval[l][2u * y + 1u]);
+        const uint32_t y = (key >> h) & 1u;  // the tensor's bit above the tile
+        f = cmul(f, rs.lval[l][2u * y + (rs.lx[l] ? x : b0)]);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const uint32_t e = (uint32_t)lane + 32u * h;
-        if (e < nent) ws.leaf_tab[e] = cmul(tlow[h], cp[e & 1u]);
+        if (e < nent) ws.leaf_tab[e] = cmul(tlow[h], f);
     }
     __syncwarp();
 }

@@ -294,6 +294,93 @@ static int make_buckets(const Network& net, const std::vector<int>& order, int m
     return QT_OK;
 }
 
+// Merged eliminations (the paper's merged-index contraction, §II-C): when a
+// bucket's consumer only extends it (the consumer's one earlier result is
+// this bucket's, and it adds no variable, so its width is one less), the two
+// eliminations become one bucket that sums both variables. The consumer's
+// summed variable is bit 0 of the bucket's output, so in the merged bucket
+// the summed variables are the bucket's own and that bit; the output is the
+// consumer's. The intermediate result is never written. Operands keep their
+// index bits: the bucket's own operands move their output bit 0 into the
+// summed mask, the consumer's gate tensors carry the second summed variable.
+// Pairs are taken from the leaves up (kMaxSum = 2), for buckets of at least
+// 2^kMergeMinOut outputs.
+static void merge_chains(NetPlan* np) {
+    auto& bs = np->buckets;
+    const int nb = (int)bs.size();
+    std::vector<uint8_t> gone(nb, 0);
+    std::vector<int> into(nb);  // an absorbed consumer's results now come from this bucket
+    for (int b = 0; b < nb; ++b) into[b] = b;
+    for (int b = 0; b < nb; ++b) {
+        if (gone[b]) continue;
+        HBucket& B = bs[b];
+        const int p = B.parent;
+        if (p < 0 || B.n_sum >= kMaxSum || B.width - B.n_sum < kMergeMinOut) continue;
+        HBucket& P = bs[p];
+        if (P.n_sum != 1 || P.width != B.width - 1) continue;
+        int nonleaf = 0;
+        bool from_b = false;
+        for (const HOperand& op : P.ops)
+            if (op.src >= 0) {
+                nonleaf++;
+                from_b = op.src == b;
+            }
+        if (nonleaf != 1 || !from_b || B.ops.size() + P.ops.size() - 1 > (size_t)kMaxOps) continue;
+        // the consumer's gate tensors go into the merged bucket's gate table,
+        // with the bucket's own tensors of rank <= 2
+        int small = 0;
+        bool all_small = true;
+        for (const HOperand& op : B.ops) small += op.rank <= 2;
+        for (const HOperand& op : P.ops)
+            if (op.src < 0) {
+                small++;
+                all_small = all_small && op.rank <= 2;
+            }
+        if (!all_small || small > kMaxFoldLeaves) continue;
+        const uint32_t sbit = 1u << B.n_sum;
+        for (HOperand& op : B.ops) {
+            if (op.mask & 1u) op.smask |= sbit;
+            op.mask >>= 1;
+        }
+        for (const HOperand& op : P.ops) {
+            if (op.src >= 0) continue;
+            HOperand q = op;
+            q.smask = sbit;  // the consumer's summed variable; its output bits are the merged output's
+            B.ops.push_back(q);
+        }
+        B.n_sum++;
+        B.var2 = P.var;
+        B.parent = P.parent;
+        gone[p] = 1;
+        into[p] = b;
+    }
+    // renumber the remaining buckets (elimination order kept)
+    std::vector<int> id(nb, -1);
+    int k = 0;
+    for (int b = 0; b < nb; ++b)
+        if (!gone[b]) id[b] = k++;
+    for (int b = 0; b < nb; ++b)
+        if (gone[b]) id[b] = id[into[b]];
+    if (k == nb) return;
+    std::vector<HBucket> out;
+    out.reserve(k);
+    for (int b = 0; b < nb; ++b) {
+        if (gone[b]) continue;
+        HBucket B = std::move(bs[b]);
+        B.parent = B.parent >= 0 ? id[B.parent] : -1;
+        B.n_deps = 0;
+        B.level = 0;
+        for (HOperand& op : B.ops)
+            if (op.src >= 0) {
+                op.src = id[op.src];
+                B.n_deps++;
+                B.level = std::max(B.level, out[op.src].level + 1);
+            }
+        out.push_back(std::move(B));
+    }
+    bs = std::move(out);
+}
+
 // Operands of rank <= 2 (gate tensors, and results of 4 entries or fewer) may
 // be folded into the per-tile product table.
 static bool foldable(const HOperand& op) { return op.rank <= 2; }
@@ -304,9 +391,13 @@ static bool foldable(const HOperand& op) { return op.rank <= 2; }
 // 2^(popc(M & (2^cb - 1)) + 1) elements starting at 2 * pext(o0, M). Gate
 // tensors are folded into one per-tile table when their tile bits number at
 // most kLeafBits; otherwise they are staged like the others.
+// Takes the device view of a bucket (device_view): operands with smask 0
+// carry no summed variable and must be folded.
 static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_elems, int* cb_out, bool* fold_out) {
     (void)net;
-    const int n_out = B.width - 1;
+    const int n_out = B.width - B.n_sum;
+    bool must_fold = false;
+    for (const HOperand& op : B.ops) must_fold = must_fold || op.smask == 0;
     for (int cb = std::min(n_out, cap); cb >= 0; --cb) {
         const uint32_t low = cb >= 32 ? 0xffffffffu : ((1u << cb) - 1u);
         uint32_t U = 0;
@@ -316,10 +407,13 @@ static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_e
                 U |= op.mask & low;
                 nleaf++;
             }
-        const bool fold = nleaf > 0 && nleaf <= kMaxFoldLeaves && __builtin_popcount(U) <= kLeafBits;
+        // the gate table holds 2^n_sum entries per value of its tile bits
+        const bool fold = nleaf > 0 && nleaf <= kMaxFoldLeaves && __builtin_popcount(U) + B.n_sum <= kLeafBits + 1;
+        if (must_fold && !fold) continue;
         long foot = 0;
         for (const HOperand& op : B.ops)
-            if (!(fold && foldable(op))) foot += 2l << __builtin_popcount(op.mask & low);
+            if (!(fold && foldable(op)))
+                foot += (1l << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & low);
         if (foot <= stage_elems) {
             *cb_out = cb;
             *fold_out = fold;
@@ -331,6 +425,21 @@ static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_e
 }
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// A bucket as the device contracts it. A merged bucket (summing s0, then s1)
+// becomes the bucket of s0 alone with outputs (o, s1), s1 as bit 0: operand
+// masks gain bit 0 where they carry s1, and smask keeps only s0 (0 for the
+// consumer's gate tensors). Other buckets are unchanged.
+static HBucket device_view(const HBucket& B) {
+    HBucket V = B;
+    if (B.n_sum == 1) return V;
+    V.n_sum = 1;
+    for (HOperand& op : V.ops) {
+        op.mask = (op.mask << 1) | ((op.smask >> 1) & 1u);
+        op.smask &= 1u;
+    }
+    return V;
+}
 
 // Fused units (§III-A and §III-C: small buckets dominate GPU time). A bucket
 // whose subtree (it and every bucket producing, directly or not, one of its
@@ -350,7 +459,7 @@ static void form_units(HostPlan* hp, int stage_elems) {
     std::vector<std::vector<uint32_t>> kids(nb);
     for (uint32_t b = 0; b < nb; ++b) {
         const DBucket& d = hp->buckets[b];
-        bool good = d.n_out <= kFuseOutBits;
+        bool good = d.n_out <= kFuseOutBits && bucket_n_sum(d.flags) == 1;  // units sum one variable per bucket
         for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) {
             const int32_t src = hp->op_src[i];
             if (src >= 0) {
@@ -480,7 +589,8 @@ static void simulate_order(HostPlan* hp) {
     const double t_unit_bucket = 0.15e-6;  // one small bucket inside a fused unit
     for (size_t b = 0; b < nb; ++b) {
         const DBucket& d = hp->buckets[b];
-        const double tile_bytes = ((double)d.total_foot + std::ldexp(1.0, d.chunk_bits)) * esize;
+        const double tile_bytes =
+            ((double)d.total_foot + std::ldexp(1.0, d.chunk_bits - (bucket_n_sum(d.flags) - 1))) * esize;
         tile_s[b] = tile_bytes / (bw / W) + t_tile;
         if (d.flags & kBucketUnitRoot) {  // the whole unit, as one group of one "tile"
             tile_s[b] = t_unit_bucket * d.unit_count;
@@ -637,6 +747,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             NetPlan& np = hp->nplans[i];
             np.order = best_order;
             status[i] = make_buckets(net, best_order, cfg.max_width, &np);
+            if (status[i] == QT_OK && cfg.merge) merge_chains(&np);
         }
     };
     unsigned nthreads = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
@@ -665,6 +776,7 @@ int layout_plan(HostPlan* hp) {
     hp->op_rank.clear();
     hp->bucket_level.clear();
     hp->bucket_var.clear();
+    hp->bucket_var2.clear();
     hp->root_bucket.clear();
     hp->sim_seconds = 0;
 
@@ -692,27 +804,28 @@ int layout_plan(HostPlan* hp) {
         const uint32_t base = (uint32_t)hp->buckets.size();
         for (size_t lb = 0; lb < np.buckets.size(); ++lb) {
             const HBucket& B = np.buckets[lb];
+            const HBucket V = device_view(B);
             DBucket d{};
             d.op_begin = (uint32_t)hp->operands.size();
             d.n_ops = (uint8_t)B.ops.size();
             d.n_out = (uint8_t)(B.width - 1);
             int cb = 0;
             bool fold = false;
-            const int tcap = cfg.tile_cap[width_class(B.width - 1)];
-            pick_tile(B, net, tcap > 0 ? tcap : cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
+            const int tcap = cfg.tile_cap[width_class(d.n_out)];
+            pick_tile(V, net, tcap > 0 ? tcap : cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
                       cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, &cb, &fold);
             d.chunk_bits = (uint8_t)cb;
-            d.flags = fold ? kBucketFoldLeaves : 0;
+            d.flags = (uint8_t)((fold ? kBucketFoldLeaves : 0) | ((B.n_sum - 1) << 3));
             {
                 const uint32_t low = (1u << cb) - 1u;
                 uint32_t foot = 0, ns = 0, nl = 0, lu = 0, lh = 0;
-                for (const HOperand& op : B.ops) {
+                for (const HOperand& op : V.ops) {
                     if (fold && foldable(op)) {
                         nl++;
                         lu |= op.mask & low;
                         lh |= op.mask & ~low;
                     } else {
-                        foot += 2u << __builtin_popcount(op.mask & low);
+                        foot += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & low);
                         ns++;
                     }
                 }
@@ -727,20 +840,22 @@ int layout_plan(HostPlan* hp) {
             d.n_tasks = 1u << (d.n_out - cb);
             d.net = (uint32_t)i;
             d.out_off = off;
-            off += align_up(1ull << d.n_out, align);
+            off += align_up(1ull << (B.width - B.n_sum), align);
             double opbytes = 0;
             uint32_t next_soff = 0, next_staged = 0, next_leaf = 0;
-            for (const HOperand& op : B.ops) {
+            for (size_t t = 0; t < B.ops.size(); ++t) {
+                const HOperand& op = V.ops[t];
                 DOperand o{};
                 o.mask = op.mask;
                 o.src = kNone;
                 o.folded = (d.flags & kBucketFoldLeaves) && foldable(op);
+                o.smask = (uint8_t)B.ops[t].smask;
                 if (o.folded) {
                     o.slot = (uint8_t)next_leaf++;
                 } else {
                     o.slot = (uint8_t)next_staged++;
                     o.soff = (uint16_t)next_soff;
-                    next_soff += 2u << __builtin_popcount(op.mask & ((1u << d.chunk_bits) - 1u));
+                    next_soff += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & ((1u << d.chunk_bits) - 1u));
                 }
                 if (op.src >= 0) {
                     o.off = 0;  // set below, once every result has its offset
@@ -769,13 +884,25 @@ int layout_plan(HostPlan* hp) {
             hp->buckets.push_back(d);
             hp->bucket_level.push_back(B.level);
             hp->bucket_var.push_back(B.var);
+            hp->bucket_var2.push_back(B.var2);
             if (B.parent < 0) hp->root_bucket.push_back(base + (uint32_t)lb);
             hp->max_width = std::max(hp->max_width, B.width);
             hp->n_levels = std::max(hp->n_levels, B.level + 1);
             hp->width_hist[B.width]++;
             hp->sum_2w += std::ldexp(1.0, B.width);
-            hp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - 1));
-            hp->flops += std::ldexp(1.0, B.width) * 6.0 * (double)(B.ops.size() - 1) + std::ldexp(1.0, B.width - 1) * 2.0;
+            hp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - B.n_sum));
+            if (B.n_sum == 2) {
+                // factored as the device computes it: the bucket of s0 (its
+                // products and x-sums), then the consumer's gate products and the
+                // s1-sum, as the two unmerged buckets would
+                double n0 = 0, n1 = 0;
+                for (const HOperand& op : B.ops) (op.smask & 1u ? n0 : n1) += 1;
+                hp->flops += std::ldexp(1.0, B.width) * 6.0 * (n0 - 1) + std::ldexp(1.0, B.width - 1) * 2.0 +
+                             std::ldexp(1.0, B.width - 1) * 6.0 * n1 + std::ldexp(1.0, B.width - 2) * 2.0;
+            } else {
+                hp->flops += std::ldexp(1.0, B.width) * 6.0 * (double)(B.ops.size() - 1) +
+                             std::ldexp(1.0, B.width - 1) * 2.0;
+            }
         }
         hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());
         hp->net_first_root.push_back((uint32_t)hp->root_bucket.size());

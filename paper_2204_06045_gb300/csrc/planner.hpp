@@ -29,15 +29,18 @@ struct HOperand {
     int src;        // local bucket producing it, or -1 for a leaf
     int leaf;       // leaf index in the network, or -1
     uint32_t mask;  // output bits it carries
-    int rank;       // its index bits, the summed one included
+    int rank;       // its index bits, the summed ones included
+    uint32_t smask = 1;  // summed variables it carries (bit k: the bucket's k-th summed variable)
 };
 
 struct HBucket {
     int var;
-    int width;  // inclusive: the summed variable counts
+    int width;  // inclusive: the summed variables count
     int parent; // local id of the consuming bucket, -1 for a scalar result
     int n_deps;
     int level;
+    int n_sum = 1;  // summed variables (more than 1: merged eliminations)
+    int var2 = -1;  // merged: the second summed variable (the absorbed consumer's)
     std::vector<HOperand> ops;
 };
 
@@ -69,6 +72,7 @@ struct PlanConfig {
     bool with_grad = false;
     bool fuse = false;       // form fused units of small subtrees (persistent energy plans)
     int tile_cap[kWidthClasses] = {0, 0, 0, 0, 0};  // most tile bits per bucket-width class (0: chunk_log2 / default)
+    bool merge = false;      // merge chains of eliminations (a bucket and the parent that only extends it)
 };
 
 // The flat plan: what gets uploaded plus host-side bookkeeping.
@@ -88,6 +92,7 @@ struct HostPlan {
     std::vector<int32_t> op_rank;
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
+    std::vector<int32_t> bucket_var2;
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
     std::vector<URec> unit_prog;        // fused units' programs, unit by unit (padded by kURecWindow records)
     uint64_t n_units = 0;

@@ -30,6 +30,18 @@ constexpr int kMaxFoldLeaves = 8;
 constexpr uint8_t kBucketFoldLeaves = 1;
 constexpr uint8_t kBucketInUnit = 2;    // inside a fused unit, not its root: never claimed on its own
 constexpr uint8_t kBucketUnitRoot = 4;  // the root (last bucket) of a fused unit
+// Merged eliminations: flags bits 3..4 hold n_sum - 1, the bucket's summed
+// variables beyond the first. In the planner (and the exported plan) an
+// operand's entry for output o and summed values s is at
+// 2^popc(smask) * pext(o, mask) + pext(s, smask). On the device a bucket
+// summing s0 and then s1 is laid out as the bucket of s0 alone, whose outputs
+// are (o, s1) with s1 as bit 0: its tiles contract s0 as usual, and the
+// epilogue adds the two outputs of each lane (s1 = 0, 1) into result o. The
+// consumer's gate tensors (smask 2: they carry s1 but not s0) are folded
+// into the gate table with equal entries for both values of s0.
+constexpr int kMaxSum = 2;          // summed variables per bucket, at most
+constexpr int kMergeMinOut = 12;    // merge only buckets of at least 2^12 outputs
+constexpr int bucket_n_sum(uint8_t flags) { return 1 + ((flags >> 3) & 3); }
 // Fused units: a subtree of small buckets (every output count at most
 // 2^kFuseOutBits, every non-gate operand produced inside the subtree) is one
 // work group; one warp contracts its buckets in elimination order with the
@@ -67,7 +79,7 @@ struct DBucket {
     uint32_t op_begin;  // first operand in the operand array
     uint8_t n_ops;      // operand count
     uint8_t flags;      // kBucketFoldLeaves: gate tensors go through the per-tile product table
-    uint8_t n_out;      // output bits (width - 1)
+    uint8_t n_out;      // output bits of the tiles (width - 1); the result has n_out + 1 - n_sum
     uint8_t chunk_bits; // log2 of the outputs per tile
     uint32_t parent;    // consuming bucket, kNone for a root (scalar result)
     uint32_t n_deps;    // operands produced by earlier buckets
@@ -86,18 +98,21 @@ struct DBucket {
     uint32_t unit_count;  // kBucketUnitRoot: the unit's buckets (the root last)
 };
 static_assert(sizeof(DBucket) == 64, "DBucket layout");
+// index bits of a bucket's result
+constexpr int result_bits(const DBucket& d) { return d.n_out + 1 - bucket_n_sum(d.flags); }
 
 // One operand on the device. 32 bytes.
 struct DOperand {
     uint64_t off;      // element offset of the operand's tensor in the arena
-    uint32_t mask;     // output bits the operand carries
+    uint32_t mask;     // output bits the operand carries (tile outputs: s1 is bit 0 when merged)
     uint32_t flags;    // kOpLeaf: a gate tensor (written before the contraction starts)
     uint32_t src;      // producing bucket, kNone for a gate tensor
     uint32_t src_tiles;// the producer's tile count
     uint16_t soff;     // staged: element offset of its tile footprint in the stage buffer
     uint8_t slot;      // position among the staged operands, or among the folded gate tensors
     uint8_t folded;    // 1: folded into the per-tile gate table
-    uint32_t pad;
+    uint8_t smask;     // summed variables it carries: bit 0 s0 (the entry pair's x), bit 1 s1
+    uint8_t pad[3];
 };
 static_assert(sizeof(DOperand) == 32, "DOperand layout");
 constexpr uint32_t kOpLeaf = 1u;

@@ -41,7 +41,7 @@ class PlanOpts(ctypes.Structure):
                 ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("no_fuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("tile_cap", ctypes.c_int8 * 8), ("adjoint_budget_bytes", ctypes.c_size_t)]
+                ("tile_cap", ctypes.c_int8 * 8), ("no_merge", ctypes.c_int32), ("adjoint_budget_bytes", ctypes.c_size_t)]
 
 
 class PlanStats(ctypes.Structure):
@@ -59,11 +59,11 @@ class PlanStats(ctypes.Structure):
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
                          ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32),
                          ("tile_log2", np.int32), ("tile_bits", np.uint32), ("folded", np.uint32),
-                         ("unit_role", np.uint32)])
+                         ("unit_role", np.uint32), ("n_sum", np.int32), ("var2", np.int32)])
 GROUP_DTYPE = np.dtype([("bucket", np.int32), ("first_tile", np.int32), ("n_tiles", np.int32),
                         ("unit_buckets", np.int32)])
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
-                          ("mask", np.uint32), ("rank", np.int32), ("pad", np.int32)])
+                          ("mask", np.uint32), ("rank", np.int32), ("smask", np.uint32)])
 
 _lib = None
 
@@ -182,7 +182,7 @@ class Plan:
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
-              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0):
+              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=True):
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
         o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
@@ -200,6 +200,7 @@ class Plan:
         o.no_fuse = 0 if fuse else 1
         o.autotune = int(autotune)
         o.adjoint_budget_bytes = int(adjoint_budget_bytes)
+        o.no_merge = 0 if merge else 1
         for i, c in enumerate(tile_cap or []):
             o.tile_cap[i] = int(c)
         return o

@@ -44,18 +44,23 @@ def evaluate(buckets, operands, gammas, betas, graph_of_network=None):
     value = np.ones(n_nets, dtype=complex)
     for b in range(buckets.shape[0]):
         B = buckets[b]
-        n_out = int(B["width"]) - 1
+        # a bucket sums n_sum variables (more than one: merged eliminations);
+        # an operand's entry for output o and summed values s is
+        # 2^popc(smask) * pext(o, mask) + pext(s, smask)
+        n_sum = int(B["n_sum"]) if "n_sum" in B.dtype.names else 1
+        n_out = int(B["width"]) - n_sum
         o = np.arange(1 << n_out, dtype=np.int64)
         acc = np.zeros(1 << n_out, dtype=complex)
         net = int(B["network"])
         g = 0 if graph_of_network is None else graph_of_network[net]
         gam = gammas[g] if np.ndim(gammas) == 2 else gammas
         bet = betas[g] if np.ndim(betas) == 2 else betas
-        for x in (0, 1):
+        for x in range(1 << n_sum):
             prod = np.ones(1 << n_out, dtype=complex)
             for t in range(int(B["op_begin"]), int(B["op_begin"]) + int(B["n_ops"])):
                 op = operands[t]
-                idx = 2 * pext(o, int(op["mask"])) + x
+                sm = int(op["smask"]) if "smask" in op.dtype.names else 1
+                idx = (pext(o, int(op["mask"])) << bin(sm).count("1")) + pext(np.int64(x), sm)
                 if op["src"] < 0:
                     T = leaf_tensor(int(op["leaf_kind"]), int(op["leaf_layer"]), gam, bet)
                 else:

@@ -80,7 +80,10 @@ def test_structure(n, seed, p):
             assert np.all(np.diff(idx) == 1), "buckets of a network are contiguous"
             wires = pl.network_wires(net, n)
             V = int(wires.sum())
-            assert sorted(B["var"][idx].tolist()) == list(range(V)), "each variable eliminated once"
+            merged = idx[B["n_sum"][idx] > 1]
+            assert (B["n_sum"][idx] <= 2).all() and (B["var2"][idx] >= 0).sum() == len(merged)
+            assert sorted(B["var"][idx].tolist() + B["var2"][merged].tolist()) == list(range(V)), \
+                "each variable eliminated once"
             roots = idx[B["parent"][idx] < 0]
             assert len(roots) == 1, "one connected network, one scalar result"
             assert B["width"][roots[0]] == 1
@@ -95,19 +98,24 @@ def test_structure(n, seed, p):
                 assert len(kids) == B["n_deps"][b]
                 for k in kids:
                     assert B["parent"][k] == b
+                n_res = B["width"][b] - B["n_sum"][b]  # the result's index bits
+                alls = 0
                 for op in ops:
-                    assert bin(int(op["mask"])).count("1") == op["rank"] - 1
-                    assert int(op["mask"]) >> (B["width"][b] - 1) == 0
+                    assert bin(int(op["mask"])).count("1") + bin(int(op["smask"])).count("1") == op["rank"]
+                    assert int(op["mask"]) >> n_res == 0
+                    assert 1 <= int(op["smask"]) < (1 << B["n_sum"][b])
+                    alls |= int(op["smask"])
                     if op["src"] >= 0:
-                        assert op["rank"] == B["width"][op["src"]] - 1
+                        assert op["rank"] == B["width"][op["src"]] - B["n_sum"][op["src"]]
                         assert B["level"][b] > B["level"][op["src"]]
                     else:
                         assert op["rank"] in (1, 2)
+                assert alls == (1 << B["n_sum"][b]) - 1, "every summed variable is carried"
                 # the union of operand bits is the whole output index
                 allm = 0
                 for op in ops:
                     allm |= int(op["mask"])
-                assert allm == (1 << (B["width"][b] - 1)) - 1
+                assert allm == (1 << n_res) - 1
         # statistics agree with the exported schedule
         assert st["n_buckets"] == B.shape[0]
         assert st["max_width"] == B["width"].max()
@@ -115,7 +123,7 @@ def test_structure(n, seed, p):
         assert st["sum_2w"] == float(np.sum(2.0 ** B["width"]))
         opbytes = sum(float(np.sum(2.0 ** O["rank"][B["op_begin"][b]:B["op_begin"][b] + B["n_ops"][b]]))
                       for b in range(B.shape[0]))
-        outbytes = np.sum(2.0 ** (B["width"] - 1))
+        outbytes = np.sum(2.0 ** (B["width"] - B["n_sum"]))
         assert np.isclose(st["alg_bytes"], 8 * (opbytes + outbytes))
 
 
@@ -428,3 +436,44 @@ def test_adjoint_budget_splits_networks_into_passes():
     with pytest.raises(qtgb.QTError) as ei:
         host_plan(n, edges, p, with_grad=True, adjoint_budget_bytes=1 << 20)
     assert ei.value.code == qtgb.QT_ENOMEM
+
+
+@pytest.mark.parametrize("n,seed,p", [(16, 23, 3), (20, 1020, 4), (30, 1000, 4)])
+def test_merged_eliminations_give_the_same_values(n, seed, p):
+    """Merged eliminations (the default; opts.no_merge turns them off): chains
+    of eliminations merged pairwise (buckets summing two
+    variables) contract, in the numpy evaluator of the exported schedule, to
+    the same network values as the unmerged schedule and the oracle."""
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with host_plan(n, edges, p, merge=True) as pl:
+        Bm, Om = pl.export()
+        stm = pl.stats()
+    with host_plan(n, edges, p, merge=False) as pl:
+        B1, _ = pl.export()
+        st1 = pl.stats()
+    merged = Bm["n_sum"] > 1
+    assert merged.any() and (Bm["n_sum"] <= 2).all()
+    assert len(Bm) == len(B1) - int(merged.sum())
+    assert stm["alg_bytes"] < st1["alg_bytes"]
+    # every operand's index bits: its output bits plus its summed variables
+    for k in np.nonzero(merged)[0]:
+        for t in range(Bm["op_begin"][k], Bm["op_begin"][k] + Bm["n_ops"][k]):
+            assert bin(int(Om["mask"][t])).count("1") + bin(int(Om["smask"][t])).count("1") == Om["rank"][t]
+    if n <= 20:
+        vals = evaluate(Bm, Om, g, b)
+        np.testing.assert_allclose(vals.real, oracle.sv_zz(n, edges, g, b), rtol=0, atol=1e-12)
+        assert np.abs(vals.imag).max() < 1e-12
+
+
+@pytest.mark.parametrize("kw", [dict(with_grad=True), dict(sched="per_bucket")])
+def test_merge_applies_to_persistent_forward_plans_only(kw):
+    """The reverse sweep and the per-bucket kernel sum one variable per bucket:
+    their plans are never merged."""
+    n, seed, p = 18, 5, 4
+    edges = synth.random_regular_graph(n, seed)
+    with host_plan(n, edges, p, merge=True, **kw) as pl:
+        B, _ = pl.export()
+    with host_plan(n, edges, p, merge=True) as pl:
+        Bm, _ = pl.export()
+    assert (B["n_sum"] == 1).all() and (Bm["n_sum"] > 1).any()
