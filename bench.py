@@ -57,6 +57,7 @@ def parse():
                     help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5); "
                          "c3: 64-graph batch; c5: gradients on N=50 p=4")
     ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the plan-time autotuner's line")
     ap.add_argument("--shard", action="store_true",
                     help="with N GPUs: split the N=30 p=4 graph's networks over the ranks (LPT by cost) and "
                          "all-reduce the partial energies every step (strong scaling); default: replicas")
@@ -467,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
         "plan": main["plan"], "check": main["check"],
         "c128": {k: results["c128"][k] for k in ("value", "ms_per_step", "e2e", "roofline", "clocks", "plan", "check")},
     }
-    if world == 1:
+    if world == 1 and not args.no_autotune:
         # the plan-time autotuner on the same workload: what it chooses and the kernel time it gets
         t = time.perf_counter()
         with qtgb.plan(n, edges, p, dtype="c64", autotune=3) as tp:

@@ -304,7 +304,10 @@ static int make_buckets(const Network& net, const std::vector<int>& order, int m
 // index bits: the bucket's own operands move their output bit 0 into the
 // summed mask, the consumer's gate tensors carry the second summed variable.
 // Pairs are taken from the leaves up (kMaxSum = 2), for buckets of at least
-// 2^kMergeMinOut outputs.
+// 2^kMergeMinOut outputs, so that a merged result (more than 2^8 outputs) is
+// never one a fused unit would have taken; the consumer's gate tensors must
+// fit the merged bucket's gate table.
+constexpr int kMergeMinOut = 10;
 static void merge_chains(NetPlan* np) {
     auto& bs = np->buckets;
     const int nb = (int)bs.size();

@@ -40,7 +40,6 @@ constexpr uint8_t kBucketUnitRoot = 4;  // the root (last bucket) of a fused uni
 // consumer's gate tensors (smask 2: they carry s1 but not s0) are folded
 // into the gate table with equal entries for both values of s0.
 constexpr int kMaxSum = 2;          // summed variables per bucket, at most
-constexpr int kMergeMinOut = 12;    // merge only buckets of at least 2^12 outputs
 constexpr int bucket_n_sum(uint8_t flags) { return 1 + ((flags >> 3) & 3); }
 // Fused units: a subtree of small buckets (every output count at most
 // 2^kFuseOutBits, every non-gate operand produced inside the subtree) is one
