@@ -145,13 +145,16 @@ typedef struct {
     int32_t level;     /* 0 for buckets whose operands are all leaves */
     int32_t var;       /* the summed variable, numbered within the network */
     int32_t tile_log2; /* log2 of the outputs per tile of the persistent kernel (a merged bucket's
-                          tiles run over pairs (o, s1), s1 lowest: 2^(tile_log2 - 1) results) */
+                          tiles run over (o, s1), s1 lowest: 2^(tile_log2 - n_sum + 1) results) */
     uint32_t tile_bits;/* the output bits that vary within a tile (popcount = tile_log2): the
                           lowest ones, so tile c holds outputs c * 2^tile_log2 + j */
     uint32_t folded;   /* operands (bit i: the bucket's i-th) folded into the per-tile gate table */
     uint32_t unit_role;/* 0: scheduled on its own; 1: inside a fused unit; 2: the root of a fused unit */
     int32_t n_sum;     /* summed variables (more than 1: merged eliminations); outputs 2^(width - n_sum) */
     int32_t var2;      /* a merged bucket's second summed variable (its consumer's), else -1 */
+    int32_t var3;      /* a third summed variable (the consumer's consumer's), else -1; merges take
+                          two variables per bucket, so -1 */
+    int32_t pad3;
 } qt_bucket_info;
 
 /* One operand of a bucket. With one summed variable (smask = 1) the operand's

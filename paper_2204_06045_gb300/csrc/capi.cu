@@ -826,6 +826,8 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.unit_role = (d.flags & qt::kBucketInUnit) ? 1u : (d.flags & qt::kBucketUnitRoot) ? 2u : 0u;
             o.n_sum = qt::bucket_n_sum(d.flags);
             o.var2 = hp.bucket_var2[b];
+            o.var3 = hp.bucket_var3[b];
+            o.pad3 = 0;
         }
     }
     if (operands) {
@@ -838,10 +840,11 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.smask = hp.operands[i].smask;
             o.mask = hp.operands[i].mask;
         }
-        // a merged bucket's operands carry s1 as bit 0 of their device masks
+        // a merged bucket's operands carry s1 (and s2) in the low bits of their device masks
         for (const qt::DBucket& d : hp.buckets) {
-            if (qt::bucket_n_sum(d.flags) == 1) continue;
-            for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) operands[i].mask >>= 1;
+            const int m = qt::bucket_n_sum(d.flags) - 1;
+            if (m == 0) continue;
+            for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) operands[i].mask >>= m;
         }
     }
     return QT_OK;

@@ -23,6 +23,7 @@ namespace qt {
 namespace {
 
 constexpr int kWarps = kPersistentThreads / 32;
+static_assert(kMaxSum == 2, "the tile epilogues add the two outputs of a lane: two summed variables at most");
 constexpr int kUnroll = 4;  // iterations of 64 outputs in flight per warp
 
 // The (x = 0, x = 1) entries at element e (even) of a tensor. Gate tensors are
@@ -214,7 +215,7 @@ struct RunSlot {
     uint32_t total_foot;  // staged elements per tile
     uint8_t n_out, cb, n_staged, n_leaves;
     uint8_t n_ops;
-    uint8_t merged;       // merged eliminations: each lane's two outputs add into one result
+    uint8_t merged;       // 1: merged eliminations (s0, s1): each lane's two outputs add into one result
     uint32_t bad;         // the plan's footprint exceeds the stage: not computed
     // per-group constants of the unrolled tile loop, for the staged operands
     // and the gate table (at most kFast of them)
@@ -224,6 +225,7 @@ struct RunSlot {
     uint8_t n_hi;                    // folded tensors whose output bit lies above the tile
     uint8_t hi_idx[kMaxFoldLeaves];  // their slots
     uint8_t hi_shift[kMaxFoldLeaves];// position of that bit within the chunk index
+    uint8_t hi_ebit[kMaxFoldLeaves]; // bit of a gate-table entry's index holding the tensor's bit in the tile
     uint32_t unit_begin;             // a fused unit: 1 + its first entry in the unit list (0: none)
     uint32_t unit_count;
 };
@@ -421,7 +423,7 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
         rs.n_staged = B.n_staged;
         rs.n_leaves = B.n_leaves;
         rs.n_ops = B.n_ops;
-        rs.merged = bucket_n_sum(B.flags) > 1;
+        rs.merged = (uint8_t)(bucket_n_sum(B.flags) - 1);
         rs.unit_begin = 0;
         rs.unit_count = 0;
         rs.bad = !fits;
@@ -450,6 +452,10 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             if (rs.lmask[l] & ~low) {
                 rs.hi_idx[nh] = (uint8_t)l;
                 rs.hi_shift[nh] = (uint8_t)(31 - __clz(rs.lmask[l]) - rs.cb);
+                // with x the tensor's bit in the tile is x (entry bit 0); without
+                // x it is one of the output bits in leaf_u (rank <= 2)
+                const uint32_t lb = rs.lmask[l] & low;
+                rs.hi_ebit[nh] = rs.lx[l] ? (uint8_t)0 : (uint8_t)(1 + __popc(rs.leaf_u & (lb - 1u)));
                 ++nh;
             }
         rs.n_hi = nh;
@@ -645,12 +651,13 @@ __device__ void tile_from_smem_generic(const WarpSmem<R>& ws, int sl, int st, ty
             if (i < niter) {
                 const C r0 = cadd(acc[u][0][0], acc[u][0][1]);
                 const C r1 = cadd(acc[u][1][0], acc[u][1][1]);
-                if (rs.n_out == 0)
+                if (rs.n_out == 0) {
                     out[0] = r0;
-                else if (rs.merged)  // outputs (o, s1 = 0, 1) add into result o
-                    out[((uint64_t)o0 >> 1) + ((uint64_t)i << 5) + (uint64_t)lane] = cadd(r0, r1);
-                else
+                } else if (rs.merged == 0) {
                     st_two(out, (uint64_t)o0 + ((uint64_t)i << 6) + ((uint64_t)lane << 1), r0, r1);
+                } else {  // merged: outputs (o, s1 = 0, 1) add into result o
+                    out[((uint64_t)o0 >> 1) + ((uint64_t)i << 5) + (uint64_t)lane] = cadd(r0, r1);
+                }
             }
         }
     }
@@ -694,8 +701,6 @@ __device__ __forceinline__ void stg_one(double2* p, double2 a) {
 // operands in shared memory, every loop fully unrolled. A lane owns outputs
 // 2*lane + {0,1} + 64*i; an operand's pair for such an output sits at the
 // lane's offset plus the steps of the iteration's bits, all fixed per group.
-// In a merged bucket the two outputs are s1 = 0, 1 of result lane + 32*i:
-// the lane adds them.
 template <typename R, int N, int NI>
 __device__ __forceinline__ void tile_fast(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
                                           const RunSlot<R>& rs, typename CT<R>::c* out, int lane) {
@@ -735,10 +740,59 @@ __device__ __forceinline__ void tile_fast(const uint32_t (&sbase)[N], const uint
             }
         }
         const C r0 = cadd(p00, p01), r1 = cadd(p10, p11);
-        if (rs.merged)
-            stg_one(out + (i * 32 + lane), cadd(r0, r1));
-        else
-            stg_two(out + (i * 64 + 2 * lane), r0, r1);
+        if constexpr (sizeof(R) == 4) {
+            if (rs.merged) {  // merged bucket: the lane's outputs are s1 = 0, 1 of result lane + 32*i
+                stg_one(out + (i * 32 + lane), cadd(r0, r1));
+                continue;
+            }
+        }
+        stg_two(out + (i * 64 + 2 * lane), r0, r1);
+    }
+}
+
+// A merged bucket's tile (cb >= 6) in complex128: operands as in tile_fast,
+// but a lane's two outputs are s1 = 0, 1 of one result, which the lane adds
+// (result lane + 32*i). A loop over the iterations rather than unrolled code:
+// FP64-bound, the complex128 kernel gains more from the smaller code than from
+// the unrolled addressing (complex64 keeps the pair sum inside tile_fast,
+// whose unrolled loads it needs).
+template <typename R, int N>
+__device__ __forceinline__ void tile_merged(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
+                                            const RunSlot<R>& rs, typename CT<R>::c* out, int lane) {
+    using C = typename CT<R>::c;
+    constexpr uint32_t PB = 2 * sizeof(C);
+    uint32_t a0[N], second[N], d[N][5];
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+        a0[t] = sbase[t] + PB * rs.loff[t][lane];
+        second[t] = (smask[t] & 1u) ? PB : 0u;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) d[t][k] = PB * rs.dstep[t][k];  // zero above the tile
+    }
+    const C* tag = nullptr;
+    const uint32_t ni = 1u << (rs.cb - 6);
+    for (uint32_t i = 0; i < ni; ++i) {
+        C p00, p01, p10, p11;
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            uint32_t q = a0[t];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) q += ((i >> k) & 1u) ? d[t][k] : 0u;
+            const Pair<C> a = lds_pair(q, tag);
+            const Pair<C> b = lds_pair(q + second[t], tag);
+            if (t == 0) {
+                p00 = a.v0;
+                p01 = a.v1;
+                p10 = b.v0;
+                p11 = b.v1;
+            } else {
+                p00 = cmul(p00, a.v0);
+                p01 = cmul(p01, a.v1);
+                p10 = cmul(p10, b.v0);
+                p11 = cmul(p11, b.v1);
+            }
+        }
+        stg_one(out + (i * 32 + lane), cadd(cadd(p00, p01), cadd(p10, p11)));
     }
 }
 
@@ -757,6 +811,12 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
         smask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
     C* tile_out = out + ((uint64_t)chunk << (rs.cb - rs.merged));
+    if constexpr (sizeof(R) == 8) {
+        if (rs.merged) {
+            tile_merged<R, N>(sbase, smask, rs, tile_out, lane);
+            return;
+        }
+    }
     switch (rs.cb) {
         case 6: tile_fast<R, N, 1>(sbase, smask, rs, tile_out, lane); break;
         case 7: tile_fast<R, N, 2>(sbase, smask, rs, tile_out, lane); break;
@@ -793,10 +853,11 @@ __device__ bool wait_stage(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, u
 // whose bits lie inside the tile give a table over the tile bits that is the
 // same for every tile of a group: each lane keeps its two entries in `tlow`.
 // A tensor with a bit above the tile (one at most: rank <= 2) takes one of two
-// values per tile. With x it depends on x alone within the tile; without x its
-// other bit is output bit 0, which is then in leaf_u, so that entry e sees it
-// as bit 1 of e. The table of a tile is tlow times one of four per-tile
-// factors, picked by e & 3; each lane computes its own.
+// values per tile. Within the tile it depends on one bit of the entry index
+// (hi_ebit): x, or for a tensor without x its output bit in leaf_u (s1 or s2,
+// the lowest output bits, so the entry bit is at most 2). The table of a tile
+// is tlow times those tensors' entries; each lane computes its own factor,
+// the same for both of its entries (e and e + 32).
 template <typename R>
 __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs, uint32_t chunk, bool first,
                                            typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane) {
@@ -827,15 +888,13 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
     for (int h = 0; h < rs.n_hi; ++h) key |= ((chunk >> rs.hi_shift[h]) & 1u) << h;
     if (!first && key == hi_key) return;
     hi_key = key;
-    // this lane's entries e = lane + 32h all have e & 3 = lane & 3
-    const uint32_t x = (uint32_t)lane & 1u, b0 = ((uint32_t)lane >> 1) & 1u;
     C f;
     f.x = (R)1;
     f.y = (R)0;
     for (int h = 0; h < rs.n_hi; ++h) {
         const int l = rs.hi_idx[h];
         const uint32_t y = (key >> h) & 1u;  // the tensor's bit above the tile
-        f = cmul(f, rs.lval[l][2u * y + (rs.lx[l] ? x : b0)]);
+        f = cmul(f, rs.lval[l][2u * y + (((uint32_t)lane >> rs.hi_ebit[h]) & 1u)]);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {

@@ -303,10 +303,11 @@ static int make_buckets(const Network& net, const std::vector<int>& order, int m
 // consumer's. The intermediate result is never written. Operands keep their
 // index bits: the bucket's own operands move their output bit 0 into the
 // summed mask, the consumer's gate tensors carry the second summed variable.
-// Pairs are taken from the leaves up (kMaxSum = 2), for buckets of at least
-// 2^kMergeMinOut outputs, so that a merged result (more than 2^8 outputs) is
-// never one a fused unit would have taken; the consumer's gate tensors must
-// fit the merged bucket's gate table.
+// A merged bucket may go on to absorb its own consumer on the same rule, up
+// to kMaxSum eliminations. Chains are taken from the leaves up, for buckets
+// of at least 2^kMergeMinOut outputs, so that a merged result (more than 2^8
+// outputs) is never one a fused unit would have taken; the consumers' gate
+// tensors must fit the merged bucket's gate table.
 constexpr int kMergeMinOut = 10;
 static void merge_chains(NetPlan* np) {
     auto& bs = np->buckets;
@@ -315,47 +316,53 @@ static void merge_chains(NetPlan* np) {
     std::vector<int> into(nb);  // an absorbed consumer's results now come from this bucket
     for (int b = 0; b < nb; ++b) into[b] = b;
     for (int b = 0; b < nb; ++b) {
-        if (gone[b]) continue;
-        HBucket& B = bs[b];
-        const int p = B.parent;
-        if (p < 0 || B.n_sum >= kMaxSum || B.width - B.n_sum < kMergeMinOut) continue;
-        HBucket& P = bs[p];
-        if (P.n_sum != 1 || P.width != B.width - 1) continue;
-        int nonleaf = 0;
-        bool from_b = false;
-        for (const HOperand& op : P.ops)
-            if (op.src >= 0) {
-                nonleaf++;
-                from_b = op.src == b;
+        // absorb consumers while the chain allows (a merged bucket may absorb its next consumer)
+        while (!gone[b]) {
+            HBucket& B = bs[b];
+            const int p = B.parent;
+            if (p < 0 || B.n_sum >= kMaxSum || B.width - B.n_sum < kMergeMinOut) break;
+            HBucket& P = bs[p];
+            // P's indices are exactly B's outputs
+            if (P.n_sum != 1 || P.width != B.width - B.n_sum) break;
+            int nonleaf = 0;
+            bool from_b = false;
+            for (const HOperand& op : P.ops)
+                if (op.src >= 0) {
+                    nonleaf++;
+                    from_b = op.src == b;
+                }
+            if (nonleaf != 1 || !from_b || B.ops.size() + P.ops.size() - 1 > (size_t)kMaxOps) break;
+            // the consumer's gate tensors go into the merged bucket's gate table,
+            // with the bucket's own tensors of rank <= 2
+            int small = 0;
+            bool all_small = true;
+            for (const HOperand& op : B.ops) small += op.rank <= 2;
+            for (const HOperand& op : P.ops)
+                if (op.src < 0) {
+                    small++;
+                    all_small = all_small && op.rank <= 2;
+                }
+            if (!all_small || small > kMaxFoldLeaves) break;
+            const uint32_t sbit = 1u << B.n_sum;
+            for (HOperand& op : B.ops) {
+                if (op.mask & 1u) op.smask |= sbit;
+                op.mask >>= 1;
             }
-        if (nonleaf != 1 || !from_b || B.ops.size() + P.ops.size() - 1 > (size_t)kMaxOps) continue;
-        // the consumer's gate tensors go into the merged bucket's gate table,
-        // with the bucket's own tensors of rank <= 2
-        int small = 0;
-        bool all_small = true;
-        for (const HOperand& op : B.ops) small += op.rank <= 2;
-        for (const HOperand& op : P.ops)
-            if (op.src < 0) {
-                small++;
-                all_small = all_small && op.rank <= 2;
+            for (const HOperand& op : P.ops) {
+                if (op.src >= 0) continue;
+                HOperand q = op;
+                q.smask = sbit;  // the consumer's summed variable; its output bits are the merged output's
+                B.ops.push_back(q);
             }
-        if (!all_small || small > kMaxFoldLeaves) continue;
-        const uint32_t sbit = 1u << B.n_sum;
-        for (HOperand& op : B.ops) {
-            if (op.mask & 1u) op.smask |= sbit;
-            op.mask >>= 1;
+            (B.n_sum == 1 ? B.var2 : B.var3) = P.var;
+            B.n_sum++;
+            B.parent = P.parent;
+            gone[p] = 1;
+            into[p] = b;
+            if (B.parent >= 0)  // P's consumer now reads B's result
+                for (HOperand& op : bs[B.parent].ops)
+                    if (op.src == p) op.src = b;
         }
-        for (const HOperand& op : P.ops) {
-            if (op.src >= 0) continue;
-            HOperand q = op;
-            q.smask = sbit;  // the consumer's summed variable; its output bits are the merged output's
-            B.ops.push_back(q);
-        }
-        B.n_sum++;
-        B.var2 = P.var;
-        B.parent = P.parent;
-        gone[p] = 1;
-        into[p] = b;
     }
     // renumber the remaining buckets (elimination order kept)
     std::vector<int> id(nb, -1);
@@ -396,12 +403,15 @@ static bool foldable(const HOperand& op) { return op.rank <= 2; }
 // most kLeafBits; otherwise they are staged like the others.
 // Takes the device view of a bucket (device_view): operands with smask 0
 // carry no summed variable and must be folded.
-static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_elems, int* cb_out, bool* fold_out) {
+// A merged bucket's tiles hold whole groups of its summed outputs (min_cb
+// bits: n_sum - 1).
+static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_elems, int min_cb, int* cb_out,
+                      bool* fold_out) {
     (void)net;
     const int n_out = B.width - B.n_sum;
     bool must_fold = false;
     for (const HOperand& op : B.ops) must_fold = must_fold || op.smask == 0;
-    for (int cb = std::min(n_out, cap); cb >= 0; --cb) {
+    for (int cb = std::max(std::min(n_out, cap), min_cb); cb >= min_cb; --cb) {
         const uint32_t low = cb >= 32 ? 0xffffffffu : ((1u << cb) - 1u);
         uint32_t U = 0;
         int nleaf = 0;
@@ -429,16 +439,18 @@ static void pick_tile(const HBucket& B, const Network& net, int cap, int stage_e
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
-// A bucket as the device contracts it. A merged bucket (summing s0, then s1)
-// becomes the bucket of s0 alone with outputs (o, s1), s1 as bit 0: operand
-// masks gain bit 0 where they carry s1, and smask keeps only s0 (0 for the
-// consumer's gate tensors). Other buckets are unchanged.
+// A bucket as the device contracts it. A merged bucket (summing s0, then s1,
+// then s2) becomes the bucket of s0 alone with outputs (o, s1, s2), s1 as bit
+// 0 and s2 as bit 1: operand masks gain those bits where they carry s1 or s2,
+// and smask keeps only s0 (0 for the consumers' gate tensors). Other buckets
+// are unchanged.
 static HBucket device_view(const HBucket& B) {
     HBucket V = B;
     if (B.n_sum == 1) return V;
+    const int m = B.n_sum - 1;
     V.n_sum = 1;
     for (HOperand& op : V.ops) {
-        op.mask = (op.mask << 1) | ((op.smask >> 1) & 1u);
+        op.mask = (op.mask << m) | ((op.smask >> 1) & ((1u << m) - 1u));
         op.smask &= 1u;
     }
     return V;
@@ -780,6 +792,7 @@ int layout_plan(HostPlan* hp) {
     hp->bucket_level.clear();
     hp->bucket_var.clear();
     hp->bucket_var2.clear();
+    hp->bucket_var3.clear();
     hp->root_bucket.clear();
     hp->sim_seconds = 0;
 
@@ -816,7 +829,7 @@ int layout_plan(HostPlan* hp) {
             bool fold = false;
             const int tcap = cfg.tile_cap[width_class(d.n_out)];
             pick_tile(V, net, tcap > 0 ? tcap : cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
-                      cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, &cb, &fold);
+                      cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, B.n_sum - 1, &cb, &fold);
             d.chunk_bits = (uint8_t)cb;
             d.flags = (uint8_t)((fold ? kBucketFoldLeaves : 0) | ((B.n_sum - 1) << 3));
             {
@@ -888,23 +901,23 @@ int layout_plan(HostPlan* hp) {
             hp->bucket_level.push_back(B.level);
             hp->bucket_var.push_back(B.var);
             hp->bucket_var2.push_back(B.var2);
+            hp->bucket_var3.push_back(B.var3);
             if (B.parent < 0) hp->root_bucket.push_back(base + (uint32_t)lb);
             hp->max_width = std::max(hp->max_width, B.width);
             hp->n_levels = std::max(hp->n_levels, B.level + 1);
             hp->width_hist[B.width]++;
             hp->sum_2w += std::ldexp(1.0, B.width);
             hp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - B.n_sum));
-            if (B.n_sum == 2) {
-                // factored as the device computes it: the bucket of s0 (its
-                // products and x-sums), then the consumer's gate products and the
-                // s1-sum, as the two unmerged buckets would
-                double n0 = 0, n1 = 0;
-                for (const HOperand& op : B.ops) (op.smask & 1u ? n0 : n1) += 1;
-                hp->flops += std::ldexp(1.0, B.width) * 6.0 * (n0 - 1) + std::ldexp(1.0, B.width - 1) * 2.0 +
-                             std::ldexp(1.0, B.width - 1) * 6.0 * n1 + std::ldexp(1.0, B.width - 2) * 2.0;
-            } else {
-                hp->flops += std::ldexp(1.0, B.width) * 6.0 * (double)(B.ops.size() - 1) +
-                             std::ldexp(1.0, B.width - 1) * 2.0;
+            {
+                // a merged bucket counts the flops of its unmerged buckets: the
+                // bucket of s0 (products of its operands, sums over s0), then each
+                // consumer's gate products and its sum; operand t belongs to the
+                // bucket of its earliest summed variable
+                double n_k[4] = {0, 0, 0, 0};
+                for (const HOperand& op : B.ops) n_k[__builtin_ctz(op.smask)] += 1;
+                for (int k = 0; k < B.n_sum; ++k)
+                    hp->flops += std::ldexp(1.0, B.width - k) * 6.0 * (n_k[k] - (k == 0 ? 1 : 0)) +
+                                 std::ldexp(1.0, B.width - k - 1) * 2.0;
             }
         }
         hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());

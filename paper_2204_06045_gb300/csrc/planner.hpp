@@ -41,6 +41,7 @@ struct HBucket {
     int level;
     int n_sum = 1;  // summed variables (more than 1: merged eliminations)
     int var2 = -1;  // merged: the second summed variable (the absorbed consumer's)
+    int var3 = -1;  // merged: the third (the consumer's consumer's)
     std::vector<HOperand> ops;
 };
 
@@ -93,6 +94,7 @@ struct HostPlan {
     std::vector<int32_t> bucket_level;
     std::vector<int32_t> bucket_var;
     std::vector<int32_t> bucket_var2;
+    std::vector<int32_t> bucket_var3;
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
     std::vector<URec> unit_prog;        // fused units' programs, unit by unit (padded by kURecWindow records)
     uint64_t n_units = 0;

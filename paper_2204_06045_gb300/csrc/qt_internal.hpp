@@ -37,8 +37,9 @@ constexpr uint8_t kBucketUnitRoot = 4;  // the root (last bucket) of a fused uni
 // summing s0 and then s1 is laid out as the bucket of s0 alone, whose outputs
 // are (o, s1) with s1 as bit 0: its tiles contract s0 as usual, and the
 // epilogue adds the two outputs of each lane (s1 = 0, 1) into result o. The
-// consumer's gate tensors (smask 2: they carry s1 but not s0) are folded
-// into the gate table with equal entries for both values of s0.
+// consumer's gate tensors (no s0) are folded into the gate table with equal
+// entries for both values of s0. The planner's chains and device view take
+// more summed variables (s2 as device bit 1); the kernel's epilogues take two.
 constexpr int kMaxSum = 2;          // summed variables per bucket, at most
 constexpr int bucket_n_sum(uint8_t flags) { return 1 + ((flags >> 3) & 3); }
 // Fused units: a subtree of small buckets (every output count at most

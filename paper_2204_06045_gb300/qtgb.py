@@ -59,7 +59,8 @@ class PlanStats(ctypes.Structure):
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
                          ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32),
                          ("tile_log2", np.int32), ("tile_bits", np.uint32), ("folded", np.uint32),
-                         ("unit_role", np.uint32), ("n_sum", np.int32), ("var2", np.int32)])
+                         ("unit_role", np.uint32), ("n_sum", np.int32), ("var2", np.int32),
+                         ("var3", np.int32), ("pad3", np.int32)])
 GROUP_DTYPE = np.dtype([("bucket", np.int32), ("first_tile", np.int32), ("n_tiles", np.int32),
                         ("unit_buckets", np.int32)])
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),

@@ -4,7 +4,9 @@ A bucket whose consumer only extends it by its own summed variable is merged
 with that consumer: one bucket sums two variables (s0, then s1) and the
 intermediate result is never written. The persistent kernel contracts it as
 the bucket of s0 with outputs (o, s1), the consumer's gate tensors folded into
-its gate table, and adds each lane's two outputs (s1 = 0, 1) into result o.
+its gate table, and adds each lane's two outputs (s1 = 0, 1) into result o
+(inside the unrolled tile loop for complex64, in a compact loop of its own for
+complex128).
 These tests run merged plans against the state vector, the stored goldens and
 the oracle's own bucket elimination, with the tolerances of the other GPU
 parity tests (1e-10 complex128, 1e-5 complex64 per edge, as in
@@ -64,10 +66,10 @@ def test_merged_small_graphs_match_state_vector(dtype, order, n, seed, p):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("cap", [3, 5, 6, 7, 11])
+@pytest.mark.parametrize("cap", [2, 3, 5, 6, 7, 11])
 def test_merged_tile_shapes(dtype, cap):
-    """Tile caps below 6 send merged tiles through the generic tile loop (a lane
-    per result), 6..11 through the unrolled one (1 to 32 iterations of 64
+    """Tile caps below 6 send merged tiles through the generic tile loop (2 to
+    32 active lanes), 6..11 through the unrolled one (1 to 32 iterations of 64
     outputs); the gate table then sees the consumer's gates inside and above
     the tile."""
     n, seed, p = 18, 5, 4
