@@ -287,13 +287,14 @@ def wide_buckets(peak, torch):
     of the edges whose plain greedy order reaches a maximum bucket width of
     26..28 (chosen on a host-only plan of every edge). The per-bucket and
     per-network bandwidths are those of plain buckets (one summed variable
-    each, merging off): a merged bucket moves fewer bytes for the same work.
-    The merged plans' times for the same networks are reported beside them."""
+    each, no merging, no slicing): a merged bucket moves fewer bytes for the
+    same work. The times of the same networks with merged eliminations, and
+    with the default plan (merged and sliced), are reported beside them."""
     from paper_2204_06045_gb300 import qtgb, synth
     n, p, seed = 1000, 5, 1000
     edges = synth.random_regular_graph(n, seed)
     g, b = synth.angles(p, seed)
-    with qtgb.plan(n, edges, p, host_only=True) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
         B, _ = hp.export()
     mw = np.zeros(edges.shape[0], dtype=np.int64)
     np.maximum.at(mw, B["network"], B["width"])
@@ -303,7 +304,7 @@ def wide_buckets(peak, torch):
            "edges": sel.tolist()}
     ref = golden_c4()
     for dtype in ("c64", "c128"):
-        with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, merge=False) as pl:
+        with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, merge=False, slice_width=-1) as pl:
             zz, _ = pl.energy(g, b)  # also leaves real data in every operand
             if ref is not None:
                 want = np.array([ref[int(e)] for e in sel])
@@ -327,10 +328,11 @@ def wide_buckets(peak, torch):
         # single-edge contraction: each network alone in its own plan, every bucket of it in one
         # persistent launch; algorithmic bytes of the network over the kernel's time
         tot = {}
-        for merge in (False, True):
+        variants = {"plain": dict(merge=False, slice_width=-1), "merged": dict(slice_width=-1), "default": {}}
+        for key, kw in variants.items():
             nb = nm = 0.0
             for e in sel:
-                with qtgb.plan_subset(n, edges, p, [int(e)], dtype=dtype, merge=merge) as one:
+                with qtgb.plan_subset(n, edges, p, [int(e)], dtype=dtype, **kw) as one:
                     for _ in range(2):
                         one.energy(g, b)
                     one.kernel_time(reset=True)
@@ -339,15 +341,19 @@ def wide_buckets(peak, torch):
                     ms, _ = one.kernel_time(reset=True)
                     nb += one.stats()["alg_bytes"]
                     nm += ms
-            tot[merge] = (nb, nm)
-        nb, nm = tot[False]
+            tot[key] = (nb, nm)
+        nb, nm = tot["plain"]
         out[dtype]["networks"] = {"count": int(sel.size), "agg_gbs": nb / nm / 1e6, "frac_of_peak": nb / nm / 1e6 / peak,
                                   "bytes": nb, "ms": nm,
                                   "note": "each network alone, plain buckets: all its buckets in one persistent launch "
                                           "(mean of 3 after 2)"}
-        mb, mm = tot[True]
+        mb, mm = tot["merged"]
         out[dtype]["networks_merged"] = {"ms": mm, "bytes": mb, "agg_gbs": mb / mm / 1e6, "speedup_vs_plain": nm / mm,
-                                         "note": "the same networks with merged eliminations (the default plan)"}
+                                         "note": "the same networks with merged eliminations"}
+        db, dm = tot["default"]
+        out[dtype]["networks_default"] = {"ms": dm, "bytes": db, "agg_gbs": db / dm / 1e6, "speedup_vs_plain": nm / dm,
+                                          "note": "the same networks with the default plan: merged eliminations and "
+                                                  "index slicing"}
     return out
 
 
@@ -446,6 +452,7 @@ def run_ours(args, rank, world, local_rank):
                                  ncu_traffic(tag)),
             "clocks": clk.summary(),
             "plan": {"buckets": st["n_buckets"], "merged_buckets": int((pl.export()[0]["n_sum"] > 1).sum()),
+                     "slices": st["n_slices"], "slice_bits": st["slice_bits"], "fused_units": st["n_units"],
                      "max_width": st["max_width"], "sum_2w": st["sum_2w"],
                      "tasks": st["n_tasks"], "plan_seconds": st["plan_seconds"]},
             "check": dict(energy=float(E.item()), **accuracy(zz.cpu().numpy(), float(E.item()), ref_zz, ref_E)),
@@ -462,7 +469,7 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": main["value"] * PAPER_SECONDS_PER_EVAL, "dtype": "c64", "data": "synthetic",
         "config": config_dict("complex64 with FP32 arithmetic, persistent dependency-queue kernel, "
-                              "merged eliminations"),
+                              "merged eliminations, index slicing to width 22 (complex128: 20)"),
         "e2e": main["e2e"], "roofline": main["roofline"], "clocks": main["clocks"],
         "gpu_launches": 3 * args.steps,
         "plan": main["plan"], "check": main["check"],

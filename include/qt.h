@@ -94,7 +94,7 @@ typedef struct {
                               the device over `autotune` evaluations; the choice is in qt_plan_stats */
     int8_t tile_cap[8];    /* most tile bits (log2 outputs per tile, 1..11) per width class, 0: default
                               (chunk_log2, else 9); the first 5 entries are used */
-    int32_t no_merge;      /* nonzero: no merged eliminations. By default a bucket of 2^12 outputs or
+    int32_t no_merge;      /* nonzero: no merged eliminations. By default a bucket of 2^10 outputs or
                               more and the consumer that only extends it become one bucket summing
                               both variables, the intermediate never written (persistent-schedule
                               plans without gradients; the others never merge) */
@@ -102,6 +102,13 @@ typedef struct {
                               cotangents; a plan that needs more runs its networks in passes that fit
                               (each pass saves its own results; energies and gradients are summed over
                               passes); a network that alone exceeds it gives QT_ENOMEM. 0: no budget */
+    int32_t slice_width;   /* index slicing: a network whose greedy order is wider than this target
+                              gets variables fixed, one at a time, until it is not (or max_slice_bits
+                              are fixed); its value is the sum over the 2^s assignments of the fixed
+                              variables of networks without them, all contracted in the same launch.
+                              2..31: the target; 0: the default target (22 complex64, 20 complex128);
+                              -1: no slicing. Forward plans only (gradient plans are never sliced) */
+    int32_t max_slice_bits;/* most variables fixed per network (1..16); 0: 8 */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -132,6 +139,8 @@ typedef struct {
     double tune_seconds;    /* host time spent autotuning (0 without opts.autotune) */
     int32_t tune_candidates;/* configurations the autotuner laid out and timed */
     int32_t n_passes;       /* gradient plans over opts.adjoint_budget_bytes: passes over the networks */
+    int32_t slice_bits;     /* most variables fixed in any one network (opts.slice_width) */
+    int64_t n_slices;       /* slices over all networks (1 per network without slicing) */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */
@@ -154,7 +163,8 @@ typedef struct {
     int32_t var2;      /* a merged bucket's second summed variable (its consumer's), else -1 */
     int32_t var3;      /* a third summed variable (the consumer's consumer's), else -1; merges take
                           two variables per bucket, so -1 */
-    int32_t pad3;
+    int32_t slice;     /* the slice of its network the bucket belongs to (0 without slicing); in a
+                          sliced network, variables are numbered after removing the fixed ones */
 } qt_bucket_info;
 
 /* One operand of a bucket. With one summed variable (smask = 1) the operand's
@@ -167,7 +177,28 @@ typedef struct {
     int32_t rank;      /* index bits of the operand (summed bits included) */
     uint32_t smask;    /* summed variables it carries; its entry for output o and summed values s is
                           2^popc(smask) * pext(o, mask) + pext(s, smask) */
+    int32_t leaf_sub;  /* leaves: element offset into the gate tensor's entries: 2 * (fixed value)
+                          for a gate with one variable fixed by slicing (entries for the free
+                          variable x at leaf_sub + x), else 0 */
+    int32_t pad;
 } qt_operand_info;
+
+/* A gate tensor of a sliced network whose variables are all fixed: in slice
+ * `slice` of `network` the network's value is multiplied by entry `entry` of
+ * the gate (QT_LEAF_* kind, layer as in qt_operand_info). */
+typedef struct {
+    int32_t network;
+    int32_t slice;
+    int32_t leaf_kind;
+    int32_t leaf_layer;
+    int32_t entry;
+    int32_t pad;
+} qt_fixed_info;
+
+/* The fixed gate entries of every slice (host-side inspection). `out` holds
+ * at least *n_out entries on entry, or is NULL to ask for the count; *n_out
+ * receives the count. */
+int qt_plan_export_fixed(qt_plan_t plan, qt_fixed_info *out, int64_t *n_out);
 
 #define QT_LEAF_PLUS 0   /* [1, 1]/sqrt 2: |+> and <+| */
 #define QT_LEAF_ZOBS 1   /* [1, -1]: the observable Z on an edge endpoint */

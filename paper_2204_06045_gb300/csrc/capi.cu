@@ -179,7 +179,8 @@ int upload(qt_plan_t P) {
         {nullptr, 0, 0},                                       {hp.runs.data(), bytes_of(hp.runs), 0},
         {nullptr, 0, 0},                                       {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
-        {hp.unit_prog.data(), bytes_of(hp.unit_prog), 0},
+        {hp.unit_prog.data(), bytes_of(hp.unit_prog), 0},     {hp.net_first_factor.data(), bytes_of(hp.net_first_factor), 0},
+        {hp.factor.data(), bytes_of(hp.factor), 0},
     };
     size_t total = 0;
     for (auto& pc : pieces) {
@@ -232,6 +233,8 @@ int upload(qt_plan_t P) {
     de.net_first_root = reinterpret_cast<const uint32_t*>(base + pieces[5].off);
     de.root_bucket = reinterpret_cast<const uint32_t*>(base + pieces[6].off);
     de.graph_first_net = reinterpret_cast<const int32_t*>(base + pieces[7].off);
+    de.net_first_factor = reinterpret_cast<const uint32_t*>(base + pieces[9].off);
+    de.factor = reinterpret_cast<const uint64_t*>(base + pieces[10].off);
     de.n_graphs = n_graphs;
     de.arena = P->d_arena;
     de.zz = P->d_out;
@@ -653,6 +656,12 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     // the reverse sweep, the per-bucket kernel and fused units sum one
     // variable per bucket: merging is a forward, persistent-schedule option
     cfg.merge = o.no_merge == 0 && o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad;
+    if (o.slice_width < -1 || o.slice_width == 1 || o.slice_width > 31) return QT_EINVAL;
+    if (o.max_slice_bits < 0 || o.max_slice_bits > 16) return QT_EINVAL;
+    // default target widths: measured best on the N=30 p=4 and N=1000 p=5 networks
+    const int sw = o.slice_width == 0 ? (o.dtype == QT_C128 ? 20 : 22) : std::max(0, o.slice_width);
+    cfg.slice_width = cfg.with_grad ? 0 : sw;  // the reverse sweep takes unsliced networks
+    cfg.max_slice_bits = o.max_slice_bits ? o.max_slice_bits : 8;
     for (int c = 0; c < qt::kWidthClasses; ++c) {
         if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
         cfg.tile_cap[c] = o.tile_cap[c];
@@ -800,6 +809,9 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->tune_seconds = P->tune_seconds;
     out->tune_candidates = P->tune_candidates;
     out->n_passes = P->parts.empty() ? 1 : (int32_t)P->parts.size();
+    out->slice_bits = 0;
+    for (const qt::Network& net : hp.nets) out->slice_bits = std::max(out->slice_bits, (int32_t)net.slice_bits);
+    out->n_slices = (int64_t)hp.n_slices;
     return QT_OK;
 }
 
@@ -827,7 +839,7 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.n_sum = qt::bucket_n_sum(d.flags);
             o.var2 = hp.bucket_var2[b];
             o.var3 = hp.bucket_var3[b];
-            o.pad3 = 0;
+            o.slice = hp.bucket_slice[b];
         }
     }
     if (operands) {
@@ -839,6 +851,8 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             o.rank = hp.op_rank[i];
             o.smask = hp.operands[i].smask;
             o.mask = hp.operands[i].mask;
+            o.leaf_sub = hp.op_leaf_sub[i];
+            o.pad = 0;
         }
         // a merged bucket's operands carry s1 (and s2) in the low bits of their device masks
         for (const qt::DBucket& d : hp.buckets) {
@@ -847,6 +861,30 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) operands[i].mask >>= m;
         }
     }
+    return QT_OK;
+}
+
+int qt_plan_export_fixed(qt_plan_t P, qt_fixed_info* out, int64_t* n_out) {
+    if (!P || !n_out) return QT_EINVAL;
+    const qt::HostPlan& hp = P->hp;
+    int64_t k = 0;
+    for (size_t i = 0; i < hp.nets.size(); ++i) {
+        const qt::Network& net = hp.nets[i];
+        for (uint32_t sl = 0; sl < (1u << net.slice_bits); ++sl)
+            for (const qt::FixedLeaf& fl : net.fixed) {
+                if (out) {
+                    qt_fixed_info& f = out[k];
+                    f.network = (int32_t)i;
+                    f.slice = (int32_t)sl;
+                    f.leaf_kind = fl.kind;
+                    f.leaf_layer = fl.layer;
+                    f.entry = (int32_t)(((sl >> fl.f[0]) & 1u) + (fl.rank == 2 ? 2u * ((sl >> fl.f[1]) & 1u) : 0u));
+                    f.pad = 0;
+                }
+                ++k;
+            }
+    }
+    *n_out = k;
     return QT_OK;
 }
 
@@ -1113,7 +1151,7 @@ size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Byte offsets of every piece inside the scratch array.
 struct ScratchLayout {
-    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net, unit_list;
+    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net, unit_list, net_first_factor, factor;
     size_t counters, counters_bytes, ctl_bytes, cnt_bytes;
     size_t angles, out, arena, total;
 };
@@ -1134,6 +1172,8 @@ ScratchLayout scratch_layout(const qt::HostPlan& hp, size_t esize) {
     L.root_bucket = take(hp.root_bucket.size() * sizeof(uint32_t));
     L.graph_first_net = take(hp.graph_first_net.size() * sizeof(int32_t));
     L.unit_list = take(hp.unit_prog.size() * sizeof(qt::URec));
+    L.net_first_factor = take(hp.net_first_factor.size() * sizeof(uint32_t));
+    L.factor = take(hp.factor.size() * sizeof(uint64_t));
     L.ctl_bytes = 256;
     L.cnt_bytes = pad256(2 * nb * sizeof(uint32_t));
     L.counters_bytes = L.ctl_bytes + L.cnt_bytes + (size_t)(hp.n_groups - hp.runs.size()) * sizeof(qt::DSlot);
@@ -1221,6 +1261,10 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     if (!hp.unit_prog.empty())
         QT_CUDA(cudaMemcpyAsync(base + L.unit_list, hp.unit_prog.data(), bytes_of(hp.unit_prog),
                                 cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemcpyAsync(base + L.net_first_factor, hp.net_first_factor.data(), bytes_of(hp.net_first_factor),
+                            cudaMemcpyHostToDevice, s));
+    if (!hp.factor.empty())
+        QT_CUDA(cudaMemcpyAsync(base + L.factor, hp.factor.data(), bytes_of(hp.factor), cudaMemcpyHostToDevice, s));
     // the array keeps the previous call's contents: counters and the queue start at zero
     QT_CUDA(cudaMemsetAsync(base + L.counters, 0, L.counters_bytes, s));
     double* d_angles = reinterpret_cast<double*>(base + L.angles);
@@ -1249,6 +1293,8 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     de.net_first_root = reinterpret_cast<const uint32_t*>(base + L.net_first_root);
     de.root_bucket = reinterpret_cast<const uint32_t*>(base + L.root_bucket);
     de.graph_first_net = reinterpret_cast<const int32_t*>(base + L.graph_first_net);
+    de.net_first_factor = reinterpret_cast<const uint32_t*>(base + L.net_first_factor);
+    de.factor = reinterpret_cast<const uint64_t*>(base + L.factor);
     de.n_graphs = G;
     de.arena = dp.arena;
     double* d_out = reinterpret_cast<double*>(base + L.out);

@@ -1275,16 +1275,26 @@ __global__ void k_epilogue(DevEpilogue de) {
     const int g = blockIdx.x;
     const int first = de.graph_first_net[g], last = de.graph_first_net[g + 1];
     for (int net = first + threadIdx.x; net < last; net += blockDim.x) {
-        double vr = 1.0, vi = 0.0;
-        for (uint32_t r = de.net_first_root[net]; r < de.net_first_root[net + 1]; ++r) {
-            const C v = arena[de.buckets[de.root_bucket[r]].out_off];
+        // the network's value: over its slices (one without slicing), the
+        // product of the slice's root results and fixed gate entries, summed
+        double sr = 0.0, si = 0.0, vr = 1.0, vi = 0.0;
+        const uint32_t f0 = de.net_first_factor[net], f1 = de.net_first_factor[net + 1];
+        for (uint32_t f = f0; f < f1; ++f) {
+            const uint64_t w = de.factor[f];
+            if ((w & kFirstFactor) && f != f0) {
+                sr += vr;
+                si += vi;
+                vr = 1.0;
+                vi = 0.0;
+            }
+            const C v = arena[w & ~kFirstFactor];
             const double xr = (double)v.x, xi = (double)v.y;
             const double nr = vr * xr - vi * xi, ni = vr * xi + vi * xr;
             vr = nr;
             vi = ni;
         }
-        de.zz[net] = vr;
-        de.zz_imag[net] = vi;
+        de.zz[net] = sr + vr;
+        de.zz_imag[net] = si + vi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -50,6 +50,8 @@ struct DevEpilogue {
     const uint32_t* net_first_root;  // n_nets + 1
     const uint32_t* root_bucket;
     const int32_t* graph_first_net;  // n_graphs + 1
+    const uint32_t* net_first_factor;  // n_nets + 1
+    const uint64_t* factor;  // arena element offsets; kFirstFactor marks the first factor of each slice
     int32_t n_graphs;
     const void* arena;
     double* zz;        // n_nets

@@ -206,6 +206,124 @@ static void order_min_fill(const Network& net, bool randomized, uint64_t seed, s
 }
 
 // ---------------------------------------------------------------------------
+// Index slicing. A network's value is a sum over every assignment of its
+// variables (§II-B contraction), so fixing s of them splits it into 2^s
+// networks of the remaining variables whose values add up to it, each with
+// its own, possibly much narrower, buckets: the memory and the work of a
+// bucket grow as 2^width (§II-B). A gate tensor left with one free variable
+// becomes a rank-1 tensor: the gates here (ZZ, the mixer and their
+// conjugates) are symmetric in their two variables, so its entries for the
+// free variable x sit at x + 2 * (fixed value) in the gate's table. A gate
+// whose variables are all fixed is a scalar per slice.
+// Choice of variables: while the min-fill width exceeds the target, among the
+// variables of the widest bucket (the kSliceCandidates of highest degree),
+// fix the one whose removal gives the narrowest order (ties: the smaller sum
+// of 2^width).
+// ---------------------------------------------------------------------------
+constexpr int kSliceCandidates = 12;
+
+// Fix variable v of the network (the next slice bit) and renumber the others.
+static void fix_variable(Network* net, int v, int orig_id) {
+    const int k = (int)net->fixed_vars.size();
+    net->fixed_vars.push_back(orig_id);
+    std::vector<Leaf> kept;
+    kept.reserve(net->leaves.size());
+    for (const Leaf& L : net->leaves) {
+        const bool has = L.v[0] == v || (L.rank == 2 && L.v[1] == v);
+        if (!has) {
+            kept.push_back(L);
+        } else if (L.rank == 1) {
+            // every variable fixed: a scalar per slice
+            if (L.fix >= 0)
+                net->fixed.push_back(FixedLeaf{L.kind, L.layer, 2, {k, L.fix}});
+            else
+                net->fixed.push_back(FixedLeaf{L.kind, L.layer, 1, {k, -1}});
+        } else {
+            Leaf R = L;
+            R.rank = 1;
+            R.v[0] = L.v[0] == v ? L.v[1] : L.v[0];
+            R.v[1] = -1;
+            R.fix = k;
+            kept.push_back(R);
+        }
+    }
+    for (Leaf& L : kept)
+        for (int i = 0; i < L.rank; ++i)
+            if (L.v[i] > v) L.v[i]--;
+    net->leaves = std::move(kept);
+    net->nvars--;
+    net->slice_bits = k + 1;
+}
+
+// Variables of the widest bucket of an elimination order, by degree in the
+// interaction graph (highest first).
+static std::vector<int> widest_bucket(const Network& net, const std::vector<int>& order) {
+    const int V = net.nvars, W = (V + 63) / 64;
+    std::vector<uint64_t> adj((size_t)V * W, 0);
+    auto row = [&](int v) { return &adj[(size_t)v * W]; };
+    std::vector<int> deg(V, 0);
+    for (auto& L : net.leaves)
+        if (L.rank == 2 && L.v[0] != L.v[1]) {
+            row(L.v[0])[L.v[1] >> 6] |= 1ull << (L.v[1] & 63);
+            row(L.v[1])[L.v[0] >> 6] |= 1ull << (L.v[0] & 63);
+        }
+    for (int v = 0; v < V; ++v)
+        for (int w = 0; w < W; ++w) deg[v] += popc64(row(v)[w]);
+    std::vector<int> best;
+    for (int v : order) {
+        std::vector<int> nb;
+        std::vector<uint64_t> nv(row(v), row(v) + W);
+        for (int w = 0; w < W; ++w)
+            for (uint64_t bits = nv[w]; bits; bits &= bits - 1) nb.push_back((w << 6) | __builtin_ctzll(bits));
+        if (nb.size() + 1 > best.size()) {
+            best = nb;
+            best.push_back(v);
+        }
+        for (int a : nb) {
+            uint64_t* ra = row(a);
+            for (int u = 0; u < W; ++u) ra[u] |= nv[u];
+            ra[a >> 6] &= ~(1ull << (a & 63));
+            ra[v >> 6] &= ~(1ull << (v & 63));
+        }
+        std::fill(row(v), row(v) + W, 0ull);
+    }
+    std::stable_sort(best.begin(), best.end(), [&](int a, int b) { return deg[a] > deg[b]; });
+    return best;
+}
+
+static void slice_network(Network* net, int target, int max_bits) {
+    std::vector<int> orig(net->nvars);
+    for (int i = 0; i < net->nvars; ++i) orig[i] = i;
+    std::vector<int> ord;
+    double cost = 0;
+    int w = 0;
+    order_min_fill(*net, false, 0, &ord, &cost, &w);
+    while (w > target && net->slice_bits < max_bits && net->nvars > 1) {
+        std::vector<int> cand = widest_bucket(*net, ord);
+        if ((int)cand.size() > kSliceCandidates) cand.resize(kSliceCandidates);
+        int best = -1, best_w = 1 << 30;
+        double best_c = 0;
+        for (int c : cand) {
+            Network t = *net;
+            fix_variable(&t, c, orig[c]);
+            std::vector<int> o2;
+            double c2 = 0;
+            int w2 = 0;
+            order_min_fill(t, false, 0, &o2, &c2, &w2);
+            if (w2 < best_w || (w2 == best_w && c2 < best_c)) {
+                best = c;
+                best_w = w2;
+                best_c = c2;
+            }
+        }
+        if (best < 0) break;
+        fix_variable(net, best, orig[best]);
+        orig.erase(orig.begin() + best);
+        order_min_fill(*net, false, 0, &ord, &cost, &w);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Bucket schedule for one order (§II-B). Every tensor goes to the bucket of
 // its earliest variable. Bucket v multiplies its tensors and sums v out; the
 // result's variables are the rest of the bucket's union, kept in rank order,
@@ -743,6 +861,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             net.graph = g;
             net.edge = graphs[g].edge_of((size_t)(i - hp->graph_first_net[g]));
             build_network(graphs[g], cfg.p, net.edge, &net);
+            if (cfg.slice_width > 0) slice_network(&net, cfg.slice_width, cfg.max_slice_bits);
             std::vector<int> best_order, ord;
             double best_cost = 0, c = 0;
             int best_w = 0, w = 0;
@@ -814,112 +933,141 @@ int layout_plan(HostPlan* hp) {
     hp->n_levels = 0;
     hp->sum_2w = hp->alg_bytes = hp->flops = 0;
     std::fill(hp->width_hist, hp->width_hist + 64, 0);
+    hp->bucket_slice.clear();
+    hp->op_leaf_sub.clear();
+    hp->net_first_factor.assign(1, 0);
+    hp->factor.clear();
+    hp->n_slices = 0;
     for (int i = 0; i < n_nets; ++i) {
         const NetPlan& np = hp->nplans[i];
         const Network& net = hp->nets[i];
-        const uint32_t base = (uint32_t)hp->buckets.size();
-        for (size_t lb = 0; lb < np.buckets.size(); ++lb) {
-            const HBucket& B = np.buckets[lb];
-            const HBucket V = device_view(B);
-            DBucket d{};
-            d.op_begin = (uint32_t)hp->operands.size();
-            d.n_ops = (uint8_t)B.ops.size();
-            d.n_out = (uint8_t)(B.width - 1);
-            int cb = 0;
-            bool fold = false;
-            const int tcap = cfg.tile_cap[width_class(d.n_out)];
-            pick_tile(V, net, tcap > 0 ? tcap : cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
-                      cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, B.n_sum - 1, &cb, &fold);
-            d.chunk_bits = (uint8_t)cb;
-            d.flags = (uint8_t)((fold ? kBucketFoldLeaves : 0) | ((B.n_sum - 1) << 3));
-            {
-                const uint32_t low = (1u << cb) - 1u;
-                uint32_t foot = 0, ns = 0, nl = 0, lu = 0, lh = 0;
-                for (const HOperand& op : V.ops) {
-                    if (fold && foldable(op)) {
-                        nl++;
-                        lu |= op.mask & low;
-                        lh |= op.mask & ~low;
-                    } else {
-                        foot += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & low);
-                        ns++;
-                    }
-                }
-                d.total_foot = foot;
-                d.n_staged = (uint8_t)ns;
-                d.n_leaves = (uint8_t)nl;
-                d.leaf_u = lu;
-                d.leaf_hi = lh;
-            }
-            d.parent = B.parent >= 0 ? base + (uint32_t)B.parent : kNone;
-            d.n_deps = (uint32_t)B.n_deps;
-            d.n_tasks = 1u << (d.n_out - cb);
-            d.net = (uint32_t)i;
-            d.out_off = off;
-            off += align_up(1ull << (B.width - B.n_sum), align);
-            double opbytes = 0;
-            uint32_t next_soff = 0, next_staged = 0, next_leaf = 0;
-            for (size_t t = 0; t < B.ops.size(); ++t) {
-                const HOperand& op = V.ops[t];
-                DOperand o{};
-                o.mask = op.mask;
-                o.src = kNone;
-                o.folded = (d.flags & kBucketFoldLeaves) && foldable(op);
-                o.smask = (uint8_t)B.ops[t].smask;
-                if (o.folded) {
-                    o.slot = (uint8_t)next_leaf++;
-                } else {
-                    o.slot = (uint8_t)next_staged++;
-                    o.soff = (uint16_t)next_soff;
-                    next_soff += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & ((1u << d.chunk_bits) - 1u));
-                }
-                if (op.src >= 0) {
-                    o.off = 0;  // set below, once every result has its offset
-                    o.flags = 0;
-                } else {
-                    const Leaf& lf = net.leaves[op.leaf];
-                    o.off = ((uint64_t)net.graph * L + leaf_index(lf.kind, lf.layer)) * kLeafSlots;
-                    o.flags = kOpLeaf;
-                }
-                hp->operands.push_back(o);
-                hp->op_src.push_back(op.src >= 0 ? (int32_t)(base + op.src) : -1);
-                hp->op_leaf_kind.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].kind);
-                hp->op_leaf_layer.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].layer);
-                hp->op_rank.push_back(op.rank);
+        // every slice of the network: the same buckets, its own gate entries
+        for (uint32_t sl = 0; sl < (1u << net.slice_bits); ++sl) {
+            const uint32_t base = (uint32_t)hp->buckets.size();
+            const size_t root0 = hp->root_bucket.size();
+            for (size_t lb = 0; lb < np.buckets.size(); ++lb) {
+                const HBucket& B = np.buckets[lb];
+                const HBucket V = device_view(B);
+                DBucket d{};
+                d.op_begin = (uint32_t)hp->operands.size();
+                d.n_ops = (uint8_t)B.ops.size();
+                d.n_out = (uint8_t)(B.width - 1);
+                int cb = 0;
+                bool fold = false;
+                const int tcap = cfg.tile_cap[width_class(d.n_out)];
+                pick_tile(V, net, tcap > 0 ? tcap : cfg.chunk_log2 > 0 ? cfg.chunk_log2 : kDefaultTileBits,
+                          cfg.dtype == 1 ? kStageElemsC128 : kStageElemsC64, B.n_sum - 1, &cb, &fold);
+                d.chunk_bits = (uint8_t)cb;
+                d.flags = (uint8_t)((fold ? kBucketFoldLeaves : 0) | ((B.n_sum - 1) << 3));
                 {
-                    int8_t prm = -1;
-                    if (op.src < 0) {
-                        const Leaf& lf = net.leaves[op.leaf];
-                        if (lf.kind == QT_LEAF_ZZ || lf.kind == QT_LEAF_ZZ_CONJ) prm = (int8_t)lf.layer;
-                        if (lf.kind == QT_LEAF_RX || lf.kind == QT_LEAF_RX_CONJ) prm = (int8_t)(cfg.p + lf.layer);
+                    const uint32_t low = (1u << cb) - 1u;
+                    uint32_t foot = 0, ns = 0, nl = 0, lu = 0, lh = 0;
+                    for (const HOperand& op : V.ops) {
+                        if (fold && foldable(op)) {
+                            nl++;
+                            lu |= op.mask & low;
+                            lh |= op.mask & ~low;
+                        } else {
+                            foot += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & low);
+                            ns++;
+                        }
                     }
-                    hp->op_param.push_back(prm);
+                    d.total_foot = foot;
+                    d.n_staged = (uint8_t)ns;
+                    d.n_leaves = (uint8_t)nl;
+                    d.leaf_u = lu;
+                    d.leaf_hi = lh;
                 }
-                opbytes += std::ldexp(1.0, op.rank);
+                d.parent = B.parent >= 0 ? base + (uint32_t)B.parent : kNone;
+                d.n_deps = (uint32_t)B.n_deps;
+                d.n_tasks = 1u << (d.n_out - cb);
+                d.net = (uint32_t)i;
+                d.out_off = off;
+                off += align_up(1ull << (B.width - B.n_sum), align);
+                double opbytes = 0;
+                uint32_t next_soff = 0, next_staged = 0, next_leaf = 0;
+                for (size_t t = 0; t < B.ops.size(); ++t) {
+                    const HOperand& op = V.ops[t];
+                    DOperand o{};
+                    o.mask = op.mask;
+                    o.src = kNone;
+                    o.folded = (d.flags & kBucketFoldLeaves) && foldable(op);
+                    o.smask = (uint8_t)B.ops[t].smask;
+                    if (o.folded) {
+                        o.slot = (uint8_t)next_leaf++;
+                    } else {
+                        o.slot = (uint8_t)next_staged++;
+                        o.soff = (uint16_t)next_soff;
+                        next_soff += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & ((1u << d.chunk_bits) - 1u));
+                    }
+                    if (op.src >= 0) {
+                        o.off = 0;  // set below, once every result has its offset
+                        o.flags = 0;
+                    } else {
+                        const Leaf& lf = net.leaves[op.leaf];
+                        o.off = ((uint64_t)net.graph * L + leaf_index(lf.kind, lf.layer)) * kLeafSlots +
+                                (lf.fix >= 0 ? 2u * ((sl >> lf.fix) & 1u) : 0u);
+                        o.flags = kOpLeaf;
+                    }
+                    hp->operands.push_back(o);
+                    hp->op_src.push_back(op.src >= 0 ? (int32_t)(base + op.src) : -1);
+                    hp->op_leaf_kind.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].kind);
+                    hp->op_leaf_layer.push_back(op.src >= 0 ? -1 : net.leaves[op.leaf].layer);
+                    hp->op_rank.push_back(op.rank);
+                    hp->op_leaf_sub.push_back(op.src >= 0 || net.leaves[op.leaf].fix < 0
+                                                  ? 0
+                                                  : (int32_t)(2u * ((sl >> net.leaves[op.leaf].fix) & 1u)));
+                    {
+                        int8_t prm = -1;
+                        if (op.src < 0) {
+                            const Leaf& lf = net.leaves[op.leaf];
+                            if (lf.kind == QT_LEAF_ZZ || lf.kind == QT_LEAF_ZZ_CONJ) prm = (int8_t)lf.layer;
+                            if (lf.kind == QT_LEAF_RX || lf.kind == QT_LEAF_RX_CONJ) prm = (int8_t)(cfg.p + lf.layer);
+                        }
+                        hp->op_param.push_back(prm);
+                    }
+                    opbytes += std::ldexp(1.0, op.rank);
+                }
+                hp->buckets.push_back(d);
+                hp->bucket_level.push_back(B.level);
+                hp->bucket_var.push_back(B.var);
+                hp->bucket_var2.push_back(B.var2);
+                hp->bucket_var3.push_back(B.var3);
+                hp->bucket_slice.push_back((int32_t)sl);
+                if (B.parent < 0) hp->root_bucket.push_back(base + (uint32_t)lb);
+                hp->max_width = std::max(hp->max_width, B.width);
+                hp->n_levels = std::max(hp->n_levels, B.level + 1);
+                hp->width_hist[B.width]++;
+                hp->sum_2w += std::ldexp(1.0, B.width);
+                hp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - B.n_sum));
+                {
+                    // a merged bucket counts the flops of its unmerged buckets: the
+                    // bucket of s0 (products of its operands, sums over s0), then each
+                    // consumer's gate products and its sum; operand t belongs to the
+                    // bucket of its earliest summed variable
+                    double n_k[4] = {0, 0, 0, 0};
+                    for (const HOperand& op : B.ops) n_k[__builtin_ctz(op.smask)] += 1;
+                    for (int k = 0; k < B.n_sum; ++k)
+                        hp->flops += std::ldexp(1.0, B.width - k) * 6.0 * (n_k[k] - (k == 0 ? 1 : 0)) +
+                                     std::ldexp(1.0, B.width - k - 1) * 2.0;
+                }
             }
-            hp->buckets.push_back(d);
-            hp->bucket_level.push_back(B.level);
-            hp->bucket_var.push_back(B.var);
-            hp->bucket_var2.push_back(B.var2);
-            hp->bucket_var3.push_back(B.var3);
-            if (B.parent < 0) hp->root_bucket.push_back(base + (uint32_t)lb);
-            hp->max_width = std::max(hp->max_width, B.width);
-            hp->n_levels = std::max(hp->n_levels, B.level + 1);
-            hp->width_hist[B.width]++;
-            hp->sum_2w += std::ldexp(1.0, B.width);
-            hp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - B.n_sum));
-            {
-                // a merged bucket counts the flops of its unmerged buckets: the
-                // bucket of s0 (products of its operands, sums over s0), then each
-                // consumer's gate products and its sum; operand t belongs to the
-                // bucket of its earliest summed variable
-                double n_k[4] = {0, 0, 0, 0};
-                for (const HOperand& op : B.ops) n_k[__builtin_ctz(op.smask)] += 1;
-                for (int k = 0; k < B.n_sum; ++k)
-                    hp->flops += std::ldexp(1.0, B.width - k) * 6.0 * (n_k[k] - (k == 0 ? 1 : 0)) +
-                                 std::ldexp(1.0, B.width - k - 1) * 2.0;
+            // the slice's factors of the network's value: its root results,
+            // then the entries of its fully fixed gates
+            bool first = true;
+            auto push_factor = [&](uint64_t e) {
+                hp->factor.push_back(e | (first ? kFirstFactor : 0));
+                first = false;
+            };
+            for (size_t r = root0; r < hp->root_bucket.size(); ++r) push_factor(hp->buckets[hp->root_bucket[r]].out_off);
+            for (const FixedLeaf& fl : net.fixed) {
+                uint32_t e = (sl >> fl.f[0]) & 1u;
+                if (fl.rank == 2) e += 2u * ((sl >> fl.f[1]) & 1u);
+                push_factor(((uint64_t)net.graph * L + leaf_index(fl.kind, fl.layer)) * kLeafSlots + e);
             }
+            hp->n_slices++;
         }
+        hp->net_first_factor.push_back((uint32_t)hp->factor.size());
         hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());
         hp->net_first_root.push_back((uint32_t)hp->root_bucket.size());
         hp->net_graph.push_back((uint32_t)net.graph);

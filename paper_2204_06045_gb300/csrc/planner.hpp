@@ -15,6 +15,17 @@ struct Leaf {
     int layer;  // 0-based layer for ZZ / mixer tensors, -1 otherwise
     int rank;
     int v[2];
+    int fix = -1;  // sliced networks: a rank-2 gate with one variable fixed, the fixed variable's
+                   // slice bit (its entries for the other variable x are at x + 2 * value)
+};
+
+// A gate tensor of a sliced network whose variables are all fixed: a scalar
+// per slice, entry val(f[0]) (rank 1) or val(f[0]) + 2 val(f[1]) (rank 2).
+struct FixedLeaf {
+    int kind;
+    int layer;
+    int rank;
+    int f[2];  // slice bits of its variables
 };
 
 struct Network {
@@ -23,6 +34,11 @@ struct Network {
     int nvars = 0;
     std::vector<Leaf> leaves;
     std::vector<int> wire_vars;  // variables on each qubit's wire
+    // index slicing: 2^slice_bits slices, slice s fixing variable k of
+    // fixed_vars (numbered in the unsliced network) to bit k of s
+    int slice_bits = 0;
+    std::vector<int> fixed_vars;
+    std::vector<FixedLeaf> fixed;
 };
 
 struct HOperand {
@@ -74,6 +90,8 @@ struct PlanConfig {
     bool fuse = false;       // form fused units of small subtrees (persistent energy plans)
     int tile_cap[kWidthClasses] = {0, 0, 0, 0, 0};  // most tile bits per bucket-width class (0: chunk_log2 / default)
     bool merge = false;      // merge chains of eliminations (a bucket and the parent that only extends it)
+    int slice_width = 0;     // > 0: slice networks whose greedy width exceeds it (forward plans)
+    int max_slice_bits = 0;  // most variables fixed per network
 };
 
 // The flat plan: what gets uploaded plus host-side bookkeeping.
@@ -95,6 +113,14 @@ struct HostPlan {
     std::vector<int32_t> bucket_var;
     std::vector<int32_t> bucket_var2;
     std::vector<int32_t> bucket_var3;
+    std::vector<int32_t> bucket_slice;  // the slice of its network a bucket belongs to
+    std::vector<int32_t> op_leaf_sub;   // leaf operands: element offset within the gate tensor (sliced gates)
+    // epilogue: per network, factors of its value (arena element offsets, bit
+    // 63 set on the first factor of each slice): value = sum over slices of
+    // the product of the slice's factors (root results and fixed gate entries)
+    std::vector<uint32_t> net_first_factor;  // n_nets + 1
+    std::vector<uint64_t> factor;
+    uint64_t n_slices = 0;               // slices over all networks (1 per unsliced network)
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
     std::vector<URec> unit_prog;        // fused units' programs, unit by unit (padded by kURecWindow records)
     uint64_t n_units = 0;

@@ -42,6 +42,9 @@ constexpr uint8_t kBucketUnitRoot = 4;  // the root (last bucket) of a fused uni
 // more summed variables (s2 as device bit 1); the kernel's epilogues take two.
 constexpr int kMaxSum = 2;          // summed variables per bucket, at most
 constexpr int bucket_n_sum(uint8_t flags) { return 1 + ((flags >> 3) & 3); }
+// Epilogue factor lists (element offsets into the arena): this bit marks the
+// first factor of a slice's product.
+constexpr uint64_t kFirstFactor = 1ull << 63;
 // Fused units: a subtree of small buckets (every output count at most
 // 2^kFuseOutBits, every non-gate operand produced inside the subtree) is one
 // work group; one warp contracts its buckets in elimination order with the

@@ -23,7 +23,7 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
-           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard")
+           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed")
 
 
 class QTError(RuntimeError):
@@ -41,7 +41,8 @@ class PlanOpts(ctypes.Structure):
                 ("with_grad", ctypes.c_int32), ("spin_limit", ctypes.c_uint64), ("chunk_log2", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("no_fuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("tile_cap", ctypes.c_int8 * 8), ("no_merge", ctypes.c_int32), ("adjoint_budget_bytes", ctypes.c_size_t)]
+                ("tile_cap", ctypes.c_int8 * 8), ("no_merge", ctypes.c_int32), ("adjoint_budget_bytes", ctypes.c_size_t),
+                ("slice_width", ctypes.c_int32), ("max_slice_bits", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -53,18 +54,21 @@ class PlanStats(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("sim_seconds", ctypes.c_double),
                 ("n_units", ctypes.c_int64), ("n_fused", ctypes.c_int64), ("tile_cap", ctypes.c_int32 * 8),
                 ("run_tiles", ctypes.c_int32), ("tune_seconds", ctypes.c_double), ("tune_candidates", ctypes.c_int32),
-                ("n_passes", ctypes.c_int32)]
+                ("n_passes", ctypes.c_int32), ("slice_bits", ctypes.c_int32), ("n_slices", ctypes.c_int64)]
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
                          ("parent", np.int32), ("n_deps", np.int32), ("level", np.int32), ("var", np.int32),
                          ("tile_log2", np.int32), ("tile_bits", np.uint32), ("folded", np.uint32),
                          ("unit_role", np.uint32), ("n_sum", np.int32), ("var2", np.int32),
-                         ("var3", np.int32), ("pad3", np.int32)])
+                         ("var3", np.int32), ("slice", np.int32)])
 GROUP_DTYPE = np.dtype([("bucket", np.int32), ("first_tile", np.int32), ("n_tiles", np.int32),
                         ("unit_buckets", np.int32)])
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
-                          ("mask", np.uint32), ("rank", np.int32), ("smask", np.uint32)])
+                          ("mask", np.uint32), ("rank", np.int32), ("smask", np.uint32), ("leaf_sub", np.int32),
+                          ("pad", np.int32)])
+FIXED_DTYPE = np.dtype([("network", np.int32), ("slice", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
+                        ("entry", np.int32), ("pad", np.int32)])
 
 _lib = None
 
@@ -98,6 +102,7 @@ def lib():
         L.qt_energy_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_fma_peak.argtypes = [i32, dp]
         L.qt_plan_export_groups.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        L.qt_plan_export_fixed.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_shard.argtypes = [i32, i32, i32p, i32, i32, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp), i32p,
                                     i32p]
         L.qt_last_imag.argtypes = [vp, dp]
@@ -116,7 +121,8 @@ def lib():
         for name in ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
-                     "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard"):
+                     "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard",
+                     "qt_plan_export_fixed"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -183,7 +189,9 @@ class Plan:
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
-              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=True):
+              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=True,
+              slice_width=0, max_slice_bits=0):
+        # slice_width: 0 the library's default target, -1 no slicing
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
         o.sched = {"persistent": QT_SCHED_PERSISTENT, "per_bucket": QT_SCHED_PER_BUCKET}[sched]
@@ -202,6 +210,8 @@ class Plan:
         o.autotune = int(autotune)
         o.adjoint_budget_bytes = int(adjoint_budget_bytes)
         o.no_merge = 0 if merge else 1
+        o.slice_width = int(slice_width)
+        o.max_slice_bits = int(max_slice_bits)
         for i, c in enumerate(tile_cap or []):
             o.tile_cap[i] = int(c)
         return o
@@ -308,6 +318,14 @@ class Plan:
         out = np.zeros(n, dtype=GROUP_DTYPE)
         cnt = ctypes.c_int64(0)
         _check(lib().qt_plan_export_groups(self._h, out.ctypes.data, ctypes.byref(cnt)), "qt_plan_export_groups")
+        return out[:cnt.value]
+
+    def export_fixed(self) -> np.ndarray:
+        """Fixed gate entries of every slice (network, slice, leaf_kind, leaf_layer, entry)."""
+        cnt = ctypes.c_int64(0)
+        _check(lib().qt_plan_export_fixed(self._h, None, ctypes.byref(cnt)), "qt_plan_export_fixed")
+        out = np.zeros(max(1, cnt.value), dtype=FIXED_DTYPE)
+        _check(lib().qt_plan_export_fixed(self._h, out.ctypes.data, ctypes.byref(cnt)), "qt_plan_export_fixed")
         return out[:cnt.value]
 
     def energy(self, gammas, betas, edge_zz=None, energy=None, stream=None):

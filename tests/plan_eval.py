@@ -37,11 +37,17 @@ def pext(o: np.ndarray, mask: int) -> np.ndarray:
     return r
 
 
-def evaluate(buckets, operands, gammas, betas, graph_of_network=None):
-    """Complex value of every network of the exported schedule."""
+def evaluate(buckets, operands, gammas, betas, graph_of_network=None, fixed=None):
+    """Complex value of every network of the exported schedule.
+
+    A sliced network's value is the sum over its slices of the product of the
+    slice's root results and its fixed gate entries (`fixed`, from
+    export_fixed); a gate with one variable fixed reads its entries from
+    leaf_sub on."""
     n_nets = int(buckets["network"].max()) + 1
     res = {}
-    value = np.ones(n_nets, dtype=complex)
+    sliced = "slice" in buckets.dtype.names
+    slice_val = {}  # (network, slice) -> product
     for b in range(buckets.shape[0]):
         B = buckets[b]
         # a bucket sums n_sum variables (more than one: merged eliminations);
@@ -63,11 +69,24 @@ def evaluate(buckets, operands, gammas, betas, graph_of_network=None):
                 idx = (pext(o, int(op["mask"])) << bin(sm).count("1")) + pext(np.int64(x), sm)
                 if op["src"] < 0:
                     T = leaf_tensor(int(op["leaf_kind"]), int(op["leaf_layer"]), gam, bet)
+                    if "leaf_sub" in op.dtype.names:
+                        T = T[int(op["leaf_sub"]):]
                 else:
                     T = res[int(op["src"])]
                 prod = prod * T[idx]
             acc += prod
         res[b] = acc
         if B["parent"] < 0:
-            value[net] *= acc[0]
+            key = (net, int(B["slice"]) if sliced else 0)
+            slice_val[key] = slice_val.get(key, 1.0 + 0j) * acc[0]
+    for f in (fixed if fixed is not None else []):
+        net = int(f["network"])
+        g = 0 if graph_of_network is None else graph_of_network[net]
+        gam = gammas[g] if np.ndim(gammas) == 2 else gammas
+        bet = betas[g] if np.ndim(betas) == 2 else betas
+        key = (net, int(f["slice"]))
+        slice_val[key] = slice_val[key] * leaf_tensor(int(f["leaf_kind"]), int(f["leaf_layer"]), gam, bet)[int(f["entry"])]
+    value = np.zeros(n_nets, dtype=complex)
+    for (net, _), v in slice_val.items():
+        value[net] += v
     return value

@@ -7,8 +7,8 @@ the bucket of s0 with outputs (o, s1), the consumer's gate tensors folded into
 its gate table, and adds each lane's two outputs (s1 = 0, 1) into result o
 (inside the unrolled tile loop for complex64, in a compact loop of its own for
 complex128).
-These tests run merged plans against the state vector, the stored goldens and
-the oracle's own bucket elimination, with the tolerances of the other GPU
+These tests run merged (unsliced) plans against the state vector, the stored
+goldens and the oracle's own bucket elimination, with the tolerances of the other GPU
 parity tests (1e-10 complex128, 1e-5 complex64 per edge, as in
 test_gpu_energy).
 """
@@ -44,7 +44,7 @@ def _gpu():
 
 def _merged_tiles(n, edges, p, **kw):
     """Tile bits of the merged buckets of the plan these options give."""
-    with qtgb.plan(n, edges, p, host_only=True, merge=True, **kw) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, merge=True, **kw, slice_width=-1) as hp:
         B, _ = hp.export()
     return B["tile_log2"][B["n_sum"] > 1]
 
@@ -56,7 +56,7 @@ def test_merged_small_graphs_match_state_vector(dtype, order, n, seed, p):
     edges = synth.random_regular_graph(n, seed)
     g, b = synth.angles(p, seed)
     assert _merged_tiles(n, edges, p, dtype=dtype).size > 0
-    with qtgb.plan(n, edges, p, dtype=dtype, order=order, merge=True) as pl:
+    with qtgb.plan(n, edges, p, dtype=dtype, order=order, merge=True, slice_width=-1) as pl:
         zz, E = pl.energy(g, b)
         im = pl.last_imag()
     ref = oracle.sv_zz(n, edges, g, b)
@@ -79,7 +79,7 @@ def test_merged_tile_shapes(dtype, cap):
     assert tiles.size > 0 and tiles.max() <= cap
     if cap <= 6:
         assert tiles.max() == cap
-    with qtgb.plan(n, edges, p, dtype=dtype, merge=True, tile_cap=[cap] * 5) as pl:
+    with qtgb.plan(n, edges, p, dtype=dtype, merge=True, tile_cap=[cap] * 5, slice_width=-1) as pl:
         zz, E = pl.energy(g, b)
     ref = oracle.sv_zz(n, edges, g, b)
     assert scaled_err(zz, ref) <= TOL[dtype]
@@ -102,11 +102,11 @@ def test_merged_c2_n30_p4_matches_statevector_golden(dtype, order):
     n, p = 30, 4
     edges = synth.random_regular_graph(n, 1000)
     g, b = np.array(rows["gamma"]), np.array(rows["beta"])
-    with qtgb.plan(n, edges, p, dtype=dtype, order=order, merge=True) as pl:
+    with qtgb.plan(n, edges, p, dtype=dtype, order=order, merge=True, slice_width=-1) as pl:
         st = pl.stats()
         zz, E = pl.energy(g, b)
         im = pl.last_imag()
-    with qtgb.plan(n, edges, p, dtype=dtype, host_only=True, merge=False) as hp:
+    with qtgb.plan(n, edges, p, dtype=dtype, host_only=True, merge=False, slice_width=-1) as hp:
         st1 = hp.stats()
     assert st["n_buckets"] < st1["n_buckets"] and st["alg_bytes"] < 0.6 * st1["alg_bytes"]
     assert scaled_err(zz, np.array(zz_ref)) <= TOL[dtype]
@@ -129,12 +129,12 @@ def test_merged_c4_wide_networks_match_min_fill_golden(dtype):
     n, p = 1000, 5
     edges = synth.random_regular_graph(n, 1000)
     g, b = synth.angles(p, 1000)
-    with qtgb.plan(n, edges, p, host_only=True) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
         B, _ = hp.export()
     mw = np.zeros(edges.shape[0], dtype=np.int64)
     np.maximum.at(mw, B["network"], B["width"])
     sel = np.nonzero((mw >= 26) & (mw <= 28))[0]
-    with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, merge=True) as pl:
+    with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, merge=True, slice_width=-1) as pl:
         zz, _ = pl.energy(g, b)
         im = pl.last_imag()
     assert scaled_err(zz, np.array([ref[int(e)] for e in sel])) <= TOL[dtype]
@@ -150,7 +150,7 @@ def test_merged_c3_batch_sampled_edges_match_oracle(dtype):
     G = np.array([gg for _, _, gg, _ in graphs])
     Bt = np.array([bb for _, _, _, bb in graphs])
     spec = [(n, e) for n, e, _, _ in graphs]
-    with qtgb.plan_batch(spec, p, dtype=dtype, merge=True) as pl:
+    with qtgb.plan_batch(spec, p, dtype=dtype, merge=True, slice_width=-1) as pl:
         assert pl.stats()["n_units"] > 0
         energies, zz = pl.energy_batch(G, Bt)
     rng = np.random.default_rng(11)
@@ -171,7 +171,7 @@ def test_merged_and_unmerged_agree_on_a_batch():
     spec = [(n, e) for n, e, _, _ in graphs]
     out = {}
     for dtype, merge in [("c128", True), ("c64", True), ("c64", False)]:
-        with qtgb.plan_batch(spec, 3, dtype=dtype, merge=merge) as pl:
+        with qtgb.plan_batch(spec, 3, dtype=dtype, merge=merge, slice_width=-1) as pl:
             out[(dtype, merge)] = pl.energy_batch(G, Bt)
     e_ref, zz_ref = out[("c128", True)]
     for key in [("c64", True), ("c64", False)]:

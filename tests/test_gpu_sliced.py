@@ -1,0 +1,139 @@
+"""GPU parity of index slicing (opts.slice_width).
+
+A network wider than the target has variables fixed; its value is the sum,
+over the 2^s assignments of the fixed variables, of networks without them.
+Gates left with one free variable read the entry pair at 2 * (fixed value) of
+their table; gates with every variable fixed are scalars the epilogue
+multiplies into their slice's product before the slices are summed. These
+tests run sliced plans against the state vector, the stored goldens and the
+oracle's bucket elimination, with the tolerances of the other GPU parity tests
+(1e-10 complex128, 1e-5 complex64 per edge, as in test_gpu_energy).
+"""
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_06045_gb300 import qtgb, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = Path(__file__).parent / "golden"
+TOL = {"c128": 1e-10, "c64": 1e-5}
+
+
+def scaled_err(x, ref):
+    x, ref = np.asarray(x, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    d = np.abs(x - ref)
+    return float(max(np.max(d / np.abs(1.0 - ref)), np.max(d)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_06045_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("sched,order", [("persistent", "simulated"), ("persistent", "ready_queue"),
+                                         ("per_bucket", "simulated")])
+@pytest.mark.parametrize("n,seed,p,width", [(14, 22, 3, 8), (18, 5, 4, 14)])
+def test_sliced_small_graphs_match_state_vector(dtype, sched, order, n, seed, p, width):
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype=dtype, sched=sched, order=order, slice_width=width) as pl:
+        st = pl.stats()
+        zz, E = pl.energy(g, b)
+        im = pl.last_imag()
+    assert st["slice_bits"] > 0 and st["n_slices"] > edges.shape[0]
+    ref = oracle.sv_zz(n, edges, g, b)
+    assert scaled_err(zz, ref) <= TOL[dtype]
+    assert abs(E - oracle.energy_from_zz(ref)) <= TOL[dtype] * abs(E)
+    assert np.abs(im).max() <= 10 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_sliced_c2_n30_p4_matches_statevector_golden(dtype):
+    """Networks of greedy width up to 26 sliced to width 20 or less."""
+    if not (GOLDEN / "c2_n30_p4_statevector.txt").exists():
+        pytest.skip("golden not generated")
+    rows, zz_ref = {}, []
+    for line in (GOLDEN / "c2_n30_p4_statevector.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        parts = line.split()
+        if parts[0] == "edge":
+            zz_ref.append(float(parts[4]))
+        else:
+            rows[parts[0]] = [float(x) for x in parts[1:]]
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = np.array(rows["gamma"]), np.array(rows["beta"])
+    with qtgb.plan(n, edges, p, dtype=dtype, slice_width=20) as pl:
+        st = pl.stats()
+        zz, E = pl.energy(g, b)
+    assert st["max_width"] <= 20 and st["slice_bits"] > 0
+    assert scaled_err(zz, np.array(zz_ref)) <= TOL[dtype]
+    assert abs(E - rows["energy"][0]) <= TOL[dtype] * abs(E)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_sliced_c4_wide_networks_match_min_fill_golden(dtype):
+    """The N=1000 p=5 networks of greedy width 26..28, sliced to width 24."""
+    path = GOLDEN / "c4_n1000_p5_bucket.txt"
+    if not path.exists():
+        pytest.skip("golden not generated")
+    ref = {}
+    for line in path.read_text().splitlines():
+        parts = line.split()
+        if parts and parts[0] == "edge":
+            ref[int(parts[1])] = float(parts[4])
+    n, p = 1000, 5
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    with qtgb.plan(n, edges, p, host_only=True, merge=False, slice_width=-1) as hp:
+        B, _ = hp.export()
+    mw = np.zeros(edges.shape[0], dtype=np.int64)
+    np.maximum.at(mw, B["network"], B["width"])
+    sel = np.nonzero((mw >= 26) & (mw <= 28))[0]
+    with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, slice_width=24) as pl:
+        st = pl.stats()
+        zz, _ = pl.energy(g, b)
+    assert st["max_width"] <= 24 and st["slice_bits"] > 0
+    assert scaled_err(zz, np.array([ref[int(e)] for e in sel])) <= TOL[dtype]
+
+
+def test_sliced_batch_with_fused_units_matches_oracle():
+    """A batch whose slices are small enough to run as fused units."""
+    graphs = synth.batch(6, 2, lo=30, hi=80, base_seed=900)
+    spec = [(n, e) for n, e, _, _ in graphs]
+    G = np.array([gg for _, _, gg, _ in graphs])
+    Bt = np.array([bb for _, _, _, bb in graphs])
+    with qtgb.plan_batch(spec, 2, dtype="c128", slice_width=5) as pl:
+        st = pl.stats()
+        energies, zz = pl.energy_batch(G, Bt)
+    assert st["slice_bits"] > 0 and st["n_units"] > 0
+    first = np.cumsum([0] + [e.shape[0] for _, e, _, _ in graphs])
+    rng = np.random.default_rng(5)
+    for f in np.sort(rng.choice(first[-1], size=20, replace=False)):
+        gi = int(np.searchsorted(first, f, side="right") - 1)
+        n, edges, gg, bb = graphs[gi]
+        ref, _ = oracle.edge_bucket(n, edges, gg, bb, int(f - first[gi]), seed=int(f))
+        assert scaled_err([zz[f]], [ref.real]) <= TOL["c128"]
+
+
+def test_sliced_plan_without_device_allocation():
+    """qt_energy_noalloc uploads the epilogue's factor lists into its static array too."""
+    n, seed, p = 14, 22, 3
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype="c128", host_only=True, slice_width=8) as pl:
+        energies, zz = pl.energy_noalloc(g, b)
+    ref = oracle.sv_zz(n, edges, g, b)
+    assert scaled_err(zz, ref) <= TOL["c128"]
+    assert abs(energies[0] - oracle.energy_from_zz(ref)) <= TOL["c128"] * abs(energies[0])

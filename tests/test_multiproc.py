@@ -83,7 +83,7 @@ def _shard_rank(rank, world, port, out):
             cost = float(pl.stats()["sum_2w"])
             if mine.size:
                 B, O = pl.export()
-                zz = evaluate(B, O, g, b).real
+                zz = evaluate(B, O, g, b, fixed=pl.export_fixed()).real
             else:
                 zz = np.zeros(0)
         part = torch.tensor([0.5 * float(np.sum(1.0 - zz))], dtype=torch.float64)

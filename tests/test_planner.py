@@ -29,6 +29,8 @@ def _built():
 
 
 def host_plan(n, edges, p, **kw):
+    """A host-only plan; unsliced unless the test asks for slicing."""
+    kw.setdefault("slice_width", -1)
     return qtgb.plan(n, edges, p, host_only=True, **kw)
 
 
@@ -60,7 +62,7 @@ def test_batch_schedule_matches_oracle():
     p = 2
     G = np.array([synth.angles(p, s)[0] for s in (1, 2, 3)])
     Bt = np.array([synth.angles(p, s)[1] for s in (1, 2, 3)])
-    with qtgb.plan_batch(graphs, p, host_only=True) as pl:
+    with qtgb.plan_batch(graphs, p, host_only=True, slice_width=-1) as pl:
         B, O = pl.export()
         gon = np.repeat(np.arange(3), [e.shape[0] for _, e in graphs])
         vals = evaluate(B, O, G, Bt, gon)
@@ -478,3 +480,62 @@ def test_merge_applies_to_persistent_forward_plans_only(kw):
     with host_plan(n, edges, p, merge=True) as pl:
         Bm, _ = pl.export()
     assert (B["n_sum"] == 1).all() and (Bm["n_sum"] > 1).any()
+
+
+@pytest.mark.parametrize("n,seed,p,width", [(12, 21, 2, 5), (14, 22, 3, 8), (16, 23, 3, 9), (18, 5, 4, 17)])
+def test_sliced_networks_sum_to_the_same_values(n, seed, p, width):
+    """opts.slice_width: every network wider than the target gets variables
+    fixed; its slices (2^s networks over the other variables, one per
+    assignment of the fixed ones) contract, in the numpy evaluator, to values
+    whose sum per network is the state vector's <Z_jZ_k>."""
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with host_plan(n, edges, p, slice_width=width) as pl:
+        B, O = pl.export()
+        F = pl.export_fixed()
+        st = pl.stats()
+    with host_plan(n, edges, p) as pl:
+        st0 = pl.stats()
+    assert st0["max_width"] > width and st["slice_bits"] >= 1
+    assert st["n_slices"] > edges.shape[0] and st["max_width"] <= max(width, st0["max_width"] - st["slice_bits"])
+    for net in range(edges.shape[0]):
+        idx = np.nonzero(B["network"] == net)[0]
+        slices = np.unique(B["slice"][idx])
+        assert slices.tolist() == list(range(len(slices))) and len(slices) & (len(slices) - 1) == 0
+        # every slice is the same schedule: widths, operand counts and masks agree
+        per = [idx[B["slice"][idx] == s] for s in slices]
+        for q in per[1:]:
+            assert (B["width"][q] == B["width"][per[0]]).all() and (B["n_ops"][q] == B["n_ops"][per[0]]).all()
+            assert (B["var"][q] == B["var"][per[0]]).all()
+        # fixed gate entries: the same gates in every slice, entries in range
+        f = F[F["network"] == net]
+        if len(slices) > 1:
+            assert len(f) % len(slices) == 0
+    assert ((O["leaf_sub"] == 0) | (O["leaf_sub"] == 2)).all()
+    assert (O["leaf_sub"][O["src"] >= 0] == 0).all()
+    assert ((F["entry"] >= 0) & (F["entry"] < 4)).all()
+    vals = evaluate(B, O, g, b, fixed=F)
+    np.testing.assert_allclose(vals.real, oracle.sv_zz(n, edges, g, b), rtol=0, atol=1e-12)
+    assert np.abs(vals.imag).max() < 1e-12
+
+
+def test_slicing_options():
+    n, seed, p = 16, 23, 3
+    edges = synth.random_regular_graph(n, seed)
+    for bad in (dict(slice_width=1), dict(slice_width=32), dict(slice_width=-2), dict(max_slice_bits=17)):
+        with pytest.raises(qtgb.QTError):
+            host_plan(n, edges, p, **bad)
+    with host_plan(n, edges, p, slice_width=6, max_slice_bits=2) as pl:
+        st = pl.stats()
+    assert st["slice_bits"] == 2 and st["max_width"] > 6  # the bit budget ran out first
+    with host_plan(n, edges, p, slice_width=6, with_grad=True) as pl:  # gradient plans are not sliced
+        st = pl.stats()
+    assert st["slice_bits"] == 0 and st["n_slices"] == edges.shape[0]
+    with host_plan(n, edges, p, slice_width=30) as pl:  # nothing that wide: no slices
+        assert pl.stats()["n_slices"] == edges.shape[0] and len(pl.export_fixed()) == 0
+    # the default target: 22 for complex64, 20 for complex128 (N=30 p=4 reaches width 26)
+    e30 = synth.random_regular_graph(30, 1000)
+    for dtype, target in (("c64", 22), ("c128", 20)):
+        with qtgb.plan(30, e30, 4, host_only=True, dtype=dtype) as pl:
+            st = pl.stats()
+        assert st["slice_bits"] > 0 and st["max_width"] <= target
