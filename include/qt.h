@@ -240,15 +240,19 @@ int qt_plan_batch(int32_t n_graphs, const int32_t *n_vertices, const int32_t *n_
 /*
  * One rank's share of a graph's lightcone networks, for splitting one energy
  * over `world` processes (one GPU each). Every network is planned on the host
- * for its cost (sum over its buckets of 2^width); networks go to ranks by
- * longest-processing-time-first (the costliest network to the least loaded
- * rank). The plan holds the networks of rank `rank`: its qt_energy gives
- * that rank's edge values and the partial energy sum over its edges of
- * (1 - e_jk)/2, and its qt_energy_grad the partial gradient; the full E and
- * gradient are the sums over ranks (one reduction of 2p + 1 doubles).
+ * for its cost (sum over its buckets of 2^width); the units are the networks'
+ * slices (opts.slice_width; one per unsliced network), each costing its
+ * slice's sum, and go to ranks by longest-processing-time-first (the
+ * costliest unit to the least loaded rank). The plan holds the units of rank
+ * `rank`: its qt_energy gives, per edge of the shard, the sum of e_jk over the
+ * rank's slices of that edge's network (the whole e_jk when the rank holds
+ * them all), and the partial energy: the rank holding a network's slice 0
+ * counts the edge's 1/2, every rank subtracts 1/2 of its partial e_jk. The
+ * full e_jk, E and gradient are sums over ranks (one reduction of 2p + 1
+ * doubles for E and the gradient; gradient plans are never sliced).
  * shard_edges (may be NULL, else n_edges int32 of room) receives the rank's
- * edges in increasing order, *n_shard their count. A rank with no network
- * gets a plan of no networks (energy 0). Options as for qt_plan.
+ * edges in increasing order, *n_shard their count. A rank with no unit gets
+ * a plan of no networks (energy 0). Options as for qt_plan.
  */
 int qt_plan_shard(int32_t n_vertices, int32_t n_edges, const int32_t *edges, int32_t p, int32_t world,
                   int32_t rank, const qt_plan_opts *opts, qt_plan_t *out, int32_t *shard_edges,

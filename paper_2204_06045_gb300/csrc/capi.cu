@@ -180,7 +180,7 @@ int upload(qt_plan_t P) {
         {nullptr, 0, 0},                                       {hp.net_first_root.data(), bytes_of(hp.net_first_root), 0},
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
         {hp.unit_prog.data(), bytes_of(hp.unit_prog), 0},     {hp.net_first_factor.data(), bytes_of(hp.net_first_factor), 0},
-        {hp.factor.data(), bytes_of(hp.factor), 0},
+        {hp.factor.data(), bytes_of(hp.factor), 0},            {hp.graph_owned.data(), bytes_of(hp.graph_owned), 0},
     };
     size_t total = 0;
     for (auto& pc : pieces) {
@@ -235,6 +235,7 @@ int upload(qt_plan_t P) {
     de.graph_first_net = reinterpret_cast<const int32_t*>(base + pieces[7].off);
     de.net_first_factor = reinterpret_cast<const uint32_t*>(base + pieces[9].off);
     de.factor = reinterpret_cast<const uint64_t*>(base + pieces[10].off);
+    de.graph_owned = reinterpret_cast<const int32_t*>(base + pieces[11].off);
     de.n_graphs = n_graphs;
     de.arena = P->d_arena;
     de.zz = P->d_out;
@@ -735,23 +736,35 @@ int qt_plan_shard(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int
     qt_plan_t full = nullptr;
     int rc = qt_plan(n_vertices, n_edges, edges, p, &ho, &full);
     if (rc != QT_OK) return rc;
-    std::vector<double> cost(n_edges);
-    for (int e = 0; e < n_edges; ++e) cost[e] = full->hp.nplans[e].cost;
+    // units: every slice of every network (one per unsliced network), each
+    // costing its slice's sum of 2^width
+    struct Unit {
+        double cost;
+        int edge;
+        uint32_t slice;
+    };
+    std::vector<Unit> units;
+    std::vector<uint32_t> n_sl(n_edges);
+    for (int e = 0; e < n_edges; ++e) {
+        n_sl[e] = 1u << full->hp.nets[e].slice_bits;
+        for (uint32_t s = 0; s < n_sl[e]; ++s) units.push_back(Unit{full->hp.nplans[e].cost, e, s});
+    }
     qt_plan_free(full);
-    // LPT: the costliest network first (ties: lower edge), to the least loaded rank (ties: lower rank)
-    std::vector<int> idx(n_edges);
-    for (int e = 0; e < n_edges; ++e) idx[e] = e;
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // LPT: the costliest unit first (ties: lower edge, then slice), to the least loaded rank (ties: lower rank)
+    std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.cost > b.cost; });
     std::vector<double> load(world, 0.0);
-    std::vector<int> owner(n_edges, 0);
-    for (int e : idx) {
+    std::vector<std::vector<uint32_t>> my_slices(n_edges);
+    std::vector<uint8_t> my_owner(n_edges, 0);
+    for (const Unit& u : units) {
         const int r = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        owner[e] = r;
-        load[r] += cost[e];
+        load[r] += u.cost;
+        if (r != rank) continue;
+        my_slices[u.edge].push_back(u.slice);
+        if (u.slice == 0) my_owner[u.edge] = 1;  // the rank holding slice 0 counts the edge's 1/2
     }
     std::vector<int32_t> mine;
     for (int e = 0; e < n_edges; ++e)
-        if (owner[e] == rank) mine.push_back(e);
+        if (!my_slices[e].empty()) mine.push_back(e);
     *n_shard = (int32_t)mine.size();
     if (shard_edges && !mine.empty()) std::memcpy(shard_edges, mine.data(), mine.size() * sizeof(int32_t));
     std::vector<qt::GraphIn> gs(1);
@@ -759,6 +772,12 @@ int qt_plan_shard(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int
     if (!mine.empty()) {  // an empty shard is a graph without edges: no networks, energy 0
         for (int e = 0; e < n_edges; ++e) gs[0].edges.emplace_back(edges[2 * e], edges[2 * e + 1]);
         gs[0].sel = mine;
+        for (int e : mine) {
+            std::sort(my_slices[e].begin(), my_slices[e].end());
+            // all of a network's slices: leave the selection empty (the plain plan)
+            gs[0].sel_slices.push_back(my_slices[e].size() == n_sl[e] ? std::vector<uint32_t>() : my_slices[e]);
+            gs[0].sel_owner.push_back(my_owner[e]);
+        }
     }
     return make_plan(gs, p, opts, out);
 }
@@ -870,8 +889,9 @@ int qt_plan_export_fixed(qt_plan_t P, qt_fixed_info* out, int64_t* n_out) {
     int64_t k = 0;
     for (size_t i = 0; i < hp.nets.size(); ++i) {
         const qt::Network& net = hp.nets[i];
-        for (uint32_t sl = 0; sl < (1u << net.slice_bits); ++sl)
+        for (uint32_t j = 0; j < net.n_emitted(); ++j)
             for (const qt::FixedLeaf& fl : net.fixed) {
+                const uint32_t sl = net.slice_at(j);
                 if (out) {
                     qt_fixed_info& f = out[k];
                     f.network = (int32_t)i;
@@ -1151,7 +1171,8 @@ size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Byte offsets of every piece inside the scratch array.
 struct ScratchLayout {
-    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net, unit_list, net_first_factor, factor;
+    size_t buckets, ops, runs, net_first_root, root_bucket, graph_first_net, unit_list, net_first_factor, factor,
+        graph_owned;
     size_t counters, counters_bytes, ctl_bytes, cnt_bytes;
     size_t angles, out, arena, total;
 };
@@ -1174,6 +1195,7 @@ ScratchLayout scratch_layout(const qt::HostPlan& hp, size_t esize) {
     L.unit_list = take(hp.unit_prog.size() * sizeof(qt::URec));
     L.net_first_factor = take(hp.net_first_factor.size() * sizeof(uint32_t));
     L.factor = take(hp.factor.size() * sizeof(uint64_t));
+    L.graph_owned = take(hp.graph_owned.size() * sizeof(int32_t));
     L.ctl_bytes = 256;
     L.cnt_bytes = pad256(2 * nb * sizeof(uint32_t));
     L.counters_bytes = L.ctl_bytes + L.cnt_bytes + (size_t)(hp.n_groups - hp.runs.size()) * sizeof(qt::DSlot);
@@ -1265,6 +1287,8 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
                             cudaMemcpyHostToDevice, s));
     if (!hp.factor.empty())
         QT_CUDA(cudaMemcpyAsync(base + L.factor, hp.factor.data(), bytes_of(hp.factor), cudaMemcpyHostToDevice, s));
+    QT_CUDA(cudaMemcpyAsync(base + L.graph_owned, hp.graph_owned.data(), bytes_of(hp.graph_owned),
+                            cudaMemcpyHostToDevice, s));
     // the array keeps the previous call's contents: counters and the queue start at zero
     QT_CUDA(cudaMemsetAsync(base + L.counters, 0, L.counters_bytes, s));
     double* d_angles = reinterpret_cast<double*>(base + L.angles);
@@ -1295,6 +1319,7 @@ int qt_energy_noalloc(qt_plan_t P, const double* gammas, const double* betas, do
     de.graph_first_net = reinterpret_cast<const int32_t*>(base + L.graph_first_net);
     de.net_first_factor = reinterpret_cast<const uint32_t*>(base + L.net_first_factor);
     de.factor = reinterpret_cast<const uint64_t*>(base + L.factor);
+    de.graph_owned = reinterpret_cast<const int32_t*>(base + L.graph_owned);
     de.n_graphs = G;
     de.arena = dp.arena;
     double* d_out = reinterpret_cast<double*>(base + L.out);

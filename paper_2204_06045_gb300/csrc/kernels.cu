@@ -1300,7 +1300,7 @@ __global__ void k_epilogue(DevEpilogue de) {
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int net = first; net < last; ++net) s += de.zz[net];
-        de.energies[g] = 0.5 * (double)(last - first) - 0.5 * s;
+        de.energies[g] = 0.5 * (double)de.graph_owned[g] - 0.5 * s;
     }
 }
 

@@ -52,6 +52,7 @@ struct DevEpilogue {
     const int32_t* graph_first_net;  // n_graphs + 1
     const uint32_t* net_first_factor;  // n_nets + 1
     const uint64_t* factor;  // arena element offsets; kFirstFactor marks the first factor of each slice
+    const int32_t* graph_owned;  // n_graphs: networks whose 1/2 the energy counts (all, unless sharded by slice)
     int32_t n_graphs;
     const void* arena;
     double* zz;        // n_nets

@@ -862,6 +862,19 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             net.edge = graphs[g].edge_of((size_t)(i - hp->graph_first_net[g]));
             build_network(graphs[g], cfg.p, net.edge, &net);
             if (cfg.slice_width > 0) slice_network(&net, cfg.slice_width, cfg.max_slice_bits);
+            {
+                const size_t li = (size_t)(i - hp->graph_first_net[g]);
+                if (li < graphs[g].sel_slices.size()) {
+                    net.slices = graphs[g].sel_slices[li];
+                    for (uint32_t s : net.slices)
+                        if (s >= (1u << net.slice_bits)) {
+                            status[i] = QT_EINVAL;  // a slice the network does not have
+                            break;
+                        }
+                    if (status[i] != QT_OK) continue;
+                }
+                if (li < graphs[g].sel_owner.size()) net.owner = graphs[g].sel_owner[li] != 0;
+            }
             std::vector<int> best_order, ord;
             double best_cost = 0, c = 0;
             int best_w = 0, w = 0;
@@ -937,12 +950,14 @@ int layout_plan(HostPlan* hp) {
     hp->op_leaf_sub.clear();
     hp->net_first_factor.assign(1, 0);
     hp->factor.clear();
+    hp->graph_owned.assign(graphs.size(), 0);
     hp->n_slices = 0;
     for (int i = 0; i < n_nets; ++i) {
         const NetPlan& np = hp->nplans[i];
         const Network& net = hp->nets[i];
         // every slice of the network: the same buckets, its own gate entries
-        for (uint32_t sl = 0; sl < (1u << net.slice_bits); ++sl) {
+        for (uint32_t k = 0; k < net.n_emitted(); ++k) {
+            const uint32_t sl = net.slice_at(k);
             const uint32_t base = (uint32_t)hp->buckets.size();
             const size_t root0 = hp->root_bucket.size();
             for (size_t lb = 0; lb < np.buckets.size(); ++lb) {
@@ -1068,6 +1083,8 @@ int layout_plan(HostPlan* hp) {
             hp->n_slices++;
         }
         hp->net_first_factor.push_back((uint32_t)hp->factor.size());
+        if ((int)hp->graph_owned.size() <= net.graph) hp->graph_owned.resize(net.graph + 1, 0);
+        hp->graph_owned[net.graph] += net.owner ? 1 : 0;
         hp->net_first_bucket.push_back((uint32_t)hp->buckets.size());
         hp->net_first_root.push_back((uint32_t)hp->root_bucket.size());
         hp->net_graph.push_back((uint32_t)net.graph);

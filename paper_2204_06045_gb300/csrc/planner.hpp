@@ -39,6 +39,10 @@ struct Network {
     int slice_bits = 0;
     std::vector<int> fixed_vars;
     std::vector<FixedLeaf> fixed;
+    std::vector<uint32_t> slices;  // the slices this plan contracts, increasing (empty: all)
+    bool owner = true;             // the plan counts the network's 1/2 in the energy (sharded slices: one plan does)
+    uint32_t n_emitted() const { return slices.empty() ? (1u << slice_bits) : (uint32_t)slices.size(); }
+    uint32_t slice_at(uint32_t k) const { return slices.empty() ? k : slices[k]; }
 };
 
 struct HOperand {
@@ -72,6 +76,10 @@ struct GraphIn {
     int n = 0;
     std::vector<std::pair<int, int>> edges;
     std::vector<int> sel;  // edges whose networks are planned; empty: every edge
+    // per planned network (parallel to sel): the slices to contract (empty:
+    // all) and whether this plan counts the network's 1/2 in the energy
+    std::vector<std::vector<uint32_t>> sel_slices;
+    std::vector<uint8_t> sel_owner;
     size_t n_nets() const { return sel.empty() ? edges.size() : sel.size(); }
     int edge_of(size_t i) const { return sel.empty() ? (int)i : sel[i]; }
 };
@@ -120,6 +128,7 @@ struct HostPlan {
     // the product of the slice's factors (root results and fixed gate entries)
     std::vector<uint32_t> net_first_factor;  // n_nets + 1
     std::vector<uint64_t> factor;
+    std::vector<int32_t> graph_owned;        // per graph: networks whose 1/2 the energy counts
     uint64_t n_slices = 0;               // slices over all networks (1 per unsliced network)
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
     std::vector<URec> unit_prog;        // fused units' programs, unit by unit (padded by kURecWindow records)

@@ -137,3 +137,28 @@ def test_sliced_plan_without_device_allocation():
     ref = oracle.sv_zz(n, edges, g, b)
     assert scaled_err(zz, ref) <= TOL["c128"]
     assert abs(energies[0] - oracle.energy_from_zz(ref)) <= TOL["c128"] * abs(energies[0])
+
+
+def test_slice_shards_add_up_to_the_full_plan():
+    """qt_plan_shard with slicing: the ranks' plans (run one after another on
+    this GPU) hold subsets of the networks' slices; their per-edge values and
+    partial energies (the rank holding slice 0 counts the edge's 1/2) add up to
+    the unsharded plan's."""
+    n, seed, p, world = 16, 23, 3, 3
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype="c128", slice_width=8) as full:
+        zz_full, E_full = full.energy(g, b)
+    zz_sum = np.zeros(edges.shape[0])
+    E_sum = 0.0
+    holders = np.zeros(edges.shape[0], dtype=int)
+    for r in range(world):
+        with qtgb.plan_shard(n, edges, p, world, r, dtype="c128", slice_width=8) as pl:
+            mine = pl.shard_edges
+            zz, E = pl.energy(g, b)
+        zz_sum[mine] += zz
+        holders[mine] += 1
+        E_sum += E
+    assert holders.max() > 1  # some network's slices are spread over ranks
+    np.testing.assert_allclose(zz_sum, zz_full, rtol=0, atol=1e-10)
+    assert abs(E_sum - E_full) <= 1e-10 * abs(E_full)

@@ -52,7 +52,7 @@ def test_two_gloo_ranks_take_the_slowest_time_and_count_every_rank():
     build.build()
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -102,7 +102,7 @@ def test_sharded_energy_over_gloo_ranks_matches_oracle():
     build.build()
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_shard_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -118,4 +118,64 @@ def test_sharded_energy_over_gloo_ranks_matches_oracle():
     for r in range(world):
         np.testing.assert_allclose(res[r][1], zz[res[r][0]], atol=1e-12)
     costs = [res[r][3] for r in range(world)]
+    assert max(costs) <= 1.5 * min(costs)
+
+
+def _slice_shard_rank(rank, world, port, out):
+    """One rank's units (network slices) of a sliced graph, contracted with the
+    test-side evaluator; per-edge partial values summed over ranks."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, str(ROOT))
+    sys.path.insert(0, str(ROOT / "tests"))
+    from plan_eval import evaluate
+    from paper_2204_06045_gb300 import qtgb, synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n, p = 14, 3
+        edges = synth.random_regular_graph(n, 22)
+        g, b = synth.angles(p, 22)
+        dense = torch.zeros(edges.shape[0], dtype=torch.float64)
+        units = []
+        with qtgb.plan_shard(n, edges, p, world, rank, host_only=True, slice_width=7) as pl:
+            mine = pl.shard_edges
+            cost = float(pl.stats()["sum_2w"])
+            if mine.size:
+                B, O = pl.export()
+                zz = evaluate(B, O, g, b, fixed=pl.export_fixed()).real
+                dense[torch.as_tensor(mine, dtype=torch.long)] = torch.as_tensor(zz)
+                units = sorted({(int(mine[net]), int(s)) for net, s in zip(B["network"], B["slice"])})
+        dist.all_reduce(dense, op=dist.ReduceOp.SUM)
+        out[rank] = (units, dense.tolist(), cost)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sliced_networks_sharded_over_gloo_ranks_match_oracle():
+    """§8(e) balance with slicing: the units are network slices, so one wide
+    network's slices may sit on several ranks; each rank's value for an edge
+    is the sum over its slices, and the sum over ranks is the oracle's e_jk.
+    Every slice of every network is held by exactly one rank."""
+    import oracle
+    from paper_2204_06045_gb300 import build, qtgb, synth
+    build.build()
+    world = 3
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_slice_shard_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    n, p = 14, 3
+    edges = synth.random_regular_graph(n, 22)
+    g, b = synth.angles(p, 22)
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=7) as full:
+        B, _ = full.export()
+    want = sorted({(int(e), int(s)) for e, s in zip(B["network"], B["slice"])})
+    held = sorted(u for r in range(world) for u in res[r][0])
+    assert held == want  # a partition of all (edge, slice) units
+    split = {e for e, _ in want if len({r for r in range(world) for (e2, _) in res[r][0] if e2 == e}) > 1}
+    assert split, "some network's slices sit on more than one rank"
+    zz = oracle.sv_zz(n, edges, g, b)
+    for r in range(world):
+        np.testing.assert_allclose(res[r][1], zz, atol=1e-12)
+    costs = [res[r][2] for r in range(world)]
     assert max(costs) <= 1.5 * min(costs)
