@@ -506,9 +506,10 @@ def run_c3(args, world, local_rank):
     G = np.array([g for _, _, g, _ in graphs])
     Bt = np.array([b for _, _, _, b in graphs])
     res = {}
-    for dtype, sched, steps in (("c64", "persistent", args.steps), ("c128", "persistent", args.steps),
-                                ("c128", "per_bucket", 1)):
-        with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], 3, dtype=dtype, sched=sched) as pl:
+    for dtype, sched, steps, dedup in (("c64", "persistent", args.steps, False),
+                                       ("c128", "persistent", args.steps, False), ("c128", "per_bucket", 1, False),
+                                       ("c64", "persistent", args.steps, True)):
+        with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], 3, dtype=dtype, sched=sched, dedup=dedup) as pl:
             st = pl.stats()
             gd = torch.tensor(G.ravel(), dtype=torch.float64, device="cuda")
             bd = torch.tensor(Bt.ravel(), dtype=torch.float64, device="cuda")
@@ -525,8 +526,9 @@ def run_c3(args, world, local_rank):
             e1.record(s)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
-            res[f"{dtype}_{sched}"] = {"ms_per_step": ms, "graph_evals_per_s": 64 / (ms * 1e-3), "steps": steps,
-                                       "buckets": st["n_buckets"], "alg_bytes": st["alg_bytes"]}
+            res[f"{dtype}_{sched}" + ("_dedup" if dedup else "")] = {
+                "ms_per_step": ms, "graph_evals_per_s": 64 / (ms * 1e-3), "steps": steps,
+                "buckets": st["n_buckets"], "alg_bytes": st["alg_bytes"], "networks_contracted": st["n_unique"]}
     # accuracy: 64 seeded sample edges against the oracle's bucket elimination of their networks
     import oracle
     rng = np.random.default_rng(7)
@@ -550,7 +552,10 @@ def run_c3(args, world, local_rank):
             "config": {"workload": "64 seeded random 3-regular graphs, N uniform even in [50,1000] (synth.batch), "
                                    "p=3, per-graph angles; every edge's lightcone network in one persistent launch"},
             "plain_c128_per_bucket": res["c128_per_bucket"], "c128_persistent": res["c128_persistent"],
-            "speedup_vs_plain_c128": res["c128_per_bucket"]["ms_per_step"] / main["ms_per_step"], "check": check}
+            "speedup_vs_plain_c128": res["c128_per_bucket"]["ms_per_step"] / main["ms_per_step"], "check": check,
+            "c64_dedup": dict(res["c64_persistent_dedup"],
+                              note="opts.dedup: one network per isomorphism class of tree lightcones per graph "
+                                   "(off in the main line)")}
     print(json.dumps(line), flush=True)
 
 

@@ -109,6 +109,11 @@ typedef struct {
                               2..31: the target; 0: the default target (22 complex64, 20 complex128);
                               -1: no slicing. Forward plans only (gradient plans are never sliced) */
     int32_t max_slice_bits;/* most variables fixed per network (1..16); 0: 8 */
+    int32_t dedup;         /* nonzero: lightcone deduplication. Within each graph, networks whose
+                              lightcones are isomorphic trees (the qubits within distance p of the
+                              edge, labelled by distance) are contracted once: the others take that
+                              network's value. Forward plans only (ignored with gradients or slice
+                              shards). 0: every network is contracted */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -141,6 +146,7 @@ typedef struct {
     int32_t n_passes;       /* gradient plans over opts.adjoint_budget_bytes: passes over the networks */
     int32_t slice_bits;     /* most variables fixed in any one network (opts.slice_width) */
     int64_t n_slices;       /* slices over all networks (1 per network without slicing) */
+    int64_t n_unique;       /* networks contracted (opts.dedup: the others share their values) */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */
@@ -194,6 +200,10 @@ typedef struct {
     int32_t entry;
     int32_t pad;
 } qt_fixed_info;
+
+/* Lightcone deduplication (host-side inspection): rep[i] = the network whose
+ * value network i takes (i itself when it is contracted); n_networks int32. */
+int qt_plan_export_reps(qt_plan_t plan, int32_t *rep);
 
 /* The fixed gate entries of every slice (host-side inspection). `out` holds
  * at least *n_out entries on entry, or is NULL to ask for the count; *n_out

@@ -663,6 +663,7 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     const int sw = o.slice_width == 0 ? (o.dtype == QT_C128 ? 20 : 22) : std::max(0, o.slice_width);
     cfg.slice_width = cfg.with_grad ? 0 : sw;  // the reverse sweep takes unsliced networks
     cfg.max_slice_bits = o.max_slice_bits ? o.max_slice_bits : 8;
+    cfg.dedup = o.dedup != 0 && !cfg.with_grad;
     for (int c = 0; c < qt::kWidthClasses; ++c) {
         if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
         cfg.tile_cap[c] = o.tile_cap[c];
@@ -733,6 +734,7 @@ int qt_plan_shard(int32_t n_vertices, int32_t n_edges, const int32_t* edges, int
     qt_plan_opts ho = opts ? *opts : default_opts();
     ho.host_only = 1;
     ho.autotune = 0;
+    ho.dedup = 0;  // every network's own cost (a shard deduplicates within itself)
     qt_plan_t full = nullptr;
     int rc = qt_plan(n_vertices, n_edges, edges, p, &ho, &full);
     if (rc != QT_OK) return rc;
@@ -831,6 +833,7 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     out->slice_bits = 0;
     for (const qt::Network& net : hp.nets) out->slice_bits = std::max(out->slice_bits, (int32_t)net.slice_bits);
     out->n_slices = (int64_t)hp.n_slices;
+    out->n_unique = (int64_t)hp.n_unique;
     return QT_OK;
 }
 
@@ -880,6 +883,12 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
             for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) operands[i].mask >>= m;
         }
     }
+    return QT_OK;
+}
+
+int qt_plan_export_reps(qt_plan_t P, int32_t* rep) {
+    if (!P || !rep) return QT_EINVAL;
+    for (size_t i = 0; i < P->hp.nets.size(); ++i) rep[i] = P->hp.nets[i].rep >= 0 ? P->hp.nets[i].rep : (int32_t)i;
     return QT_OK;
 }
 

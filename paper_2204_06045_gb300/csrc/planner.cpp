@@ -9,7 +9,9 @@
 #include <cmath>
 #include <queue>
 #include <set>
+#include <string>
 #include <thread>
+#include <unordered_map>
 
 #include "../../include/qt.h"
 
@@ -203,6 +205,62 @@ static void order_min_fill(const Network& net, bool randomized, uint64_t seed, s
         std::fill(row(v), row(v) + W, 0ull);
         alive[v >> 6] &= ~(1ull << (v & 63));
     }
+}
+
+// ---------------------------------------------------------------------------
+// Lightcone deduplication. A network is fixed by its lightcone: the qubits
+// within distance p of the edge, labelled by that distance, and the graph
+// edges with an endpoint within distance p - 1 (the gates A1/A2 place). Two
+// edges of one graph with isomorphic lightcones give the same network up to
+// the names of its variables, so the same <Z_jZ_k> at the graph's angles.
+// For a lightcone that is a tree the key below is canonical: the AHU encoding
+// of the tree hanging from the edge (each vertex: its children's encodings,
+// sorted), so equal keys mean isomorphic lightcones and isomorphic tree
+// lightcones get equal keys. A lightcone with a cycle gets no key (its
+// network is always contracted).
+// ---------------------------------------------------------------------------
+static std::string lightcone_key(const std::vector<std::vector<int>>& nbr, int p, int j, int k) {
+    const int n = (int)nbr.size();
+    std::vector<int> dist(n, -1), seen;
+    std::queue<int> bfs;
+    dist[j] = dist[k] = 0;
+    bfs.push(j);
+    bfs.push(k);
+    seen.push_back(j);
+    seen.push_back(k);
+    while (!bfs.empty()) {
+        const int a = bfs.front();
+        bfs.pop();
+        if (dist[a] == p) continue;
+        for (int b : nbr[a])
+            if (dist[b] < 0) {
+                dist[b] = dist[a] + 1;
+                bfs.push(b);
+                seen.push_back(b);
+            }
+    }
+    // the lightcone's edges: both ends within distance p, one within p - 1
+    size_t n_edges = 0;
+    for (int a : seen)
+        for (int b : nbr[a])
+            if (a < b && dist[b] >= 0 && std::min(dist[a], dist[b]) <= p - 1) ++n_edges;
+    if (n_edges + 1 != seen.size()) return std::string();  // a cycle: no key
+    // encodings bottom-up: vertices in decreasing distance
+    std::vector<std::string> enc(n);
+    std::vector<int> order(seen.begin(), seen.end());
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dist[a] > dist[b]; });
+    for (int v : order) {
+        std::vector<const std::string*> kids;
+        for (int u : nbr[v])
+            if (dist[u] == dist[v] + 1 && dist[v] <= p - 1 && !(dist[v] == 0 && (u == j || u == k)))
+                kids.push_back(&enc[u]);
+        std::sort(kids.begin(), kids.end(), [](const std::string* a, const std::string* b) { return *a < *b; });
+        std::string s = "(";
+        for (const std::string* c : kids) s += *c;
+        s += ")";
+        enc[v] = std::move(s);
+    }
+    return std::min(enc[j], enc[k]) + "|" + std::max(enc[j], enc[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -850,6 +908,43 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
     hp->nets.assign(n_nets, Network());
     hp->nplans.assign(n_nets, NetPlan());
     std::vector<int> status(n_nets, QT_OK);
+    std::vector<int> rep(n_nets, -1);
+    if (cfg.dedup) {
+        // keys in parallel, then per graph the first network of each key is contracted
+        std::vector<std::string> key(n_nets);
+        std::vector<std::vector<std::vector<int>>> nbr(graphs.size());
+        for (size_t g = 0; g < graphs.size(); ++g) {
+            nbr[g].assign(graphs[g].n, {});
+            for (auto& e : graphs[g].edges) {
+                nbr[g][e.first].push_back(e.second);
+                nbr[g][e.second].push_back(e.first);
+            }
+        }
+        std::atomic<int> nk{0};
+        auto keyer = [&]() {
+            for (;;) {
+                const int i = nk.fetch_add(1);
+                if (i >= n_nets) break;
+                const int g = (int)(std::upper_bound(hp->graph_first_net.begin(), hp->graph_first_net.end(), i) -
+                                    hp->graph_first_net.begin()) - 1;
+                const auto& ed = graphs[g].edges[graphs[g].edge_of((size_t)(i - hp->graph_first_net[g]))];
+                key[i] = lightcone_key(nbr[g], cfg.p, ed.first, ed.second);
+            }
+        };
+        const unsigned nt = std::max(1u, std::min({std::thread::hardware_concurrency(), 64u, (unsigned)n_nets}));
+        std::vector<std::thread> kp;
+        for (unsigned t = 0; t + 1 < nt; ++t) kp.emplace_back(keyer);
+        keyer();
+        for (auto& th : kp) th.join();
+        for (size_t g = 0; g < graphs.size(); ++g) {
+            std::unordered_map<std::string, int> first;
+            for (int i = hp->graph_first_net[g]; i < hp->graph_first_net[g + 1]; ++i) {
+                if (key[i].empty() || !graphs[g].sel_slices.empty()) continue;  // cycles, and slice shards: contracted
+                auto it = first.emplace(key[i], i);
+                if (!it.second) rep[i] = it.first->second;
+            }
+        }
+    }
     std::atomic<int> next{0};
     auto worker = [&]() {
         for (;;) {
@@ -861,6 +956,8 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             net.graph = g;
             net.edge = graphs[g].edge_of((size_t)(i - hp->graph_first_net[g]));
             build_network(graphs[g], cfg.p, net.edge, &net);
+            net.rep = rep[i];
+            if (net.rep >= 0) continue;  // takes its representative's value: nothing to plan
             if (cfg.slice_width > 0) slice_network(&net, cfg.slice_width, cfg.max_slice_bits);
             {
                 const size_t li = (size_t)(i - hp->graph_first_net[g]);
@@ -951,12 +1048,20 @@ int layout_plan(HostPlan* hp) {
     hp->net_first_factor.assign(1, 0);
     hp->factor.clear();
     hp->graph_owned.assign(graphs.size(), 0);
+    hp->n_unique = 0;
     hp->n_slices = 0;
     for (int i = 0; i < n_nets; ++i) {
         const NetPlan& np = hp->nplans[i];
         const Network& net = hp->nets[i];
+        if (net.rep >= 0) {
+            // the representative's value: its factor list (it comes earlier)
+            for (uint32_t f = hp->net_first_factor[net.rep]; f < hp->net_first_factor[net.rep + 1]; ++f) {
+                const uint64_t w = hp->factor[f];
+                hp->factor.push_back(w);
+            }
+        }
         // every slice of the network: the same buckets, its own gate entries
-        for (uint32_t k = 0; k < net.n_emitted(); ++k) {
+        for (uint32_t k = 0; k < (net.rep >= 0 ? 0u : net.n_emitted()); ++k) {
             const uint32_t sl = net.slice_at(k);
             const uint32_t base = (uint32_t)hp->buckets.size();
             const size_t root0 = hp->root_bucket.size();
@@ -1082,6 +1187,7 @@ int layout_plan(HostPlan* hp) {
             }
             hp->n_slices++;
         }
+        hp->n_unique += net.rep < 0 ? 1 : 0;
         hp->net_first_factor.push_back((uint32_t)hp->factor.size());
         if ((int)hp->graph_owned.size() <= net.graph) hp->graph_owned.resize(net.graph + 1, 0);
         hp->graph_owned[net.graph] += net.owner ? 1 : 0;

@@ -41,6 +41,8 @@ struct Network {
     std::vector<FixedLeaf> fixed;
     std::vector<uint32_t> slices;  // the slices this plan contracts, increasing (empty: all)
     bool owner = true;             // the plan counts the network's 1/2 in the energy (sharded slices: one plan does)
+    int rep = -1;                  // lightcone deduplication: the earlier network of the same graph whose
+                                   // value this one takes (it is not contracted); -1: contracted itself
     uint32_t n_emitted() const { return slices.empty() ? (1u << slice_bits) : (uint32_t)slices.size(); }
     uint32_t slice_at(uint32_t k) const { return slices.empty() ? k : slices[k]; }
 };
@@ -98,6 +100,7 @@ struct PlanConfig {
     bool fuse = false;       // form fused units of small subtrees (persistent energy plans)
     int tile_cap[kWidthClasses] = {0, 0, 0, 0, 0};  // most tile bits per bucket-width class (0: chunk_log2 / default)
     bool merge = false;      // merge chains of eliminations (a bucket and the parent that only extends it)
+    bool dedup = false;      // contract one network per isomorphism class of tree lightcones (per graph)
     int slice_width = 0;     // > 0: slice networks whose greedy width exceeds it (forward plans)
     int max_slice_bits = 0;  // most variables fixed per network
 };
@@ -130,6 +133,7 @@ struct HostPlan {
     std::vector<uint64_t> factor;
     std::vector<int32_t> graph_owned;        // per graph: networks whose 1/2 the energy counts
     uint64_t n_slices = 0;               // slices over all networks (1 per unsliced network)
+    uint64_t n_unique = 0;               // networks contracted (the others take a representative's value)
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)
     std::vector<URec> unit_prog;        // fused units' programs, unit by unit (padded by kURecWindow records)
     uint64_t n_units = 0;

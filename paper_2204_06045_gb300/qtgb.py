@@ -23,7 +23,8 @@ LEAF_KINDS = ("plus", "zobs", "zz", "zz_conj", "rx", "rx_conj")
 EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "qt_plan_export", "qt_plan_network_wires",
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
-           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed")
+           "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed",
+           "qt_plan_export_reps")
 
 
 class QTError(RuntimeError):
@@ -42,7 +43,7 @@ class PlanOpts(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("no_fuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("tile_cap", ctypes.c_int8 * 8), ("no_merge", ctypes.c_int32), ("adjoint_budget_bytes", ctypes.c_size_t),
-                ("slice_width", ctypes.c_int32), ("max_slice_bits", ctypes.c_int32)]
+                ("slice_width", ctypes.c_int32), ("max_slice_bits", ctypes.c_int32), ("dedup", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -54,7 +55,8 @@ class PlanStats(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("sim_seconds", ctypes.c_double),
                 ("n_units", ctypes.c_int64), ("n_fused", ctypes.c_int64), ("tile_cap", ctypes.c_int32 * 8),
                 ("run_tiles", ctypes.c_int32), ("tune_seconds", ctypes.c_double), ("tune_candidates", ctypes.c_int32),
-                ("n_passes", ctypes.c_int32), ("slice_bits", ctypes.c_int32), ("n_slices", ctypes.c_int64)]
+                ("n_passes", ctypes.c_int32), ("slice_bits", ctypes.c_int32), ("n_slices", ctypes.c_int64),
+                ("n_unique", ctypes.c_int64)]
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
@@ -103,6 +105,7 @@ def lib():
         L.qt_fma_peak.argtypes = [i32, dp]
         L.qt_plan_export_groups.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_export_fixed.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        L.qt_plan_export_reps.argtypes = [vp, i32p]
         L.qt_plan_shard.argtypes = [i32, i32, i32p, i32, i32, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp), i32p,
                                     i32p]
         L.qt_last_imag.argtypes = [vp, dp]
@@ -122,7 +125,7 @@ def lib():
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
                      "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard",
-                     "qt_plan_export_fixed"):
+                     "qt_plan_export_fixed", "qt_plan_export_reps"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -190,7 +193,7 @@ class Plan:
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
               order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=True,
-              slice_width=0, max_slice_bits=0):
+              slice_width=0, max_slice_bits=0, dedup=False):
         # slice_width: 0 the library's default target, -1 no slicing
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
@@ -212,6 +215,7 @@ class Plan:
         o.no_merge = 0 if merge else 1
         o.slice_width = int(slice_width)
         o.max_slice_bits = int(max_slice_bits)
+        o.dedup = 1 if dedup else 0
         for i, c in enumerate(tile_cap or []):
             o.tile_cap[i] = int(c)
         return o
@@ -319,6 +323,13 @@ class Plan:
         cnt = ctypes.c_int64(0)
         _check(lib().qt_plan_export_groups(self._h, out.ctypes.data, ctypes.byref(cnt)), "qt_plan_export_groups")
         return out[:cnt.value]
+
+    def export_reps(self) -> np.ndarray:
+        """Per network, the network whose value it takes (itself when contracted)."""
+        out = np.zeros(max(1, self.stats()["n_networks"]), dtype=np.int32)
+        _check(lib().qt_plan_export_reps(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+               "qt_plan_export_reps")
+        return out[:self.stats()["n_networks"]]
 
     def export_fixed(self) -> np.ndarray:
         """Fixed gate entries of every slice (network, slice, leaf_kind, leaf_layer, entry)."""

@@ -539,3 +539,44 @@ def test_slicing_options():
         with qtgb.plan(30, e30, 4, host_only=True, dtype=dtype) as pl:
             st = pl.stats()
         assert st["slice_bits"] > 0 and st["max_width"] <= target
+
+
+@pytest.mark.parametrize("n,seed,p", [(20, 3, 1), (60, 3, 2), (100, 7, 3)])
+def test_deduplicated_networks_take_their_representatives_values(n, seed, p):
+    """opts.dedup: networks whose lightcones are isomorphic trees are
+    contracted once. Every network's value (its representative's) equals its
+    own contraction in the full plan; representatives come first and are
+    contracted; duplicates have no buckets."""
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with host_plan(n, edges, p, dedup=True) as pl:
+        B, O = pl.export()
+        F = pl.export_fixed()
+        R = pl.export_reps()
+        st = pl.stats()
+    with host_plan(n, edges, p) as pl:
+        B0, O0 = pl.export()
+        st0 = pl.stats()
+    assert st["n_unique"] < st["n_networks"] == edges.shape[0] and st0["n_unique"] == st0["n_networks"]
+    assert st["n_buckets"] < st0["n_buckets"]
+    reps = np.unique(R)
+    assert (R <= np.arange(R.size)).all() and (R[reps] == reps).all() and reps.size == st["n_unique"]
+    assert set(np.unique(B["network"]).tolist()) == set(reps.tolist())
+    vals = evaluate(B, O, g, b, fixed=F)
+    mine = np.array([vals[R[i]] for i in range(R.size)])
+    full = evaluate(B0, O0, g, b)
+    np.testing.assert_allclose(mine, full, rtol=0, atol=1e-12)
+    if n <= 20:
+        np.testing.assert_allclose(mine.real, oracle.sv_zz(n, edges, g, b), rtol=0, atol=1e-12)
+
+
+def test_dedup_stays_within_a_graph_and_off_for_gradients():
+    graphs = [(40, synth.random_regular_graph(40, 1)), (40, synth.random_regular_graph(40, 2))]
+    with qtgb.plan_batch(graphs, 2, host_only=True, dedup=True, slice_width=-1) as pl:
+        R = pl.export_reps()
+    m0 = graphs[0][1].shape[0]
+    assert (R[:m0] < m0).all() and (R[m0:] >= m0).all()  # no sharing across graphs (their angles differ)
+    assert len(np.unique(R[:m0])) < m0 and len(np.unique(R[m0:])) < R.size - m0
+    with host_plan(40, graphs[0][1], 2, dedup=True, with_grad=True) as pl:
+        st = pl.stats()
+    assert st["n_unique"] == st["n_networks"]
