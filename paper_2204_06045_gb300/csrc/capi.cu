@@ -271,11 +271,6 @@ int upload(qt_plan_t P) {
     }
     if (hp.cfg.with_grad) {
         // op_param | net_graph | task buckets | task tiles | op_bwd | op_roff | zero ranges
-        struct Piece {
-            const void* src;
-            size_t bytes;
-            size_t off;
-        };
         Piece pc[7] = {{hp.op_param.data(), bytes_of(hp.op_param), 0},   {hp.net_graph.data(), bytes_of(hp.net_graph), 0},
                        {hp.bwd_bucket.data(), bytes_of(hp.bwd_bucket), 0}, {hp.bwd_tile.data(), bytes_of(hp.bwd_tile), 0},
                        {hp.op_bwd.data(), bytes_of(hp.op_bwd), 0},         {hp.op_roff.data(), bytes_of(hp.op_roff), 0},

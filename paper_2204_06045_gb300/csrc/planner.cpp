@@ -1167,9 +1167,9 @@ int layout_plan(HostPlan* hp) {
                     // bucket of its earliest summed variable
                     double n_k[4] = {0, 0, 0, 0};
                     for (const HOperand& op : B.ops) n_k[__builtin_ctz(op.smask)] += 1;
-                    for (int k = 0; k < B.n_sum; ++k)
-                        hp->flops += std::ldexp(1.0, B.width - k) * 6.0 * (n_k[k] - (k == 0 ? 1 : 0)) +
-                                     std::ldexp(1.0, B.width - k - 1) * 2.0;
+                    for (int v = 0; v < B.n_sum; ++v)
+                        hp->flops += std::ldexp(1.0, B.width - v) * 6.0 * (n_k[v] - (v == 0 ? 1 : 0)) +
+                                     std::ldexp(1.0, B.width - v - 1) * 2.0;
                 }
             }
             // the slice's factors of the network's value: its root results,
