@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
-    ap.add_argument("--workload", choices=["c2", "c3", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "einsum"], default="c2",
                     help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5); "
-                         "c3: 64-graph batch; c5: gradients on N=50 p=4")
+                         "c3: 64-graph batch; c5: gradients on N=50 p=4; einsum: the wide N=1000 p=5 buckets, "
+                         "this kernel against torch.einsum on the same contractions")
     ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the plan-time autotuner's line")
     ap.add_argument("--shard", action="store_true",
@@ -355,6 +356,77 @@ def wide_buckets(peak, torch):
                                           "note": "the same networks with the default plan: merged eliminations and "
                                                   "index slicing"}
     return out
+
+
+_LETTERS = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+
+
+def bucket_einsum(B, O, k):
+    """einsum subscripts and operand shapes of bucket k of an exported plan
+    (a plain bucket: one summed variable). An operand's entry for output o and
+    summed value x is at 2 * pext(o, mask) + x, so in C order its dimensions
+    are its output bits from the highest down, then x; the output's are its
+    bits from the highest down."""
+    n_out = int(B["width"][k]) - int(B["n_sum"][k])
+    if int(B["n_sum"][k]) != 1 or n_out + 1 > len(_LETTERS):
+        raise ValueError("a plain bucket of at most 51 output bits")
+    out = _LETTERS[:n_out]
+    x = _LETTERS[n_out]
+    subs, shapes = [], []
+    for t in range(int(B["op_begin"][k]), int(B["op_begin"][k]) + int(B["n_ops"][k])):
+        bits = [i for i in range(n_out) if (int(O["mask"][t]) >> i) & 1]
+        subs.append("".join(out[i] for i in reversed(bits)) + x)
+        shapes.append((2,) * (len(bits) + 1))
+    return ",".join(subs) + "->" + out[::-1], shapes
+
+
+def run_einsum(args, world, local_rank):
+    """NEXT-4 comparison point: every bucket of width >= 24 of the 15 widest
+    N=1000 p=5 networks (plain buckets), timed alone in the persistent kernel
+    (qt_bucket_time) and as torch.einsum on random complex64 tensors of the
+    same shapes on the same GPU (CUDA events, mean of 3 after 1)."""
+    import torch
+    from paper_2204_06045_gb300 import build, qtgb, synth
+    torch.cuda.set_device(local_rank)
+    build.build()
+    n, p, seed = 1000, 5, 1000
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
+        B0, _ = hp.export()
+    mw = np.zeros(edges.shape[0], dtype=np.int64)
+    np.maximum.at(mw, B0["network"], B0["width"])
+    sel = np.nonzero((mw >= 26) & (mw <= 28))[0]
+    rows = []
+    with qtgb.plan_subset(n, edges, p, sel, dtype="c64", merge=False, slice_width=-1) as pl:
+        pl.energy(g, b)
+        B, O = pl.export()
+        for k in np.nonzero(B["width"] >= 24)[0]:
+            ms_ours, by = pl.bucket_time(int(k), reps=3)
+            spec, shapes = bucket_einsum(B, O, int(k))
+            ops = [torch.randn(sh, dtype=torch.complex64, device="cuda") for sh in shapes]
+            torch.einsum(spec, *ops)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                torch.einsum(spec, *ops)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_lib = e0.elapsed_time(e1) / 3
+            del ops
+            rows.append({"bucket": int(k), "width": int(B["width"][k]), "n_ops": int(B["n_ops"][k]),
+                         "alg_bytes": by, "ms": ms_ours, "einsum_ms": ms_lib})
+    ours = sum(r["ms"] for r in rows)
+    lib = sum(r["einsum_ms"] for r in rows)
+    line = {"metric": "wide-bucket contraction time, this kernel vs torch.einsum (N=1000 p=5, width >= 24)",
+            "value": lib / ours, "unit": "x (einsum time / this kernel's)", "n_gpus": 1, "steps": 3, "warmup": 1,
+            "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"{len(rows)} plain buckets of width >= 24 of the 15 networks of greedy width "
+                                   "26..28, random 3-regular N=1000 seed 1000, p=5"},
+            "ms": ours, "einsum_ms": lib, "agg_gbs": sum(r["alg_bytes"] for r in rows) / ours / 1e6,
+            "buckets": rows}
+    print(json.dumps(line), flush=True)
 
 
 def time_device(pl, gd, bd, zz, E, steps, warmup, dist, torch):
@@ -667,6 +739,9 @@ def main():
     elif args.workload == "c5":
         if rank == 0:
             run_c5(args, world, local_rank)
+    elif args.workload == "einsum":
+        if rank == 0:
+            run_einsum(args, world, local_rank)
     elif args.shard:
         run_shard(args, rank, world, local_rank)
     else:

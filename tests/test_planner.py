@@ -580,3 +580,36 @@ def test_dedup_stays_within_a_graph_and_off_for_gradients():
     with host_plan(40, graphs[0][1], 2, dedup=True, with_grad=True) as pl:
         st = pl.stats()
     assert st["n_unique"] == st["n_networks"]
+
+
+def test_bucket_einsum_spec_is_the_contraction():
+    """bench.bucket_einsum (the subscripts the library-einsum comparison runs):
+    numpy.einsum over random operands reshaped by it equals the bucket
+    contraction out[o] = sum_x prod_t T_t[2 pext(o, M_t) + x] (§II-B)."""
+    import sys
+    sys.path.insert(0, str(Path(__file__).resolve().parents[1]))
+    import bench
+    from plan_eval import pext
+    n, seed, p = 14, 22, 3
+    edges = synth.random_regular_graph(n, seed)
+    with host_plan(n, edges, p, merge=False) as pl:
+        B, O = pl.export()
+    rng = np.random.default_rng(0)
+    checked = 0
+    for k in range(len(B)):
+        if B["width"][k] > 12:
+            continue
+        spec, shapes = bench.bucket_einsum(B, O, k)
+        flat = [rng.standard_normal(2 ** len(sh)) + 1j * rng.standard_normal(2 ** len(sh)) for sh in shapes]
+        got = np.einsum(spec, *[f.reshape(sh) for f, sh in zip(flat, shapes)]).reshape(-1)
+        n_out = int(B["width"][k]) - 1
+        o = np.arange(1 << n_out, dtype=np.int64)
+        want = np.zeros(1 << n_out, dtype=complex)
+        for x in (0, 1):
+            prod = np.ones(1 << n_out, dtype=complex)
+            for t, f in zip(range(int(B["op_begin"][k]), int(B["op_begin"][k]) + int(B["n_ops"][k])), flat):
+                prod = prod * f[2 * pext(o, int(O["mask"][t])) + x]
+            want += prod
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+        checked += 1
+    assert checked > 50
