@@ -112,8 +112,13 @@ typedef struct {
     int32_t dedup;         /* nonzero: lightcone deduplication. Within each graph, networks whose
                               lightcones are isomorphic trees (the qubits within distance p of the
                               edge, labelled by distance) are contracted once: the others take that
-                              network's value. Forward plans only (ignored with gradients or slice
-                              shards). 0: every network is contracted */
+                              network's value. Forward plans only (ignored with gradients, slice
+                              shards or energy_budget_bytes). 0: every network is contracted */
+    size_t energy_budget_bytes; /* energy plans (single graph): device bytes for the gate tables and
+                              results; a plan that needs more runs in passes that fit, over the
+                              networks' slices (opts.slice_width), on one shared arena; per-edge values
+                              and the energy are summed over passes; a slice that alone exceeds it
+                              gives QT_ENOMEM. 0: no budget */
 } qt_plan_opts;
 
 /* Plan statistics. Widths count the summed index (inclusive); a bucket of
@@ -143,10 +148,13 @@ typedef struct {
     int32_t run_tiles;      /* most tiles per work group in effect */
     double tune_seconds;    /* host time spent autotuning (0 without opts.autotune) */
     int32_t tune_candidates;/* configurations the autotuner laid out and timed */
-    int32_t n_passes;       /* gradient plans over opts.adjoint_budget_bytes: passes over the networks */
+    int32_t n_passes;       /* plans over opts.adjoint_budget_bytes (gradients, passes over networks) or
+                               opts.energy_budget_bytes (energies, passes over slices); 1 otherwise */
     int32_t slice_bits;     /* most variables fixed in any one network (opts.slice_width) */
     int64_t n_slices;       /* slices over all networks (1 per network without slicing) */
     int64_t n_unique;       /* networks contracted (opts.dedup: the others share their values) */
+    int64_t pass_arena_bytes; /* plans in passes: device bytes of the arena the passes share (the
+                               largest pass); 0 otherwise */
 } qt_plan_stats;
 
 /* One bucket of the schedule as seen by host-side inspection (tests). */

@@ -531,39 +531,68 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
 // (with the leaf tables); each pass is a plan of its own, all on one arena of
 // the largest pass's size. A network that alone exceeds the budget is refused
 // (QT_ENOMEM): networks are not split. Single-graph plans only.
+// A plan over a memory budget runs in passes, each a sub-plan of one graph on
+// one shared arena. Gradient plans pass over whole networks (results and
+// their cotangents); energy plans over networks' slices (results only), a
+// pass counting an edge's 1/2 only if it holds the network's slice 0.
 int make_passes(qt_plan_t P, const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_opts& o) {
     const qt::HostPlan& hp = P->hp;
     if (graphs.size() != 1) return QT_ESTATE;
+    const bool grad = hp.cfg.with_grad;
+    const size_t budget = grad ? o.adjoint_budget_bytes : o.energy_budget_bytes;
     const size_t leaf_bytes = (size_t)hp.leaf_elems * P->esize;
-    if (leaf_bytes >= o.adjoint_budget_bytes) return QT_ENOMEM;
-    const size_t room = o.adjoint_budget_bytes - leaf_bytes;
+    if (leaf_bytes >= budget) return QT_ENOMEM;
+    const size_t room = budget - leaf_bytes;
     const qt::GraphIn& g0 = graphs[0];
-    std::vector<int32_t> cur;
+    struct Pass {
+        std::vector<int32_t> edges;
+        std::vector<std::vector<uint32_t>> slices;
+        std::vector<uint8_t> owner;
+    };
+    std::vector<Pass> passes(1);
     size_t cur_bytes = 0;
     for (size_t i = 0; i < hp.nets.size(); ++i) {
-        size_t nb = 0;  // results and their cotangents (128-byte aligned results)
+        const qt::Network& net = hp.nets[i];
+        const uint32_t n_sl = 1u << net.slice_bits;
+        std::vector<size_t> nb(n_sl, 0);  // per slice: results (and cotangents), 128-byte aligned
         for (uint32_t b = hp.net_first_bucket[i]; b < hp.net_first_bucket[i + 1]; ++b)
-            nb += 2 * (((size_t)1 << qt::result_bits(hp.buckets[b])) * P->esize + 128);
-        if (nb > room) return QT_ENOMEM;
-        if (cur_bytes + nb > room && !cur.empty()) {
-            P->part_edges.push_back(cur);
-            cur.clear();
-            cur_bytes = 0;
+            nb[hp.bucket_slice[b]] += (grad ? 2 : 1) * (((size_t)1 << qt::result_bits(hp.buckets[b])) * P->esize + 128);
+        for (uint32_t s = 0; s < n_sl; ++s) {
+            if (nb[s] > room) return QT_ENOMEM;
+            if (cur_bytes + nb[s] > room && !passes.back().edges.empty()) {
+                passes.emplace_back();
+                cur_bytes = 0;
+            }
+            Pass& ps = passes.back();
+            const int32_t e = (int32_t)g0.edge_of(i);
+            if (ps.edges.empty() || ps.edges.back() != e) {
+                ps.edges.push_back(e);
+                ps.slices.emplace_back();
+                ps.owner.push_back(0);
+            }
+            ps.slices.back().push_back(s);
+            if (s == 0) ps.owner.back() = 1;
+            cur_bytes += nb[s];
         }
-        cur.push_back((int32_t)g0.edge_of(i));
-        cur_bytes += nb;
     }
-    if (!cur.empty()) P->part_edges.push_back(cur);
+    if (passes.back().edges.empty()) passes.pop_back();
     qt_plan_opts so = o;
     so.adjoint_budget_bytes = 0;
+    so.energy_budget_bytes = 0;
     so.host_only = 1;
     so.autotune = 0;
+    so.dedup = 0;
     size_t arena = 0;
-    for (const auto& pe : P->part_edges) {
+    for (Pass& ps : passes) {
         std::vector<qt::GraphIn> gs(1);
         gs[0].n = g0.n;
         gs[0].edges = g0.edges;
-        gs[0].sel = pe;
+        gs[0].sel = ps.edges;
+        if (!grad) {
+            gs[0].sel_slices = ps.slices;
+            gs[0].sel_owner = ps.owner;
+        }
+        P->part_edges.push_back(ps.edges);
         qt_plan_t part = nullptr;
         const int rc = make_plan(gs, p, &so, &part);
         if (rc != QT_OK) return rc;
@@ -591,7 +620,10 @@ int make_passes(qt_plan_t P, const std::vector<qt::GraphIn>& graphs, int32_t p, 
 int run_passes(qt_plan_t P, const double* gammas, const double* betas, double* edge_zz, double* energy,
                double* dg, double* db, void* stream, bool grad) {
     const int p = P->hp.cfg.p;
-    const size_t m = P->hp.graphs[0].edges.size();
+    const qt::GraphIn& g0 = P->hp.graphs[0];
+    const size_t m = P->hp.nets.size();  // outputs: one per planned network, in the plan's order
+    std::vector<int64_t> pos(g0.edges.size(), -1);
+    for (size_t i = 0; i < m; ++i) pos[g0.edge_of(i)] = (int64_t)i;
     std::vector<double> g(p), b(p), zz(m, 0.0), gs(p, 0.0), bs(p, 0.0);
     QT_CUDA(cudaMemcpy(g.data(), gammas, sizeof(double) * p, cudaMemcpyDefault));
     QT_CUDA(cudaMemcpy(b.data(), betas, sizeof(double) * p, cudaMemcpyDefault));
@@ -610,7 +642,7 @@ int run_passes(qt_plan_t P, const double* gammas, const double* betas, double* e
                 bs[i] += pb[i];
             }
         }
-        for (size_t i = 0; i < pe.size(); ++i) zz[pe[i]] = pz[i];
+        for (size_t i = 0; i < pe.size(); ++i) zz[pos[pe[i]]] += pz[i];  // energy passes may split a network's slices
         E += pE;
     }
     if (edge_zz) QT_CUDA(cudaMemcpy(edge_zz, zz.data(), sizeof(double) * m, cudaMemcpyDefault));
@@ -658,7 +690,8 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     const int sw = o.slice_width == 0 ? (o.dtype == QT_C128 ? 20 : 22) : std::max(0, o.slice_width);
     cfg.slice_width = cfg.with_grad ? 0 : sw;  // the reverse sweep takes unsliced networks
     cfg.max_slice_bits = o.max_slice_bits ? o.max_slice_bits : 8;
-    cfg.dedup = o.dedup != 0 && !cfg.with_grad;
+    // a duplicate network takes its representative's value within one plan: not across passes
+    cfg.dedup = o.dedup != 0 && !cfg.with_grad && o.energy_budget_bytes == 0;
     for (int c = 0; c < qt::kWidthClasses; ++c) {
         if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
         cfg.tile_cap[c] = o.tile_cap[c];
@@ -684,7 +717,8 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     P->arena_bytes = (size_t)P->hp.total_elems * P->esize;
     P->host_only = o.host_only != 0;
     P->trace = o.trace != 0;
-    if (cfg.with_grad && o.adjoint_budget_bytes > 0 && P->arena_bytes > o.adjoint_budget_bytes) {
+    if ((cfg.with_grad && o.adjoint_budget_bytes > 0 && P->arena_bytes > o.adjoint_budget_bytes) ||
+        (!cfg.with_grad && o.energy_budget_bytes > 0 && P->arena_bytes > o.energy_budget_bytes)) {
         rc = make_passes(P.get(), graphs, p, o);
         if (rc != QT_OK) return rc;
         *out = P.release();
@@ -829,6 +863,9 @@ int qt_plan_stats_get(qt_plan_t P, qt_plan_stats* out) {
     for (const qt::Network& net : hp.nets) out->slice_bits = std::max(out->slice_bits, (int32_t)net.slice_bits);
     out->n_slices = (int64_t)hp.n_slices;
     out->n_unique = (int64_t)hp.n_unique;
+    out->pass_arena_bytes = 0;
+    for (const auto& part : P->parts)
+        out->pass_arena_bytes = std::max<int64_t>(out->pass_arena_bytes, (int64_t)part->hp.total_elems * part->esize);
     return QT_OK;
 }
 

@@ -43,7 +43,8 @@ class PlanOpts(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("run_tiles", ctypes.c_int32), ("trace", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("no_fuse", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("tile_cap", ctypes.c_int8 * 8), ("no_merge", ctypes.c_int32), ("adjoint_budget_bytes", ctypes.c_size_t),
-                ("slice_width", ctypes.c_int32), ("max_slice_bits", ctypes.c_int32), ("dedup", ctypes.c_int32)]
+                ("slice_width", ctypes.c_int32), ("max_slice_bits", ctypes.c_int32), ("dedup", ctypes.c_int32),
+                ("energy_budget_bytes", ctypes.c_size_t)]
 
 
 class PlanStats(ctypes.Structure):
@@ -56,7 +57,7 @@ class PlanStats(ctypes.Structure):
                 ("n_units", ctypes.c_int64), ("n_fused", ctypes.c_int64), ("tile_cap", ctypes.c_int32 * 8),
                 ("run_tiles", ctypes.c_int32), ("tune_seconds", ctypes.c_double), ("tune_candidates", ctypes.c_int32),
                 ("n_passes", ctypes.c_int32), ("slice_bits", ctypes.c_int32), ("n_slices", ctypes.c_int64),
-                ("n_unique", ctypes.c_int64)]
+                ("n_unique", ctypes.c_int64), ("pass_arena_bytes", ctypes.c_int64)]
 
 
 BUCKET_DTYPE = np.dtype([("network", np.int32), ("width", np.int32), ("n_ops", np.int32), ("op_begin", np.int32),
@@ -193,7 +194,7 @@ class Plan:
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
               order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=True,
-              slice_width=0, max_slice_bits=0, dedup=False):
+              slice_width=0, max_slice_bits=0, dedup=False, energy_budget_bytes=0):
         # slice_width: 0 the library's default target, -1 no slicing
         o = PlanOpts()
         o.dtype = {"c64": QT_C64, "c128": QT_C128}[dtype]
@@ -216,6 +217,7 @@ class Plan:
         o.slice_width = int(slice_width)
         o.max_slice_bits = int(max_slice_bits)
         o.dedup = 1 if dedup else 0
+        o.energy_budget_bytes = int(energy_budget_bytes)
         for i, c in enumerate(tile_cap or []):
             o.tile_cap[i] = int(c)
         return o

@@ -162,3 +162,28 @@ def test_slice_shards_add_up_to_the_full_plan():
     assert holders.max() > 1  # some network's slices are spread over ranks
     np.testing.assert_allclose(zz_sum, zz_full, rtol=0, atol=1e-10)
     assert abs(E_sum - E_full) <= 1e-10 * abs(E_full)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_energy_budget_passes_match_the_whole_plan(dtype):
+    """opts.energy_budget_bytes: the N=30 p=4 plan run in passes over its
+    slices (one shared arena a tenth of the whole plan's) gives the whole
+    plan's per-edge values and energy; a subset plan in passes returns its
+    networks' values in its own order."""
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    with qtgb.plan(n, edges, p, dtype=dtype) as pl:
+        full = pl.stats()["arena_bytes"]
+        zz_f, E_f = pl.energy(g, b)
+    with qtgb.plan(n, edges, p, dtype=dtype, energy_budget_bytes=full // 10) as pl:
+        st = pl.stats()
+        zz, E = pl.energy(g, b)
+    assert st["n_passes"] > 1 and st["pass_arena_bytes"] <= full // 10
+    assert scaled_err(zz, zz_f) <= TOL[dtype]
+    assert abs(E - E_f) <= TOL[dtype] * abs(E_f)
+    sel = np.array([3, 17, 40, 8])
+    with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, energy_budget_bytes=full // 20) as pl:
+        assert pl.stats()["n_passes"] > 1
+        zz_s, _ = pl.energy(g, b)
+    assert scaled_err(zz_s, zz_f[sel]) <= TOL[dtype]

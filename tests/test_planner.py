@@ -613,3 +613,24 @@ def test_bucket_einsum_spec_is_the_contraction():
         np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
         checked += 1
     assert checked > 50
+
+
+def test_energy_budget_runs_in_passes_that_fit():
+    """opts.energy_budget_bytes: an energy plan over the budget is cut into
+    passes over its networks' slices, each pass's arena within the budget; a
+    slice that alone exceeds it gives QT_ENOMEM."""
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    with qtgb.plan(n, edges, p, host_only=True) as pl:
+        full = pl.stats()["arena_bytes"]
+    last = 1
+    for budget in (full // 2, full // 5, full // 12):
+        with qtgb.plan(n, edges, p, host_only=True, energy_budget_bytes=budget) as pl:
+            st = pl.stats()
+        assert st["n_passes"] > last and 0 < st["pass_arena_bytes"] <= budget
+        last = st["n_passes"]
+    with qtgb.plan(n, edges, p, host_only=True, energy_budget_bytes=full * 2) as pl:
+        assert pl.stats()["n_passes"] == 1 and pl.stats()["pass_arena_bytes"] == 0
+    with pytest.raises(qtgb.QTError) as ei:
+        qtgb.plan(n, edges, p, host_only=True, energy_budget_bytes=1 << 20)
+    assert ei.value.code == qtgb.QT_ENOMEM
