@@ -634,3 +634,23 @@ def test_energy_budget_runs_in_passes_that_fit():
     with pytest.raises(qtgb.QTError) as ei:
         qtgb.plan(n, edges, p, host_only=True, energy_budget_bytes=1 << 20)
     assert ei.value.code == qtgb.QT_ENOMEM
+
+
+@pytest.mark.parametrize("n,seed,p", [(200, 5, 2), (400, 9, 3)])
+def test_dedup_key_is_complete_on_tree_lightcones(n, seed, p):
+    """In a 3-regular graph all tree lightcones of one p are the same tree, so
+    deduplication contracts exactly the lightcones with a cycle plus one; the
+    count of cycles comes from networkx, independently of the planner."""
+    edges = synth.random_regular_graph(n, seed)
+    G = nx.Graph()
+    G.add_edges_from(map(tuple, edges))
+    cyclic = 0
+    for j, k in edges:
+        d = nx.multi_source_dijkstra_path_length(G, [int(j), int(k)], cutoff=p)
+        V = set(d)
+        E = [(a, c) for a, c in G.subgraph(V).edges() if min(d[a], d[c]) <= p - 1]
+        cyclic += len(E) != len(V) - 1
+    with host_plan(n, edges, p, dedup=True) as pl:
+        st = pl.stats()
+    assert cyclic < edges.shape[0]
+    assert st["n_unique"] == cyclic + 1
