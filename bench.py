@@ -626,7 +626,7 @@ def run_c3(args, world, local_rank):
             "plain_c128_per_bucket": res["c128_per_bucket"], "c128_persistent": res["c128_persistent"],
             "speedup_vs_plain_c128": res["c128_per_bucket"]["ms_per_step"] / main["ms_per_step"], "check": check,
             "c64_dedup": dict(res["c64_persistent_dedup"],
-                              note="opts.dedup: one network per isomorphism class of tree lightcones per graph "
+                              note="opts.dedup: one network per isomorphism class of lightcones per graph "
                                    "(off in the main line)")}
     print(json.dumps(line), flush=True)
 

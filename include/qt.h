@@ -110,8 +110,8 @@ typedef struct {
                               -1: no slicing. Forward plans only (gradient plans are never sliced) */
     int32_t max_slice_bits;/* most variables fixed per network (1..16); 0: 8 */
     int32_t dedup;         /* nonzero: lightcone deduplication. Within each graph, networks whose
-                              lightcones are isomorphic trees (the qubits within distance p of the
-                              edge, labelled by distance) are contracted once: the others take that
+                              lightcones are isomorphic (the qubits within distance p of the edge,
+                              labelled by distance) are contracted once: the others take that
                               network's value. Forward plans only (ignored with gradients, slice
                               shards or energy_budget_bytes). 0: every network is contracted */
     size_t energy_budget_bytes; /* energy plans (single graph): device bytes for the gate tables and

@@ -213,12 +213,81 @@ static void order_min_fill(const Network& net, bool randomized, uint64_t seed, s
 // edges with an endpoint within distance p - 1 (the gates A1/A2 place). Two
 // edges of one graph with isomorphic lightcones give the same network up to
 // the names of its variables, so the same <Z_jZ_k> at the graph's angles.
-// For a lightcone that is a tree the key below is canonical: the AHU encoding
-// of the tree hanging from the edge (each vertex: its children's encodings,
-// sorted), so equal keys mean isomorphic lightcones and isomorphic tree
-// lightcones get equal keys. A lightcone with a cycle gets no key (its
-// network is always contracted).
+// For a lightcone that is a tree the key is the AHU encoding of the tree
+// hanging from the edge (each vertex: its children's encodings, sorted); for
+// one with cycles, the smallest individualization-refinement certificate
+// below. Both are canonical: equal keys exactly for isomorphic lightcones. A
+// lightcone whose search gives up gets no key (its network is contracted).
 // ---------------------------------------------------------------------------
+// Canonical key of a lightcone with cycles: individualization-refinement on
+// its core (the pendant trees stripped into the labels of the vertices that
+// carry them). Colours start from those labels and are refined by each vertex's
+// neighbour colours, renumbered by sorted signatures each round (so they do
+// not depend on vertex ids). While a colour class holds several vertices,
+// each of them is individualized in turn (split off above its class) and the
+// search recurses; every discrete colouring orders the vertices, and the key
+// is the smallest certificate (labels and edges in that order) over all
+// leaves. Equal keys mean isomorphic lightcones, and isomorphic lightcones get
+// equal keys. A search over kKeyLeaves leaves gives up: no key.
+constexpr int kKeyLeaves = 256;
+
+static void refine_colours(const std::vector<std::vector<int>>& adj, std::vector<int>* colour) {
+    std::vector<int>& c = *colour;
+    const int n = (int)adj.size();
+    int classes = (int)std::set<int>(c.begin(), c.end()).size();
+    for (;;) {
+        std::vector<std::vector<int>> sig(n);
+        for (int v = 0; v < n; ++v) {
+            sig[v].push_back(c[v]);
+            std::vector<int> nb;
+            for (int u : adj[v]) nb.push_back(c[u]);
+            std::sort(nb.begin(), nb.end());
+            sig[v].insert(sig[v].end(), nb.begin(), nb.end());
+        }
+        std::vector<std::vector<int>> uniq(sig);
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        for (int v = 0; v < n; ++v) c[v] = (int)(std::lower_bound(uniq.begin(), uniq.end(), sig[v]) - uniq.begin());
+        if ((int)uniq.size() == classes) return;
+        classes = (int)uniq.size();
+    }
+}
+
+static void search_key(const std::vector<std::vector<int>>& adj, const std::vector<std::string>& label,
+                       std::vector<int> colour, std::string* best, int* leaves) {
+    if (*leaves > kKeyLeaves) return;
+    refine_colours(adj, &colour);
+    const int n = (int)adj.size();
+    std::vector<int> count(n + 1, 0);
+    for (int v = 0; v < n; ++v) count[colour[v]]++;
+    int cell = -1;
+    for (int c = 0; c < n && cell < 0; ++c)
+        if (count[c] > 1) cell = c;
+    if (cell < 0) {  // discrete: certificate in colour order
+        std::vector<int> at(n);
+        for (int v = 0; v < n; ++v) at[colour[v]] = v;
+        std::string cert;
+        for (int i = 0; i < n; ++i) cert += label[at[i]] + ",";
+        std::vector<std::pair<int, int>> ed;
+        for (int v = 0; v < n; ++v)
+            for (int u : adj[v])
+                if (colour[v] < colour[u]) ed.emplace_back(colour[v], colour[u]);
+        std::sort(ed.begin(), ed.end());
+        for (auto& e : ed) cert += std::to_string(e.first) + "-" + std::to_string(e.second) + ";";
+        if (best->empty() || cert < *best) *best = cert;
+        ++*leaves;
+        return;
+    }
+    for (int v = 0; v < n; ++v) {
+        if (colour[v] != cell) continue;
+        std::vector<int> c2(n);
+        for (int w = 0; w < n; ++w) c2[w] = 2 * colour[w];
+        c2[v] = 2 * colour[v] + 1;  // v alone, just above the rest of its class
+        search_key(adj, label, c2, best, leaves);
+        if (*leaves > kKeyLeaves) return;
+    }
+}
+
 static std::string lightcone_key(const std::vector<std::vector<int>>& nbr, int p, int j, int k) {
     const int n = (int)nbr.size();
     std::vector<int> dist(n, -1), seen;
@@ -244,7 +313,70 @@ static std::string lightcone_key(const std::vector<std::vector<int>>& nbr, int p
     for (int a : seen)
         for (int b : nbr[a])
             if (a < b && dist[b] >= 0 && std::min(dist[a], dist[b]) <= p - 1) ++n_edges;
-    if (n_edges + 1 != seen.size()) return std::string();  // a cycle: no key
+    if (n_edges + 1 != seen.size()) {
+        // cycles: strip the pendant trees (leaves inward), each vertex's label
+        // gathering its distance and the sorted encodings of the trees it
+        // carries; then search the labelled core
+        const int nv = (int)seen.size();
+        std::vector<int> local(n, -1);
+        for (int i = 0; i < nv; ++i) local[seen[i]] = i;
+        std::vector<std::vector<int>> nb(nv);
+        for (int i = 0; i < nv; ++i)
+            for (int b : nbr[seen[i]])
+                if (dist[b] >= 0 && std::min(dist[seen[i]], dist[b]) <= p - 1) nb[i].push_back(local[b]);
+        std::vector<int> deg(nv);
+        std::vector<uint8_t> gone(nv, 0);
+        std::vector<std::vector<std::string>> hang(nv);
+        auto finish = [&](int v) {
+            std::sort(hang[v].begin(), hang[v].end());
+            std::string l = std::to_string(dist[seen[v]]) + "[";
+            for (const std::string& h : hang[v]) l += h;
+            return l + "]";
+        };
+        std::vector<int> leaf;
+        for (int i = 0; i < nv; ++i) {
+            deg[i] = (int)nb[i].size();
+            if (deg[i] == 1) leaf.push_back(i);
+        }
+        while (!leaf.empty()) {
+            std::vector<int> next;
+            for (int u : leaf) {
+                if (gone[u] || deg[u] != 1) continue;
+                gone[u] = 1;
+                for (int w : nb[u])
+                    if (!gone[w]) {
+                        hang[w].push_back("(" + finish(u) + ")");
+                        if (--deg[w] == 1) next.push_back(w);
+                    }
+            }
+            leaf.swap(next);
+        }
+        std::vector<int> core;
+        std::vector<int> at(nv, -1);
+        for (int i = 0; i < nv; ++i)
+            if (!gone[i]) {
+                at[i] = (int)core.size();
+                core.push_back(i);
+            }
+        std::vector<std::vector<int>> adj(core.size());
+        std::vector<std::string> label(core.size());
+        for (size_t c = 0; c < core.size(); ++c) {
+            label[c] = finish(core[c]);
+            for (int w : nb[core[c]])
+                if (!gone[w]) adj[c].push_back(at[w]);
+        }
+        std::vector<std::string> names(label);
+        std::sort(names.begin(), names.end());
+        names.erase(std::unique(names.begin(), names.end()), names.end());
+        std::vector<int> colour(core.size());
+        for (size_t c = 0; c < core.size(); ++c)
+            colour[c] = (int)(std::lower_bound(names.begin(), names.end(), label[c]) - names.begin());
+        std::string best;
+        int leaves = 0;
+        search_key(adj, label, colour, &best, &leaves);
+        if (leaves > kKeyLeaves || best.empty()) return std::string();
+        return "G" + best;
+    }
     // encodings bottom-up: vertices in decreasing distance
     std::vector<std::string> enc(n);
     std::vector<int> order(seen.begin(), seen.end());
@@ -260,7 +392,7 @@ static std::string lightcone_key(const std::vector<std::vector<int>>& nbr, int p
         s += ")";
         enc[v] = std::move(s);
     }
-    return std::min(enc[j], enc[k]) + "|" + std::max(enc[j], enc[k]);
+    return "T" + std::min(enc[j], enc[k]) + "|" + std::max(enc[j], enc[k]);
 }
 
 // ---------------------------------------------------------------------------

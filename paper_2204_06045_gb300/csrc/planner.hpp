@@ -100,7 +100,7 @@ struct PlanConfig {
     bool fuse = false;       // form fused units of small subtrees (persistent energy plans)
     int tile_cap[kWidthClasses] = {0, 0, 0, 0, 0};  // most tile bits per bucket-width class (0: chunk_log2 / default)
     bool merge = false;      // merge chains of eliminations (a bucket and the parent that only extends it)
-    bool dedup = false;      // contract one network per isomorphism class of tree lightcones (per graph)
+    bool dedup = false;      // contract one network per isomorphism class of lightcones (per graph)
     int slice_width = 0;     // > 0: slice networks whose greedy width exceeds it (forward plans)
     int max_slice_bits = 0;  // most variables fixed per network
 };

@@ -1,7 +1,7 @@
 """GPU parity of lightcone deduplication (opts.dedup).
 
-Within one graph, networks whose lightcones are isomorphic trees are
-contracted once; the others take that network's value (the epilogue reads the
+Within one graph, networks whose lightcones are isomorphic are contracted
+once; the others take that network's value (the epilogue reads the
 representative's results). These tests run deduplicated plans against the
 state vector, the full plans and the oracle's bucket elimination, with the
 tolerances of the other GPU parity tests (1e-10 complex128, 1e-5 complex64

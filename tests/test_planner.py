@@ -636,21 +636,28 @@ def test_energy_budget_runs_in_passes_that_fit():
     assert ei.value.code == qtgb.QT_ENOMEM
 
 
-@pytest.mark.parametrize("n,seed,p", [(200, 5, 2), (400, 9, 3)])
-def test_dedup_key_is_complete_on_tree_lightcones(n, seed, p):
-    """In a 3-regular graph all tree lightcones of one p are the same tree, so
-    deduplication contracts exactly the lightcones with a cycle plus one; the
-    count of cycles comes from networkx, independently of the planner."""
+@pytest.mark.parametrize("n,seed,p", [(200, 5, 2), (400, 9, 3), (60, 11, 3), (90, 4, 3)])
+def test_dedup_contracts_one_network_per_lightcone_class(n, seed, p):
+    """opts.dedup contracts exactly one network per isomorphism class of
+    lightcones (qubits within distance p of the edge, labelled by distance;
+    the graph edges with an endpoint within p - 1): the classes are counted
+    here with networkx's isomorphism test, independently of the planner's
+    keys (AHU codes for trees, a canonical search for lightcones with cycles)."""
     edges = synth.random_regular_graph(n, seed)
     G = nx.Graph()
     G.add_edges_from(map(tuple, edges))
-    cyclic = 0
+    classes = {}
     for j, k in edges:
         d = nx.multi_source_dijkstra_path_length(G, [int(j), int(k)], cutoff=p)
-        V = set(d)
-        E = [(a, c) for a, c in G.subgraph(V).edges() if min(d[a], d[c]) <= p - 1]
-        cyclic += len(E) != len(V) - 1
+        H = nx.Graph()
+        H.add_nodes_from((v, {"d": d[v]}) for v in d)
+        H.add_edges_from((a, c) for a, c in G.subgraph(d).edges() if min(d[a], d[c]) <= p - 1)
+        sig = (H.number_of_nodes(), H.number_of_edges(), tuple(sorted(d.values())))
+        reps = classes.setdefault(sig, [])
+        if not any(nx.is_isomorphic(R, H, node_match=lambda a, c: a["d"] == c["d"]) for R in reps):
+            reps.append(H)
+    n_classes = sum(len(r) for r in classes.values())
     with host_plan(n, edges, p, dedup=True) as pl:
         st = pl.stats()
-    assert cyclic < edges.shape[0]
-    assert st["n_unique"] == cyclic + 1
+    assert n_classes < edges.shape[0]
+    assert st["n_unique"] == n_classes
