@@ -543,7 +543,7 @@ def test_slicing_options():
 
 @pytest.mark.parametrize("n,seed,p", [(20, 3, 1), (60, 3, 2), (100, 7, 3)])
 def test_deduplicated_networks_take_their_representatives_values(n, seed, p):
-    """opts.dedup: networks whose lightcones are isomorphic trees are
+    """opts.dedup: networks whose lightcones are isomorphic are
     contracted once. Every network's value (its representative's) equals its
     own contraction in the full plan; representatives come first and are
     contracted; duplicates have no buckets."""
