@@ -381,7 +381,7 @@ def bucket_einsum(B, O, k):
 
 
 def run_einsum(args, world, local_rank):
-    """NEXT-4 comparison point: every bucket of width >= 24 of the 15 widest
+    """A library comparison point: every bucket of width >= 24 of the 15 widest
     N=1000 p=5 networks (plain buckets), timed alone in the persistent kernel
     (qt_bucket_time) and as torch.einsum on random complex64 tensors of the
     same shapes on the same GPU (CUDA events, mean of 3 after 1)."""

@@ -94,7 +94,7 @@ def _shard_rank(rank, world, port, out):
 
 
 def test_sharded_energy_over_gloo_ranks_matches_oracle():
-    """§8(e): one graph's networks split over ranks by LPT on their cost; the
+    """One graph's networks split over ranks by LPT on their cost; the
     ranks' partial energies sum to the oracle's energy, every edge is held by
     exactly one rank, and the loads are balanced."""
     import oracle
@@ -151,7 +151,7 @@ def _slice_shard_rank(rank, world, port, out):
 
 
 def test_sliced_networks_sharded_over_gloo_ranks_match_oracle():
-    """§8(e) balance with slicing: the units are network slices, so one wide
+    """Balance with slicing: the units are network slices, so one wide
     network's slices may sit on several ranks; each rank's value for an edge
     is the sum over its slices, and the sum over ranks is the oracle's e_jk.
     Every slice of every network is held by exactly one rank."""
