@@ -1071,7 +1071,11 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
         for (size_t g = 0; g < graphs.size(); ++g) {
             std::unordered_map<std::string, int> first;
             for (int i = hp->graph_first_net[g]; i < hp->graph_first_net[g + 1]; ++i) {
-                if (key[i].empty() || !graphs[g].sel_slices.empty()) continue;  // cycles, and slice shards: contracted
+                // only networks the plan holds whole (every slice, its 1/2 counted) share values
+                const size_t li = (size_t)(i - hp->graph_first_net[g]);
+                const bool part = (li < graphs[g].sel_slices.size() && !graphs[g].sel_slices[li].empty()) ||
+                                  (li < graphs[g].sel_owner.size() && !graphs[g].sel_owner[li]);
+                if (key[i].empty() || part) continue;
                 auto it = first.emplace(key[i], i);
                 if (!it.second) rep[i] = it.first->second;
             }

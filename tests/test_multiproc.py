@@ -179,3 +179,52 @@ def test_sliced_networks_sharded_over_gloo_ranks_match_oracle():
         np.testing.assert_allclose(res[r][1], zz, atol=1e-12)
     costs = [res[r][2] for r in range(world)]
     assert max(costs) <= 1.5 * min(costs)
+
+
+def _dedup_shard_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, str(ROOT))
+    sys.path.insert(0, str(ROOT / "tests"))
+    from plan_eval import evaluate
+    from paper_2204_06045_gb300 import qtgb, synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n, p = 80, 2
+        edges = synth.random_regular_graph(n, 31)
+        g, b = synth.angles(p, 31)
+        dense = torch.zeros(edges.shape[0], dtype=torch.float64)
+        with qtgb.plan_shard(n, edges, p, world, rank, host_only=True, dedup=True) as pl:
+            mine = pl.shard_edges
+            st = pl.stats()
+            if mine.size:
+                B, O = pl.export()
+                vals = evaluate(B, O, g, b, fixed=pl.export_fixed()).real
+                R = pl.export_reps()
+                dense[torch.as_tensor(mine, dtype=torch.long)] = torch.as_tensor(
+                    np.array([vals[R[i]] for i in range(R.size)]))
+        dist.all_reduce(dense, op=dist.ReduceOp.SUM)
+        out[rank] = (dense.tolist(), int(st["n_unique"]), int(st["n_networks"]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_deduplicated_shards_over_gloo_ranks_match_oracle():
+    """Each rank deduplicates the networks of its own shard (their costs are
+    counted undeduplicated when the shards are drawn): the per-edge values
+    summed over ranks are the oracle's."""
+    import oracle
+    from paper_2204_06045_gb300 import build, synth
+    build.build()
+    world = 3
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_dedup_shard_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    n, p = 80, 2
+    edges = synth.random_regular_graph(n, 31)
+    g, b = synth.angles(p, 31)
+    want = oracle.bucket_zz(n, edges, g, b)[0].real
+    for r in range(world):
+        np.testing.assert_allclose(res[r][0], want, atol=1e-12)
+    assert sum(res[r][1] for r in range(world)) < sum(res[r][2] for r in range(world))
