@@ -59,6 +59,7 @@ def parse():
                          "this kernel against torch.einsum on the same contractions")
     ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the plan-time autotuner's line")
+    ap.add_argument("--no-alt", action="store_true", help="skip the alternative plans (restarts, deduplication)")
     ap.add_argument("--shard", action="store_true",
                     help="with N GPUs: split the N=30 p=4 graph's networks over the ranks (LPT by cost) and "
                          "all-reduce the partial energies every step (strong scaling); default: replicas")
@@ -429,6 +430,63 @@ def run_einsum(args, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def alt_plans(n, p, edges, g, b, ref_zz, default, torch):
+    """Exploratory, beside the headline (which these do not change): the same
+    workload planned with 64 randomised min-fill restarts (fewer algorithmic
+    bytes), and the 64-graph batch with lightcone deduplication. Each entry
+    records its kernel time, bytes and agreement, or the error it met."""
+    from paper_2204_06045_gb300 import qtgb, synth
+    m = edges.shape[0]
+    out = {}
+    for dtype, steps in (("c64", 100), ("c128", 20)):
+        try:
+            with qtgb.plan(n, edges, p, dtype=dtype, restarts=64, seed=7) as pl:
+                st = pl.stats()
+                gd = torch.tensor(g, dtype=torch.float64, device="cuda")
+                bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+                zz = torch.zeros(m, dtype=torch.float64, device="cuda")
+                E = torch.zeros(1, dtype=torch.float64, device="cuda")
+                ms, kms, _ = time_device(pl, gd, bd, zz, E, steps, 3, None, torch)
+                err = float(np.max(np.abs(zz.cpu().numpy() - ref_zz))) if ref_zz is not None else None
+            out[f"restarts64_{dtype}"] = {
+                "ms_per_step": ms / steps, "kernel_ms": kms, "alg_bytes": st["alg_bytes"],
+                "default_kernel_ms": default[dtype]["roofline"]["kernel_ms"],
+                "default_alg_bytes": default[dtype]["roofline"]["alg_bytes_per_launch"], "max_abs_err_zz": err}
+        except Exception as ex:  # recorded, not fatal: the headline stands without it
+            out[f"restarts64_{dtype}"] = {"error": repr(ex)}
+    try:
+        graphs = synth.batch(64, 3, lo=50, hi=1000, base_seed=1000)
+        spec = [(nn, e) for nn, e, _, _ in graphs]
+        G = np.array([gg for _, _, gg, _ in graphs])
+        Bt = np.array([bb for _, _, _, bb in graphs])
+        res = {}
+        for dedup in (False, True):
+            with qtgb.plan_batch(spec, 3, dtype="c64", dedup=dedup) as pl:
+                st = pl.stats()
+                gd = torch.tensor(G.ravel(), dtype=torch.float64, device="cuda")
+                bd = torch.tensor(Bt.ravel(), dtype=torch.float64, device="cuda")
+                en = torch.zeros(64, dtype=torch.float64, device="cuda")
+                s = torch.cuda.current_stream()
+                for _ in range(3):
+                    pl.energy_batch(gd, bd, energies=en, stream=s)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for _ in range(50):
+                    pl.energy_batch(gd, bd, energies=en, stream=s)
+                e1.record(s)
+                torch.cuda.synchronize()
+                res[dedup] = (e0.elapsed_time(e1) / 50, en.cpu().numpy(), st["n_unique"], st["alg_bytes"])
+        out["batch64_p3_dedup_c64"] = {
+            "ms_per_step": res[True][0], "graph_evals_per_s": 64 / (res[True][0] * 1e-3),
+            "ms_per_step_without": res[False][0], "speedup": res[False][0] / res[True][0],
+            "networks_contracted": res[True][2], "alg_bytes": res[True][3], "alg_bytes_without": res[False][3],
+            "max_rel_energy_diff": float(np.max(np.abs(res[True][1] - res[False][1]) / np.abs(res[False][1])))}
+    except Exception as ex:
+        out["batch64_p3_dedup_c64"] = {"error": repr(ex)}
+    return out
+
+
 def time_device(pl, gd, bd, zz, E, steps, warmup, dist, torch):
     s = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -559,6 +617,8 @@ def run_ours(args, rank, world, local_rank):
         line["autotune_c64"] = {"tile_cap_by_width_class": st["tile_cap"], "run_tiles": st["run_tiles"],
                                 "candidates": st["tune_candidates"], "plan_seconds": time.perf_counter() - t,
                                 "kernel_ms": kms_t, "default_kernel_ms": main["roofline"]["kernel_ms"]}
+    if world == 1 and not args.no_alt:
+        line["alt_plans"] = alt_plans(n, p, edges, g, b, ref_zz, {"c64": main, "c128": results["c128"]}, torch)
     if world == 1 and not args.no_buckets:
         line["bucket_gbs"] = wide_buckets(peak, torch)
     if world == 1 and not args.no_cpu_baseline:
