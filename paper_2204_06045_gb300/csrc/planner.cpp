@@ -1180,6 +1180,30 @@ int layout_plan(HostPlan* hp) {
     hp->sum_2w = hp->alg_bytes = hp->flops = 0;
     std::fill(hp->width_hist, hp->width_hist + 64, 0);
     hp->bucket_slice.clear();
+    {
+        // sizes of the flat arrays, so that they grow once
+        size_t nb = 0, no = 0;
+        for (int i = 0; i < n_nets; ++i) {
+            if (hp->nets[i].rep >= 0) continue;
+            size_t ops = 0;
+            for (const HBucket& B : hp->nplans[i].buckets) ops += B.ops.size();
+            nb += hp->nplans[i].buckets.size() * hp->nets[i].n_emitted();
+            no += ops * hp->nets[i].n_emitted();
+        }
+        hp->buckets.reserve(nb);
+        hp->bucket_level.reserve(nb);
+        hp->bucket_var.reserve(nb);
+        hp->bucket_var2.reserve(nb);
+        hp->bucket_var3.reserve(nb);
+        hp->bucket_slice.reserve(nb);
+        hp->operands.reserve(no);
+        hp->op_src.reserve(no);
+        hp->op_leaf_kind.reserve(no);
+        hp->op_leaf_layer.reserve(no);
+        hp->op_rank.reserve(no);
+        hp->op_leaf_sub.reserve(no);
+        hp->op_param.reserve(no);
+    }
     hp->op_leaf_sub.clear();
     hp->net_first_factor.assign(1, 0);
     hp->factor.clear();
@@ -1203,7 +1227,9 @@ int layout_plan(HostPlan* hp) {
             const size_t root0 = hp->root_bucket.size();
             for (size_t lb = 0; lb < np.buckets.size(); ++lb) {
                 const HBucket& B = np.buckets[lb];
-                const HBucket V = device_view(B);
+                HBucket merged_view;  // only merged buckets need a device view of their own
+                if (B.n_sum > 1) merged_view = device_view(B);
+                const HBucket& V = B.n_sum > 1 ? merged_view : B;
                 DBucket d{};
                 d.op_begin = (uint32_t)hp->operands.size();
                 d.n_ops = (uint8_t)B.ops.size();
