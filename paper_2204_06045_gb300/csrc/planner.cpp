@@ -779,17 +779,16 @@ static void form_units(HostPlan* hp, int stage_elems) {
     if (!hp->cfg.fuse) return;
     const uint32_t nb = (uint32_t)hp->buckets.size();
     std::vector<uint8_t> ok(nb, 0);  // the bucket's whole subtree is small
-    std::vector<std::vector<uint32_t>> kids(nb);
+    // a bucket's producers, in operand order (read from its operands in place)
+    auto each_kid = [hp](uint32_t u, auto&& f) {
+        const DBucket& d = hp->buckets[u];
+        for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i)
+            if (hp->op_src[i] >= 0) f((uint32_t)hp->op_src[i]);
+    };
     for (uint32_t b = 0; b < nb; ++b) {
         const DBucket& d = hp->buckets[b];
         bool good = d.n_out <= kFuseOutBits && bucket_n_sum(d.flags) == 1;  // units sum one variable per bucket
-        for (uint32_t i = d.op_begin; i < d.op_begin + d.n_ops; ++i) {
-            const int32_t src = hp->op_src[i];
-            if (src >= 0) {
-                kids[b].push_back((uint32_t)src);
-                good = good && ok[src];  // producers precede their consumer
-            }
-        }
+        each_kid(b, [&](uint32_t c) { good = good && ok[c]; });  // producers precede their consumer
         ok[b] = good;
     }
     // first-fit placement of a subtree's intermediates; false if it overflows
@@ -810,16 +809,16 @@ static void form_units(HostPlan* hp, int stage_elems) {
                 off[k] = at;
             }
             // u's producers are consumed now: free their space
-            for (uint32_t c : kids[u]) {
+            each_kid(u, [&](uint32_t c) {
                 const uint32_t co = hp->buckets[c].scr_off, cs = 1u << hp->buckets[c].n_out;
                 auto it = std::find(used.begin(), used.end(), std::make_pair(co, cs));
                 if (it != used.end()) used.erase(it);
-            }
+            });
             if (u != root) hp->buckets[u].scr_off = (uint16_t)off[k];
         }
         return true;
     };
-    std::vector<uint32_t> stack, members;
+    std::vector<uint32_t> stack, members, todo;
     for (uint32_t r = nb; r-- > 0;) {  // parents before producers: maximal subtrees first
         const DBucket& d = hp->buckets[r];
         if (!ok[r] || (d.flags & kBucketInUnit)) continue;
@@ -829,12 +828,12 @@ static void form_units(HostPlan* hp, int stage_elems) {
             const uint32_t root = stack.back();
             stack.pop_back();
             members.clear();
-            std::vector<uint32_t> todo(1, root);
+            todo.assign(1, root);
             while (!todo.empty()) {
                 const uint32_t u = todo.back();
                 todo.pop_back();
                 members.push_back(u);
-                for (uint32_t c : kids[u]) todo.push_back(c);
+                each_kid(u, [&](uint32_t c) { todo.push_back(c); });
             }
             std::sort(members.begin(), members.end());  // elimination order
             if (place(members, root)) {
@@ -857,7 +856,7 @@ static void form_units(HostPlan* hp, int stage_elems) {
                 hp->n_units++;
                 hp->n_fused += members.size();
             } else {
-                for (uint32_t c : kids[root]) stack.push_back(c);  // split at the root
+                each_kid(root, [&](uint32_t c) { stack.push_back(c); });  // split at the root
             }
         }
     }
