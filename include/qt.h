@@ -210,6 +210,39 @@ typedef struct {
     int32_t pad;
 } qt_fixed_info;
 
+/* The arrays the device kernels read (host-side inspection and tests): per
+ * bucket its result's arena offset, operands, tile outputs (n_out; a merged
+ * bucket's outputs are (o, s1) with s1 as bit 0) and summed variables; per
+ * operand its arena offset (a gate's slot plus any slice offset, or the
+ * producer's result), its mask over the bucket's tile outputs, whether its
+ * entries pair over the bucket's first summed variable (then entry
+ * 2 * pext(o, mask) + x, else pext(o, mask)), and whether it is a gate; the
+ * epilogue's factor lists (arena offsets, bit 63 on each slice's first factor;
+ * per network factors [net_first_factor[i], net_first_factor[i + 1])) and per
+ * graph the networks whose 1/2 the energy counts. Arena layout: per graph
+ * 2 + 4p gate tensors of 4 entries from element 0 (|+>, Z, then per layer ZZ,
+ * ZZ*, mixer, mixer*), entry x + 2y. Any pointer may be NULL; *n_factors
+ * receives the factor count (call once with factor NULL to size it). */
+typedef struct {
+    uint64_t out_off;
+    int32_t op_begin;
+    int32_t n_ops;
+    int32_t n_out;
+    int32_t n_sum;
+} qt_dev_bucket;
+
+typedef struct {
+    uint64_t off;
+    uint32_t mask;
+    int32_t pairs_x;
+    int32_t leaf;
+    int32_t pad;
+} qt_dev_operand;
+
+int qt_plan_export_device(qt_plan_t plan, qt_dev_bucket *buckets, qt_dev_operand *operands,
+                          uint32_t *net_first_factor, uint64_t *factor, int32_t *graph_owned,
+                          int64_t *n_factors);
+
 /* Lightcone deduplication (host-side inspection): rep[i] = the network whose
  * value network i takes (i itself when it is contracted); n_networks int32. */
 int qt_plan_export_reps(qt_plan_t plan, int32_t *rep);

@@ -918,6 +918,30 @@ int qt_plan_export(qt_plan_t P, qt_bucket_info* buckets, qt_operand_info* operan
     return QT_OK;
 }
 
+int qt_plan_export_device(qt_plan_t P, qt_dev_bucket* buckets, qt_dev_operand* operands, uint32_t* net_first_factor,
+                          uint64_t* factor, int32_t* graph_owned, int64_t* n_factors) {
+    if (!P) return QT_EINVAL;
+    const qt::HostPlan& hp = P->hp;
+    if (buckets)
+        for (size_t b = 0; b < hp.buckets.size(); ++b) {
+            const qt::DBucket& d = hp.buckets[b];
+            buckets[b] = qt_dev_bucket{d.out_off, (int32_t)d.op_begin, (int32_t)d.n_ops, (int32_t)d.n_out,
+                                       (int32_t)qt::bucket_n_sum(d.flags)};
+        }
+    if (operands)
+        for (size_t i = 0; i < hp.operands.size(); ++i) {
+            const qt::DOperand& o = hp.operands[i];
+            operands[i] = qt_dev_operand{o.off, o.mask, (int32_t)(o.smask & 1u), (o.flags & qt::kOpLeaf) ? 1 : 0, 0};
+        }
+    if (net_first_factor)
+        std::memcpy(net_first_factor, hp.net_first_factor.data(), hp.net_first_factor.size() * sizeof(uint32_t));
+    if (factor && !hp.factor.empty()) std::memcpy(factor, hp.factor.data(), hp.factor.size() * sizeof(uint64_t));
+    if (graph_owned && !hp.graph_owned.empty())
+        std::memcpy(graph_owned, hp.graph_owned.data(), hp.graph_owned.size() * sizeof(int32_t));
+    if (n_factors) *n_factors = (int64_t)hp.factor.size();
+    return QT_OK;
+}
+
 int qt_plan_export_reps(qt_plan_t P, int32_t* rep) {
     if (!P || !rep) return QT_EINVAL;
     for (size_t i = 0; i < P->hp.nets.size(); ++i) rep[i] = P->hp.nets[i].rep >= 0 ? P->hp.nets[i].rep : (int32_t)i;

@@ -24,7 +24,7 @@ EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "q
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
            "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed",
-           "qt_plan_export_reps")
+           "qt_plan_export_reps", "qt_plan_export_device")
 
 
 class QTError(RuntimeError):
@@ -70,6 +70,10 @@ GROUP_DTYPE = np.dtype([("bucket", np.int32), ("first_tile", np.int32), ("n_tile
 OPERAND_DTYPE = np.dtype([("src", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                           ("mask", np.uint32), ("rank", np.int32), ("smask", np.uint32), ("leaf_sub", np.int32),
                           ("pad", np.int32)])
+DEV_BUCKET_DTYPE = np.dtype([("out_off", np.uint64), ("op_begin", np.int32), ("n_ops", np.int32),
+                             ("n_out", np.int32), ("n_sum", np.int32)])
+DEV_OPERAND_DTYPE = np.dtype([("off", np.uint64), ("mask", np.uint32), ("pairs_x", np.int32), ("leaf", np.int32),
+                              ("pad", np.int32)])
 FIXED_DTYPE = np.dtype([("network", np.int32), ("slice", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                         ("entry", np.int32), ("pad", np.int32)])
 
@@ -107,6 +111,7 @@ def lib():
         L.qt_plan_export_groups.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_export_fixed.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_export_reps.argtypes = [vp, i32p]
+        L.qt_plan_export_device.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_shard.argtypes = [i32, i32, i32p, i32, i32, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp), i32p,
                                     i32p]
         L.qt_last_imag.argtypes = [vp, dp]
@@ -126,7 +131,7 @@ def lib():
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
                      "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard",
-                     "qt_plan_export_fixed", "qt_plan_export_reps"):
+                     "qt_plan_export_fixed", "qt_plan_export_reps", "qt_plan_export_device"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -325,6 +330,21 @@ class Plan:
         cnt = ctypes.c_int64(0)
         _check(lib().qt_plan_export_groups(self._h, out.ctypes.data, ctypes.byref(cnt)), "qt_plan_export_groups")
         return out[:cnt.value]
+
+    def export_device(self):
+        """The arrays the kernels read: (buckets, operands, net_first_factor, factor, graph_owned)."""
+        st = self.stats()
+        nf = ctypes.c_int64(0)
+        _check(lib().qt_plan_export_device(self._h, None, None, None, None, None, ctypes.byref(nf)),
+               "qt_plan_export_device")
+        b = np.zeros(max(1, st["n_buckets"]), dtype=DEV_BUCKET_DTYPE)
+        o = np.zeros(max(1, st["n_operands"]), dtype=DEV_OPERAND_DTYPE)
+        nff = np.zeros(st["n_networks"] + 1, dtype=np.uint32)
+        f = np.zeros(max(1, nf.value), dtype=np.uint64)
+        go = np.zeros(max(1, st["n_graphs"]), dtype=np.int32)
+        _check(lib().qt_plan_export_device(self._h, b.ctypes.data, o.ctypes.data, nff.ctypes.data, f.ctypes.data,
+                                           go.ctypes.data, ctypes.byref(nf)), "qt_plan_export_device")
+        return b[:st["n_buckets"]], o[:st["n_operands"]], nff, f[:nf.value], go[:st["n_graphs"]]
 
     def export_reps(self) -> np.ndarray:
         """Per network, the network whose value it takes (itself when contracted)."""
