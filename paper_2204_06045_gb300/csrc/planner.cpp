@@ -54,35 +54,51 @@ int leaf_index(int kind, int layer) {
 // mixer is a rank-2 tensor from the current variable to a fresh one. The bra
 // half mirrors the ket half with conjugated tensors.
 // ---------------------------------------------------------------------------
-static void build_network(const GraphIn& g, int p, int eidx, Network* net) {
-    const int n = g.n;
-    std::vector<std::vector<int>> nbr(n);
-    for (auto& e : g.edges) {
-        nbr[e.first].push_back(e.second);
-        nbr[e.second].push_back(e.first);
+// adj[v]: (neighbour, edge index) pairs of vertex v, in edge order
+using Adjacency = std::vector<std::vector<std::pair<int, int>>>;
+
+static Adjacency graph_adjacency(const GraphIn& g) {
+    Adjacency adj(g.n);
+    for (size_t i = 0; i < g.edges.size(); ++i) {
+        adj[g.edges[i].first].emplace_back(g.edges[i].second, (int)i);
+        adj[g.edges[i].second].emplace_back(g.edges[i].first, (int)i);
     }
+    return adj;
+}
+
+static void build_network(const GraphIn& g, const Adjacency& adj, int p, int eidx, Network* net) {
+    const int n = g.n;
     const int j = g.edges[eidx].first, k = g.edges[eidx].second;
-    std::vector<int> dist(n, -1);
+    std::vector<int> dist(n, -1), cone;
     std::queue<int> bfs;
     dist[j] = dist[k] = 0;
     bfs.push(j);
     bfs.push(k);
+    cone.push_back(j);
+    cone.push_back(k);
     while (!bfs.empty()) {
         int a = bfs.front();
         bfs.pop();
         if (dist[a] == p) continue;
-        for (int b : nbr[a])
-            if (dist[b] < 0) {
-                dist[b] = dist[a] + 1;
-                bfs.push(b);
+        for (const auto& nb : adj[a])
+            if (dist[nb.first] < 0) {
+                dist[nb.first] = dist[a] + 1;
+                bfs.push(nb.first);
+                cone.push_back(nb.first);
             }
     }
-    auto in_zz = [&](int a, int b, int layer1) {
-        int da = dist[a] < 0 ? (1 << 30) : dist[a];
-        int db = dist[b] < 0 ? (1 << 30) : dist[b];
-        return std::min(da, db) <= p - layer1;
-    };
-    auto has_mixer = [&](int q, int layer1) { return dist[q] >= 0 && dist[q] <= p - layer1; };
+    // the qubits of the lightcone in vertex order, and the edges a ZZ gate may
+    // sit on (an endpoint within distance p - 1, so both ends in the
+    // lightcone) in edge order: the order of the gates below
+    std::sort(cone.begin(), cone.end());
+    std::vector<int> zz_edges;
+    for (int v : cone)
+        if (dist[v] <= p - 1)
+            for (const auto& nb : adj[v]) zz_edges.push_back(nb.second);
+    std::sort(zz_edges.begin(), zz_edges.end());
+    zz_edges.erase(std::unique(zz_edges.begin(), zz_edges.end()), zz_edges.end());
+    auto in_zz = [&](int a, int b, int layer1) { return std::min(dist[a], dist[b]) <= p - layer1; };
+    auto has_mixer = [&](int q, int layer1) { return dist[q] <= p - layer1; };
 
     net->nvars = 0;
     net->leaves.clear();
@@ -91,16 +107,17 @@ static void build_network(const GraphIn& g, int p, int eidx, Network* net) {
     auto add1 = [&](int kind, int v) { net->leaves.push_back(Leaf{kind, -1, 1, {v, -1}}); };
     auto add2 = [&](int kind, int layer, int a, int b) { net->leaves.push_back(Leaf{kind, layer, 2, {a, b}}); };
 
-    for (int q = 0; q < n; ++q)
-        if (dist[q] >= 0) {
-            cur[q] = net->nvars++;
-            net->wire_vars[q] = 1;
-            add1(QT_LEAF_PLUS, cur[q]);
-        }
+    for (int q : cone) {
+        cur[q] = net->nvars++;
+        net->wire_vars[q] = 1;
+        add1(QT_LEAF_PLUS, cur[q]);
+    }
     for (int l = 1; l <= p; ++l) {
-        for (auto& e : g.edges)
+        for (int ei : zz_edges) {
+            const auto& e = g.edges[ei];
             if (in_zz(e.first, e.second, l)) add2(QT_LEAF_ZZ, l - 1, cur[e.first], cur[e.second]);
-        for (int q = 0; q < n; ++q)
+        }
+        for (int q : cone)
             if (has_mixer(q, l)) {
                 int nv = net->nvars++;
                 net->wire_vars[q]++;
@@ -111,18 +128,19 @@ static void build_network(const GraphIn& g, int p, int eidx, Network* net) {
     add1(QT_LEAF_ZOBS, cur[j]);
     add1(QT_LEAF_ZOBS, cur[k]);
     for (int l = p; l >= 1; --l) {
-        for (int q = 0; q < n; ++q)
+        for (int q : cone)
             if (has_mixer(q, l)) {
                 int nv = net->nvars++;
                 net->wire_vars[q]++;
                 add2(QT_LEAF_RX_CONJ, l - 1, cur[q], nv);
                 cur[q] = nv;
             }
-        for (auto& e : g.edges)
+        for (int ei : zz_edges) {
+            const auto& e = g.edges[ei];
             if (in_zz(e.first, e.second, l)) add2(QT_LEAF_ZZ_CONJ, l - 1, cur[e.first], cur[e.second]);
+        }
     }
-    for (int q = 0; q < n; ++q)
-        if (dist[q] >= 0) add1(QT_LEAF_PLUS, cur[q]);
+    for (int q : cone) add1(QT_LEAF_PLUS, cur[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1080,6 +1098,8 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             }
         }
     }
+    std::vector<Adjacency> adjs(graphs.size());
+    for (size_t g = 0; g < graphs.size(); ++g) adjs[g] = graph_adjacency(graphs[g]);
     std::atomic<int> next{0};
     auto worker = [&]() {
         for (;;) {
@@ -1090,7 +1110,7 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             Network& net = hp->nets[i];
             net.graph = g;
             net.edge = graphs[g].edge_of((size_t)(i - hp->graph_first_net[g]));
-            build_network(graphs[g], cfg.p, net.edge, &net);
+            build_network(graphs[g], adjs[g], cfg.p, net.edge, &net);
             net.rep = rep[i];
             if (net.rep >= 0) continue;  // takes its representative's value: nothing to plan
             if (cfg.slice_width > 0) slice_network(&net, cfg.slice_width, cfg.max_slice_bits);
