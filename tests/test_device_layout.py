@@ -76,3 +76,53 @@ def test_layout_of_slice_shards_adds_up():
     ref = oracle.sv_zz(n, edges, g, b)
     np.testing.assert_allclose(zz, ref, rtol=0, atol=1e-12)
     assert E == pytest.approx(oracle.energy_from_zz(ref), abs=1e-10)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(slice_width=-1), dict(slice_width=8)])
+def test_operands_without_the_summed_variable_are_folded(kw):
+    """The kernels read an operand that lacks the bucket's summed variable
+    (a merged bucket's consumer gates) only from the gate table: every such
+    operand of the device layout is folded, and has rank <= 2."""
+    n, seed, p = 18, 5, 4
+    edges = synth.random_regular_graph(n, seed)
+    with qtgb.plan(n, edges, p, host_only=True, **kw) as pl:
+        B, O = pl.export()
+        DB, DO, _, _, _ = pl.export_device()
+    seen = 0
+    for k in range(len(B)):
+        for t in range(int(B["op_begin"][k]), int(B["op_begin"][k]) + int(B["n_ops"][k])):
+            if not DO["pairs_x"][t]:
+                seen += 1
+                assert (int(B["folded"][k]) >> (t - int(B["op_begin"][k]))) & 1
+                assert O["rank"][t] <= 2 and DO["leaf"][t] == 1
+    assert (seen > 0) == bool((B["n_sum"] > 1).any())
+
+
+def test_symmetric_graphs_deduplicate_to_one_network():
+    """K4 and the prism at p=1: every edge's lightcone is the whole graph and
+    all are isomorphic (edge-transitive graphs), so one network is contracted."""
+    for n, edges in ((4, synth.complete_graph(4)), (6, synth.prism_graph())):
+        with qtgb.plan(n, edges, 1, host_only=True, dedup=True) as pl:
+            st = pl.stats()
+        if n == 4:
+            assert st["n_unique"] == 1
+        else:  # the prism's triangle edges and its rung edges are two edge orbits
+            assert st["n_unique"] == 2
+
+
+def test_more_ranks_than_units():
+    """With more ranks than slices, some ranks hold nothing; the rest hold
+    every (edge, slice) unit exactly once."""
+    n, seed, p = 10, 3, 1
+    edges = synth.random_regular_graph(n, seed)
+    world = edges.shape[0] + 5
+    held = []
+    for r in range(world):
+        with qtgb.plan_shard(n, edges, p, world, r, host_only=True, slice_width=3) as pl:
+            mine = pl.shard_edges
+            if mine.size:
+                B, _ = pl.export()
+                held += sorted({(int(mine[net]), int(s)) for net, s in zip(B["network"], B["slice"])})
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=3) as full:
+        B, _ = full.export()
+    assert sorted(held) == sorted({(int(e), int(s)) for e, s in zip(B["network"], B["slice"])})
