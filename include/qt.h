@@ -243,6 +243,13 @@ int qt_plan_export_device(qt_plan_t plan, qt_dev_bucket *buckets, qt_dev_operand
                           uint32_t *net_first_factor, uint64_t *factor, int32_t *graph_owned,
                           int64_t *n_factors);
 
+/* Pass k (0 <= k < qt_plan_stats.n_passes) of a plan that runs in passes,
+ * for host-side inspection: *pass is a handle owned by `plan` (valid while
+ * it lives; do not free it), pass_edges (may be NULL, else n_edges int32 of
+ * room) receives the graph edges of the pass's networks in its order, and
+ * *n_edges their count. QT_ESTATE for a plan without passes. */
+int qt_plan_pass(qt_plan_t plan, int32_t k, qt_plan_t *pass, int32_t *pass_edges, int32_t *n_edges);
+
 /* Lightcone deduplication (host-side inspection): rep[i] = the network whose
  * value network i takes (i itself when it is contracted); n_networks int32. */
 int qt_plan_export_reps(qt_plan_t plan, int32_t *rep);

@@ -942,6 +942,17 @@ int qt_plan_export_device(qt_plan_t P, qt_dev_bucket* buckets, qt_dev_operand* o
     return QT_OK;
 }
 
+int qt_plan_pass(qt_plan_t P, int32_t k, qt_plan_t* pass, int32_t* pass_edges, int32_t* n_edges) {
+    if (!P || !pass || !n_edges) return QT_EINVAL;
+    if (P->parts.empty()) return QT_ESTATE;
+    if (k < 0 || k >= (int32_t)P->parts.size()) return QT_EINVAL;
+    *pass = P->parts[k].get();
+    const auto& pe = P->part_edges[k];
+    *n_edges = (int32_t)pe.size();
+    if (pass_edges && !pe.empty()) std::memcpy(pass_edges, pe.data(), pe.size() * sizeof(int32_t));
+    return QT_OK;
+}
+
 int qt_plan_export_reps(qt_plan_t P, int32_t* rep) {
     if (!P || !rep) return QT_EINVAL;
     for (size_t i = 0; i < P->hp.nets.size(); ++i) rep[i] = P->hp.nets[i].rep >= 0 ? P->hp.nets[i].rep : (int32_t)i;

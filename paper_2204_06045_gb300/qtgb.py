@@ -24,7 +24,7 @@ EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "q
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
            "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed",
-           "qt_plan_export_reps", "qt_plan_export_device")
+           "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass")
 
 
 class QTError(RuntimeError):
@@ -112,6 +112,7 @@ def lib():
         L.qt_plan_export_fixed.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_export_reps.argtypes = [vp, i32p]
         L.qt_plan_export_device.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+        L.qt_plan_pass.argtypes = [vp, i32, ctypes.POINTER(vp), i32p, i32p]
         L.qt_plan_shard.argtypes = [i32, i32, i32p, i32, i32, i32, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp), i32p,
                                     i32p]
         L.qt_last_imag.argtypes = [vp, dp]
@@ -131,7 +132,7 @@ def lib():
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
                      "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard",
-                     "qt_plan_export_fixed", "qt_plan_export_reps", "qt_plan_export_device"):
+                     "qt_plan_export_fixed", "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -187,8 +188,9 @@ def _stream_ptr(stream):
 class Plan:
     """A planned QAOA MaxCut energy evaluation on one graph or a batch of graphs."""
 
-    def __init__(self, handle, n_edges_per_graph, p, dtype, n_vertices):
+    def __init__(self, handle, n_edges_per_graph, p, dtype, n_vertices, owned=True):
         self._h = ctypes.c_void_p(handle)
+        self._owned = owned  # False: a pass of another plan, which frees it
         self.n_edges = list(n_edges_per_graph)
         self.n_vertices = list(n_vertices)
         self.p = p
@@ -280,7 +282,7 @@ class Plan:
         return cls(h.value, ms.tolist(), p, opts.get("dtype", "c64"), ns.tolist())
 
     def close(self):
-        if self._h is not None and self._h.value:
+        if self._h is not None and self._h.value and self._owned:
             lib().qt_plan_free(self._h)
         self._h = None
 
@@ -345,6 +347,20 @@ class Plan:
         _check(lib().qt_plan_export_device(self._h, b.ctypes.data, o.ctypes.data, nff.ctypes.data, f.ctypes.data,
                                            go.ctypes.data, ctypes.byref(nf)), "qt_plan_export_device")
         return b[:st["n_buckets"]], o[:st["n_operands"]], nff, f[:nf.value], go[:st["n_graphs"]]
+
+    def passes(self):
+        """The passes of a plan that runs in passes: (pass plan, its graph edges) pairs. The pass
+        plans belong to this plan (valid while it is open)."""
+        out = []
+        for k in range(self.stats()["n_passes"] if self.stats()["pass_arena_bytes"] else 0):
+            h = ctypes.c_void_p()
+            edges = np.zeros(max(1, sum(self.n_edges)), dtype=np.int32)
+            cnt = ctypes.c_int32(0)
+            _check(lib().qt_plan_pass(self._h, k, ctypes.byref(h), edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      ctypes.byref(cnt)), "qt_plan_pass")
+            out.append((Plan(h.value, [cnt.value], self.p, self.dtype, self.n_vertices, owned=False),
+                        edges[:cnt.value].copy()))
+        return out
 
     def export_reps(self) -> np.ndarray:
         """Per network, the network whose value it takes (itself when contracted)."""

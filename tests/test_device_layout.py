@@ -126,3 +126,27 @@ def test_more_ranks_than_units():
     with qtgb.plan(n, edges, p, host_only=True, slice_width=3) as full:
         B, _ = full.export()
     assert sorted(held) == sorted({(int(e), int(s)) for e, s in zip(B["network"], B["slice"])})
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(slice_width=6)])
+def test_layout_of_energy_passes_adds_up(kw):
+    """opts.energy_budget_bytes: each pass's own device arrays, emulated, give
+    partial per-edge values and energies (a network's slice 0 in one pass
+    counting the edge's 1/2) that sum to the state vector's."""
+    n, seed, p = 14, 22, 3
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, host_only=True, dtype="c128", **kw) as whole:
+        budget = whole.stats()["arena_bytes"] // 6
+    zz = np.zeros(edges.shape[0])
+    E = 0.0
+    with qtgb.plan(n, edges, p, host_only=True, dtype="c128", energy_budget_bytes=budget, **kw) as pl:
+        passes = pl.passes()
+        assert len(passes) == pl.stats()["n_passes"] > 1
+        for part, pe in passes:
+            vals, energies = emulate(part, g, b, p)
+            zz[pe] += vals.real
+            E += energies[0]
+    ref = oracle.sv_zz(n, edges, g, b)
+    np.testing.assert_allclose(zz, ref, rtol=0, atol=1e-12)
+    assert E == pytest.approx(oracle.energy_from_zz(ref), abs=1e-10)
