@@ -112,9 +112,10 @@ typedef struct {
     int32_t dedup;         /* nonzero: lightcone deduplication. Within each graph, networks whose
                               lightcones are isomorphic (the qubits within distance p of the edge,
                               labelled by distance) are contracted once: the others take that
-                              network's value. Forward plans only (ignored with gradients or
-                              energy_budget_bytes; a shard deduplicates the networks it holds whole).
-                              0: every network is contracted */
+                              network's value; in gradient plans the reverse sweep seeds it once for
+                              its whole class. Ignored for plans in passes (energy_budget_bytes, or
+                              adjoint_budget_bytes with gradients); a shard deduplicates the networks
+                              it holds whole. 0: every network is contracted */
     size_t energy_budget_bytes; /* energy plans (single graph): device bytes for the gate tables and
                               results; a plan that needs more runs in passes that fit, over the
                               networks' slices (opts.slice_width), on one shared arena; per-edge values

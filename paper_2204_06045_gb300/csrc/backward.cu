@@ -25,7 +25,8 @@ namespace {
 // ---------------------------------------------------------------------------
 
 // Each root's cotangent is the product of its network's other roots (1 when,
-// as usual, the network is connected).
+// as usual, the network is connected), times the number of networks sharing
+// the network's value (deduplicated plans; 1 otherwise).
 template <typename R>
 __global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
     using C = typename CT<R>::c;
@@ -41,9 +42,10 @@ __global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
             vr = nr;
             vi = ni;
         }
+        const double w = de.net_weight ? (double)de.net_weight[net] : 1.0;
         C c;
-        c.x = (R)vr;
-        c.y = (R)vi;
+        c.x = (R)(vr * w);
+        c.y = (R)(vi * w);
         arena[de.buckets[de.root_bucket[r]].out_off + cot_delta] = c;
     }
 }

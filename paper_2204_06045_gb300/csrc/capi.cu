@@ -181,6 +181,7 @@ int upload(qt_plan_t P) {
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
         {hp.unit_prog.data(), bytes_of(hp.unit_prog), 0},     {hp.net_first_factor.data(), bytes_of(hp.net_first_factor), 0},
         {hp.factor.data(), bytes_of(hp.factor), 0},            {hp.graph_owned.data(), bytes_of(hp.graph_owned), 0},
+        {hp.net_weight.data(), bytes_of(hp.net_weight), 0},
     };
     size_t total = 0;
     for (auto& pc : pieces) {
@@ -236,6 +237,7 @@ int upload(qt_plan_t P) {
     de.net_first_factor = reinterpret_cast<const uint32_t*>(base + pieces[9].off);
     de.factor = reinterpret_cast<const uint64_t*>(base + pieces[10].off);
     de.graph_owned = reinterpret_cast<const int32_t*>(base + pieces[11].off);
+    de.net_weight = hp.net_weight.empty() ? nullptr : reinterpret_cast<const int32_t*>(base + pieces[12].off);
     de.n_graphs = n_graphs;
     de.arena = P->d_arena;
     de.zz = P->d_out;
@@ -691,7 +693,7 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     cfg.slice_width = cfg.with_grad ? 0 : sw;  // the reverse sweep takes unsliced networks
     cfg.max_slice_bits = o.max_slice_bits ? o.max_slice_bits : 8;
     // a duplicate network takes its representative's value within one plan: not across passes
-    cfg.dedup = o.dedup != 0 && !cfg.with_grad && o.energy_budget_bytes == 0;
+    cfg.dedup = o.dedup != 0 && o.energy_budget_bytes == 0 && !(cfg.with_grad && o.adjoint_budget_bytes > 0);
     for (int c = 0; c < qt::kWidthClasses; ++c) {
         if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
         cfg.tile_cap[c] = o.tile_cap[c];

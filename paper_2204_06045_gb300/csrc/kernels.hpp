@@ -53,6 +53,8 @@ struct DevEpilogue {
     const uint32_t* net_first_factor;  // n_nets + 1
     const uint64_t* factor;  // arena element offsets; kFirstFactor marks the first factor of each slice
     const int32_t* graph_owned;  // n_graphs: networks whose 1/2 the energy counts (all, unless sharded by slice)
+    const int32_t* net_weight;   // gradient plans with deduplicated networks: per network, the networks
+                                 // sharing its value (its class; 0 for a duplicate); null: 1 each
     int32_t n_graphs;
     const void* arena;
     double* zz;        // n_nets

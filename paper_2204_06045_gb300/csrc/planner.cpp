@@ -1228,6 +1228,7 @@ int layout_plan(HostPlan* hp) {
     hp->factor.clear();
     hp->graph_owned.assign(graphs.size(), 0);
     hp->n_unique = 0;
+    hp->net_weight.clear();
     hp->n_slices = 0;
     for (int i = 0; i < n_nets; ++i) {
         const NetPlan& np = hp->nplans[i];
@@ -1369,6 +1370,11 @@ int layout_plan(HostPlan* hp) {
             hp->n_slices++;
         }
         hp->n_unique += net.rep < 0 ? 1 : 0;
+        if (net.rep >= 0) {  // the reverse sweep seeds a representative once for its whole class
+            if (hp->net_weight.empty()) hp->net_weight.assign(n_nets, 1);
+            hp->net_weight[net.rep]++;
+            hp->net_weight[i] = 0;
+        }
         hp->net_first_factor.push_back((uint32_t)hp->factor.size());
         if ((int)hp->graph_owned.size() <= net.graph) hp->graph_owned.resize(net.graph + 1, 0);
         hp->graph_owned[net.graph] += net.owner ? 1 : 0;

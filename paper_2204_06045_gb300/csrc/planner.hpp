@@ -132,6 +132,8 @@ struct HostPlan {
     std::vector<uint32_t> net_first_factor;  // n_nets + 1
     std::vector<uint64_t> factor;
     std::vector<int32_t> graph_owned;        // per graph: networks whose 1/2 the energy counts
+    std::vector<int32_t> net_weight;         // deduplicated plans: per network, the networks sharing its
+                                             // value (0 for a duplicate); empty without duplicates
     uint64_t n_slices = 0;               // slices over all networks (1 per unsliced network)
     uint64_t n_unique = 0;               // networks contracted (the others take a representative's value)
     std::vector<DRun> runs;             // static claim order (all groups, or the groups of buckets without producers)

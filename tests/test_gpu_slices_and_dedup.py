@@ -260,3 +260,21 @@ def test_deduplicated_plan_without_device_allocation():
         energies, zz = pl.energy_noalloc(g, b)
     ref = oracle.sv_zz(n, edges, g, b)
     assert scaled_err(zz, ref) <= TOL["c128"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_deduplicated_gradient_matches_the_full_plan(dtype):
+    """opts.dedup with gradients: the reverse sweep seeds each representative
+    once for its whole class; energy and derivatives equal the full plan's."""
+    n, seed, p = 60, 3, 2
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True, dedup=True) as pl:
+        assert pl.stats()["n_unique"] < edges.shape[0]
+        E, dg, db = pl.energy_grad(g, b)
+    with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True) as pl:
+        E_f, dg_f, db_f = pl.energy_grad(g, b)
+    tol = {"c128": 1e-9, "c64": 1e-4}[dtype]
+    assert abs(E[0] - E_f[0]) <= tol * abs(E_f[0])
+    np.testing.assert_allclose(dg, dg_f, rtol=0, atol=tol * max(1.0, np.abs(dg_f).max()))
+    np.testing.assert_allclose(db, db_f, rtol=0, atol=tol * max(1.0, np.abs(db_f).max()))

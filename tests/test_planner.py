@@ -570,16 +570,17 @@ def test_deduplicated_networks_take_their_representatives_values(n, seed, p):
         np.testing.assert_allclose(mine.real, oracle.sv_zz(n, edges, g, b), rtol=0, atol=1e-12)
 
 
-def test_dedup_stays_within_a_graph_and_off_for_gradients():
+def test_dedup_stays_within_a_graph_and_off_for_passes():
     graphs = [(40, synth.random_regular_graph(40, 1)), (40, synth.random_regular_graph(40, 2))]
     with qtgb.plan_batch(graphs, 2, host_only=True, dedup=True, slice_width=-1) as pl:
         R = pl.export_reps()
     m0 = graphs[0][1].shape[0]
     assert (R[:m0] < m0).all() and (R[m0:] >= m0).all()  # no sharing across graphs (their angles differ)
     assert len(np.unique(R[:m0])) < m0 and len(np.unique(R[m0:])) < R.size - m0
-    with host_plan(40, graphs[0][1], 2, dedup=True, with_grad=True) as pl:
-        st = pl.stats()
-    assert st["n_unique"] == st["n_networks"]
+    with host_plan(40, graphs[0][1], 2, dedup=True, with_grad=True) as pl:  # the sweep seeds a class once
+        assert pl.stats()["n_unique"] < pl.stats()["n_networks"]
+    with host_plan(40, graphs[0][1], 2, dedup=True, with_grad=True, adjoint_budget_bytes=1 << 16) as pl:
+        assert pl.stats()["n_unique"] == pl.stats()["n_networks"]  # plans in passes contract every network
 
 
 def test_bucket_einsum_spec_is_the_contraction():
