@@ -4,7 +4,10 @@ Usage: python tests/golden/make_golden.py [name ...]
 Names: c2_sv (N=30 p=4 state vector, ~16 GiB of host memory, minutes),
        c5_grad (N=20 p=4 parameter-shift gradient), c5_bucket (N=50 p=4 bucket
        elimination at the seeded angles), c4_bucket (every edge of N=1000 p=5
-       by bucket elimination in a min-fill order, ~minutes).
+       by bucket elimination in a min-fill order, ~minutes), c5_fd (central
+       differences of 8 sampled N=50 p=4 edges' share of the energy, bucket
+       elimination), dedup_fd (the same for every edge of an N=60 p=2 graph
+       whose lightcones repeat).
 Each file records the seeds and the oracle route that produced it. Inputs come
 from the seeded generators in ``paper_2204_06045_gb300.synth``; every value is
 computed by ``oracle`` and nothing else.
@@ -119,7 +122,59 @@ def c4_bucket():
            rows)
 
 
-JOBS = {"c2_sv": c2_sv, "c5_grad": c5_grad, "c5_bucket": c5_bucket, "c4_bucket": c4_bucket}
+def _fd_share(n, edges, g, b, sel, h):
+    """Energy share E_S = |S|/2 - 1/2 sum_{e in S} <Z_jZ_k> of the edges in S and its
+    central differences (step h) in every angle; each <Z_jZ_k> by the oracle's
+    bucket elimination in its own min-fill order (route 2, complex128)."""
+    def E(gg, bb):
+        s = 0.0
+        for e in sel:
+            v, _ = oracle.edge_bucket_min_fill(n, edges, gg, bb, int(e), seed=int(e), max_width=30)
+            s += v.real
+        return 0.5 * len(sel) - 0.5 * s
+    dg, db = oracle.grad_fd(E, g, b, h=h)
+    return E(g, b), dg, db
+
+
+def _write_fd(name, header, n, edges, g, b, sel, h):
+    t = time.time()
+    E, dg, db = _fd_share(n, edges, g, b, sel, h)
+    dt = time.time() - t
+    rows = [["gamma"] + [repr(float(x)) for x in g], ["beta"] + [repr(float(x)) for x in b],
+            ["edges"] + [str(int(e)) for e in sel], ["h", repr(h)], ["energy", repr(E)],
+            ["dE_dgamma"] + [repr(float(x)) for x in dg], ["dE_dbeta"] + [repr(float(x)) for x in db]]
+    _write(name, header + [f"({oracle.get_threads()} threads, {dt:.0f} s). Written by tests/golden/make_golden.py."],
+           rows)
+
+
+def c5_fd():
+    """N=50 p=4 (seed 1000): 8 edges drawn by PCG64(5050) without replacement."""
+    n, seed, p = 50, 1000, 4
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    sel = np.sort(np.random.default_rng(5050).choice(edges.shape[0], size=8, replace=False))
+    _write_fd("c5_n50_p4_fd.txt",
+              [f"Energy share of 8 sampled edges and its angle derivatives on the seeded random 3-regular graph",
+               f"N={n} (seed {seed}), p={p}, angles synth.angles(p, seed); edges drawn by numpy PCG64(5050).",
+               "E_S = |S|/2 - 1/2 sum_{e in S} <Z_jZ_k>; derivatives by central differences (step h) of E_S,",
+               "every <Z_jZ_k> by oracle.edge_bucket_min_fill (complex128 bucket elimination, route 2)"],
+              n, edges, g, b, sel, 1e-5)
+
+
+def dedup_fd():
+    """N=60 p=2 (seed 3), every edge: a graph whose lightcones repeat."""
+    n, seed, p = 60, 3, 2
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    _write_fd("dedup_n60_p2_fd.txt",
+              [f"Energy and angle derivatives on the seeded random 3-regular graph N={n} (seed {seed}), p={p},",
+               "angles synth.angles(p, seed); many of its lightcones are isomorphic. Derivatives by central",
+               "differences (step h) of E, every <Z_jZ_k> by oracle.edge_bucket_min_fill (route 2)"],
+              n, edges, g, b, np.arange(edges.shape[0]), 1e-5)
+
+
+JOBS = {"c2_sv": c2_sv, "c5_grad": c5_grad, "c5_bucket": c5_bucket, "c4_bucket": c4_bucket, "c5_fd": c5_fd,
+        "dedup_fd": dedup_fd}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(JOBS)

@@ -68,7 +68,43 @@ def test_n20_p4_matches_parameter_shift_golden(dtype, tol, sched):
     assert abs(E[0] - rows["energy"][0]) <= (1e-10 if dtype == "c128" else 1e-5) * abs(E[0])
 
 
-def test_c5_n50_p4_matches_finite_differences():
+def _golden_rows(name):
+    rows = {}
+    for line in (GOLDEN / name).read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            rows[k] = np.array([float(x) for x in v])
+    return rows
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_c5_n50_p4_sampled_edges_match_oracle_finite_differences(dtype):
+    """N=50 p=4 (seed 1000), 8 seeded edges: the adjoint of a subset plan of
+    their networks against central differences (h = 1e-5) of their energy
+    share computed by the oracle's own bucket elimination (stored values)."""
+    rows = _golden_rows("c5_n50_p4_fd.txt")
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    np.testing.assert_array_equal(g, rows["gamma"])
+    np.testing.assert_array_equal(b, rows["beta"])
+    sel = rows["edges"].astype(np.int32)
+    with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, with_grad=True) as pl:
+        E, dg, db = pl.energy_grad(g, b)
+    ref = np.concatenate([rows["dE_dgamma"], rows["dE_dbeta"]])
+    got = np.concatenate([dg, db])
+    if dtype == "c128":
+        assert np.abs(got - ref).max() <= 1e-6, (got, ref)
+        assert abs(E[0] - rows["energy"][0]) <= 1e-10 * abs(rows["energy"][0])
+    else:
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), (got, ref)
+        assert abs(E[0] - rows["energy"][0]) <= 1e-5 * abs(rows["energy"][0])
+
+
+def test_c5_n50_p4_adjoint_matches_differences_of_its_own_energy():
+    """Self-consistency of the whole N=50 p=4 graph: the complex128 adjoint
+    against central differences of this library's own complex128 energy (the
+    oracle comparison is the sampled-edge test above)."""
     n, p = 50, 4
     edges = synth.random_regular_graph(n, 1000)
     g, b = synth.angles(p, 1000)
@@ -130,6 +166,36 @@ def test_torch_autograd_function():
     ps = oracle.grad_param_shift(n, edges, g0, b0)
     np.testing.assert_allclose(g.grad.numpy(), 2 * ps[0], atol=1e-9)
     np.testing.assert_allclose(b.grad.numpy(), 2 * ps[1], atol=1e-9)
+    assert abs(E.item() - oracle.sv_energy(n, edges, g0, b0)) < 1e-10
+
+
+def test_torch_autograd_function_on_device(monkeypatch):
+    """CUDA angle tensors: the angles, energy and gradient stay on the device
+    (no host copy of the angles, no host sync inside forward); the values
+    match the oracle's parameter shift once the stream has run."""
+    n, p = 12, 2
+    edges = synth.random_regular_graph(n, 9)
+    g0, b0 = synth.angles(p, 9)
+    with grad_plan(n, edges, p) as pl:
+        g = torch.tensor(g0, dtype=torch.float64, device="cuda", requires_grad=True)
+        b = torch.tensor(b0, dtype=torch.float64, device="cuda", requires_grad=True)
+
+        def no_host(*a, **k):
+            raise AssertionError("host copy or host sync inside forward")
+
+        with monkeypatch.context() as m:
+            m.setattr(torch.Tensor, "cpu", no_host)
+            m.setattr(torch.Tensor, "numpy", no_host)
+            m.setattr(torch.Tensor, "item", no_host)
+            m.setattr(torch.cuda.Stream, "synchronize", no_host)
+            E = qtgb.qaoa_energy(pl, g, b)
+            (2.0 * E).backward()
+        assert E.is_cuda and g.grad.is_cuda and b.grad.is_cuda
+        torch.cuda.synchronize()
+        pl.sync()
+    ps = oracle.grad_param_shift(n, edges, g0, b0)
+    np.testing.assert_allclose(g.grad.cpu().numpy(), 2 * ps[0], atol=1e-9)
+    np.testing.assert_allclose(b.grad.cpu().numpy(), 2 * ps[1], atol=1e-9)
     assert abs(E.item() - oracle.sv_energy(n, edges, g0, b0)) < 1e-10
 
 

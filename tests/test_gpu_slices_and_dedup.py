@@ -278,3 +278,52 @@ def test_deduplicated_gradient_matches_the_full_plan(dtype):
     assert abs(E[0] - E_f[0]) <= tol * abs(E_f[0])
     np.testing.assert_allclose(dg, dg_f, rtol=0, atol=tol * max(1.0, np.abs(dg_f).max()))
     np.testing.assert_allclose(db, db_f, rtol=0, atol=tol * max(1.0, np.abs(db_f).max()))
+
+
+def test_deduplicated_gradient_matches_oracle_finite_differences():
+    """The N=60 p=2 graph whose lightcones repeat, complex128, deduplicated:
+    energy and gradient against central differences (h = 1e-5) of the
+    oracle's bucket-elimination energy (stored values)."""
+    rows = {}
+    for line in (Path(__file__).parent / "golden" / "dedup_n60_p2_fd.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            rows[k] = np.array([float(x) for x in v])
+    n, seed, p = 60, 3, 2
+    edges = synth.random_regular_graph(n, seed)
+    g, b = synth.angles(p, seed)
+    with qtgb.plan(n, edges, p, dtype="c128", with_grad=True, dedup=True) as pl:
+        assert pl.stats()["n_unique"] < edges.shape[0]
+        E, dg, db = pl.energy_grad(g, b)
+    ref = np.concatenate([rows["dE_dgamma"], rows["dE_dbeta"]])
+    assert np.abs(np.concatenate([dg, db]) - ref).max() <= 1e-6
+    assert abs(E[0] - rows["energy"][0]) <= 1e-10 * abs(rows["energy"][0])
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_deduplicated_batch_gradient_matches_full_plans(dtype):
+    """A batch gradient plan with deduplication over three graphs of
+    different sizes (duplicates in each): per graph, energy and derivatives
+    equal those of the full batch plan, and those of each graph planned alone."""
+    p = 2
+    graphs = [(60, synth.random_regular_graph(60, 3)), (40, synth.random_regular_graph(40, 8)),
+              (80, synth.random_regular_graph(80, 11))]
+    G = np.array([synth.angles(p, s)[0] for s in (3, 8, 11)])
+    B = np.array([synth.angles(p, s)[1] for s in (3, 8, 11)])
+    with qtgb.plan_batch(graphs, p, dtype=dtype, with_grad=True, dedup=True) as pl:
+        st = pl.stats()
+        E, dg, db = pl.energy_grad(G, B)
+    with qtgb.plan_batch(graphs, p, dtype=dtype, with_grad=True) as pl:
+        E_f, dg_f, db_f = pl.energy_grad(G, B)
+    assert st["n_unique"] < st["n_networks"]
+    tol = {"c128": 1e-9, "c64": 1e-4}[dtype]
+    for i, (n, e) in enumerate(graphs):
+        with qtgb.plan(n, e, p, dtype=dtype, with_grad=True, dedup=True) as one:
+            E1, dg1, db1 = one.energy_grad(G[i], B[i])
+        sl = slice(i * p, (i + 1) * p)
+        for a, b_ in ((E[i], E_f[i]), (E[i], E1[0])):
+            assert abs(a - b_) <= tol * abs(b_)
+        scale = max(1.0, np.abs(np.concatenate([dg_f[sl], db_f[sl]])).max())
+        for got_g, got_b in ((dg[sl], db[sl]), (dg1, db1)):
+            np.testing.assert_allclose(got_g, dg_f[sl], rtol=0, atol=tol * scale)
+            np.testing.assert_allclose(got_b, db_f[sl], rtol=0, atol=tol * scale)
