@@ -498,6 +498,10 @@ def _autograd_function():
         forward runs qt_energy_grad (the energy and its adjoint in one call) and
         keeps the gradient; backward scales it by the incoming gradient.
         ``gammas`` and ``betas`` are float64 tensors of length p (CPU or CUDA).
+        CUDA tensors stay on the device: their pointers and the current stream
+        go to the call, which enqueues its work without waiting for it, and the
+        energy and gradient are written to CUDA tensors (a kernel-side error
+        surfaces at the plan's next synchronous call or ``plan.sync()``).
         """
 
         @staticmethod
@@ -505,8 +509,14 @@ def _autograd_function():
             g = gammas.detach().to(torch.float64).contiguous()
             b = betas.detach().to(torch.float64).contiguous()
             if g.is_cuda:
-                torch.cuda.current_stream().synchronize()
-            E, dg, db = plan.energy_grad(g.cpu().numpy(), b.cpu().numpy())
+                b = b.to(g.device)
+                E = torch.empty(1, dtype=torch.float64, device=g.device)
+                dg = torch.empty(plan.p, dtype=torch.float64, device=g.device)
+                db = torch.empty(plan.p, dtype=torch.float64, device=g.device)
+                plan.energy_grad(g, b, energy=E, dgamma=dg, dbeta=db, stream=torch.cuda.current_stream(g.device))
+                ctx.save_for_backward(dg, db.to(betas.device))
+                return E[0]
+            E, dg, db = plan.energy_grad(g.numpy(), b.cpu().numpy())
             ctx.save_for_backward(torch.as_tensor(dg, dtype=torch.float64, device=gammas.device),
                                   torch.as_tensor(db, dtype=torch.float64, device=betas.device))
             return torch.as_tensor(E[0], dtype=torch.float64, device=gammas.device)
