@@ -113,9 +113,11 @@ typedef struct {
                               lightcones are isomorphic (the qubits within distance p of the edge,
                               labelled by distance) are contracted once: the others take that
                               network's value; in gradient plans the reverse sweep seeds it once for
-                              its whole class. Ignored for plans in passes (energy_budget_bytes, or
-                              adjoint_budget_bytes with gradients); a shard deduplicates the networks
-                              it holds whole. 0: every network is contracted */
+                              its whole class. A budget (energy_budget_bytes, or
+                              adjoint_budget_bytes with gradients) that the deduplicated plan fits
+                              keeps it; one it exceeds runs every network in passes, without
+                              deduplication. A shard deduplicates the networks it holds whole.
+                              0: every network is contracted */
     size_t energy_budget_bytes; /* energy plans (single graph): device bytes for the gate tables and
                               results; a plan that needs more runs in passes that fit, over the
                               networks' slices (opts.slice_width), on one shared arena; per-edge values

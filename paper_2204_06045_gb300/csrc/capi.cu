@@ -692,8 +692,9 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     const int sw = o.slice_width == 0 ? (o.dtype == QT_C128 ? 20 : 22) : std::max(0, o.slice_width);
     cfg.slice_width = cfg.with_grad ? 0 : sw;  // the reverse sweep takes unsliced networks
     cfg.max_slice_bits = o.max_slice_bits ? o.max_slice_bits : 8;
-    // a duplicate network takes its representative's value within one plan: not across passes
-    cfg.dedup = o.dedup != 0 && o.energy_budget_bytes == 0 && !(cfg.with_grad && o.adjoint_budget_bytes > 0);
+    // a duplicate network takes its representative's value within one plan, so passes do
+    // not deduplicate; the choice waits until the deduplicated plan's size is known
+    cfg.dedup = o.dedup != 0;
     for (int c = 0; c < qt::kWidthClasses; ++c) {
         if (o.tile_cap[c] != 0 && (o.tile_cap[c] < 1 || o.tile_cap[c] > 11)) return QT_EINVAL;
         cfg.tile_cap[c] = o.tile_cap[c];
@@ -715,12 +716,27 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
         return QT_EINVAL;
     }
     if (rc != QT_OK) return rc;
-    if (o.arena_bytes && (size_t)P->hp.total_elems * P->esize > o.arena_bytes) return QT_ENOMEM;
     P->arena_bytes = (size_t)P->hp.total_elems * P->esize;
+    const size_t budget = cfg.with_grad ? o.adjoint_budget_bytes : o.energy_budget_bytes;
+    const bool passes = budget > 0 && P->arena_bytes > budget;
+    if (passes && cfg.dedup) {
+        // over budget even deduplicated: plan every network, then split it into passes
+        cfg.dedup = false;
+        P->hp = qt::HostPlan();
+        try {
+            rc = qt::build_host_plan(graphs, cfg, &P->hp);
+        } catch (const std::bad_alloc&) {
+            return QT_ENOMEM;
+        } catch (...) {
+            return QT_EINVAL;
+        }
+        if (rc != QT_OK) return rc;
+        P->arena_bytes = (size_t)P->hp.total_elems * P->esize;
+    }
+    if (o.arena_bytes && P->arena_bytes > o.arena_bytes) return QT_ENOMEM;
     P->host_only = o.host_only != 0;
     P->trace = o.trace != 0;
-    if ((cfg.with_grad && o.adjoint_budget_bytes > 0 && P->arena_bytes > o.adjoint_budget_bytes) ||
-        (!cfg.with_grad && o.energy_budget_bytes > 0 && P->arena_bytes > o.energy_budget_bytes)) {
+    if (passes) {
         rc = make_passes(P.get(), graphs, p, o);
         if (rc != QT_OK) return rc;
         *out = P.release();

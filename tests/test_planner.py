@@ -583,6 +583,25 @@ def test_dedup_stays_within_a_graph_and_off_for_passes():
         assert pl.stats()["n_unique"] == pl.stats()["n_networks"]  # plans in passes contract every network
 
 
+@pytest.mark.parametrize("grad", [False, True])
+def test_dedup_kept_under_a_budget_the_deduplicated_plan_fits(grad):
+    """A budget set but not exceeded by the deduplicated plan keeps deduplication
+    (no passes); one below it runs every network in passes."""
+    n, seed, p = 60, 3, 2
+    edges = synth.random_regular_graph(n, seed)
+    key = "adjoint_budget_bytes" if grad else "energy_budget_bytes"
+    with host_plan(n, edges, p, dedup=True, with_grad=grad, slice_width=-1) as pl:
+        st = pl.stats()
+    assert st["n_unique"] < st["n_networks"]
+    with host_plan(n, edges, p, dedup=True, with_grad=grad, slice_width=-1, **{key: st["arena_bytes"]}) as pl:
+        s2 = pl.stats()
+        assert s2["n_unique"] == st["n_unique"] and s2["n_passes"] == 1 and s2["pass_arena_bytes"] == 0
+    with host_plan(n, edges, p, dedup=True, with_grad=grad, slice_width=-1, **{key: st["arena_bytes"] // 2}) as pl:
+        s3 = pl.stats()
+        assert s3["n_passes"] >= 2 and s3["n_unique"] == s3["n_networks"]
+        assert 0 < s3["pass_arena_bytes"] <= st["arena_bytes"] // 2
+
+
 def test_bucket_einsum_spec_is_the_contraction():
     """bench.bucket_einsum (the subscripts the library-einsum comparison runs):
     numpy.einsum over random operands reshaped by it equals the bucket
