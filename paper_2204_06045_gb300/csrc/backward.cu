@@ -37,7 +37,7 @@ __global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
         double vr = 1.0, vi = 0.0;
         for (uint32_t q = de.net_first_root[net]; q < de.net_first_root[net + 1]; ++q) {
             if (q == r) continue;
-            const C v = arena[de.buckets[de.root_bucket[q]].out_off];
+            const C v = elem_ld(arena, de.buckets[de.root_bucket[q]].out_off);
             const double nr = vr * (double)v.x - vi * (double)v.y, ni = vr * (double)v.y + vi * (double)v.x;
             vr = nr;
             vi = ni;
@@ -46,31 +46,23 @@ __global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
         C c;
         c.x = (R)(vr * w);
         c.y = (R)(vi * w);
-        arena[de.buckets[de.root_bucket[r]].out_off + cot_delta] = c;
+        elem_st(arena, de.buckets[de.root_bucket[r]].out_off + cot_delta, c);
     }
 }
 
-__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-
 // Pair (x = 0, x = 1) of an operand entry through the read-only path: every
-// value the reverse sweep reads was written by an earlier launch.
+// value the reverse sweep reads was written by an earlier launch. Tensors are
+// stored in planar pairs (device_common.cuh).
 __device__ __forceinline__ Pair<float2> ldg_pair(const float2* p) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    return unpack_pair(__ldg(reinterpret_cast<const float4*>(p)));
 }
-__device__ __forceinline__ Pair<double2> ldg_pair(const double2* p) {
-    return {__ldg(p), __ldg(p + 1)};
-}
+__device__ __forceinline__ Pair<double2> ldg_pair(const double2* p) { return unpack_pair(__ldg(p), __ldg(p + 1)); }
 __device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+    *reinterpret_cast<float4*>(p) = pack_pair(a, b);
 }
 __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
-    p[0] = a;
-    p[1] = b;
+    p[0] = make_double2(a.x, b.x);
+    p[1] = make_double2(a.y, b.y);
 }
 __device__ __forceinline__ void smem_add(float2* p, float2 v) {
     atomicAdd(&p->x, v.x);
@@ -148,7 +140,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
     for (uint32_t k = 0; k < (1u << kb); ++k) {
         const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
         C r = C{};
-        if (active) r = __ldg(rbar + o);
+        if (active) r = elem_ldg(rbar, o);
         Pair<C> P[NMAX];
         uint32_t li[NMAX];  // pair index within the tile's block of the operand
 #pragma unroll
@@ -181,7 +173,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
                     const C c = cmul(pre, S[t]);  // Rbar[o] * prod_{u != t} P[u]
                     switch (mode[t]) {
                         case kBwdGate: {
-                            const C d = __ldg(arena + off[t] + db.dleaf_delta + 2u * (base[t] + li[t]) + x);
+                            const C d = elem_ldg(arena + off[t] + db.dleaf_delta + 2u * (base[t] + li[t]), x);
                             const R v = c.x * d.x - c.y * d.y;
                             const R y = v - comp[t];
                             const R s2 = acc[t] + y;
@@ -209,7 +201,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
                             break;
                         }
                         case kBwdAtomic:
-                            if (active) atomic_add_c(arena + off[t] + db.cot_delta + 2u * (base[t] + li[t]) + x, c);
+                            if (active) elem_atomic_add(arena + off[t] + db.cot_delta + 2u * (base[t] + li[t]), x, c);
                             break;
                         default:
                             break;
@@ -232,9 +224,9 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
             C* dst = arena + off[t] + db.cot_delta + 2u * base[t];
             for (uint32_t e = lane; e < fp; e += 32) {
                 if (mode[t] == kBwdRedStore)
-                    dst[e] = red[roff[t] + e];
+                    elem_st(dst, e, red[roff[t] + e]);
                 else
-                    atomic_add_c(dst + e, red[roff[t] + e]);
+                    elem_atomic_add(dst, e, red[roff[t] + e]);
             }
         }
     }
@@ -271,7 +263,7 @@ __global__ void k_zero_ranges(typename CT<R>::c* arena, const uint64_t* ranges, 
     for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
         C* p = arena + ranges[2 * r];
         const uint32_t cnt = (uint32_t)ranges[2 * r + 1];
-        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) p[i] = C{};
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) elem_st(p, i, C{});
     }
 }
 

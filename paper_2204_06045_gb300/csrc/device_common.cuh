@@ -38,6 +38,69 @@ struct Pair {
     C v0, v1;
 };
 
+// Element layout of every tensor (gate tables, results, cotangents): entries
+// 2k and 2k+1 form a pair -- the x = 0 and x = 1 entries of the summed
+// variable of the bucket that reads the tensor -- stored planar as
+// (Re[2k], Re[2k+1], Im[2k], Im[2k+1]). A pair starts at the byte where an
+// interleaved pair would (element 2k of a complex array), so pair addresses
+// are plain `base + 2k`; only single entries sit apart within their pair.
+// Every tensor starts at an even element offset.
+__device__ __forceinline__ Pair<float2> unpack_pair(float4 v) {
+    return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+__device__ __forceinline__ float4 pack_pair(float2 a, float2 b) { return make_float4(a.x, b.x, a.y, b.y); }
+__device__ __forceinline__ Pair<double2> unpack_pair(double2 re, double2 im) {
+    return {make_double2(re.x, im.x), make_double2(re.y, im.y)};
+}
+
+// Entry e of a tensor whose first element is `base` (read, write, atomic add).
+template <typename C>
+__device__ __forceinline__ auto elem_scalar(C* base, uint64_t e) {
+    using R = decltype(base->x);
+    return reinterpret_cast<R*>(base + (e & ~1ull)) + (e & 1u);  // its real part; the imaginary part is 2 further
+}
+template <typename C>
+__device__ __forceinline__ auto elem_scalar(const C* base, uint64_t e) {
+    using R = decltype(base->x);
+    return reinterpret_cast<const R*>(base + (e & ~1ull)) + (e & 1u);
+}
+template <typename C>
+__device__ __forceinline__ C elem_ld(const C* base, uint64_t e) {
+    const auto p = elem_scalar(base, e);
+    C v;
+    v.x = p[0];
+    v.y = p[2];
+    return v;
+}
+template <typename C>
+__device__ __forceinline__ C elem_ldg(const C* base, uint64_t e) {  // read-only path
+    const auto p = elem_scalar(base, e);
+    C v;
+    v.x = __ldg(p);
+    v.y = __ldg(p + 2);
+    return v;
+}
+template <typename C>
+__device__ __forceinline__ C elem_ldcg(const C* base, uint64_t e) {  // at L2 (written by another SM)
+    const auto p = elem_scalar(base, e);
+    C v;
+    v.x = __ldcg(p);
+    v.y = __ldcg(p + 2);
+    return v;
+}
+template <typename C>
+__device__ __forceinline__ void elem_st(C* base, uint64_t e, C v) {
+    const auto p = elem_scalar(base, e);
+    p[0] = v.x;
+    p[2] = v.y;
+}
+template <typename C>
+__device__ __forceinline__ void elem_atomic_add(C* base, uint64_t e, C v) {
+    const auto p = elem_scalar(base, e);
+    atomicAdd(p, v.x);
+    atomicAdd(p + 2, v.y);
+}
+
 // Bits of x selected by m, packed to the low end (parallel bit extract).
 __device__ __forceinline__ uint32_t pext_u32(uint32_t x, uint32_t m) {
     uint32_t r = 0, t = x & m;

@@ -32,31 +32,26 @@ constexpr int kUnroll = 4;  // iterations of 64 outputs in flight per warp
 // may have written them from another SM.
 __device__ __forceinline__ Pair<float2> ld_pair(const float2* T, uint64_t e, bool leaf) {
     const float4* p = reinterpret_cast<const float4*>(T + e);
-    float4 v = leaf ? __ldg(p) : __ldcg(p);
-    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    return unpack_pair(leaf ? __ldg(p) : __ldcg(p));
 }
 __device__ __forceinline__ Pair<double2> ld_pair(const double2* T, uint64_t e, bool leaf) {
     const double2* p = T + e;
-    double2 a = leaf ? __ldg(p) : __ldcg(p);
-    double2 b = leaf ? __ldg(p + 1) : __ldcg(p + 1);
-    return {a, b};
+    return unpack_pair(leaf ? __ldg(p) : __ldcg(p), leaf ? __ldg(p + 1) : __ldcg(p + 1));
 }
 
+// A pair through a generic pointer (shared memory, or a tensor written before this kernel).
 __device__ __forceinline__ Pair<float2> ld_pair_smem(const float2* p) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    return unpack_pair(*reinterpret_cast<const float4*>(p));
 }
-__device__ __forceinline__ Pair<double2> ld_pair_smem(const double2* p) { return {p[0], p[1]}; }
+__device__ __forceinline__ Pair<double2> ld_pair_smem(const double2* p) { return unpack_pair(p[0], p[1]); }
 
-__device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
-__device__ __forceinline__ double2 ldcg_c(const double2* p) { return __ldcg(p); }
-
+// Outputs o and o + 1 (o even): one pair.
 __device__ __forceinline__ void st_two(float2* out, uint64_t o, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(out + o) = make_float4(a.x, a.y, b.x, b.y);
+    *reinterpret_cast<float4*>(out + o) = pack_pair(a, b);
 }
 __device__ __forceinline__ void st_two(double2* out, uint64_t o, double2 a, double2 b) {
-    out[o] = a;
-    out[o + 1] = b;
+    out[o] = make_double2(a.x, b.x);
+    out[o + 1] = make_double2(a.y, b.y);
 }
 
 struct OpStage {
@@ -123,7 +118,7 @@ __device__ __forceinline__ void contract_tile(const DBucket& B, uint32_t chunk, 
                 C r0 = cadd(acc[u][0][0], acc[u][0][1]);
                 C r1 = cadd(acc[u][1][0], acc[u][1][1]);
                 if (B.n_out == 0) {
-                    out[0] = r0;  // scalar result: one output
+                    elem_st(out, 0, r0);  // scalar result: one output
                 } else {
                     st_two(out, (uint64_t)obase + ((uint64_t)i << 6) + ((uint64_t)lane << 1), r0, r1);
                 }
@@ -226,6 +221,8 @@ struct RunSlot {
     uint8_t hi_idx[kMaxFoldLeaves];  // their slots
     uint8_t hi_shift[kMaxFoldLeaves];// position of that bit within the chunk index
     uint8_t hi_ebit[kMaxFoldLeaves]; // bit of a gate-table entry's index holding the tensor's bit in the tile
+    uint8_t lsh[kMaxFoldLeaves][2];  // folded tensors within the tile: the bits of a table entry's index
+                                     // that give bits 0 and 1 of the tensor's entry (31: none); 255: above
     uint32_t unit_begin;             // a fused unit: 1 + its first entry in the unit list (0: none)
     uint32_t unit_count;
 };
@@ -268,17 +265,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-
-// Bits of j deposited at the set bits of m (parallel bit deposit).
-__device__ __forceinline__ uint32_t pdep_u32(uint32_t j, uint32_t m) {
-    uint32_t r = 0;
-    for (uint32_t k = 0; m; ++k) {
-        const uint32_t low = m & (0u - m);
-        if ((j >> k) & 1u) r |= low;
-        m ^= low;
-    }
-    return r;
-}
 
 // Queue positions are claimed with one atomic each; lane 0 claims the next
 // position as soon as it takes the current one, so the claim's round trip
@@ -400,7 +386,8 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             const C* T = static_cast<const C*>(dp.arena) + op.off;
             if ((op.flags & kOpLeaf) || results_ready) {
 #pragma unroll
-                for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = (op.flags & kOpLeaf) ? T[i] : ldcg_c(T + i);
+                for (int i = 0; i < kLeafSlots; ++i)
+                    rs.lval[op.slot][i] = (op.flags & kOpLeaf) ? elem_ld(T, i) : elem_ldcg(T, i);
             }
         } else {
             rs.goff[op.slot] = op.off;
@@ -445,6 +432,26 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             rs.dstep[t][lane] = ((m >> bit) & 1u) ? (uint16_t)(1u << __popc(m & ((1u << bit) - 1u))) : (uint16_t)0;
         }
     }
+    if (lane < rs.n_leaves) {
+        // table entry e = 2 j + x, j the tile outputs of leaf_u compressed: the
+        // tensor's entry index takes x (if it pairs over x) and then its output
+        // bits, the k-th of which is bit 1 + (its rank within leaf_u) of e
+        const uint32_t lm = rs.lmask[lane];
+        const uint32_t b0 = lm & (0u - lm), b1 = (lm & (lm - 1u)) & (0u - (lm & (lm - 1u)));  // its lowest two bits
+        const uint32_t p0 = 1u + __popc(rs.leaf_u & (b0 - 1u)), p1 = 1u + __popc(rs.leaf_u & (b1 - 1u));
+        uint32_t s0 = 31u, s1 = 31u;
+        if (lm & ~low)
+            s0 = 255u;
+        else if (rs.lx[lane]) {
+            s0 = 0u;
+            if (b0) s1 = p0;
+        } else {
+            if (b0) s0 = p0;
+            if (b1) s1 = p1;
+        }
+        rs.lsh[lane][0] = (uint8_t)s0;
+        rs.lsh[lane][1] = (uint8_t)s1;
+    }
     if (lane == 0) {
         rs.n_fast = fast ? (uint8_t)nf : (uint8_t)0;
         uint8_t nh = 0;
@@ -473,7 +480,7 @@ __device__ void load_folded_results(const DevPlan& dp, WarpSmem<R>& ws, int sl, 
         if (op.folded && !(op.flags & kOpLeaf)) {
             const typename CT<R>::c* T = static_cast<const typename CT<R>::c*>(dp.arena) + op.off;
 #pragma unroll
-            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = ldcg_c(T + i);
+            for (int i = 0; i < kLeafSlots; ++i) rs.lval[op.slot][i] = elem_ldcg(T, i);
         }
     }
     __syncwarp();
@@ -536,69 +543,6 @@ __device__ __forceinline__ bool issue_tile(const DevPlan& dp, WarpSmem<R>& ws, i
     return true;
 }
 
-// N operands from shared memory (the last may be the folded gate table), a
-// tile of 2^cb outputs written straight to global memory.
-template <typename R, int N>
-__device__ __forceinline__ void tile_from_smem(const typename CT<R>::c* const (&base)[N], const uint32_t (&mask)[N],
-                                               typename CT<R>::c* out, int cb, int n_out, uint32_t o0, int lane) {
-    using C = typename CT<R>::c;
-    const int lane_bits = cb >= 6 ? 5 : (cb >= 1 ? cb - 1 : 0);
-    const bool active = (lane >> lane_bits) == 0;
-    const uint32_t niter = cb >= 6 ? 1u << (cb - 6) : 1u;
-    const uint32_t lane_mask = (1u << (lane_bits + 1)) - 1u;
-    uint32_t lb[N], mi[N];
-    int si[N];
-    bool b0[N], contig[N];
-#pragma unroll
-    for (int t = 0; t < N; ++t) {
-        lb[t] = pext_u32((uint32_t)lane << 1, mask[t] & lane_mask);
-        mi[t] = cb >= 6 ? (mask[t] >> 6) & (niter - 1u) : 0u;
-        si[t] = __popc(mask[t] & 63u);
-        b0[t] = (mask[t] & 1u) != 0u;
-        contig[t] = (mi[t] & (mi[t] + 1u)) == 0u;
-    }
-    if (!active) return;
-    for (uint32_t i0 = 0; i0 < niter; i0 += kUnrollS) {
-        C acc[kUnrollS][2][2];
-#pragma unroll
-        for (int t = 0; t < N; ++t) {
-#pragma unroll
-            for (int u = 0; u < kUnrollS; ++u) {
-                const uint32_t i = i0 + u;
-                if (i < niter) {
-                    const uint32_t ip = contig[t] ? (i & mi[t]) : pext_u32(i, mi[t]);
-                    const uint32_t e = 2u * (lb[t] + (ip << si[t]));
-                    const Pair<C> a = ld_pair_smem(base[t] + e);
-                    const Pair<C> b = b0[t] ? ld_pair_smem(base[t] + e + 2) : a;
-                    if (t == 0) {
-                        acc[u][0][0] = a.v0;
-                        acc[u][0][1] = a.v1;
-                        acc[u][1][0] = b.v0;
-                        acc[u][1][1] = b.v1;
-                    } else {
-                        acc[u][0][0] = cmul(acc[u][0][0], a.v0);
-                        acc[u][0][1] = cmul(acc[u][0][1], a.v1);
-                        acc[u][1][0] = cmul(acc[u][1][0], b.v0);
-                        acc[u][1][1] = cmul(acc[u][1][1], b.v1);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kUnrollS; ++u) {
-            const uint32_t i = i0 + u;
-            if (i < niter) {
-                const C r0 = cadd(acc[u][0][0], acc[u][0][1]);
-                const C r1 = cadd(acc[u][1][0], acc[u][1][1]);
-                if (n_out == 0)
-                    out[0] = r0;
-                else
-                    st_two(out, (uint64_t)o0 + ((uint64_t)i << 6) + ((uint64_t)lane << 1), r0, r1);
-            }
-        }
-    }
-}
-
 // Any number of operands (descriptors re-read from shared memory per use).
 template <typename R>
 __device__ void tile_from_smem_generic(const WarpSmem<R>& ws, int sl, int st, typename CT<R>::c* out, uint32_t chunk,
@@ -652,11 +596,11 @@ __device__ void tile_from_smem_generic(const WarpSmem<R>& ws, int sl, int st, ty
                 const C r0 = cadd(acc[u][0][0], acc[u][0][1]);
                 const C r1 = cadd(acc[u][1][0], acc[u][1][1]);
                 if (rs.n_out == 0) {
-                    out[0] = r0;
+                    elem_st(out, 0, r0);
                 } else if (rs.merged == 0) {
                     st_two(out, (uint64_t)o0 + ((uint64_t)i << 6) + ((uint64_t)lane << 1), r0, r1);
                 } else {  // merged: outputs (o, s1 = 0, 1) add into result o
-                    out[((uint64_t)o0 >> 1) + ((uint64_t)i << 5) + (uint64_t)lane] = cadd(r0, r1);
+                    elem_st(out, ((uint64_t)o0 >> 1) + ((uint64_t)i << 5) + (uint64_t)lane, cadd(r0, r1));
                 }
             }
         }
@@ -672,133 +616,162 @@ __device__ __forceinline__ uint32_t opaque_zero() {
     asm volatile("mov.u32 %0, 0;" : "=r"(z));
     return z;
 }
-__device__ __forceinline__ Pair<float2> lds_pair(uint32_t a, const float2*) {
-    float4 v;
-    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+
+// Packed FP32 pairs (f32x2): two floats in one 64-bit register, operated on
+// by one instruction (sm_100 and later). A planar complex64 entry pair loads
+// as two of them: the real parts (x = 0, 1) and the imaginary parts.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
-__device__ __forceinline__ Pair<double2> lds_pair(uint32_t a, const double2*) {
-    double2 u, w;
-    asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(u.x), "=d"(u.y) : "r"(a));
-    asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w.x), "=d"(w.y) : "r"(a + 16u));
-    return {u, w};
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_neg(f32x2 a) { return a ^ 0x8000000080000000ull; }  // both signs, exact
+__device__ __forceinline__ float x2_lo(f32x2 a) { return __uint_as_float((uint32_t)a); }
+__device__ __forceinline__ float x2_hi(f32x2 a) { return __uint_as_float((uint32_t)(a >> 32)); }
+
+// Arithmetic of the tile loop on one output's entry pair (x = 0, 1): load from
+// shared memory, multiply by another operand's pair, sum over x, and add two
+// outputs' pairs (a merged bucket's s1 = 0 and 1). complex64 keeps the pair as
+// packed real and imaginary parts, so a complex product of both x is four
+// f32x2 instructions (and one integer sign flip) instead of eight; complex128
+// multiplies each entry in FP64.
+template <typename R>
+struct TileMath;
+template <>
+struct TileMath<float> {
+    struct P {
+        f32x2 re, im;
+    };
+    static __device__ __forceinline__ P load(uint32_t a) {
+        P r;
+        asm("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(r.re), "=l"(r.im) : "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ P mul(P p, P a) {
+        P r;
+        r.re = x2_fma(p.re, a.re, x2_neg(x2_mul(p.im, a.im)));
+        r.im = x2_fma(p.re, a.im, x2_mul(p.im, a.re));
+        return r;
+    }
+    static __device__ __forceinline__ float2 xsum(P p) {
+        return make_float2(x2_lo(p.re) + x2_hi(p.re), x2_lo(p.im) + x2_hi(p.im));
+    }
+    static __device__ __forceinline__ P add(P a, P b) { return {x2_add(a.re, b.re), x2_add(a.im, b.im)}; }
+};
+template <>
+struct TileMath<double> {
+    using P = Pair<double2>;
+    static __device__ __forceinline__ P load(uint32_t a) {
+        double2 re, im;
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(re.x), "=d"(re.y) : "r"(a));
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(im.x), "=d"(im.y) : "r"(a + 16u));
+        return unpack_pair(re, im);
+    }
+    static __device__ __forceinline__ P mul(P p, P a) { return {cmul(p.v0, a.v0), cmul(p.v1, a.v1)}; }
+    static __device__ __forceinline__ double2 xsum(P p) { return cadd(p.v0, p.v1); }
+    static __device__ __forceinline__ P add(P a, P b) { return {cadd(a.v0, b.v0), cadd(a.v1, b.v1)}; }
+};
+
+// Outputs o, o + 1 (o even) of a result: one planar pair, one store.
 __device__ __forceinline__ void stg_two(float2* p, float2 a, float2 b) {
-    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a.x), "f"(b.x), "f"(a.y), "f"(b.y));
 }
 __device__ __forceinline__ void stg_two(double2* p, double2 a, double2 b) {
-    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(a.x), "d"(a.y));
-    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p + 1), "d"(b.x), "d"(b.y));
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(a.x), "d"(b.x));
+    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p + 1), "d"(a.y), "d"(b.y));
 }
-__device__ __forceinline__ void stg_one(float2* p, float2 a) {
-    asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a.x), "f"(a.y));
-}
-__device__ __forceinline__ void stg_one(double2* p, double2 a) {
-    asm volatile("st.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(a.x), "d"(a.y));
+// One output per lane, lane l writing output l of `p` (32 consecutive
+// outputs, p even): lanes 2k and 2k + 1 hold one pair, which lane 2k stores.
+template <typename C>
+__device__ __forceinline__ void stg_lanes(C* p, C v, int lane) {
+    C w;
+    w.x = __shfl_xor_sync(kFull, v.x, 1);
+    w.y = __shfl_xor_sync(kFull, v.y, 1);
+    if ((lane & 1) == 0) stg_two(p + lane, v, w);
 }
 
-// The hot path for tiles of at least 64 outputs (cb = 6 + log2 NI): N
-// operands in shared memory, every loop fully unrolled. A lane owns outputs
-// 2*lane + {0,1} + 64*i; an operand's pair for such an output sits at the
-// lane's offset plus the steps of the iteration's bits, all fixed per group.
-template <typename R, int N, int NI>
-__device__ __forceinline__ void tile_fast(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
-                                          const RunSlot<R>& rs, typename CT<R>::c* out, int lane) {
+// The tile loop for tiles of at least 64 outputs (cb >= 6): N operands in
+// shared memory, the last of which may be the folded gate table. A lane owns
+// outputs 2*lane + {0,1} + 64*i, i < 2^(cb-6); an operand's pair for such an
+// output sits at the lane's offset (loff) plus the steps (dstep) of the set
+// bits of i, all fixed per group. U = 2^UB iterations are unrolled per trip
+// (cb >= 6 + UB), the trips running over i's bits above bit UB - 1, which
+// keeps the code small: every bucket shape runs one of a few loop bodies per
+// operand count. A merged bucket (s0, s1) adds a lane's two outputs (s1 = 0,
+// 1) into one result, lane + 32*i.
+template <typename R, int N, int U, bool Exact>
+__device__ __forceinline__ void tile_loop(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
+                                          const RunSlot<R>& rs, typename CT<R>::c* out, int lane, int n_rt) {
     using C = typename CT<R>::c;
-    constexpr uint32_t PB = 2 * sizeof(C);  // bytes of one (x=0, x=1) pair
-    constexpr int IB = NI == 1 ? 0 : NI == 2 ? 1 : NI == 4 ? 2 : NI == 8 ? 3 : NI == 16 ? 4 : 5;
-    uint32_t a0[N], second[N], d[N][IB > 0 ? IB : 1];
+    using M = TileMath<R>;
+    constexpr uint32_t PB = 2 * sizeof(C);  // bytes of one (x = 0, x = 1) pair
+    constexpr int UB = U == 1 ? 0 : U == 2 ? 1 : U == 4 ? 2 : 3;
+    constexpr int HB = 5 - UB;  // iteration bits above the unrolled ones (tiles of at most 2^11 outputs)
+    uint32_t a0[N], second[N], du[N][UB > 0 ? UB : 1], dh[N][HB];
 #pragma unroll
     for (int t = 0; t < N; ++t) {
         a0[t] = sbase[t] + PB * rs.loff[t][lane];
         second[t] = (smask[t] & 1u) ? PB : 0u;  // the lane's second output uses the next pair
 #pragma unroll
-        for (int k = 0; k < IB; ++k) d[t][k] = PB * rs.dstep[t][k];
-    }
-    const C* tag = nullptr;
+        for (int k = 0; k < UB; ++k) du[t][k] = PB * rs.dstep[t][k];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-        C p00, p01, p10, p11;  // [output][x]
+        for (int k = 0; k < HB; ++k) dh[t][k] = PB * rs.dstep[t][UB + k];
+    }
+    const uint32_t trips = 1u << (rs.cb - 6 - UB);
+    const bool merged = rs.merged != 0;
+    for (uint32_t j = 0; j < trips; ++j) {
+        uint32_t qb[N];
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            uint32_t q = a0[t];
+            qb[t] = a0[t];
 #pragma unroll
-            for (int k = 0; k < IB; ++k)
-                if ((i >> k) & 1) q += d[t][k];
-            const Pair<C> a = lds_pair(q, tag);
-            const Pair<C> b = lds_pair(q + second[t], tag);
-            if (t == 0) {
-                p00 = a.v0;
-                p01 = a.v1;
-                p10 = b.v0;
-                p11 = b.v1;
-            } else {
-                p00 = cmul(p00, a.v0);
-                p01 = cmul(p01, a.v1);
-                p10 = cmul(p10, b.v0);
-                p11 = cmul(p11, b.v1);
-            }
+            for (int k = 0; k < HB; ++k) qb[t] += ((j >> k) & 1u) ? dh[t][k] : 0u;
         }
-        const C r0 = cadd(p00, p01), r1 = cadd(p10, p11);
-        if constexpr (sizeof(R) == 4) {
-            if (rs.merged) {  // merged bucket: the lane's outputs are s1 = 0, 1 of result lane + 32*i
-                stg_one(out + (i * 32 + lane), cadd(r0, r1));
-                continue;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            typename M::P p0, p1;  // the lane's two outputs, each an (x = 0, 1) pair of products
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                if (!Exact && t >= n_rt) break;  // a uniform branch: the operand count of the group
+                uint32_t q = qb[t];
+#pragma unroll
+                for (int k = 0; k < UB; ++k)
+                    if ((u >> k) & 1) q += du[t][k];
+                const typename M::P a = M::load(q);
+                typename M::P b = a;
+                if (second[t]) b = M::load(q + second[t]);
+                if (t == 0) {
+                    p0 = a;
+                    p1 = b;
+                } else {
+                    p0 = M::mul(p0, a);
+                    p1 = M::mul(p1, b);
+                }
             }
+            const uint32_t i = j * U + (uint32_t)u;
+            if (merged)
+                stg_lanes(out + i * 32, M::xsum(M::add(p0, p1)), lane);
+            else
+                stg_two(out + (i * 64 + 2 * lane), M::xsum(p0), M::xsum(p1));
         }
-        stg_two(out + (i * 64 + 2 * lane), r0, r1);
     }
 }
 
-// A merged bucket's tile (cb >= 6) in complex128: operands as in tile_fast,
-// but a lane's two outputs are s1 = 0, 1 of one result, which the lane adds
-// (result lane + 32*i). A loop over the iterations rather than unrolled code:
-// FP64-bound, the complex128 kernel gains more from the smaller code than from
-// the unrolled addressing (complex64 keeps the pair sum inside tile_fast,
-// whose unrolled loads it needs).
-template <typename R, int N>
-__device__ __forceinline__ void tile_merged(const uint32_t (&sbase)[N], const uint32_t (&smask)[N],
-                                            const RunSlot<R>& rs, typename CT<R>::c* out, int lane) {
-    using C = typename CT<R>::c;
-    constexpr uint32_t PB = 2 * sizeof(C);
-    uint32_t a0[N], second[N], d[N][5];
-#pragma unroll
-    for (int t = 0; t < N; ++t) {
-        a0[t] = sbase[t] + PB * rs.loff[t][lane];
-        second[t] = (smask[t] & 1u) ? PB : 0u;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) d[t][k] = PB * rs.dstep[t][k];  // zero above the tile
-    }
-    const C* tag = nullptr;
-    const uint32_t ni = 1u << (rs.cb - 6);
-    for (uint32_t i = 0; i < ni; ++i) {
-        C p00, p01, p10, p11;
-#pragma unroll
-        for (int t = 0; t < N; ++t) {
-            uint32_t q = a0[t];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) q += ((i >> k) & 1u) ? d[t][k] : 0u;
-            const Pair<C> a = lds_pair(q, tag);
-            const Pair<C> b = lds_pair(q + second[t], tag);
-            if (t == 0) {
-                p00 = a.v0;
-                p01 = a.v1;
-                p10 = b.v0;
-                p11 = b.v1;
-            } else {
-                p00 = cmul(p00, a.v0);
-                p01 = cmul(p01, a.v1);
-                p10 = cmul(p10, b.v0);
-                p11 = cmul(p11, b.v1);
-            }
-        }
-        stg_one(out + (i * 32 + lane), cadd(cadd(p00, p01), cadd(p10, p11)));
-    }
-}
-
-template <typename R, int N>
+// N operands (Exact), or at most N with n of them used.
+template <typename R, int N, bool Exact>
 __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st, typename CT<R>::c* out,
-                                           uint32_t chunk, int lane) {
+                                           uint32_t chunk, int lane, int n) {
     using C = typename CT<R>::c;
     const RunSlot<R>& rs = ws.slot[sl];
     const uint32_t low = (1u << rs.cb) - 1u;
@@ -811,20 +784,10 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
         smask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
     C* tile_out = out + ((uint64_t)chunk << (rs.cb - rs.merged));
-    if constexpr (sizeof(R) == 8) {
-        if (rs.merged) {
-            tile_merged<R, N>(sbase, smask, rs, tile_out, lane);
-            return;
-        }
-    }
-    switch (rs.cb) {
-        case 6: tile_fast<R, N, 1>(sbase, smask, rs, tile_out, lane); break;
-        case 7: tile_fast<R, N, 2>(sbase, smask, rs, tile_out, lane); break;
-        case 8: tile_fast<R, N, 4>(sbase, smask, rs, tile_out, lane); break;
-        case 9: tile_fast<R, N, 8>(sbase, smask, rs, tile_out, lane); break;
-        case 10: tile_fast<R, N, 16>(sbase, smask, rs, tile_out, lane); break;
-        default: tile_fast<R, N, 32>(sbase, smask, rs, tile_out, lane); break;
-    }
+    if (rs.cb == 6)
+        tile_loop<R, N, 1, Exact>(sbase, smask, rs, tile_out, lane, n);
+    else
+        tile_loop<R, N, 2, Exact>(sbase, smask, rs, tile_out, lane, n);
 }
 
 // Wait (bounded) until the copies into stage st have landed. Returns false
@@ -862,26 +825,20 @@ template <typename R>
 __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs, uint32_t chunk, bool first,
                                            typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane) {
     using C = typename CT<R>::c;
-    const uint32_t low = (1u << rs.cb) - 1u;
     const uint32_t nent = 2u << __popc(rs.leaf_u);
     if (first) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t e = (uint32_t)lane + 32u * h;
-            C v;
-            v.x = (R)1;
-            v.y = (R)0;
-            if (e < nent) {
-                const uint32_t x = e & 1u;
-                const uint32_t o = pdep_u32(e >> 1, rs.leaf_u);
-                for (int l = 0; l < rs.n_leaves; ++l)
-                    if ((rs.lmask[l] & ~low) == 0u) {
-                        const uint32_t jl = pext_u32(o, rs.lmask[l]);
-                        v = cmul(v, rs.lval[l][rs.lx[l] ? 2u * jl + x : jl]);
-                    }
-            }
-            tlow[h] = v;
+        C v0, v1;  // entries lane and lane + 32
+        v0.x = v1.x = (R)1;
+        v0.y = v1.y = (R)0;
+        const uint32_t e0 = (uint32_t)lane, e1 = e0 + 32u;
+        for (int l = 0; l < rs.n_leaves; ++l) {
+            const uint32_t s0 = rs.lsh[l][0], s1 = rs.lsh[l][1];
+            if (s0 == 255u) continue;  // a bit above the tile: per tile, below
+            v0 = cmul(v0, rs.lval[l][((e0 >> s0) & 1u) | (((e0 >> s1) & 1u) << 1)]);
+            v1 = cmul(v1, rs.lval[l][((e1 >> s0) & 1u) | (((e1 >> s1) & 1u) << 1)]);
         }
+        tlow[0] = v0;
+        tlow[1] = v1;
     }
     // the table changes only when one of the high output bits changes
     uint32_t key = 0;
@@ -899,7 +856,7 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const uint32_t e = (uint32_t)lane + 32u * h;
-        if (e < nent) ws.leaf_tab[e] = cmul(tlow[h], f);
+        if (e < nent) elem_st(ws.leaf_tab, e, cmul(tlow[h], f));
     }
     __syncwarp();
 }
@@ -951,10 +908,11 @@ __device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int
                 const URec d = uops[t];
                 const uint32_t e = 2u * pext_u32(o, d.a);
                 const C* src = d.b ? scr + d.off : arena + d.off;
-                a0 = cmul(a0, src[e]);
-                a1 = cmul(a1, src[e + 1]);
+                const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
+                a0 = cmul(a0, v.v0);
+                a1 = cmul(a1, v.v1);
             }
-            dst[o] = cadd(a0, a1);
+            elem_st(dst, o, cadd(a0, a1));
         }
         __syncwarp();
     }
@@ -978,10 +936,10 @@ __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st
     clk.lap(kTrGate);
     C* out = static_cast<C*>(dp.arena) + rs.out_off;
     switch (rs.n_fast) {
-        case 1: run_tile_n<R, 1>(ws, sl, st, out, chunk, lane); break;
-        case 2: run_tile_n<R, 2>(ws, sl, st, out, chunk, lane); break;
-        case 3: run_tile_n<R, 3>(ws, sl, st, out, chunk, lane); break;
-        case 4: run_tile_n<R, 4>(ws, sl, st, out, chunk, lane); break;
+        case 1: run_tile_n<R, 1, true>(ws, sl, st, out, chunk, lane, 1); break;
+        case 2: run_tile_n<R, 2, true>(ws, sl, st, out, chunk, lane, 2); break;
+        case 3: run_tile_n<R, 3, true>(ws, sl, st, out, chunk, lane, 3); break;
+        case 4: run_tile_n<R, 4, true>(ws, sl, st, out, chunk, lane, 4); break;
         default: tile_from_smem_generic<R>(ws, sl, st, out, chunk, lane); break;
     }
     __syncwarp();
@@ -1252,7 +1210,7 @@ __global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename 
         C v;
         v.x = (R)re[i];
         v.y = (R)im[i];
-        T[i] = v;
+        elem_st(T, i, v);
     }
     if (dleaf_off) {
         C* D = T + dleaf_off;
@@ -1260,7 +1218,7 @@ __global__ void k_leaf_fill(const double* angles, int n_graphs, int p, typename 
             C v;
             v.x = (R)dre[i];
             v.y = (R)dim[i];
-            D[i] = v;
+            elem_st(D, i, v);
         }
     }
 }
@@ -1287,7 +1245,7 @@ __global__ void k_epilogue(DevEpilogue de) {
                 vr = 1.0;
                 vi = 0.0;
             }
-            const C v = arena[w & ~kFirstFactor];
+            const C v = elem_ld(arena, w & ~kFirstFactor);
             const double xr = (double)v.x, xi = (double)v.y;
             const double nr = vr * xr - vi * xi, ni = vr * xi + vi * xr;
             vr = nr;
