@@ -65,8 +65,10 @@ typedef struct {
     qt_dtype dtype;        /* element type of every tensor: complex64 (FP32 arithmetic) or complex128 */
     qt_sched sched;        /* schedule used by qt_energy (default persistent) */
     int32_t order_restarts;/* extra randomised greedy min-fill orders per network; the order
-                              with the smallest sum of 2^width is kept (default 0: plain greedy;
-                              negative: none) */
+                              with the smallest sum of 2^width is kept. 0 (default): 64 restarts for
+                              the networks whose plain greedy order reaches width 18, none for the
+                              others; > 0: that many for every network; negative: none (the plain
+                              greedy order) */
     uint64_t order_seed;   /* seed of the randomised restarts */
     int32_t max_width;     /* largest bucket width allowed, the summed index included
                               (default 31, at most 31) */
@@ -97,17 +99,20 @@ typedef struct {
     int32_t no_merge;      /* nonzero: no merged eliminations. By default a bucket of 2^10 outputs or
                               more and the consumer that only extends it become one bucket summing
                               both variables, the intermediate never written (persistent-schedule
-                              plans without gradients; the others never merge) */
+                              plans, gradient plans included; the per-bucket schedule never merges) */
     size_t adjoint_budget_bytes; /* gradient plans (single graph): device bytes for results and their
-                              cotangents; a plan that needs more runs its networks in passes that fit
-                              (each pass saves its own results; energies and gradients are summed over
-                              passes); a network that alone exceeds it gives QT_ENOMEM. 0: no budget */
+                              cotangents; a plan that needs more runs in passes that fit, over its
+                              networks' slices (each pass saves its own results and seeds each slice
+                              from its own factors; energies and gradients are summed over passes); a
+                              slice that alone exceeds it gives QT_ENOMEM. 0: no budget */
     int32_t slice_width;   /* index slicing: a network whose greedy order is wider than this target
                               gets variables fixed, one at a time, until it is not (or max_slice_bits
                               are fixed); its value is the sum over the 2^s assignments of the fixed
                               variables of networks without them, all contracted in the same launch.
                               2..31: the target; 0: the default target (22 complex64, 20 complex128);
-                              -1: no slicing. Forward plans only (gradient plans are never sliced) */
+                              -1: no slicing. Gradient plans too: each slice's root cotangents are the
+                              products of its other factors, and a gate entry fixed by slicing adds its
+                              own derivative term */
     int32_t max_slice_bits;/* most variables fixed per network (1..16); 0: 8 */
     int32_t dedup;         /* nonzero: lightcone deduplication. Within each graph, networks whose
                               lightcones are isomorphic (the qubits within distance p of the edge,
@@ -389,10 +394,12 @@ int qt_kernel_time(qt_plan_t plan, double *avg_ms, int64_t *launches, int32_t re
 
 /*
  * Time the persistent kernel on the tiles of one bucket alone (no other bucket
- * runs, no consumer is notified): `reps` launches after one warm-up launch, on
- * the plan's own stream, with CUDA events around each launch. *avg_ms receives
- * the mean, *bytes (may be NULL) the bucket's algorithmic bytes (every operand
- * read once, the result written once). The operands hold whatever the last
+ * runs, no consumer is notified): `reps` launches back to back after one
+ * warm-up launch, on the plan's own stream, each preceded by a reset of the
+ * kernel's 256-byte control word; CUDA events around the whole sequence, so
+ * the host's launch latency overlaps the previous launch. *avg_ms receives the
+ * mean per launch (the resets included), *bytes (may be NULL) the bucket's
+ * algorithmic bytes (every operand read once, the result written once). The operands hold whatever the last
  * evaluation left (run qt_energy first for meaningful data; the timing does
  * not depend on the values). Persistent plans only; host call, synchronous.
  */
@@ -467,6 +474,64 @@ int qt_energy_noalloc(qt_plan_t plan, const double *gammas, const double *betas,
 int qt_fma_peak(int32_t dtype, double *tflops);
 
 void qt_plan_free(qt_plan_t plan);
+
+/* ---- contraction of caller tensors over binary indices ---------------------
+ * The paper's "tncontract" benchmark expression (§II-E, synthetic datasets;
+ * Table III "Tensor Network Random Contraction"): tensors whose every index
+ * has size 2, contracted as
+ *     out[K] = sum over the labels not in K of  prod_t  T_t[L_t]
+ * (the labels not in the output are summed). It runs on the bucket
+ * elimination of the energy plans (§II-B; merged eliminations, §II-C): the
+ * summed labels are eliminated first, each bucket's label bit 0 of its
+ * operands, and the output's labels take the next elimination ranks in the
+ * output's bit order, so the last bucket writes the output. */
+typedef struct qt_contract_s *qt_contract_t;  /* opaque; owns its device memory */
+
+typedef struct {
+    int32_t n_buckets;   /* buckets of the elimination (merged ones counted once) */
+    int32_t max_width;   /* widest bucket, its summed labels included */
+    int32_t n_summed;    /* labels summed */
+    int32_t n_merged;    /* buckets that sum two labels */
+    double alg_bytes;    /* bytes of the buckets: every operand read once, every result written once */
+    double copy_bytes;   /* bytes of the copies: each input read and written in the arena's layout, the
+                            result read and the output written */
+    int64_t arena_bytes; /* device memory the plan holds for tensors */
+    int32_t widths[32];  /* the first 32 buckets' widths */
+} qt_contract_stats;
+
+/* Plan a contraction. n_ops operands (1..16); operand t has ranks[t] labels
+ * (1..30), listed consecutively in `labels` (host) in C order: its first label
+ * is its slowest axis, its last label bit 0 of its flat index. Labels are
+ * non-negative ints, distinct within an operand; equal labels in two operands
+ * are the same index. `out_labels` (host, out_rank of them, may be 0 for a
+ * scalar) lists the output's labels in C order; each must occur in an operand.
+ * Every operand must hold at least one summed label (an operand of output
+ * labels only would need an outer product), and the buckets must end in one
+ * result: QT_EINVAL otherwise. At most 30 distinct labels; QT_EWIDTH if a
+ * bucket has more than 16 operands or no tile of it fits the kernel's
+ * shared-memory stage. host_only != 0: no device memory (stats only). Device
+ * memory: the arena (every operand permuted, every result) plus small tables;
+ * the plan is bound to the current device. */
+int qt_contract_plan(int32_t n_ops, const int32_t *ranks, const int32_t *labels, int32_t out_rank,
+                     const int32_t *out_labels, qt_dtype dtype, int32_t host_only, qt_contract_t *out);
+
+/* Run a planned contraction. ops[t]: device pointer to operand t, 2^ranks[t]
+ * elements of the plan's dtype as interleaved (re, im) pairs -- the layout of
+ * a contiguous complex64 / complex128 array -- in C order over its labels;
+ * out: device pointer to 2^out_rank elements, written the same way. Pointers
+ * 16-byte aligned; the caller owns them. With cuda_stream == NULL the call
+ * waits and returns any kernel-side error; with a stream it only enqueues
+ * (copies in, the bucket kernel, the copy out) and qt_contract_sync reports
+ * the kernel-side status. One call at a time per plan. */
+int qt_contract_run(qt_contract_t c, const void *const *ops, void *out, void *cuda_stream);
+
+/* Wait for `cuda_stream` and return the kernel-side status of the plan's
+ * last run (QT_OK, QT_ETIMEOUT or QT_EBOUNDS). */
+int qt_contract_sync(qt_contract_t c, void *cuda_stream);
+
+int qt_contract_stats_get(qt_contract_t c, qt_contract_stats *out);
+
+void qt_contract_free(qt_contract_t c);
 
 const char *qt_error_string(int code);
 

@@ -14,6 +14,9 @@ Routes (each a plain implementation of the paper's definitions):
 * ``p1_closed_form`` -- the published p=1 formula (Wang, Hadfield, Jiang and
   Rieffel, Phys. Rev. A 97, 022304 (2018)) rewritten in this gate convention.
 * ``grad_param_shift`` / ``grad_fd`` -- gradients of the energy.
+* ``contract`` / ``contract_brute`` -- a contraction of tensors over binary
+  indices (the paper's "tncontract" expressions, §II-E): out[K] = the sum over
+  the labels not in K of the product of the operands.
 
 Gate convention: layer k applies ``exp(-i gamma_k s_a s_b)`` on every edge,
 then ``exp(-i beta_k X)`` on every qubit, from |+>^N, with ``s(x) = 1 - 2x``.
@@ -344,3 +347,39 @@ def grad_fd(energy_fn, gammas, betas, h: float = 1e-5):
         bm[k] -= h
         db[k] = (energy_fn(gammas, bp) - energy_fn(gammas, bm)) / (2 * h)
     return dg, db
+
+
+# --------------------------------------------------------------------------
+# Contractions over binary indices (§II-E, "tncontract")
+# --------------------------------------------------------------------------
+
+_SUBSCRIPTS = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+
+
+def contract(ops, labels, out_labels) -> np.ndarray:
+    """out[K] = sum over the labels not in K of prod_t ops[t][L_t], in complex128.
+
+    ``ops[t]`` has one axis of size 2 per label of ``labels[t]`` (C order);
+    the result has one per label of ``out_labels``. numpy's einsum does the
+    sum of products, the definition written as one expression."""
+    names = {}
+    for L in list(labels) + [out_labels]:
+        for x in L:
+            names.setdefault(int(x), _SUBSCRIPTS[len(names)])
+    spec = ",".join("".join(names[int(x)] for x in L) for L in labels) + "->" + "".join(
+        names[int(x)] for x in out_labels)
+    return np.einsum(spec, *[np.asarray(o, dtype=np.complex128) for o in ops], optimize=False)
+
+
+def contract_brute(ops, labels, out_labels) -> np.ndarray:
+    """The same sum as ``contract`` by explicit loops over every assignment of
+    the labels (small expressions only): the literal definition."""
+    alls = sorted({int(x) for L in labels for x in L})
+    out = np.zeros((2,) * len(out_labels), dtype=np.complex128)
+    for a in range(1 << len(alls)):
+        val = {lab: (a >> i) & 1 for i, lab in enumerate(alls)}
+        prod = 1.0 + 0.0j
+        for o, L in zip(ops, labels):
+            prod *= complex(np.asarray(o)[tuple(val[int(x)] for x in L)])
+        out[tuple(val[int(x)] for x in out_labels)] += prod
+    return out

@@ -24,29 +24,51 @@ namespace {
 // E = |E|/2 - 1/2 sum Re V, so dE/dtheta = -1/2 times those sums.
 // ---------------------------------------------------------------------------
 
-// Each root's cotangent is the product of its network's other roots (1 when,
-// as usual, the network is connected), times the number of networks sharing
-// the network's value (deduplicated plans; 1 otherwise).
+// The seeds of one network (one thread): its value is the sum over its
+// slices of the product of the slice's factors -- root results and the gate
+// entries slicing fixed (one slice, with root results only, when unsliced).
+// A root's cotangent is the product of its slice's other factors; a fixed
+// entry of an angle's gate adds Re(product of the other factors x the entry's
+// derivative) to that angle's sum. Both carry the network's weight: the
+// networks sharing its value (deduplicated plans; 1 otherwise), 0 for a
+// duplicate, which has no buckets of its own.
 template <typename R>
-__global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta) {
+__global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta, uint64_t dleaf_delta, double* grad,
+                             int p, const uint32_t* net_graph) {
     using C = typename CT<R>::c;
     C* arena = static_cast<C*>(const_cast<void*>(de.arena));
     const int net = blockIdx.x * blockDim.x + threadIdx.x;
     if (net >= n_nets) return;
-    for (uint32_t r = de.net_first_root[net]; r < de.net_first_root[net + 1]; ++r) {
-        double vr = 1.0, vi = 0.0;
-        for (uint32_t q = de.net_first_root[net]; q < de.net_first_root[net + 1]; ++q) {
-            if (q == r) continue;
-            const C v = elem_ld(arena, de.buckets[de.root_bucket[q]].out_off);
-            const double nr = vr * (double)v.x - vi * (double)v.y, ni = vr * (double)v.y + vi * (double)v.x;
-            vr = nr;
-            vi = ni;
+    const double w = de.net_weight ? (double)de.net_weight[net] : 1.0;
+    if (w == 0.0) return;
+    const uint32_t f0 = de.net_first_factor[net], f1 = de.net_first_factor[net + 1];
+    double* g = grad + (size_t)net_graph[net] * 2 * p;
+    for (uint32_t a = f0; a < f1;) {
+        uint32_t b = a + 1;  // the slice's factors are [a, b)
+        while (b < f1 && !(de.factor[b] & kFirstFactor)) ++b;
+        for (uint32_t j = a; j < b; ++j) {
+            const int8_t kind = de.factor_param[j];
+            if (kind == -1) continue;  // a fixed entry of |+> or Z: no angle
+            double vr = w, vi = 0.0;  // the product of the other factors
+            for (uint32_t k = a; k < b; ++k) {
+                if (k == j) continue;
+                const C v = elem_ld(arena, de.factor[k] & ~kFirstFactor);
+                const double nr = vr * (double)v.x - vi * (double)v.y, ni = vr * (double)v.y + vi * (double)v.x;
+                vr = nr;
+                vi = ni;
+            }
+            const uint64_t off = de.factor[j] & ~kFirstFactor;
+            if (kind == kFactorRoot) {
+                C c;
+                c.x = (R)vr;
+                c.y = (R)vi;
+                elem_st(arena, off + cot_delta, c);
+            } else {
+                const C d = elem_ld(arena, off + dleaf_delta);
+                atomicAdd(g + kind, vr * (double)d.x - vi * (double)d.y);
+            }
         }
-        const double w = de.net_weight ? (double)de.net_weight[net] : 1.0;
-        C c;
-        c.x = (R)(vr * w);
-        c.y = (R)(vi * w);
-        elem_st(arena, de.buckets[de.root_bucket[r]].out_off + cot_delta, c);
+        a = b;
     }
 }
 
@@ -96,8 +118,12 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
     const bool active = ((uint32_t)lane & ~lmask) == 0u;
     const uint32_t obase = tile << tb;
     const C* rbar = arena + B.out_off + db.cot_delta;
+    // a merged bucket (s0, s1; s1 output bit 0 of its tiles) adds its outputs
+    // (o, s1 = 0, 1) into result o: both take the result's cotangent
+    const uint32_t rshift = bucket_n_sum(B.flags) - 1;
     uint64_t off[NMAX];
     uint32_t mask[NMAX], base[NMAX], lo[NMAX], step[NMAX][KB];
+    bool px[NMAX];  // pairs over x: entry 2 j + x (the merged consumer's gate tensors: entry j for both x)
     int mode[NMAX], prm[NMAX];
     uint32_t roff[NMAX];
     uint32_t red_elems = 0;
@@ -105,6 +131,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
     for (int t = 0; t < NMAX; ++t) {
         off[t] = 0;
         mask[t] = 0;
+        px[t] = true;
         mode[t] = kBwdNone;
         prm[t] = -1;
         roff[t] = 0;
@@ -116,6 +143,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
             const DOperand o = db.ops[i];
             off[t] = o.off;
             mask[t] = o.mask;
+            px[t] = (o.smask & 1u) != 0u;
             mode[t] = db.op_bwd[i];
             prm[t] = db.op_param[i];
             roff[t] = db.op_roff[i];
@@ -140,7 +168,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
     for (uint32_t k = 0; k < (1u << kb); ++k) {
         const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
         C r = C{};
-        if (active) r = elem_ldg(rbar, o);
+        if (active) r = elem_ldg(rbar, o >> rshift);
         Pair<C> P[NMAX];
         uint32_t li[NMAX];  // pair index within the tile's block of the operand
 #pragma unroll
@@ -150,7 +178,14 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
             for (int kk = 0; kk < KB; ++kk)
                 if ((k >> kk) & 1u) q += step[t][kk];
             li[t] = q;
-            if (t < n) P[t] = ldg_pair(arena + off[t] + 2u * (base[t] + q));
+            if (t < n) {
+                if (px[t]) {
+                    P[t] = ldg_pair(arena + off[t] + 2u * (base[t] + q));
+                } else {
+                    const C v = elem_ldg(arena + off[t], base[t] + q);
+                    P[t] = {v, v};
+                }
+            }
         }
         C cd[NMAX][2];  // contributions of this output to direct operands
 #pragma unroll
@@ -173,7 +208,8 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
                     const C c = cmul(pre, S[t]);  // Rbar[o] * prod_{u != t} P[u]
                     switch (mode[t]) {
                         case kBwdGate: {
-                            const C d = elem_ldg(arena + off[t] + db.dleaf_delta + 2u * (base[t] + li[t]), x);
+                            const C d = px[t] ? elem_ldg(arena + off[t] + db.dleaf_delta + 2u * (base[t] + li[t]), x)
+                                              : elem_ldg(arena + off[t] + db.dleaf_delta, base[t] + li[t]);
                             const R v = c.x * d.x - c.y * d.y;
                             const R y = v - comp[t];
                             const R s2 = acc[t] + y;
@@ -277,13 +313,14 @@ __global__ void k_grad_final(const double* grad, int n_graphs, int p, double* dg
 
 }  // namespace
 
-cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s) {
+cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, uint64_t dleaf_delta,
+                              double* grad, int p, const uint32_t* net_graph, cudaStream_t s) {
     if (n_nets == 0) return cudaSuccess;  // a plan of graphs without edges
     const int blocks = (n_nets + 127) / 128;
     if (dtype == QT_C128)
-        k_seed_roots<double><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);
+        k_seed_roots<double><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta, dleaf_delta, grad, p, net_graph);
     else
-        k_seed_roots<float><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta);
+        k_seed_roots<float><<<blocks, 128, 0, s>>>(de, n_nets, cot_delta, dleaf_delta, grad, p, net_graph);
     return cudaGetLastError();
 }
 

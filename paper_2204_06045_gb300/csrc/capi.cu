@@ -19,6 +19,8 @@
 namespace {
 
 constexpr int kRing = 512;  // event pairs for per-launch kernel timing
+constexpr int kAutoRestarts = 64;      // default randomised min-fill restarts of a wide network
+constexpr int kAutoRestartWidth = 18;  // "wide": its plain greedy order reaches this bucket width
 
 }  // namespace
 
@@ -131,6 +133,19 @@ int cuda_fail(cudaError_t e, const char* what, int line) {
     return e == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA;
 }
 
+}  // namespace
+
+namespace qt {
+// The same report for the other C-ABI sources (the text qt_last_error_detail returns).
+int report_cuda_error(cudaError_t e, const char* file, const char* what, int line) {
+    std::snprintf(g_detail, sizeof(g_detail), "%s failed at %s:%d: %s (%s)", what, file, line, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA;
+}
+}  // namespace qt
+
+namespace {
+
 #define QT_CUDA(call)                                          \
     do {                                                       \
         cudaError_t e_ = (call);                               \
@@ -181,7 +196,7 @@ int upload(qt_plan_t P) {
         {hp.root_bucket.data(), bytes_of(hp.root_bucket), 0}, {u_graph_first_net.data(), bytes_of(u_graph_first_net), 0},
         {hp.unit_prog.data(), bytes_of(hp.unit_prog), 0},     {hp.net_first_factor.data(), bytes_of(hp.net_first_factor), 0},
         {hp.factor.data(), bytes_of(hp.factor), 0},            {hp.graph_owned.data(), bytes_of(hp.graph_owned), 0},
-        {hp.net_weight.data(), bytes_of(hp.net_weight), 0},
+        {hp.net_weight.data(), bytes_of(hp.net_weight), 0},   {hp.factor_param.data(), bytes_of(hp.factor_param), 0},
     };
     size_t total = 0;
     for (auto& pc : pieces) {
@@ -236,6 +251,7 @@ int upload(qt_plan_t P) {
     de.graph_first_net = reinterpret_cast<const int32_t*>(base + pieces[7].off);
     de.net_first_factor = reinterpret_cast<const uint32_t*>(base + pieces[9].off);
     de.factor = reinterpret_cast<const uint64_t*>(base + pieces[10].off);
+    de.factor_param = reinterpret_cast<const int8_t*>(base + pieces[13].off);
     de.graph_owned = reinterpret_cast<const int32_t*>(base + pieces[11].off);
     de.net_weight = hp.net_weight.empty() ? nullptr : reinterpret_cast<const int32_t*>(base + pieces[12].off);
     de.n_graphs = n_graphs;
@@ -590,10 +606,8 @@ int make_passes(qt_plan_t P, const std::vector<qt::GraphIn>& graphs, int32_t p, 
         gs[0].n = g0.n;
         gs[0].edges = g0.edges;
         gs[0].sel = ps.edges;
-        if (!grad) {
-            gs[0].sel_slices = ps.slices;
-            gs[0].sel_owner = ps.owner;
-        }
+        gs[0].sel_slices = ps.slices;  // a network's slices may sit in several passes (gradients too:
+        gs[0].sel_owner = ps.owner;    // each slice's roots are seeded from its own factors)
         P->part_edges.push_back(ps.edges);
         qt_plan_t part = nullptr;
         const int rc = make_plan(gs, p, &so, &part);
@@ -663,7 +677,11 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     qt::PlanConfig cfg;
     cfg.p = p;
     cfg.dtype = o.dtype;
-    cfg.restarts = std::max(0, o.order_restarts);
+    // order restarts: by default 64 for the networks whose plain greedy order is
+    // wide (their buckets carry the bytes); measured on the N=30 p=4 workload:
+    // 3.42 -> 2.31 GB per evaluation, kernel 1.21 -> 1.06 ms (complex64)
+    cfg.restarts = o.order_restarts > 0 ? o.order_restarts : o.order_restarts == 0 ? kAutoRestarts : 0;
+    cfg.restart_min_width = o.order_restarts == 0 ? kAutoRestartWidth : 0;
     cfg.seed = o.order_seed;
     cfg.max_width = o.max_width > 0 ? o.max_width : 31;
     cfg.chunk_log2 = o.chunk_log2;
@@ -683,14 +701,14 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     if (o.run_tiles < 0 || o.run_tiles > 4096) return QT_EINVAL;
     cfg.with_grad = o.with_grad != 0;
     cfg.fuse = o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad && o.no_fuse == 0;
-    // the reverse sweep, the per-bucket kernel and fused units sum one
-    // variable per bucket: merging is a forward, persistent-schedule option
-    cfg.merge = o.no_merge == 0 && o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad;
+    // the per-bucket kernel sums one variable per bucket: merging is a
+    // persistent-schedule option (fused units take only unmerged subtrees)
+    cfg.merge = o.no_merge == 0 && o.sched == QT_SCHED_PERSISTENT;
     if (o.slice_width < -1 || o.slice_width == 1 || o.slice_width > 31) return QT_EINVAL;
     if (o.max_slice_bits < 0 || o.max_slice_bits > 16) return QT_EINVAL;
     // default target widths: measured best on the N=30 p=4 and N=1000 p=5 networks
     const int sw = o.slice_width == 0 ? (o.dtype == QT_C128 ? 20 : 22) : std::max(0, o.slice_width);
-    cfg.slice_width = cfg.with_grad ? 0 : sw;  // the reverse sweep takes unsliced networks
+    cfg.slice_width = sw;
     cfg.max_slice_bits = o.max_slice_bits ? o.max_slice_bits : 8;
     // a duplicate network takes its representative's value within one plan, so passes do
     // not deduplicate; the choice waits until the deduplicated plan's size is known
@@ -1053,7 +1071,8 @@ int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, doubl
     // reverse sweep
     QT_CUDA(qt::launch_zero_ranges(P->dtype, P->d_arena, P->d_zero, P->n_zero, s));
     QT_CUDA(cudaMemsetAsync(P->d_grad, 0, sizeof(double) * 2 * G * p, s));
-    QT_CUDA(qt::launch_seed_roots(P->dtype, P->de, (int)hp.nets.size(), P->db.cot_delta, s));
+    QT_CUDA(qt::launch_seed_roots(P->dtype, P->de, (int)hp.nets.size(), P->db.cot_delta, P->db.dleaf_delta, P->d_grad,
+                                  hp.cfg.p, P->db.net_graph, s));
     for (int lv = hp.n_levels - 1; lv >= 0; --lv) {
         for (int cls = 0; cls < qt::kBwdClasses; ++cls) {
             const uint32_t i0 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls];
@@ -1150,16 +1169,18 @@ int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, do
     dp.isolated = 1;
     cudaEvent_t e0 = P->cap_ev[0], e1 = P->cap_ev[1];
     float total = 0;
-    for (int r = 0; r < reps + 1 && e == cudaSuccess; ++r) {
-        e = cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, P->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+    // isolated groups have no producers and notify no consumer: of the
+    // counters only the control word (the claim position) needs resetting
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, P->stream);
+    if (e == cudaSuccess) e = qt::launch_persistent(P->dtype, P->grid, dp, P->stream);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaMemsetAsync(P->d_counters, 0, sizeof(qt::DControl), P->stream);
         if (e == cudaSuccess) e = qt::launch_persistent(P->dtype, P->grid, dp, P->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) total += ms;  // the first launch warms up
     }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
     int32_t err = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&err, &P->dp.ctl->error, sizeof(err), cudaMemcpyDeviceToHost);
     cudaFree(d_groups);

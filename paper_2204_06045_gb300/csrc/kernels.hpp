@@ -52,6 +52,7 @@ struct DevEpilogue {
     const int32_t* graph_first_net;  // n_graphs + 1
     const uint32_t* net_first_factor;  // n_nets + 1
     const uint64_t* factor;  // arena element offsets; kFirstFactor marks the first factor of each slice
+    const int8_t* factor_param;  // per factor: kFactorRoot, a fixed gate's angle, or -1
     const int32_t* graph_owned;  // n_graphs: networks whose 1/2 the energy counts (all, unless sharded by slice)
     const int32_t* net_weight;   // gradient plans with deduplicated networks: per network, the networks
                                  // sharing its value (its class; 0 for a duplicate); null: 1 each
@@ -82,7 +83,10 @@ struct DevBwd {
 
 cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int p, void* arena, uint64_t dleaf_off,
                              cudaStream_t s);
-cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, cudaStream_t s);
+// Reverse-sweep seeds: every root result's cotangent, and the derivative terms of the gate
+// entries that slicing fixed (added to grad, n_graphs x 2p, before the -1/2 of k_grad_final).
+cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, uint64_t dleaf_delta,
+                              double* grad, int p, const uint32_t* net_graph, cudaStream_t s);
 // op_class: the level's tasks of buckets with exactly 1..4 operands (0..3), at most 8 (4) or 16 (5)
 cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s);
 
@@ -95,5 +99,8 @@ int persistent_blocks_per_sm(int dtype);
 cudaError_t launch_clear_ends(unsigned long long* t, size_t n, cudaStream_t s);
 constexpr int kPersistentThreads = 128;  // 4 warps; each warp owns its shared-memory stages
 size_t persistent_smem_bytes(int dtype);
+
+// Records a failed CUDA call for qt_last_error_detail; returns QT_ENOMEM or QT_ECUDA.
+int report_cuda_error(cudaError_t e, const char* file, const char* what, int line);
 
 }  // namespace qt

@@ -1131,9 +1131,15 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
             double best_cost = 0, c = 0;
             int best_w = 0, w = 0;
             order_min_fill(net, false, 0, &best_order, &best_cost, &best_w);
-            for (int r = 0; r < cfg.restarts; ++r) {
-                order_min_fill(net, true, mix64(cfg.seed ^ mix64((uint64_t)i * 1315423911ull + r)), &ord, &c, &w);
-                if (c < best_cost) {
+            // a restart's order is kept if cheaper and, with slicing, no wider than the target
+            // (or the greedy width, if the slice-bit budget left that wider)
+            const int w_cap = cfg.slice_width > 0 ? std::max(cfg.slice_width, best_w) : cfg.max_width;
+            for (int r = 0; r < (best_w >= cfg.restart_min_width ? cfg.restarts : 0); ++r) {
+                // seeded by the network's identity (graph, edge), so that subset, shard and pass
+                // plans of a graph order each network as the whole graph's plan does
+                const uint64_t id = ((uint64_t)g << 32) | (uint64_t)(uint32_t)net.edge;
+                order_min_fill(net, true, mix64(cfg.seed ^ mix64(id * 1315423911ull + r)), &ord, &c, &w);
+                if (c < best_cost && w <= w_cap) {
                     best_cost = c;
                     best_order = ord;
                     best_w = w;
@@ -1226,6 +1232,7 @@ int layout_plan(HostPlan* hp) {
     hp->op_leaf_sub.clear();
     hp->net_first_factor.assign(1, 0);
     hp->factor.clear();
+    hp->factor_param.clear();
     hp->graph_owned.assign(graphs.size(), 0);
     hp->n_unique = 0;
     hp->net_weight.clear();
@@ -1237,7 +1244,9 @@ int layout_plan(HostPlan* hp) {
             // the representative's value: its factor list (it comes earlier)
             for (uint32_t f = hp->net_first_factor[net.rep]; f < hp->net_first_factor[net.rep + 1]; ++f) {
                 const uint64_t w = hp->factor[f];
+                const int8_t fp = hp->factor_param[f];
                 hp->factor.push_back(w);
+                hp->factor_param.push_back(fp);
             }
         }
         // every slice of the network: the same buckets, its own gate entries
@@ -1357,15 +1366,20 @@ int layout_plan(HostPlan* hp) {
             // the slice's factors of the network's value: its root results,
             // then the entries of its fully fixed gates
             bool first = true;
-            auto push_factor = [&](uint64_t e) {
+            auto push_factor = [&](uint64_t e, int8_t prm) {
                 hp->factor.push_back(e | (first ? kFirstFactor : 0));
+                hp->factor_param.push_back(prm);
                 first = false;
             };
-            for (size_t r = root0; r < hp->root_bucket.size(); ++r) push_factor(hp->buckets[hp->root_bucket[r]].out_off);
+            for (size_t r = root0; r < hp->root_bucket.size(); ++r)
+                push_factor(hp->buckets[hp->root_bucket[r]].out_off, kFactorRoot);
             for (const FixedLeaf& fl : net.fixed) {
                 uint32_t e = (sl >> fl.f[0]) & 1u;
                 if (fl.rank == 2) e += 2u * ((sl >> fl.f[1]) & 1u);
-                push_factor(((uint64_t)net.graph * L + leaf_index(fl.kind, fl.layer)) * kLeafSlots + e);
+                int8_t prm = -1;
+                if (fl.kind == QT_LEAF_ZZ || fl.kind == QT_LEAF_ZZ_CONJ) prm = (int8_t)fl.layer;
+                if (fl.kind == QT_LEAF_RX || fl.kind == QT_LEAF_RX_CONJ) prm = (int8_t)(cfg.p + fl.layer);
+                push_factor(((uint64_t)net.graph * L + leaf_index(fl.kind, fl.layer)) * kLeafSlots + e, prm);
             }
             hp->n_slices++;
         }
@@ -1488,7 +1502,7 @@ int layout_plan(HostPlan* hp) {
                     }
                     if (mode != kBwdRedStore) {
                         const DBucket& src = hp->buckets[o.src];
-                        const uint64_t n = 1ull << src.n_out;
+                        const uint64_t n = 1ull << result_bits(src);
                         for (uint64_t c = 0; c < n; c += kZeroChunk) {
                             hp->bwd_zero.push_back(src.out_off + cot_delta + c);
                             hp->bwd_zero.push_back(std::min<uint64_t>(kZeroChunk, n - c));
@@ -1515,6 +1529,237 @@ int layout_plan(HostPlan* hp) {
             }
             hp->bwd_level_begin.push_back((uint32_t)hp->bwd_bucket.size());
         }
+    }
+    return QT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Contraction of caller-supplied tensors over binary indices (the paper's
+// "tncontract" benchmark, §II-E), planned with the same bucket elimination
+// (§II-B), merged eliminations (§II-C) and device layout as the energy plans.
+// ---------------------------------------------------------------------------
+int build_contract_plan(const std::vector<std::vector<int>>& labels, const std::vector<int>& out_labels, int dtype,
+                        int sim_workers, ContractPlan* cp) {
+    *cp = ContractPlan();
+    cp->dtype = dtype;
+    const int n_in = (int)labels.size();
+    if (n_in < 1 || n_in > kMaxOps || (dtype != 0 && dtype != 1)) return QT_EINVAL;
+    // variables: the distinct labels in order of first appearance
+    std::vector<int> count;  // operands holding each variable
+    std::unordered_map<int, int> var_of;
+    for (const auto& L : labels) {
+        if (L.empty() || L.size() > (size_t)kMaxOutBits) return QT_EINVAL;
+        std::set<int> seen;
+        for (int l : L) {
+            if (l < 0 || !seen.insert(l).second) return QT_EINVAL;
+            auto it = var_of.emplace(l, (int)count.size());
+            if (it.second) count.push_back(0);
+            count[it.first->second]++;
+        }
+    }
+    const int V = (int)count.size();
+    if (V > kMaxOutBits) return QT_EINVAL;
+    std::vector<uint8_t> free_var(V, 0);
+    {
+        std::set<int> seen;
+        for (int l : out_labels) {
+            auto it = var_of.find(l);
+            if (it == var_of.end() || !seen.insert(l).second) return QT_EINVAL;
+            free_var[it->second] = 1;
+        }
+    }
+    // elimination order: the summed variables (those in more operands first),
+    // then the output's bits from the lowest (its last label) up
+    std::vector<int> order;
+    for (int v = 0; v < V; ++v)
+        if (!free_var[v]) order.push_back(v);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return count[a] > count[b]; });
+    const int S = (int)order.size();
+    if (S == 0) return QT_EINVAL;  // nothing summed: not a contraction
+    for (int k = (int)out_labels.size() - 1; k >= 0; --k) order.push_back(var_of[out_labels[k]]);
+    std::vector<int> pos(V);
+    for (int i = 0; i < V; ++i) pos[order[i]] = i;
+    // bucket elimination of the summed variables (as make_buckets); an operand
+    // whose labels are all free would need an outer product: refused
+    struct Tens {
+        std::vector<int> vars;  // by rank
+        int src;
+    };
+    std::vector<Tens> pool;
+    std::vector<std::vector<int>> bucket_of(V);
+    for (int t = 0; t < n_in; ++t) {
+        Tens T;
+        for (int l : labels[t]) T.vars.push_back(var_of[l]);
+        std::sort(T.vars.begin(), T.vars.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        if (free_var[T.vars[0]]) return QT_EINVAL;
+        T.src = -1 - t;  // caller's operand t
+        bucket_of[T.vars[0]].push_back((int)pool.size());
+        pool.push_back(std::move(T));
+    }
+    NetPlan np;
+    for (int step = 0; step < S; ++step) {
+        const int v = order[step];
+        auto& list = bucket_of[v];
+        std::vector<int> uni;
+        for (int t : list)
+            for (int x : pool[t].vars) uni.push_back(x);
+        std::sort(uni.begin(), uni.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+        const int w = (int)uni.size();
+        if (list.empty() || (int)list.size() > kMaxOps) return QT_EWIDTH;
+        HBucket B;
+        B.var = v;
+        B.width = w;
+        B.parent = -1;
+        B.n_deps = 0;
+        B.level = 0;
+        const int bid = (int)np.buckets.size();
+        for (int t : list) {
+            const Tens& T = pool[t];
+            HOperand op;
+            op.src = T.src >= 0 ? T.src : -1;
+            op.leaf = T.src >= 0 ? -1 : -1 - T.src;
+            op.rank = (int)T.vars.size();
+            op.mask = 0;
+            for (size_t i = 1; i < T.vars.size(); ++i)
+                op.mask |= 1u << ((int)(std::find(uni.begin() + 1, uni.end(), T.vars[i]) - uni.begin()) - 1);
+            if (T.src >= 0) {
+                B.n_deps++;
+                np.buckets[T.src].parent = bid;
+                B.level = std::max(B.level, np.buckets[T.src].level + 1);
+            }
+            B.ops.push_back(op);
+        }
+        list.clear();
+        if (w > 1) {
+            Tens R;
+            R.vars.assign(uni.begin() + 1, uni.end());
+            R.src = bid;
+            bucket_of[R.vars[0]].push_back((int)pool.size());
+            pool.push_back(std::move(R));
+        }
+        np.buckets.push_back(std::move(B));
+    }
+    // one result must remain, over exactly the output's variables
+    int left = 0, last = -1;
+    for (int k = S; k < V; ++k)
+        for (int t : bucket_of[order[k]]) {
+            left++;
+            last = t;
+        }
+    int roots = 0;
+    for (const HBucket& B : np.buckets) roots += B.parent < 0;
+    if (roots != 1 || np.buckets.back().parent >= 0) return QT_EINVAL;  // pieces that would need an outer product
+    if (out_labels.empty() ? left != 0 : (left != 1 || pool[last].vars.size() != out_labels.size()))
+        return QT_EINVAL;
+    merge_chains(&np);
+    // ---- device layout: the caller's operands (permuted) first, then the results
+    const uint64_t esize = dtype == 1 ? 16 : 8;
+    const uint64_t align = 128 / esize;
+    uint64_t off = 0;
+    for (int t = 0; t < n_in; ++t) {
+        const int r = (int)labels[t].size();
+        std::vector<int> vars;
+        for (int l : labels[t]) vars.push_back(var_of[l]);
+        std::vector<int> byrank = vars;
+        std::sort(byrank.begin(), byrank.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        std::vector<uint8_t> src_bit(r);
+        for (int k = 0; k < r; ++k) {
+            const int a = (int)(std::find(vars.begin(), vars.end(), byrank[k]) - vars.begin());  // C-order axis
+            src_bit[k] = (uint8_t)(r - 1 - a);
+        }
+        cp->in_rank.push_back(r);
+        cp->in_off.push_back(off);
+        cp->in_src_bit.push_back(std::move(src_bit));
+        off += align_up(std::max<uint64_t>(1ull << r, kLeafSlots), align);
+    }
+    Network none;
+    for (const HBucket& B : np.buckets) {
+        HBucket merged_view;
+        if (B.n_sum > 1) merged_view = device_view(B);
+        const HBucket& Vw = B.n_sum > 1 ? merged_view : B;
+        DBucket d{};
+        d.op_begin = (uint32_t)cp->operands.size();
+        d.n_ops = (uint8_t)B.ops.size();
+        d.n_out = (uint8_t)(B.width - 1);
+        int cb = 0;
+        bool fold = false;
+        const int stage = dtype == 1 ? kStageElemsC128 : kStageElemsC64;
+        pick_tile(Vw, none, kDefaultTileBits, stage, B.n_sum - 1, &cb, &fold);
+        d.chunk_bits = (uint8_t)cb;
+        d.flags = (uint8_t)((fold ? kBucketFoldLeaves : 0) | ((B.n_sum - 1) << 3));
+        const uint32_t low = (1u << cb) - 1u;
+        uint32_t foot = 0, ns = 0, nl = 0, lu = 0, lh = 0;
+        for (const HOperand& op : Vw.ops) {
+            if (fold && foldable(op)) {
+                nl++;
+                lu |= op.mask & low;
+                lh |= op.mask & ~low;
+            } else {
+                foot += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & low);
+                ns++;
+            }
+        }
+        if (foot > (uint32_t)stage) return QT_EWIDTH;  // no tile's footprints fit the stage
+        d.total_foot = foot;
+        d.n_staged = (uint8_t)ns;
+        d.n_leaves = (uint8_t)nl;
+        d.leaf_u = lu;
+        d.leaf_hi = lh;
+        d.parent = B.parent >= 0 ? (uint32_t)B.parent : kNone;
+        d.n_deps = (uint32_t)B.n_deps;
+        d.n_tasks = 1u << (d.n_out - cb);
+        d.out_off = off;
+        off += align_up(std::max<uint64_t>(1ull << (B.width - B.n_sum), kLeafSlots), align);
+        double opbytes = 0;
+        uint32_t next_soff = 0, next_staged = 0, next_leaf = 0;
+        for (size_t t = 0; t < B.ops.size(); ++t) {
+            const HOperand& op = Vw.ops[t];
+            DOperand o{};
+            o.mask = op.mask;
+            o.src = kNone;
+            o.folded = fold && foldable(op);
+            o.smask = (uint8_t)B.ops[t].smask;
+            if (o.folded) {
+                o.slot = (uint8_t)next_leaf++;
+            } else {
+                o.slot = (uint8_t)next_staged++;
+                o.soff = (uint16_t)next_soff;
+                next_soff += (1u << __builtin_popcount(op.smask)) << __builtin_popcount(op.mask & low);
+            }
+            if (op.src >= 0) {
+                o.src = (uint32_t)op.src;
+                o.off = cp->buckets[op.src].out_off;
+                o.src_tiles = cp->buckets[op.src].n_tasks;
+            } else {
+                o.off = cp->in_off[op.leaf];
+                o.flags = kOpLeaf;  // written before the bucket kernel starts
+            }
+            cp->operands.push_back(o);
+            opbytes += std::ldexp(1.0, op.rank);
+        }
+        cp->buckets.push_back(d);
+        cp->widths.push_back(B.width);
+        cp->max_width = std::max(cp->max_width, B.width);
+        cp->alg_bytes += (double)esize * (opbytes + std::ldexp(1.0, B.width - B.n_sum));
+        double n_k[4] = {0, 0, 0, 0};
+        for (const HOperand& op : B.ops) n_k[__builtin_ctz(op.smask)] += 1;
+        for (int v = 0; v < B.n_sum; ++v)  // complex multiply-adds: 8 flops each (4 real mul, 4 real add)
+            cp->flops += 8.0 * (std::ldexp(1.0, B.width - v) * (n_k[v] - (v == 0 ? 1 : 0) + 0.5));
+    }
+    cp->operands.resize(cp->operands.size() + kMaxOps, DOperand{});  // kernels read a bucket's operands in 16s
+    cp->out_off = cp->buckets.back().out_off;
+    cp->out_rank = (int)out_labels.size();
+    cp->n_summed = S;
+    cp->arena_elems = off;
+    // work groups: spread each bucket over the grid (it runs alone once its producer is done)
+    const uint32_t W = (uint32_t)std::max(1, sim_workers);
+    for (uint32_t b = 0; b < (uint32_t)cp->buckets.size(); ++b) {
+        DBucket& d = cp->buckets[b];
+        d.group_tiles = std::max<uint32_t>(1, std::min<uint32_t>(kRunTiles, (d.n_tasks + W - 1) / W));
+        d.n_groups = (d.n_tasks + d.group_tiles - 1) / d.group_tiles;
+        for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
+            cp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, d.n_deps, 0, 0, 0});
     }
     return QT_OK;
 }

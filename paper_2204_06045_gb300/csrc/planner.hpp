@@ -90,6 +90,7 @@ struct PlanConfig {
     int p = 1;
     int dtype = 0;  // 0 complex64, 1 complex128
     int restarts = 0;
+    int restart_min_width = 0;  // restarts only for networks whose plain greedy order reaches this width
     uint64_t seed = 0;
     int max_width = 31;
     int chunk_log2 = 0;
@@ -131,6 +132,8 @@ struct HostPlan {
     // the product of the slice's factors (root results and fixed gate entries)
     std::vector<uint32_t> net_first_factor;  // n_nets + 1
     std::vector<uint64_t> factor;
+    std::vector<int8_t> factor_param;        // per factor: kFactorRoot for a root result, else the fixed gate's
+                                             // angle (k: gamma_k, p+k: beta_k) or -1 (|+>, Z)
     std::vector<int32_t> graph_owned;        // per graph: networks whose 1/2 the energy counts
     std::vector<int32_t> net_weight;         // deduplicated plans: per network, the networks sharing its
                                              // value (0 for a duplicate); empty without duplicates
@@ -168,6 +171,40 @@ struct HostPlan {
     int64_t width_hist[64] = {0};
     double plan_seconds = 0;
 };
+
+// A contraction of tensors over binary indices in one expression (the paper's
+// "tncontract" benchmark, §II-E): out[K] = sum over the labels not in K of the
+// product of the operands, each operand given by its labels in C order (its
+// last label is bit 0 of its flat index). It runs as a chain of buckets: the
+// summed labels are eliminated first (each bucket's variable is bit 0 of its
+// operands, as in the energy plans), and the free labels take the next ranks
+// in the output's bit order, so the last result is the output, bit for bit.
+struct ContractPlan {
+    int dtype = 0;
+    std::vector<int> in_rank;                 // per input
+    std::vector<uint64_t> in_off;             // per input: element offset of its permuted copy in the arena
+    std::vector<std::vector<uint8_t>> in_src_bit;  // per input, per internal bit k: the bit of the caller's flat
+                                                   // index (C order) it comes from
+    std::vector<DBucket> buckets;             // in elimination order (a chain or a tree ending in one result)
+    std::vector<DOperand> operands;           // padded by kMaxOps
+    std::vector<DRun> runs;                   // static claim order: every group, producers first
+    uint64_t out_off = 0;
+    int out_rank = 0;
+    uint64_t arena_elems = 0;
+    int n_summed = 0;
+    int max_width = 0;
+    double alg_bytes = 0;  // every bucket's operands read once and result written once
+    double flops = 0;      // 8 per complex multiply-add of the buckets (the paper's complex FLOP count)
+    std::vector<int> widths;  // per bucket, the summed labels included
+};
+
+// labels: per operand, its labels in C order (any non-negative ints, distinct
+// within an operand); out_labels: the output's, in C order. Every output label
+// must appear in an operand and every operand must carry at least one summed
+// label; at most 30 distinct labels, 16 operands. Returns QT_OK, QT_EINVAL or
+// QT_EWIDTH.
+int build_contract_plan(const std::vector<std::vector<int>>& labels, const std::vector<int>& out_labels, int dtype,
+                        int sim_workers, ContractPlan* cp);
 
 // Returns QT_OK or a QT_E* code.
 int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, HostPlan* out);

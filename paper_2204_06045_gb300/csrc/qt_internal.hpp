@@ -45,6 +45,7 @@ constexpr int bucket_n_sum(uint8_t flags) { return 1 + ((flags >> 3) & 3); }
 // Epilogue factor lists (element offsets into the arena): this bit marks the
 // first factor of a slice's product.
 constexpr uint64_t kFirstFactor = 1ull << 63;
+constexpr int8_t kFactorRoot = -2;  // a factor that is a root result (the others are fixed gate entries)
 // Fused units: a subtree of small buckets (every output count at most
 // 2^kFuseOutBits, every non-gate operand produced inside the subtree) is one
 // work group; one warp contracts its buckets in elimination order with the

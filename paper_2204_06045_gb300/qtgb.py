@@ -24,7 +24,8 @@ EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "q
            "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
            "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed",
-           "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass")
+           "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass", "qt_contract_plan", "qt_contract_run",
+           "qt_contract_sync", "qt_contract_stats_get", "qt_contract_free")
 
 
 class QTError(RuntimeError):
@@ -74,6 +75,12 @@ DEV_BUCKET_DTYPE = np.dtype([("out_off", np.uint64), ("op_begin", np.int32), ("n
                              ("n_out", np.int32), ("n_sum", np.int32)])
 DEV_OPERAND_DTYPE = np.dtype([("off", np.uint64), ("mask", np.uint32), ("pairs_x", np.int32), ("leaf", np.int32),
                               ("pad", np.int32)])
+class ContractStats(ctypes.Structure):
+    _fields_ = [("n_buckets", ctypes.c_int32), ("max_width", ctypes.c_int32), ("n_summed", ctypes.c_int32),
+                ("n_merged", ctypes.c_int32), ("alg_bytes", ctypes.c_double), ("copy_bytes", ctypes.c_double),
+                ("arena_bytes", ctypes.c_int64), ("widths", ctypes.c_int32 * 32)]
+
+
 FIXED_DTYPE = np.dtype([("network", np.int32), ("slice", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                         ("entry", np.int32), ("pad", np.int32)])
 
@@ -124,6 +131,12 @@ def lib():
         L.qt_trace_bucket_times.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.qt_plan_free.argtypes = [vp]
         L.qt_plan_free.restype = None
+        L.qt_contract_plan.argtypes = [i32, i32p, i32p, i32, i32p, ctypes.c_int, i32, ctypes.POINTER(vp)]
+        L.qt_contract_run.argtypes = [vp, ctypes.POINTER(vp), vp, vp]
+        L.qt_contract_sync.argtypes = [vp, vp]
+        L.qt_contract_stats_get.argtypes = [vp, ctypes.POINTER(ContractStats)]
+        L.qt_contract_free.argtypes = [vp]
+        L.qt_contract_free.restype = None
         L.qt_error_string.argtypes = [ctypes.c_int]
         L.qt_error_string.restype = ctypes.c_char_p
         L.qt_version.restype = ctypes.c_char_p
@@ -132,7 +145,8 @@ def lib():
                      "qt_energy", "qt_energy_batch", "qt_energy_grad", "qt_last_imag", "qt_sync", "qt_kernel_time",
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
                      "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard",
-                     "qt_plan_export_fixed", "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass"):
+                     "qt_plan_export_fixed", "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass",
+                     "qt_contract_plan", "qt_contract_run", "qt_contract_sync", "qt_contract_stats_get"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -471,6 +485,66 @@ class Plan:
 
     def debug_stall_bucket(self, bucket: int):
         _check(lib().qt_debug_stall_bucket(self._h, int(bucket)), "qt_debug_stall_bucket")
+
+
+class Contraction:
+    """A planned contraction of complex tensors over binary (size-2) indices:
+    out[K] = sum over the labels not in K of prod_t T_t[L_t] (qt_contract_*).
+    ``labels``: one sequence of non-negative int labels per operand, in C
+    order; ``out_labels``: the output's, in C order. Runs on device tensors."""
+
+    def __init__(self, labels, out_labels, dtype="c64", host_only=False):
+        self.labels = [list(map(int, L)) for L in labels]
+        self.out_labels = list(map(int, out_labels))
+        self.dtype = dtype
+        ranks = np.array([len(L) for L in self.labels], dtype=np.int32)
+        flat = np.array([x for L in self.labels for x in L], dtype=np.int32)
+        outl = np.array(self.out_labels if self.out_labels else [0], dtype=np.int32)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        h = ctypes.c_void_p()
+        _check(lib().qt_contract_plan(len(self.labels), ranks.ctypes.data_as(ip), flat.ctypes.data_as(ip),
+                                      len(self.out_labels), outl.ctypes.data_as(ip),
+                                      {"c64": QT_C64, "c128": QT_C128}[dtype], int(bool(host_only)),
+                                      ctypes.byref(h)), "qt_contract_plan")
+        self._h = h
+
+    def stats(self) -> dict:
+        s = ContractStats()
+        _check(lib().qt_contract_stats_get(self._h, ctypes.byref(s)), "qt_contract_stats_get")
+        d = {k: getattr(s, k) for k, _ in ContractStats._fields_ if k != "widths"}
+        d["widths"] = [int(x) for x in s.widths[:min(32, s.n_buckets)]]
+        return d
+
+    def run(self, ops, out, stream=None):
+        """ops: contiguous complex CUDA tensors (shapes 2 x ... x 2 of each operand's rank); out: the
+        output tensor, written. With a stream the call only enqueues (see ``sync``)."""
+        ptrs = (ctypes.c_void_p * len(ops))(*[o.data_ptr() for o in ops])
+        _check(lib().qt_contract_run(self._h, ptrs, out.data_ptr(), _stream_ptr(stream)), "qt_contract_run")
+        return out
+
+    def sync(self, stream=None):
+        _check(lib().qt_contract_sync(self._h, _stream_ptr(stream)), "qt_contract_sync")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().qt_contract_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def contraction(labels, out_labels, dtype="c64", host_only=False) -> Contraction:
+    return Contraction(labels, out_labels, dtype, host_only)
 
 
 def plan(n: int, edges, p: int, **opts) -> Plan:

@@ -19,6 +19,15 @@ say how the graphs or angles are drawn, so the recipe is fixed here:
 * Batches of graphs: vertex counts drawn once from ``Generator(PCG64(7))``
   (even integers, uniform in ``[lo, hi]``); graph ``g`` then uses seed
   ``base_seed + g``.
+* Random contraction expressions (the paper's "tncontract random", §II-E and
+  §III-E: every index of size 2, 4 to 25 indices): ``Generator(PCG64(s))``
+  draws the number of indices n, then the number m of contracted indices
+  (1..n-1), then how many of the n - m result indices the second tensor also
+  holds; the first tensor holds all n indices in a random order, the second
+  the m contracted ones and those result indices in a random order, and the
+  result the n - m uncontracted indices in a random order (e.g. the paper's
+  ``dacb,ad->bcd``). Tensor entries are complex normal draws of a second
+  generator.
 """
 from __future__ import annotations
 
@@ -93,3 +102,24 @@ def prism_graph() -> np.ndarray:
     """Triangular prism: 3-regular on 6 vertices with two triangles."""
     e = [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (0, 3), (1, 4), (2, 5)]
     return np.array(sorted(e), dtype=np.int32)
+
+
+def tncontract_random(seed: int, n_lo: int = 4, n_hi: int = 25):
+    """One random contraction expression: ``(labels_a, labels_b, labels_out)``, each a list of
+    int labels in C order (first label the slowest axis), labels ``0..n-1``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(rng.integers(n_lo, n_hi + 1))
+    m = int(rng.integers(1, n))  # contracted indices, at least one result index left
+    idx = rng.permutation(n)
+    summed, result = idx[:m], idx[m:]
+    k = int(rng.integers(0, result.size + 1))  # result indices the second tensor holds too
+    b = np.concatenate([summed, rng.permutation(result)[:k]])
+    return ([int(x) for x in rng.permutation(n)], [int(x) for x in rng.permutation(b)],
+            [int(x) for x in rng.permutation(result)])
+
+
+def tensor_entries(shape_rank: int, seed: int, dtype=np.complex128) -> np.ndarray:
+    """Complex normal entries for a tensor of ``shape_rank`` indices of size 2 (shape 2 x ... x 2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal((2, 1 << shape_rank))
+    return (v[0] + 1j * v[1]).astype(dtype).reshape((2,) * shape_rank)

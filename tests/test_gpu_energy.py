@@ -186,7 +186,7 @@ def test_c4_wide_networks_match_min_fill_golden(dtype):
     rows, ref = _c4_golden()
     n, p, edges, g, b = _c4_inputs()
     np.testing.assert_array_equal((g, b), (np.array(rows["gamma"]), np.array(rows["beta"])))
-    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1, restarts=-1) as hp:
         B, _ = hp.export()
     mw = np.zeros(edges.shape[0], dtype=np.int64)
     np.maximum.at(mw, B["network"], B["width"])

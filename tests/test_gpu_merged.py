@@ -102,11 +102,12 @@ def test_merged_c2_n30_p4_matches_statevector_golden(dtype, order):
     n, p = 30, 4
     edges = synth.random_regular_graph(n, 1000)
     g, b = np.array(rows["gamma"]), np.array(rows["beta"])
-    with qtgb.plan(n, edges, p, dtype=dtype, order=order, merge=True, slice_width=-1) as pl:
+    # the plain greedy order (no restarts), on which merging halves the bytes
+    with qtgb.plan(n, edges, p, dtype=dtype, order=order, merge=True, slice_width=-1, restarts=-1) as pl:
         st = pl.stats()
         zz, E = pl.energy(g, b)
         im = pl.last_imag()
-    with qtgb.plan(n, edges, p, dtype=dtype, host_only=True, merge=False, slice_width=-1) as hp:
+    with qtgb.plan(n, edges, p, dtype=dtype, host_only=True, merge=False, slice_width=-1, restarts=-1) as hp:
         st1 = hp.stats()
     assert st["n_buckets"] < st1["n_buckets"] and st["alg_bytes"] < 0.6 * st1["alg_bytes"]
     assert scaled_err(zz, np.array(zz_ref)) <= TOL[dtype]
@@ -129,7 +130,7 @@ def test_merged_c4_wide_networks_match_min_fill_golden(dtype):
     n, p = 1000, 5
     edges = synth.random_regular_graph(n, 1000)
     g, b = synth.angles(p, 1000)
-    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1, restarts=-1) as hp:
         B, _ = hp.export()
     mw = np.zeros(edges.shape[0], dtype=np.int64)
     np.maximum.at(mw, B["network"], B["width"])

@@ -103,7 +103,7 @@ def test_sliced_c4_wide_networks_match_min_fill_golden(dtype):
     n, p = 1000, 5
     edges = synth.random_regular_graph(n, 1000)
     g, b = synth.angles(p, 1000)
-    with qtgb.plan(n, edges, p, host_only=True, merge=False, slice_width=-1) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, merge=False, slice_width=-1, restarts=-1) as hp:
         B, _ = hp.export()
     mw = np.zeros(edges.shape[0], dtype=np.int64)
     np.maximum.at(mw, B["network"], B["width"])

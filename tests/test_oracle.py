@@ -267,3 +267,55 @@ def test_planted_dropped_zz_gate_is_caught():
     za[1, 3] = 0.0  # one ZZ gate of layer 2 missing
     wrong = oracle.sv_zz_gates(n, edges, za, xa)
     assert np.abs(wrong - _dense_zz(n, edges, g, b)).max() > 1e-4
+
+
+# ---- contractions over binary indices (§II-E "tncontract") ------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_contract_matches_brute_force_on_random_expressions(seed):
+    """oracle.contract (one einsum) against the literal sum over every label
+    assignment, on the paper's kind of random expression (4..7 indices)."""
+    la, lb, lo = synth.tncontract_random(seed, n_lo=4, n_hi=7)
+    A = synth.tensor_entries(len(la), 10 * seed)
+    B = synth.tensor_entries(len(lb), 10 * seed + 1)
+    np.testing.assert_allclose(oracle.contract([A, B], [la, lb], lo), oracle.contract_brute([A, B], [la, lb], lo),
+                               rtol=0, atol=1e-12)
+
+
+def test_contract_special_cases():
+    """Closed forms: all-ones operands give 2^(summed labels) everywhere; a
+    basis vector on one label selects a slice; a scalar output is the full
+    sum; a permuted output is the transpose."""
+    ones4, ones2 = np.ones((2,) * 4), np.ones((2,) * 2)
+    # the paper's example shapes, dacb,ad->bcd: one label (a) summed
+    out = oracle.contract([ones4, ones2], [[3, 0, 2, 1], [0, 3]], [1, 2, 3])
+    assert out.shape == (2, 2, 2) and np.allclose(out, 2.0)
+    out = oracle.contract([ones4, np.ones((2,) * 3)], [[2, 0, 4, 3], [4, 0, 3]], [2])  # three summed
+    assert np.allclose(out, 8.0)
+    A = synth.tensor_entries(4, 3)
+    e1 = np.array([0.0, 1.0])
+    np.testing.assert_allclose(oracle.contract([A, e1], [[0, 1, 2, 3], [1]], [0, 2, 3]), A[:, 1, :, :], atol=0)
+    np.testing.assert_allclose(oracle.contract([A, np.ones(2)], [[0, 1, 2, 3], [0]], []), A.sum(), rtol=1e-14)
+    np.testing.assert_allclose(oracle.contract([A, np.ones(2)], [[0, 1, 2, 3], [1]], [3, 0, 2]),
+                               A.sum(axis=1).transpose(2, 0, 1), rtol=1e-14)
+
+
+def test_planted_contraction_mistake_is_caught():
+    """A planted mistake -- an output axis order swapped -- fails the brute force pin."""
+    la, lb, lo = [0, 1, 2, 3], [1, 2], [0, 3]
+    A, B = synth.tensor_entries(4, 8), synth.tensor_entries(2, 9)
+    wrong = oracle.contract([A, B], [la, lb], lo[::-1])
+    assert not np.allclose(wrong, oracle.contract_brute([A, B], [la, lb], lo), atol=1e-6)
+
+
+def test_random_expressions_follow_the_paper_recipe():
+    """synth.tncontract_random: 4..25 indices; the first tensor holds all of
+    them, the second every contracted one, the result the rest; at least one
+    index contracted and one kept."""
+    for s in range(200):
+        la, lb, lo = synth.tncontract_random(s)
+        n = len(la)
+        assert 4 <= n <= 25 and sorted(la) == list(range(n))
+        summed = set(la) - set(lo)
+        assert summed and lo and summed <= set(lb) and set(lb) <= set(la)
+        assert len(set(lb)) == len(lb) and len(set(lo)) == len(lo)

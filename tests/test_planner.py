@@ -148,8 +148,10 @@ def test_lightcone_wires(p):
 
 def test_restarts_never_worse():
     n, edges = 30, synth.random_regular_graph(30, 1000)
-    with host_plan(n, edges, 4) as a, host_plan(n, edges, 4, restarts=4, seed=11) as b:
+    with host_plan(n, edges, 4, restarts=-1) as a, host_plan(n, edges, 4, restarts=4, seed=11) as b, \
+            host_plan(n, edges, 4) as c:
         assert b.stats()["sum_2w"] <= a.stats()["sum_2w"]
+        assert c.stats()["sum_2w"] <= a.stats()["sum_2w"]  # the default restarts the wide networks
 
 
 def test_width27_bytes_convention():
@@ -469,17 +471,19 @@ def test_merged_eliminations_give_the_same_values(n, seed, p):
         assert np.abs(vals.imag).max() < 1e-12
 
 
-@pytest.mark.parametrize("kw", [dict(with_grad=True), dict(sched="per_bucket")])
-def test_merge_applies_to_persistent_forward_plans_only(kw):
-    """The reverse sweep and the per-bucket kernel sum one variable per bucket:
-    their plans are never merged."""
+def test_merge_applies_to_persistent_plans_only():
+    """The per-bucket kernel sums one variable per bucket: its plans are never
+    merged. Persistent plans merge, gradient plans included (the reverse sweep
+    takes merged buckets)."""
     n, seed, p = 18, 5, 4
     edges = synth.random_regular_graph(n, seed)
-    with host_plan(n, edges, p, merge=True, **kw) as pl:
+    with host_plan(n, edges, p, merge=True, sched="per_bucket") as pl:
         B, _ = pl.export()
     with host_plan(n, edges, p, merge=True) as pl:
         Bm, _ = pl.export()
-    assert (B["n_sum"] == 1).all() and (Bm["n_sum"] > 1).any()
+    with host_plan(n, edges, p, merge=True, with_grad=True) as pl:
+        Bg, _ = pl.export()
+    assert (B["n_sum"] == 1).all() and (Bm["n_sum"] > 1).any() and (Bg["n_sum"] > 1).any()
 
 
 @pytest.mark.parametrize("n,seed,p,width", [(12, 21, 2, 5), (14, 22, 3, 8), (16, 23, 3, 9), (18, 5, 4, 17)])
@@ -528,9 +532,9 @@ def test_slicing_options():
     with host_plan(n, edges, p, slice_width=6, max_slice_bits=2) as pl:
         st = pl.stats()
     assert st["slice_bits"] == 2 and st["max_width"] > 6  # the bit budget ran out first
-    with host_plan(n, edges, p, slice_width=6, with_grad=True) as pl:  # gradient plans are not sliced
+    with host_plan(n, edges, p, slice_width=6, with_grad=True) as pl:  # gradient plans are sliced too
         st = pl.stats()
-    assert st["slice_bits"] == 0 and st["n_slices"] == edges.shape[0]
+    assert st["slice_bits"] > 0 and st["n_slices"] > edges.shape[0]
     with host_plan(n, edges, p, slice_width=30) as pl:  # nothing that wide: no slices
         assert pl.stats()["n_slices"] == edges.shape[0] and len(pl.export_fixed()) == 0
     # the default target: 22 for complex64, 20 for complex128 (N=30 p=4 reaches width 26)
@@ -602,39 +606,6 @@ def test_dedup_kept_under_a_budget_the_deduplicated_plan_fits(grad):
         assert 0 < s3["pass_arena_bytes"] <= st["arena_bytes"] // 2
 
 
-def test_bucket_einsum_spec_is_the_contraction():
-    """bench.bucket_einsum (the subscripts the library-einsum comparison runs):
-    numpy.einsum over random operands reshaped by it equals the bucket
-    contraction out[o] = sum_x prod_t T_t[2 pext(o, M_t) + x] (§II-B)."""
-    import sys
-    sys.path.insert(0, str(Path(__file__).resolve().parents[1]))
-    import bench
-    from plan_eval import pext
-    n, seed, p = 14, 22, 3
-    edges = synth.random_regular_graph(n, seed)
-    with host_plan(n, edges, p, merge=False) as pl:
-        B, O = pl.export()
-    rng = np.random.default_rng(0)
-    checked = 0
-    for k in range(len(B)):
-        if B["width"][k] > 12:
-            continue
-        spec, shapes = bench.bucket_einsum(B, O, k)
-        flat = [rng.standard_normal(2 ** len(sh)) + 1j * rng.standard_normal(2 ** len(sh)) for sh in shapes]
-        got = np.einsum(spec, *[f.reshape(sh) for f, sh in zip(flat, shapes)]).reshape(-1)
-        n_out = int(B["width"][k]) - 1
-        o = np.arange(1 << n_out, dtype=np.int64)
-        want = np.zeros(1 << n_out, dtype=complex)
-        for x in (0, 1):
-            prod = np.ones(1 << n_out, dtype=complex)
-            for t, f in zip(range(int(B["op_begin"][k]), int(B["op_begin"][k]) + int(B["n_ops"][k])), flat):
-                prod = prod * f[2 * pext(o, int(O["mask"][t])) + x]
-            want += prod
-        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
-        checked += 1
-    assert checked > 50
-
-
 def test_energy_budget_runs_in_passes_that_fit():
     """opts.energy_budget_bytes: an energy plan over the budget is cut into
     passes over its networks' slices, each pass's arena within the budget; a
@@ -681,3 +652,44 @@ def test_dedup_contracts_one_network_per_lightcone_class(n, seed, p):
         st = pl.stats()
     assert n_classes < edges.shape[0]
     assert st["n_unique"] == n_classes
+
+
+# ---- contraction plans (the paper's "tncontract" expressions, §II-E) --------
+
+def test_contraction_plans_follow_bucket_elimination():
+    """Host-only contraction plans: the paper's two printed expressions give one
+    bucket (dacb,ad->bcd: width 4) and two (caedb,eab->cde: widths 5, 4); two
+    summed labels over 2^10 or more outputs merge into one bucket; the bytes
+    are the buckets' operands read once and results written once."""
+    with qtgb.contraction([[3, 0, 2, 1], [0, 3]], [1, 2, 3], host_only=True) as c:
+        st = c.stats()
+    assert st["n_buckets"] == 1 and st["widths"] == [4] and st["n_summed"] == 1
+    assert st["alg_bytes"] == 8 * (16 + 4 + 8)
+    with qtgb.contraction([[2, 0, 4, 3, 1], [4, 0, 1]], [2, 3, 4], host_only=True) as c:
+        st = c.stats()
+    assert st["n_buckets"] == 2 and st["widths"] == [5, 4] and st["n_merged"] == 0
+    assert st["alg_bytes"] == 8 * ((32 + 8 + 16) + (16 + 8))
+    with qtgb.contraction([list(range(15)), [3, 9]], [x for x in range(15) if x not in (3, 9)], dtype="c128",
+                          host_only=True) as c:
+        st = c.stats()
+    assert st["n_buckets"] == 1 and st["n_merged"] == 1 and st["widths"] == [15]
+    assert st["alg_bytes"] == 16 * (2 ** 15 + 4 + 2 ** 13)
+    assert st["copy_bytes"] == 16 * 2 * (2 ** 15 + 4 + 2 ** 13)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_contraction_plans_are_accepted(seed):
+    """Every expression of the paper's recipe (4..25 indices) plans, the widest
+    bucket holding every index."""
+    la, lb, lo = synth.tncontract_random(seed)
+    with qtgb.contraction([la, lb], lo, host_only=True) as c:
+        st = c.stats()
+    assert st["max_width"] == len(la) and st["n_summed"] == len(la) - len(lo)
+
+
+def test_invalid_contractions_are_refused_on_the_host():
+    for labels, lo in (([[0, 1], [2, 3]], [0, 1, 2, 3]), ([[0, 0]], [0]), ([[0, 1]], [5]), ([[0, 1], [2, 3]], [1, 3]),
+                       ([[0, 1, 2], [1]], [1, 2]), ([list(range(31))], [0])):
+        with pytest.raises(qtgb.QTError) as ei:
+            qtgb.contraction(labels, lo, host_only=True)
+        assert ei.value.code == qtgb.QT_EINVAL, labels
