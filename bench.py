@@ -15,13 +15,20 @@ form). The plain complex128 form is measured beside it under "c128".
 * roofline: algorithmic bytes of one evaluation (every operand read once,
   every result written once) over the average duration of the persistent
   bucket kernel, from CUDA events recorded around it on its stream.
-* cpu_baseline: the CPU oracle's bucket elimination on a bounded sample of the
-  same workload, on all host cores (rank 0, one GPU only).
+* cpu_baseline: one whole evaluation of the same workload (all 45 networks)
+  by the CPU oracle's bucket elimination in its own greedy min-fill order, on
+  all host cores (rank 0, one GPU only), plus a one-thread estimate.
+* summary (the line's last key): the headline figures of every configuration
+  in one short object -- complex64 and complex128 evaluations/s, the roofline
+  fractions, accuracy, the wide-bucket GB/s, the 64-graph batch against the
+  plain per-bucket complex128 form, the N=50 p=4 gradient rate.
 
 ``--impl reference`` times the CPU oracle alone (there is no reference code
 base; the oracle stands in for it) and prints its line with "impl": "reference".
-Multi-GPU (torchrun): every rank evaluates its own copy of the workload (weak
-scaling); there is no data-path collective.
+Multi-GPU (torchrun): the graph's networks (their slices) are split over the
+ranks by longest-processing-time on their cost and each step ends with one
+all-reduce of the partial energy (strong scaling); ``--replicas`` runs an
+independent copy per rank instead (weak scaling, no data-path collective).
 """
 from __future__ import annotations
 
@@ -42,7 +49,7 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 PAPER_SECONDS_PER_EVAL = 1.4  # best mixed merged backend, N=30 p=4, V100 (Table II)
-REF_EDGES_PER_STEP = 3        # oracle sample per reference step
+REF_TIMED_BUDGET_S = 150.0    # the reference arm's timed steps together, about (cost-weighted groups per step)
 
 
 def parse():
@@ -52,17 +59,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
-    ap.add_argument("--workload", choices=["c2", "c3", "c5", "einsum"], default="c2",
-                    help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5); "
-                         "c3: 64-graph batch; c5: gradients on N=50 p=4; einsum: the wide N=1000 p=5 buckets, "
-                         "this kernel against torch.einsum on the same contractions")
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "tncontract"], default="c2",
+                    help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5, the "
+                         "batch, gradient and random-contraction legs); c3: 64-graph batch; c5: gradients on "
+                         "N=50 p=4; tncontract: the paper's random contraction expressions against torch.einsum")
     ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the plan-time autotuner's line")
-    ap.add_argument("--no-alt", action="store_true", help="skip the alternative plans (restarts, deduplication)")
-    ap.add_argument("--shard", action="store_true",
-                    help="with N GPUs: split the N=30 p=4 graph's networks over the ranks (LPT by cost) and "
-                         "all-reduce the partial energies every step (strong scaling); default: replicas")
+    ap.add_argument("--no-alt", action="store_true", help="skip the alternative plan (the plain greedy order)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N GPUs: every rank evaluates its own copy of the workload (weak scaling); default: "
+                         "the graph's networks split over the ranks by LPT on cost, one all-reduce per step")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 64-graph batch and gradient legs of the summary")
     return ap.parse_args()
 
 
@@ -135,52 +143,110 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(budget_s: float, max_edges=None):
-    """Time the oracle's bucket elimination on edges 0, 1, ... until the budget is spent."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in Path("/proc/cpuinfo").read_text().splitlines():
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_networks(nets):
+    """Seconds the oracle takes for each network in `nets` of the workload (complex128 bucket
+    elimination in the oracle's own greedy min-fill order), on its current thread count."""
     import oracle
     n, p, edges, g, b = workload_inputs()
+    out = []
+    for e in nets:
+        t0 = time.perf_counter()
+        oracle.edge_bucket_min_fill(n, edges, g, b, int(e), seed=int(e), max_width=31)
+        out.append(time.perf_counter() - t0)
+    return np.array(out)
+
+
+def cpu_baseline(one_thread_budget_s: float = 4.0):
+    """One whole evaluation (every network) on all host cores, timed; and a one-thread figure
+    estimated from the cheapest networks, weighted by their share of the all-core time."""
+    import oracle
+    oracle.build()
+    cores = oracle.get_threads()
+    n, p, edges, g, b = workload_inputs()
     m = edges.shape[0]
-    t0 = time.perf_counter()
-    k = 0
-    while k < m and (max_edges is None or k < max_edges):
-        oracle.edge_bucket(n, edges, g, b, k, seed=k)
-        k += 1
-        if max_edges is None and time.perf_counter() - t0 >= budget_s:
+    t = oracle_networks(range(m))
+    total = float(t.sum())
+    order = np.argsort(t)
+    picked, acc = [], 0.0
+    for e in order:  # cheapest first, within the budget at ~cores times the all-core time
+        if picked and acc + t[e] * cores > one_thread_budget_s:
             break
-    dt = time.perf_counter() - t0
-    return k, m, dt, oracle.get_threads()
-
-
-def cpu_baseline(budget_s: float):
-    k, m, dt, cores = oracle_sample(budget_s)
-    return {"value": (k / m) / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": f"complex128 CPU bucket elimination (oracle) of lightcone networks 0..{k - 1} of {m} "
-                      f"in {dt:.1f} s; evals/s = ({k}/{m}) / time"}
+        picked.append(int(e))
+        acc += t[e] * cores
+    oracle.set_threads(1)
+    try:
+        t1 = float(oracle_networks(picked).sum())
+    finally:
+        oracle.set_threads(cores)
+    share = float(t[picked].sum()) / total
+    return {"value": 1.0 / total, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"one whole evaluation: all {m} lightcone networks, complex128 bucket elimination "
+                      f"(oracle, its greedy min-fill order) on {cores} threads in {total:.2f} s",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "one_thread": {"value": share / t1 if t1 > 0 else None, "unit": "evals/s",
+                           "sample": f"{len(picked)} cheapest networks ({100 * share:.2f}% of the all-core time) on "
+                                     f"1 thread in {t1:.2f} s, scaled by that share (an estimate)"}}
 
 
 def run_reference(args, rank, world):
+    """The CPU oracle on the same workload. The first warm-up step is one whole
+    evaluation whose per-network times split the networks into G groups of
+    about equal cost (longest first); each further step evaluates the next
+    group, and a step counts as its group's share of the whole evaluation, so
+    the K timed steps stay within about REF_TIMED_BUDGET_S."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     n, p, edges, g, b = workload_inputs()
     m = edges.shape[0]
-    for _ in range(args.warmup):
-        oracle_sample(0, max_edges=REF_EDGES_PER_STEP)
-    times = []
-    for _ in range(args.steps):
-        _, _, dt, cores = oracle_sample(0, max_edges=REF_EDGES_PER_STEP)
-        times.append(dt)
-    total = sum(times)
-    value = args.steps * (REF_EDGES_PER_STEP / m) / total
-    sample = (f"each step: complex128 CPU bucket elimination (oracle) of lightcone networks 0..{REF_EDGES_PER_STEP - 1}"
-              f" of {m}; evals/s = steps * ({REF_EDGES_PER_STEP}/{m}) / time")
+    calib = oracle_networks(range(m))  # warm-up step 1: a whole evaluation
+    total = float(calib.sum())
+    G = max(1, min(m, int(np.ceil(args.steps * total / REF_TIMED_BUDGET_S))))
+    groups = [[] for _ in range(G)]
+    load = np.zeros(G)
+    for e in np.argsort(-calib):
+        k = int(np.argmin(load))
+        groups[k].append(int(e))
+        load[k] += calib[e]
+    share = load / total
+    for w in range(1, args.warmup):
+        oracle_networks(groups[w % G])
+    times, done = [], 0.0
+    for s in range(args.steps):
+        times.append(float(oracle_networks(groups[s % G]).sum()))
+        done += share[s % G]
+    total_t = sum(times)
+    value = done / total_t
+    cores = oracle.get_threads()
+    sample = (f"{m} networks split into {G} groups of about equal oracle time (from a whole evaluation in the first "
+              f"warm-up step, {total:.2f} s on {cores} threads); step k evaluates group k mod {G} and counts as its "
+              f"share of an evaluation; evals/s = sum of shares / time")
     line = {"impl": "reference", "metric": "QAOA energy evals/s (3-reg N=30 p=4)", "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value * PAPER_SECONDS_PER_EVAL, "dtype": "c128", "data": "synthetic",
-            "config": config_dict("complex128 CPU oracle (sampled)"),
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "config": config_dict("complex128 CPU oracle, bucket elimination in its greedy min-fill order"),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -255,12 +321,16 @@ def golden_c2():
 
 
 def accuracy(zz, E, ref_zz, ref_E):
+    """Errors against the stored state vector. `max_scaled_err_zz` is |d e| / max(|e|, 1e-2), the
+    survey's measure; the tests bound the relative error of each edge's energy (1 - e)/2 and the
+    absolute error of e (the adopted reading); both are printed."""
     if ref_zz is None:
         return {"reference": "unavailable"}
     d = np.abs(np.asarray(zz) - ref_zz)
     return {"reference": "2^30 complex128 state vector (oracle, stored)",
             "max_abs_err_zz": float(d.max()),
             "max_rel_err_zz": float(np.max(d / np.abs(ref_zz))),
+            "max_scaled_err_zz": float(np.max(d / np.maximum(np.abs(ref_zz), 1e-2))),
             "max_rel_err_edge_energy": float(np.max(d / np.abs(1.0 - ref_zz))),
             "rel_err_energy": float(abs(E - ref_E) / abs(ref_E))}
 
@@ -296,7 +366,7 @@ def wide_buckets(peak, torch):
     n, p, seed = 1000, 5, 1000
     edges = synth.random_regular_graph(n, seed)
     g, b = synth.angles(p, seed)
-    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
+    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1, restarts=-1) as hp:
         B, _ = hp.export()
     mw = np.zeros(edges.shape[0], dtype=np.int64)
     np.maximum.at(mw, B["network"], B["width"])
@@ -306,7 +376,7 @@ def wide_buckets(peak, torch):
            "edges": sel.tolist()}
     ref = golden_c4()
     for dtype in ("c64", "c128"):
-        with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, merge=False, slice_width=-1) as pl:
+        with qtgb.plan_subset(n, edges, p, sel, dtype=dtype, merge=False, slice_width=-1, restarts=-1) as pl:
             zz, _ = pl.energy(g, b)  # also leaves real data in every operand
             if ref is not None:
                 want = np.array([ref[int(e)] for e in sel])
@@ -330,7 +400,8 @@ def wide_buckets(peak, torch):
         # single-edge contraction: each network alone in its own plan, every bucket of it in one
         # persistent launch; algorithmic bytes of the network over the kernel's time
         tot = {}
-        variants = {"plain": dict(merge=False, slice_width=-1), "merged": dict(slice_width=-1), "default": {}}
+        variants = {"plain": dict(merge=False, slice_width=-1, restarts=-1), "merged": dict(slice_width=-1, restarts=-1),
+                    "default": {}}
         for key, kw in variants.items():
             nb = nm = 0.0
             for e in sel:
@@ -362,85 +433,88 @@ def wide_buckets(peak, torch):
 _LETTERS = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
 
 
-def bucket_einsum(B, O, k):
-    """einsum subscripts and operand shapes of bucket k of an exported plan
-    (a plain bucket: one summed variable). An operand's entry for output o and
-    summed value x is at 2 * pext(o, mask) + x, so in C order its dimensions
-    are its output bits from the highest down, then x; the output's are its
-    bits from the highest down."""
-    n_out = int(B["width"][k]) - int(B["n_sum"][k])
-    if int(B["n_sum"][k]) != 1 or n_out + 1 > len(_LETTERS):
-        raise ValueError("a plain bucket of at most 51 output bits")
-    out = _LETTERS[:n_out]
-    x = _LETTERS[n_out]
-    subs, shapes = [], []
-    for t in range(int(B["op_begin"][k]), int(B["op_begin"][k]) + int(B["n_ops"][k])):
-        bits = [i for i in range(n_out) if (int(O["mask"][t]) >> i) & 1]
-        subs.append("".join(out[i] for i in reversed(bits)) + x)
-        shapes.append((2,) * (len(bits) + 1))
-    return ",".join(subs) + "->" + out[::-1], shapes
+def tncontract_leg(torch, n_expr=24, reps=5):
+    """The paper's "tncontract random" benchmark (§II-E; Table III, Tensor Network
+    Random Contraction): seeded random expressions of 4..25 indices of size 2
+    (synth.tncontract_random, seeds 0..n_expr-1), complex64, each run through
+    qt_contract (permuting copies in, the bucket-elimination kernel, the copy out)
+    and through torch.einsum on the same GPU, both from device tensors to a device
+    tensor; CUDA events on one stream, mean of `reps` after 2. FLOP rate in the
+    paper's convention: 8 x 2^(distinct indices) per contraction / time."""
+    from paper_2204_06045_gb300 import qtgb, synth
+    rows = []
+    s = torch.cuda.current_stream()
+    for k in range(n_expr):
+        la, lb, lo = synth.tncontract_random(k)
+        n = len(la)
+        gen = torch.Generator(device="cuda").manual_seed(k)
+        A = torch.randn((2,) * n, dtype=torch.complex64, device="cuda", generator=gen)
+        B = torch.randn((2,) * len(lb), dtype=torch.complex64, device="cuda", generator=gen)
+        spec = "".join(_LETTERS[x] for x in la) + "," + "".join(_LETTERS[x] for x in lb) + "->" + \
+            "".join(_LETTERS[x] for x in lo)
+        out = torch.empty((2,) * len(lo), dtype=torch.complex64, device="cuda")
+        with qtgb.contraction([la, lb], lo, dtype="c64") as c:
+            st = c.stats()
+            for _ in range(2):
+                c.run([A, B], out, stream=s)
+            c.sync(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                c.run([A, B], out, stream=s)
+            e1.record(s)
+            c.sync(s)
+            ms = e0.elapsed_time(e1) / reps
+        for _ in range(2):
+            ref = torch.einsum(spec, A, B)
+        e0.record(s)
+        for _ in range(reps):
+            ref = torch.einsum(spec, A, B)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms_lib = e0.elapsed_time(e1) / reps
+        diff = float((out - ref).abs().max() / ref.abs().max().clamp_min(1.0))
+        rows.append({"indices": n, "summed": n - len(lo), "b_rank": len(lb), "ms": ms, "einsum_ms": ms_lib,
+                     "buckets": st["n_buckets"], "gbs": (st["alg_bytes"] + st["copy_bytes"]) / ms / 1e6,
+                     "paper_gflops": 8.0 * 2.0 ** n / ms / 1e6, "max_rel_diff_vs_einsum": diff})
+    big = [r for r in rows if r["indices"] >= 20]
+    ours, lib = sum(r["ms"] for r in big), sum(r["einsum_ms"] for r in big)
+    top = max(rows, key=lambda r: r["indices"])
+    return {"workload": f"{n_expr} random expressions (synth.tncontract_random seeds 0..{n_expr - 1}: 4..25 indices, "
+                        "the first tensor holding all, the second the contracted ones and some result indices), "
+                        "complex64, device tensors in and out",
+            "einsum_time_over_ours_20plus": lib / ours if ours > 0 else None, "expressions_20plus": len(big),
+            "ms_20plus": ours, "einsum_ms_20plus": lib,
+            "largest": {k: top[k] for k in ("indices", "ms", "einsum_ms", "paper_gflops", "gbs")},
+            "max_rel_diff_vs_einsum": max(r["max_rel_diff_vs_einsum"] for r in rows), "rows": rows}
 
 
-def run_einsum(args, world, local_rank):
-    """A library comparison point: every bucket of width >= 24 of the 15 widest
-    N=1000 p=5 networks (plain buckets), timed alone in the persistent kernel
-    (qt_bucket_time) and as torch.einsum on random complex64 tensors of the
-    same shapes on the same GPU (CUDA events, mean of 3 after 1)."""
+def run_tncontract(args, world, local_rank):
+    """--workload tncontract: the random-expression comparison as its own line."""
     import torch
-    from paper_2204_06045_gb300 import build, qtgb, synth
+    from paper_2204_06045_gb300 import build
     torch.cuda.set_device(local_rank)
     build.build()
-    n, p, seed = 1000, 5, 1000
-    edges = synth.random_regular_graph(n, seed)
-    g, b = synth.angles(p, seed)
-    with qtgb.plan(n, edges, p, host_only=True, slice_width=-1) as hp:
-        B0, _ = hp.export()
-    mw = np.zeros(edges.shape[0], dtype=np.int64)
-    np.maximum.at(mw, B0["network"], B0["width"])
-    sel = np.nonzero((mw >= 26) & (mw <= 28))[0]
-    rows = []
-    with qtgb.plan_subset(n, edges, p, sel, dtype="c64", merge=False, slice_width=-1) as pl:
-        pl.energy(g, b)
-        B, O = pl.export()
-        for k in np.nonzero(B["width"] >= 24)[0]:
-            ms_ours, by = pl.bucket_time(int(k), reps=3)
-            spec, shapes = bucket_einsum(B, O, int(k))
-            ops = [torch.randn(sh, dtype=torch.complex64, device="cuda") for sh in shapes]
-            torch.einsum(spec, *ops)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(3):
-                torch.einsum(spec, *ops)
-            e1.record()
-            torch.cuda.synchronize()
-            ms_lib = e0.elapsed_time(e1) / 3
-            del ops
-            rows.append({"bucket": int(k), "width": int(B["width"][k]), "n_ops": int(B["n_ops"][k]),
-                         "alg_bytes": by, "ms": ms_ours, "einsum_ms": ms_lib})
-    ours = sum(r["ms"] for r in rows)
-    lib = sum(r["einsum_ms"] for r in rows)
-    line = {"metric": "wide-bucket contraction time, this kernel vs torch.einsum (N=1000 p=5, width >= 24)",
-            "value": lib / ours, "unit": "x (einsum time / this kernel's)", "n_gpus": 1, "steps": 3, "warmup": 1,
-            "higher_is_better": True, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": f"{len(rows)} plain buckets of width >= 24 of the 15 networks of greedy width "
-                                   "26..28, random 3-regular N=1000 seed 1000, p=5"},
-            "ms": ours, "einsum_ms": lib, "agg_gbs": sum(r["alg_bytes"] for r in rows) / ours / 1e6,
-            "buckets": rows}
+    res = tncontract_leg(torch, n_expr=24, reps=max(1, min(args.steps, 20)))
+    line = {"metric": "tncontract random (paper §II-E): torch.einsum time / this library's time, expressions of "
+                      ">= 20 indices",
+            "value": res["einsum_time_over_ours_20plus"], "unit": "x", "n_gpus": 1, "steps": args.steps,
+            "warmup": 2, "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": res["workload"]}, "tncontract": res}
     print(json.dumps(line), flush=True)
 
 
 def alt_plans(n, p, edges, g, b, ref_zz, default, torch):
-    """Exploratory, beside the headline (which these do not change): the same
-    workload planned with 64 randomised min-fill restarts (fewer algorithmic
-    bytes), and the 64-graph batch with lightcone deduplication. Each entry
-    records its kernel time, bytes and agreement, or the error it met."""
-    from paper_2204_06045_gb300 import qtgb, synth
+    """Beside the headline (which it does not change): the same workload planned
+    with the plain greedy min-fill order (no restarts; the default plan restarts
+    the order 64 times for every network whose greedy order reaches width 18).
+    Each entry records its kernel time, bytes and agreement, or the error it met."""
+    from paper_2204_06045_gb300 import qtgb
     m = edges.shape[0]
     out = {}
     for dtype, steps in (("c64", 100), ("c128", 20)):
         try:
-            with qtgb.plan(n, edges, p, dtype=dtype, restarts=64, seed=7) as pl:
+            with qtgb.plan(n, edges, p, dtype=dtype, restarts=-1) as pl:
                 st = pl.stats()
                 gd = torch.tensor(g, dtype=torch.float64, device="cuda")
                 bd = torch.tensor(b, dtype=torch.float64, device="cuda")
@@ -448,42 +522,14 @@ def alt_plans(n, p, edges, g, b, ref_zz, default, torch):
                 E = torch.zeros(1, dtype=torch.float64, device="cuda")
                 ms, kms, _ = time_device(pl, gd, bd, zz, E, steps, 3, None, torch)
                 err = float(np.max(np.abs(zz.cpu().numpy() - ref_zz))) if ref_zz is not None else None
-            out[f"restarts64_{dtype}"] = {
+            out[f"plain_greedy_{dtype}"] = {
                 "ms_per_step": ms / steps, "kernel_ms": kms, "alg_bytes": st["alg_bytes"],
+                "plan_seconds": st["plan_seconds"],
                 "default_kernel_ms": default[dtype]["roofline"]["kernel_ms"],
-                "default_alg_bytes": default[dtype]["roofline"]["alg_bytes_per_launch"], "max_abs_err_zz": err}
+                "default_alg_bytes": default[dtype]["roofline"]["alg_bytes_per_launch"],
+                "default_plan_seconds": default[dtype]["plan"]["plan_seconds"], "max_abs_err_zz": err}
         except Exception as ex:  # recorded, not fatal: the headline stands without it
-            out[f"restarts64_{dtype}"] = {"error": repr(ex)}
-    try:
-        graphs = synth.batch(64, 3, lo=50, hi=1000, base_seed=1000)
-        spec = [(nn, e) for nn, e, _, _ in graphs]
-        G = np.array([gg for _, _, gg, _ in graphs])
-        Bt = np.array([bb for _, _, _, bb in graphs])
-        res = {}
-        for dedup in (False, True):
-            with qtgb.plan_batch(spec, 3, dtype="c64", dedup=dedup) as pl:
-                st = pl.stats()
-                gd = torch.tensor(G.ravel(), dtype=torch.float64, device="cuda")
-                bd = torch.tensor(Bt.ravel(), dtype=torch.float64, device="cuda")
-                en = torch.zeros(64, dtype=torch.float64, device="cuda")
-                s = torch.cuda.current_stream()
-                for _ in range(3):
-                    pl.energy_batch(gd, bd, energies=en, stream=s)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(s)
-                for _ in range(50):
-                    pl.energy_batch(gd, bd, energies=en, stream=s)
-                e1.record(s)
-                torch.cuda.synchronize()
-                res[dedup] = (e0.elapsed_time(e1) / 50, en.cpu().numpy(), st["n_unique"], st["alg_bytes"])
-        out["batch64_p3_dedup_c64"] = {
-            "ms_per_step": res[True][0], "graph_evals_per_s": 64 / (res[True][0] * 1e-3),
-            "ms_per_step_without": res[False][0], "speedup": res[False][0] / res[True][0],
-            "networks_contracted": res[True][2], "alg_bytes": res[True][3], "alg_bytes_without": res[False][3],
-            "max_rel_energy_diff": float(np.max(np.abs(res[True][1] - res[False][1]) / np.abs(res[False][1])))}
-    except Exception as ex:
-        out["batch64_p3_dedup_c64"] = {"error": repr(ex)}
+            out[f"plain_greedy_{dtype}"] = {"error": repr(ex)}
     return out
 
 
@@ -535,6 +581,124 @@ def job_throughput(world, units_per_rank, seconds):
     """Weak scaling: every rank processes its own units; the job's rate is all
     ranks' units over the slowest rank's time."""
     return world * units_per_rank / seconds
+
+
+def c3_leg(torch, steps):
+    """The 64-graph batch (random 3-regular, N even in [50, 1000], p=3, per-graph angles):
+    every network in one persistent complex64 launch, with and without lightcone
+    deduplication; beside it the plain form -- complex128, one launch per bucket -- on every
+    eighth graph, with the batched complex64 form timed on the same eight graphs."""
+    from paper_2204_06045_gb300 import qtgb, synth
+    graphs = synth.batch(64, 3, lo=50, hi=1000, base_seed=1000)
+    spec = [(nn, e) for nn, e, _, _ in graphs]
+    G = np.array([gg for _, _, gg, _ in graphs])
+    Bt = np.array([bb for _, _, _, bb in graphs])
+
+    def timed(sel, reps, warm, **kw):
+        with qtgb.plan_batch([spec[i] for i in sel], 3, **kw) as pl:
+            st = pl.stats()
+            gd = torch.tensor(G[sel].ravel(), dtype=torch.float64, device="cuda")
+            bd = torch.tensor(Bt[sel].ravel(), dtype=torch.float64, device="cuda")
+            en = torch.zeros(len(sel), dtype=torch.float64, device="cuda")
+            s = torch.cuda.current_stream()
+            for _ in range(warm):
+                pl.energy_batch(gd, bd, energies=en, stream=s)
+            pl.sync(s)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                pl.energy_batch(gd, bd, energies=en, stream=s)
+            e1.record(s)
+            torch.cuda.synchronize()
+            pl.sync(s)
+            return e0.elapsed_time(e1) / reps, en.cpu().numpy(), st
+
+    every = list(range(64))
+    sub = list(range(0, 64, 8))
+    ms, en, st = timed(every, steps, 3, dtype="c64")
+    ms_d, en_d, st_d = timed(every, steps, 3, dtype="c64", dedup=True)
+    ms_p, en_p, st_p = timed(sub, 1, 1, dtype="c128", sched="per_bucket")
+    ms_s, en_s, _ = timed(sub, steps, 3, dtype="c64")
+    return {"workload": "64 random 3-regular graphs, N even in [50,1000] (synth.batch, seed 1000+g), p=3",
+            "c64_graph_evals_per_s": 64e3 / ms, "c64_ms_per_batch": ms, "buckets": int(st["n_buckets"]),
+            "c64_dedup_graph_evals_per_s": 64e3 / ms_d, "dedup_networks_contracted": int(st_d["n_unique"]),
+            "dedup_max_rel_energy_diff": float(np.max(np.abs(en_d - en) / np.abs(en))),
+            "plain_subset": "graphs 0, 8, ..., 56",
+            "plain_c128_per_bucket_graph_evals_per_s": 8e3 / ms_p, "plain_launches": int(st_p["n_buckets"]),
+            "c64_batched_same_subset_graph_evals_per_s": 8e3 / ms_s,
+            "speedup_batched_c64_vs_plain_c128": ms_p / ms_s,
+            "max_rel_energy_diff_c64_vs_c128": float(np.max(np.abs(en_s - en_p) / np.abs(en_p)))}
+
+
+def c5_leg():
+    """Energy and its 2p angle derivatives on random 3-regular N=50 (seed 1000), p=4, by the
+    adjoint of the bucket elimination (host arrays in and out), complex64 and complex128; and
+    the gradient of 8 sampled edges' energy share against the oracle's central differences."""
+    from paper_2204_06045_gb300 import qtgb, synth
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    out = {"workload": "random 3-regular N=50 seed 1000, p=4: energy + dE/dgamma_k, dE/dbeta_k"}
+    grads = {}
+    for dtype, steps in (("c64", 10), ("c128", 3)):
+        with qtgb.plan(n, edges, p, dtype=dtype, with_grad=True) as pl:
+            for _ in range(2):
+                pl.energy_grad(g, b)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                E, dg, db = pl.energy_grad(g, b)
+            dt = (time.perf_counter() - t0) / steps
+        out[f"{dtype}_grad_evals_per_s"] = 1.0 / dt
+        grads[dtype] = np.concatenate([dg, db])
+    out["c64_vs_c128_max_abs_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
+    f = ROOT / "tests" / "golden" / "c5_n50_p4_fd.txt"
+    if f.exists():
+        rows = {}
+        for line in f.read_text().splitlines():
+            if line.strip() and not line.startswith("#"):
+                k, *v = line.split()
+                rows[k] = np.array([float(x) for x in v])
+        ref = np.concatenate([rows["dE_dgamma"], rows["dE_dbeta"]])
+        for dtype in ("c64", "c128"):
+            with qtgb.plan_subset(n, edges, p, rows["edges"].astype(np.int32), dtype=dtype, with_grad=True) as pl:
+                _, dg, db = pl.energy_grad(g, b)
+            out[f"{dtype}_subset_vs_oracle_fd_max_abs"] = float(np.max(np.abs(np.concatenate([dg, db]) - ref)))
+    return out
+
+
+def summarize(line):
+    """The headline figures of every configuration, short enough to read at the end of the line."""
+    r, c = line["roofline"], line["c128"]
+    s = {"c2_c64_evals_per_s": line["value"], "c2_c64_kernel_ms": r["kernel_ms"], "c2_c64_hbm_frac": r["frac"],
+         "c2_c64_e2e_evals_per_s": line["e2e"]["value"],
+         "c2_c128_evals_per_s": c["value"], "c2_c128_kernel_ms": c["roofline"]["kernel_ms"],
+         "c2_c128_fp64_frac": c["roofline"]["frac"]}
+    for dt, chk in (("c64", line["check"]), ("c128", c["check"])):
+        s[f"c2_{dt}_max_abs_err_zz"] = chk.get("max_abs_err_zz")
+        s[f"c2_{dt}_max_scaled_err_zz"] = chk.get("max_scaled_err_zz")
+        s[f"c2_{dt}_max_rel_err_edge_energy"] = chk.get("max_rel_err_edge_energy")
+    wb = line.get("bucket_gbs")
+    if wb and "c64" in wb:
+        s["wide_buckets_c64"] = {k: wb["c64"][k] for k in ("buckets", "agg_gbs", "frac_of_peak", "median_gbs", "min_gbs")}
+        s["wide_buckets_c128_agg_gbs"] = wb["c128"]["agg_gbs"]
+    if "c3" in line:
+        s["c3"] = {k: line["c3"][k] for k in ("c64_graph_evals_per_s", "c64_dedup_graph_evals_per_s",
+                                              "plain_c128_per_bucket_graph_evals_per_s",
+                                              "c64_batched_same_subset_graph_evals_per_s",
+                                              "speedup_batched_c64_vs_plain_c128")}
+    if "c5" in line:
+        s["c5"] = {k: v for k, v in line["c5"].items() if k != "workload"}
+    if "tncontract" in line:
+        s["tncontract"] = {k: line["tncontract"][k] for k in ("einsum_time_over_ours_20plus", "expressions_20plus",
+                                                             "largest", "max_rel_diff_vs_einsum")}
+    alt = line.get("alt_plans", {}).get("plain_greedy_c64", {})
+    if "kernel_ms" in alt:
+        s["plain_greedy_order_c64_kernel_ms"] = alt["kernel_ms"]
+        s["plain_greedy_order_c64_alg_gb"] = alt["alg_bytes"] / 1e9
+    if "cpu_baseline" in line:
+        s["cpu_oracle_evals_per_s"] = line["cpu_baseline"]["value"]
+    return s
 
 
 def run_ours(args, rank, world, local_rank):
@@ -621,8 +785,13 @@ def run_ours(args, rank, world, local_rank):
         line["alt_plans"] = alt_plans(n, p, edges, g, b, ref_zz, {"c64": main, "c128": results["c128"]}, torch)
     if world == 1 and not args.no_buckets:
         line["bucket_gbs"] = wide_buckets(peak, torch)
+    if world == 1 and not args.no_extra:
+        line["c3"] = c3_leg(torch, min(args.steps, 20))
+        line["c5"] = c5_leg()
+        line["tncontract"] = tncontract_leg(torch)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline()
+    line["summary"] = summarize(line)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -724,9 +893,18 @@ def run_c5(args, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def shard_step(pl, gd, bd, zz, E, s, dist):
+    """One step of the sharded energy: this rank's networks, then one all-reduce (SUM) of the
+    partial energy -- the one exchange the method has (E = |E|/2 - 1/2 sum of the edges' values)."""
+    pl.energy(gd, bd, edge_zz=zz, energy=E, stream=s)
+    if dist is not None:
+        dist.all_reduce(E, op=dist.ReduceOp.SUM)
+
+
 def run_shard(args, rank, world, local_rank):
-    """One graph's energy split over the ranks: each evaluates its networks (qt_plan_shard), then one
-    all-reduce of the partial energy per step."""
+    """One graph's energy split over the ranks: each contracts its share of the networks'
+    slices (qt_plan_shard, longest processing time first on their cost), then one all-reduce of
+    the partial energy per step (strong scaling: the job is one evaluation per step)."""
     import torch
     import torch.distributed as tdist
     from paper_2204_06045_gb300 import build, qtgb
@@ -741,44 +919,61 @@ def run_shard(args, rank, world, local_rank):
         dist.barrier()
     build.build()
     n, p, edges, g, b = workload_inputs()
+    peak, peak_kind = measured_peaks()
+    fma = qtgb.fma_peak("c64")
     with qtgb.plan_shard(n, edges, p, world, rank, dtype="c64") as pl:
+        st = pl.stats()
         gd = torch.tensor(g, dtype=torch.float64, device="cuda")
         bd = torch.tensor(b, dtype=torch.float64, device="cuda")
-        zz = torch.zeros(max(1, pl.shard_edges.size), dtype=torch.float64, device="cuda")
+        mine = pl.shard_edges
+        zz = torch.zeros(max(1, mine.size), dtype=torch.float64, device="cuda") if mine.size else None
         E = torch.zeros(1, dtype=torch.float64, device="cuda")
         s = torch.cuda.current_stream()
-
-        def step():
-            pl.energy(gd, bd, edge_zz=zz if pl.shard_edges.size else None, energy=E, stream=s)
-            if dist is not None:
-                dist.all_reduce(E, op=dist.ReduceOp.SUM)
-
         for _ in range(args.warmup):
-            step()
+            shard_step(pl, gd, bd, zz, E, s, dist)
         pl.sync(s)
+        pl.kernel_time(reset=True)
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(s)
-        for _ in range(args.steps):
-            step()
-        ev1.record(s)
-        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            ev0.record(s)
+            for _ in range(args.steps):
+                shard_step(pl, gd, bd, zz, E, s, dist)
+            ev1.record(s)
+            torch.cuda.synchronize()
         pl.sync(s)
         ms = max_over_ranks(ev0.elapsed_time(ev1), dist, torch)
+        kms, launches = pl.kernel_time(reset=True)
         energy = float(E.item())
-        nets = pl.shard_edges.size
+        # end to end: host angles in, this rank's host results out, the partial energy reduced
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, e_part = pl.energy(g, b)
+            et = torch.tensor([e_part], dtype=torch.float64, device="cuda")
+            if dist is not None:
+                dist.all_reduce(et, op=dist.ReduceOp.SUM)
+            float(et.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, torch)
     _, ref_E = golden_c2()
     if rank == 0:
+        achieved = st["alg_bytes"] / (kms * 1e-3) / 1e9 if kms > 0 else None
         line = {"metric": "QAOA energy evals/s (3-reg N=30 p=4)", "value": args.steps / (ms * 1e-3),
                 "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": args.steps / (ms * 1e-3) * PAPER_SECONDS_PER_EVAL, "dtype": "c64",
                 "data": "synthetic",
-                "config": config_dict("complex64; the graph's 45 networks split over the ranks by LPT on cost, "
+                "config": config_dict("complex64; the networks' slices split over the ranks by LPT on cost, "
                                       "one all-reduce of the partial energy per step"),
-                "gpu_launches": 3 * args.steps, "rank0_networks": int(nets),
+                "e2e": {"value": args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 2 * p * 8,
+                        "d2h_bytes_per_step": (int(mine.size) + 1) * 8},
+                "roofline": dict(roofline("c64", st, kms, launches, achieved, peak, peak_kind, fma, None),
+                                 note="rank 0's kernel and its share of the networks"),
+                "clocks": clk.summary(), "gpu_launches": 3 * args.steps, "rank0_networks": int(mine.size),
                 "check": {"energy": energy, "reference_energy": ref_E,
                           "rel_err_energy": abs(energy - ref_E) / abs(ref_E) if ref_E else None}}
         print(json.dumps(line), flush=True)
@@ -799,10 +994,10 @@ def main():
     elif args.workload == "c5":
         if rank == 0:
             run_c5(args, world, local_rank)
-    elif args.workload == "einsum":
+    elif args.workload == "tncontract":
         if rank == 0:
-            run_einsum(args, world, local_rank)
-    elif args.shard:
+            run_tncontract(args, world, local_rank)
+    elif world > 1 and not args.replicas:
         run_shard(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)

@@ -1,9 +1,13 @@
-"""The N>1 path of bench.py on CPU: world_size-2 gloo ranks (replicas).
+"""The N>1 paths of bench.py on CPU, with gloo ranks.
 
-Each rank evaluates its own copy of the workload (weak scaling, no data-path
-collective); the job's time is the slowest rank's, taken with an all-reduce
-MAX, and its rate counts every rank's units. Here the ranks time a host-only
-plan build of their own seeded graph, so the test needs no GPU.
+* Sharded (the default for N>1): one graph's networks, or their slices, split
+  over the ranks by longest processing time on their cost; each rank
+  contracts its share and one all-reduce of the partial energies completes E.
+  Here a rank contracts its share from the arrays the kernels read
+  (qt_plan_export_device, emulated on the CPU) or from the exported plan.
+* Replicas (--replicas): each rank evaluates its own copy of the workload
+  (weak scaling, no data-path collective); the job's time is the slowest
+  rank's, taken with an all-reduce MAX, and its rate counts every rank's units.
 """
 import os
 import socket
@@ -228,3 +232,72 @@ def test_deduplicated_shards_over_gloo_ranks_match_oracle():
     for r in range(world):
         np.testing.assert_allclose(res[r][0], want, atol=1e-12)
     assert sum(res[r][1] for r in range(world)) < sum(res[r][2] for r in range(world))
+
+
+class _CpuPlanStep:
+    """Stands in for a device plan in bench.shard_step: the rank's partial energy from the
+    device arrays of its host-only shard plan, emulated on the CPU."""
+
+    def __init__(self, pl, p):
+        self.pl, self.p = pl, p
+
+    def energy(self, gd, bd, edge_zz=None, energy=None, stream=None):
+        from device_eval import emulate
+        vals, en = emulate(self.pl, gd.numpy(), bd.numpy(), self.p)
+        if edge_zz is not None:
+            edge_zz[:] = torch.as_tensor(vals.real)
+        energy[0] = float(en[0])
+
+
+def _device_shard_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, str(ROOT))
+    sys.path.insert(0, str(ROOT / "tests"))
+    import bench
+    from paper_2204_06045_gb300 import qtgb, synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n, p = 16, 3
+        edges = synth.random_regular_graph(n, 40)
+        g, b = synth.angles(p, 40)
+        with qtgb.plan_shard(n, edges, p, world, rank, host_only=True, slice_width=7) as pl:
+            mine = pl.shard_edges
+            E = torch.zeros(1, dtype=torch.float64)
+            zz = torch.zeros(max(1, mine.size), dtype=torch.float64)
+            step = _CpuPlanStep(pl, p)
+            gd = torch.tensor(g, dtype=torch.float64)
+            bd = torch.tensor(b, dtype=torch.float64)
+            bench.shard_step(step, gd, bd, zz if mine.size else None, E, None, dist)
+            dense = torch.zeros(edges.shape[0], dtype=torch.float64)
+            if mine.size:
+                dense[torch.as_tensor(mine, dtype=torch.long)] = zz[:mine.size]
+            dist.all_reduce(dense, op=dist.ReduceOp.SUM)
+            slow = bench.max_over_ranks(0.001 * (rank + 1), dist, torch)
+        out[rank] = (float(E.item()), dense.tolist(), slow, mine.tolist())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_shard_step_over_gloo_ranks_matches_oracle():
+    """bench.shard_step on two gloo ranks, each rank's share contracted from the
+    device arrays of its sliced shard plan: after the step's all-reduce every
+    rank holds the oracle's energy, the ranks' per-edge values (sums over their
+    slices) add up to the oracle's, and the job's time is the slowest rank's."""
+    import oracle
+    from paper_2204_06045_gb300 import build, synth
+    build.build()
+    world = 2
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_device_shard_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    n, p = 16, 3
+    edges = synth.random_regular_graph(n, 40)
+    g, b = synth.angles(p, 40)
+    want_E = oracle.sv_energy(n, edges, g, b)
+    for r in range(world):
+        assert res[r][0] == pytest.approx(want_E, abs=1e-10)
+        np.testing.assert_allclose(res[r][1], oracle.sv_zz(n, edges, g, b), atol=1e-12)
+        assert res[r][2] == pytest.approx(0.002)
+    assert res[0][3] and res[1][3]  # both ranks hold networks
