@@ -96,10 +96,12 @@ typedef struct {
                               the device over `autotune` evaluations; the choice is in qt_plan_stats */
     int8_t tile_cap[8];    /* most tile bits (log2 outputs per tile, 1..11) per width class, 0: default
                               (chunk_log2, else 9); the first 5 entries are used */
-    int32_t no_merge;      /* nonzero: no merged eliminations. By default a bucket of 2^10 outputs or
-                              more and the consumer that only extends it become one bucket summing
-                              both variables, the intermediate never written (persistent-schedule
-                              plans, gradient plans included; the per-bucket schedule never merges) */
+    int32_t no_merge;      /* merged eliminations: a bucket of 2^10 outputs or more and the consumer
+                              that only extends it become one bucket summing both variables, the
+                              intermediate never written. 0 (default): energy plans of the persistent
+                              schedule merge, gradient plans do not (their reverse sweep ran slower);
+                              negative: gradient plans merge too; positive: no plan merges. The
+                              per-bucket schedule never merges */
     size_t adjoint_budget_bytes; /* gradient plans (single graph): device bytes for results and their
                               cotangents; a plan that needs more runs in passes that fit, over its
                               networks' slices (each pass saves its own results and seeds each slice

@@ -702,8 +702,10 @@ int make_plan(const std::vector<qt::GraphIn>& graphs, int32_t p, const qt_plan_o
     cfg.with_grad = o.with_grad != 0;
     cfg.fuse = o.sched == QT_SCHED_PERSISTENT && !cfg.with_grad && o.no_fuse == 0;
     // the per-bucket kernel sums one variable per bucket: merging is a
-    // persistent-schedule option (fused units take only unmerged subtrees)
-    cfg.merge = o.no_merge == 0 && o.sched == QT_SCHED_PERSISTENT;
+    // persistent-schedule option (fused units take only unmerged subtrees).
+    // Gradient plans merge only when asked (no_merge < 0): their reverse sweep
+    // ran slower on merged buckets (N=50 p=4: complex64 21.8 vs 20.0 ms)
+    cfg.merge = o.sched == QT_SCHED_PERSISTENT && (o.no_merge < 0 || (o.no_merge == 0 && !cfg.with_grad));
     if (o.slice_width < -1 || o.slice_width == 1 || o.slice_width > 31) return QT_EINVAL;
     if (o.max_slice_bits < 0 || o.max_slice_bits > 16) return QT_EINVAL;
     // default target widths: measured best on the N=30 p=4 and N=1000 p=5 networks

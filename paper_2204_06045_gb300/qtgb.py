@@ -214,7 +214,7 @@ class Plan:
     @staticmethod
     def _opts(dtype="c64", sched="persistent", restarts=0, seed=0, max_width=31, arena_bytes=0,
               with_grad=False, spin_limit=0, chunk_log2=0, host_only=False, run_tiles=0, trace=False,
-              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=True,
+              order="simulated", fuse=True, autotune=0, tile_cap=None, adjoint_budget_bytes=0, merge=None,
               slice_width=0, max_slice_bits=0, dedup=False, energy_budget_bytes=0):
         # slice_width: 0 the library's default target, -1 no slicing
         o = PlanOpts()
@@ -234,7 +234,9 @@ class Plan:
         o.no_fuse = 0 if fuse else 1
         o.autotune = int(autotune)
         o.adjoint_budget_bytes = int(adjoint_budget_bytes)
-        o.no_merge = 0 if merge else 1
+        # merge: None the library's default (energy plans merge, gradient plans do not),
+        # True every persistent plan, gradient plans included; False none
+        o.no_merge = 0 if merge is None else (-1 if merge else 1)
         o.slice_width = int(slice_width)
         o.max_slice_bits = int(max_slice_bits)
         o.dedup = 1 if dedup else 0

@@ -262,3 +262,49 @@ def test_gradient_under_a_memory_budget_matches_the_whole(dtype):
     np.testing.assert_allclose(zz2, zz, atol=tol)
     np.testing.assert_allclose(dg2, dg, atol=10 * tol)
     np.testing.assert_allclose(db2, db, atol=10 * tol)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_merged_gradient_plans_match_the_oracle(dtype):
+    """Gradient plans with merged eliminations (opt-in): the reverse sweep
+    through merged buckets against the N=50 p=4 sampled-edge central
+    differences and the N=20 p=4 parameter-shift golden."""
+    rows = _golden_rows("c5_n50_p4_fd.txt")
+    n, p = 50, 4
+    edges = synth.random_regular_graph(n, 1000)
+    with qtgb.plan_subset(n, edges, p, rows["edges"].astype(np.int32), dtype=dtype, with_grad=True,
+                          merge=True) as pl:
+        B, _ = pl.export()
+        E, dg, db = pl.energy_grad(rows["gamma"], rows["beta"])
+    assert (B["n_sum"] > 1).any()
+    ref = np.concatenate([rows["dE_dgamma"], rows["dE_dbeta"]])
+    tol = 1e-6 if dtype == "c128" else 1e-4 * np.abs(ref).max()
+    assert np.abs(np.concatenate([dg, db]) - ref).max() <= tol
+    g20 = _golden_grad()
+    edges20 = synth.random_regular_graph(20, 1020)
+    with grad_plan(20, edges20, 4, dtype=dtype, merge=True) as pl:
+        E, dg, db = pl.energy_grad(g20["gamma"], g20["beta"])
+    ref = np.concatenate([g20["dE_dgamma"], g20["dE_dbeta"]])
+    tol = 1e-8 if dtype == "c128" else 1e-4 * np.abs(ref).max()
+    assert np.abs(np.concatenate([dg, db]) - ref).max() <= tol
+
+
+def test_gradient_passes_split_a_network_by_slice():
+    """A budget below one network's whole arena but above each of its slices:
+    the network's slices land in several passes, each seeding its slices from
+    their own factors; energy and gradient equal the unbudgeted plan's."""
+    n, p = 30, 4
+    edges = synth.random_regular_graph(n, 1000)
+    g, b = synth.angles(p, 1000)
+    kw = dict(dtype="c128", with_grad=True, slice_width=16)
+    with qtgb.plan(n, edges, p, **kw) as pl:
+        E, dg, db = pl.energy_grad(g, b)
+        need = pl.stats()["arena_bytes"]
+    with qtgb.plan(n, edges, p, adjoint_budget_bytes=need // 40, **kw) as pl:
+        parts = [set(e.tolist()) for _, e in pl.passes()]
+        E2, dg2, db2 = pl.energy_grad(g, b)
+    split = [e for e in range(edges.shape[0]) if sum(e in s for s in parts) > 1]
+    assert len(parts) > 1 and split, "no network's slices were split over passes"
+    assert abs(E2[0] - E[0]) <= 1e-10 * abs(E[0])
+    np.testing.assert_allclose(dg2, dg, atol=1e-9)
+    np.testing.assert_allclose(db2, db, atol=1e-9)

@@ -473,8 +473,8 @@ def test_merged_eliminations_give_the_same_values(n, seed, p):
 
 def test_merge_applies_to_persistent_plans_only():
     """The per-bucket kernel sums one variable per bucket: its plans are never
-    merged. Persistent plans merge, gradient plans included (the reverse sweep
-    takes merged buckets)."""
+    merged. Persistent energy plans merge by default; gradient plans when asked
+    (the reverse sweep takes merged buckets)."""
     n, seed, p = 18, 5, 4
     edges = synth.random_regular_graph(n, seed)
     with host_plan(n, edges, p, merge=True, sched="per_bucket") as pl:
@@ -483,7 +483,10 @@ def test_merge_applies_to_persistent_plans_only():
         Bm, _ = pl.export()
     with host_plan(n, edges, p, merge=True, with_grad=True) as pl:
         Bg, _ = pl.export()
+    with host_plan(n, edges, p, with_grad=True) as pl:  # gradient plans merge only when asked
+        Bd, _ = pl.export()
     assert (B["n_sum"] == 1).all() and (Bm["n_sum"] > 1).any() and (Bg["n_sum"] > 1).any()
+    assert (Bd["n_sum"] == 1).all()
 
 
 @pytest.mark.parametrize("n,seed,p,width", [(12, 21, 2, 5), (14, 22, 3, 8), (16, 23, 3, 9), (18, 5, 4, 17)])
