@@ -1161,7 +1161,7 @@ int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, do
     const qt::DBucket& d = P->hp.buckets[bucket];
     std::vector<qt::DRun> groups;
     for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, 0});
+        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, d.n_ops});
     qt::DRun* d_groups = nullptr;
     QT_CUDA(cudaMalloc((void**)&d_groups, groups.size() * sizeof(qt::DRun)));
     cudaError_t e = cudaMemcpy(d_groups, groups.data(), groups.size() * sizeof(qt::DRun), cudaMemcpyHostToDevice);
@@ -1228,10 +1228,19 @@ int qt_debug_stall_bucket(qt_plan_t P, int64_t bucket) {
     if (!P || bucket < 0 || bucket >= (int64_t)P->hp.buckets.size()) return QT_EINVAL;
     if (P->host_only) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
-    // the bucket then never counts as complete, so its consumer is never queued
+    // the bucket then never counts as complete, so its consumer never starts:
+    // one tile more than will ever be written, both in the bucket's own count
+    // (the ready queue publishes on it) and in its consumer's operand (the
+    // static order's dependency check reads that)
     qt::DBucket d = P->hp.buckets[bucket];
-    d.n_tasks += 1;  // one tile more than will ever be written
+    d.n_tasks += 1;
     QT_CUDA(cudaMemcpy((void*)(P->dp.buckets + bucket), &d, sizeof(d), cudaMemcpyHostToDevice));
+    for (size_t i = 0; i < P->hp.operands.size(); ++i)
+        if (P->hp.op_src[i] == (int32_t)bucket) {
+            qt::DOperand o = P->hp.operands[i];
+            o.src_tiles += 1;
+            QT_CUDA(cudaMemcpy((void*)(P->dp.ops + i), &o, sizeof(o), cudaMemcpyHostToDevice));
+        }
     return QT_OK;
 }
 

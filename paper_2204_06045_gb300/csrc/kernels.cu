@@ -289,7 +289,8 @@ struct Cursor {
 };
 
 // The group at queue position q, if it may start (non-blocking): a position of
-// the static order once its bucket's producers have all finished, a position
+// the static order once its bucket's producers have all finished -- lane t
+// reads, with acquire, the tile counter of operand t's producer -- a position
 // of the ready queue once it has been published.
 __device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
     uint32_t ok = 1;
@@ -297,8 +298,12 @@ __device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* ou
     if (q < dp.n_static) {
         r = dp.runs[q];
         if (r.n_deps) {
-            if (lane == 0) ok = ld_acquire(&dp.prod_done[r.bucket]) >= r.n_deps;
-            ok = __shfl_sync(kFull, ok, 0);
+            if (lane < (int)r.n_ops) {
+                const DOperand& o = dp.ops[r.op_begin + lane];
+                const uint32_t src = o.src;
+                if (src != kNone) ok = ld_acquire(&dp.tiles_done[src]) >= o.src_tiles;
+            }
+            ok = __all_sync(kFull, ok != 0);
         }
     } else {
         if (lane == 0) {
@@ -347,9 +352,9 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             us.out_off = B.out_off;
             us.bucket = run.bucket;
             us.chunk_begin = 0;
-            us.n_chunks = 1;  // the whole unit is one "tile" of its root
+            us.n_chunks = B.n_tasks;  // the whole unit is one "tile" of its root, which counts as all of them
             us.parent = B.parent;
-            us.n_tasks = 1;
+            us.n_tasks = B.n_tasks;
             us.leaf_u = 0;
             us.leaf_hi = 0;
             us.total_foot = 0;
@@ -945,9 +950,11 @@ __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st
     __syncwarp();
 }
 
-// A group's tiles are all written. Count them; the warp that completes the
-// bucket counts one producer of the parent done, and the warp that completes
-// the parent's last producer publishes the parent's groups.
+// A group's tiles are all written. Count them. In the static order that is
+// all: a consumer reads its producers' tile counters itself. In the ready-queue
+// order the warp that completes the bucket counts one producer of the parent
+// done, and the warp that completes the parent's last producer publishes the
+// parent's groups.
 template <typename R>
 __device__ __forceinline__ void finish_group(const DevPlan& dp, const RunSlot<R>& rs, int lane) {
     fence_proxy_async_global();  // results become visible to later bulk copies
@@ -955,6 +962,15 @@ __device__ __forceinline__ void finish_group(const DevPlan& dp, const RunSlot<R>
     uint32_t push = 0;
     const uint32_t parent = rs.parent;
     if (dp.isolated) return;
+    if (dp.n_static == dp.n_groups) {
+        // static order: consumers read this counter themselves, so one release
+        // reduction, without waiting for its result, completes the group
+        if (lane == 0)
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&dp.tiles_done[rs.bucket]), "r"(rs.n_chunks)
+                         : "memory");
+        __syncwarp();
+        return;
+    }
     if (lane == 0) {
         // acquire-release adds: the group that completes the bucket has
         // acquired the other groups' results before it releases them (with its

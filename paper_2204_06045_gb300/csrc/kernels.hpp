@@ -18,7 +18,7 @@ struct DevPlan {
     uint32_t n_buckets;
     DSlot* slots;           // queue positions n_static.. n_groups-1, published at run time
     uint32_t* tiles_done;   // n_buckets: tiles written so far
-    uint32_t* prod_done;    // n_buckets: producers finished so far
+    uint32_t* prod_done;    // n_buckets: producers finished so far (ready-queue order)
     DControl* ctl;
     void* arena;            // complex64 or complex128 elements
     uint64_t spin_limit;

@@ -905,7 +905,7 @@ static void form_units(HostPlan* hp, int stage_elems) {
 
 static DRun unit_run(const HostPlan& hp, uint32_t root) {
     const DBucket& d = hp.buckets[root];
-    return DRun{root, 0, 1, d.op_begin, 0, d.unit_begin, d.unit_count, 0};  // one "tile": the whole unit
+    return DRun{root, 0, 1, d.op_begin, 0, d.unit_begin, d.unit_count, d.n_ops};  // one "tile": the whole unit
 }
 
 // Claim order by list scheduling on the host. Each of W simulated warps takes,
@@ -1007,7 +1007,7 @@ static void simulate_order(HostPlan* hp) {
             }
             const uint32_t c = r.next_tile;
             const uint32_t n = std::min(gsize[r.bucket], d.n_tasks - c);
-            hp->runs.push_back(DRun{r.bucket, c, n, d.op_begin, d.n_deps, 0, 0, 0});
+            hp->runs.push_back(DRun{r.bucket, c, n, d.op_begin, d.n_deps, 0, 0, d.n_ops});
             running.push(Ev{now + tile_s[r.bucket] * n + t_group, r.bucket});
             --free_workers;
             r.next_tile = c + n;
@@ -1456,7 +1456,7 @@ int layout_plan(HostPlan* hp) {
                 hp->runs.push_back(unit_run(*hp, b));
             } else if (d.n_deps == 0) {
                 for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-                    hp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, 0});
+                    hp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, d.n_ops});
             }
         }
     } else {
@@ -1759,7 +1759,7 @@ int build_contract_plan(const std::vector<std::vector<int>>& labels, const std::
         d.group_tiles = std::max<uint32_t>(1, std::min<uint32_t>(kRunTiles, (d.n_tasks + W - 1) / W));
         d.n_groups = (d.n_tasks + d.group_tiles - 1) / d.group_tiles;
         for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-            cp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, d.n_deps, 0, 0, 0});
+            cp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, d.n_deps, 0, 0, d.n_ops});
     }
     return QT_OK;
 }

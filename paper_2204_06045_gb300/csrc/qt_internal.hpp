@@ -128,10 +128,11 @@ struct DRun {
     uint32_t chunk_begin;
     uint32_t n_chunks;
     uint32_t op_begin;  // the bucket's first operand (saves a dependent load)
-    uint32_t n_deps;    // producers that must finish before the group may start
+    uint32_t n_deps;    // producers that must finish before the group may start (static order: each
+                        // operand's producer has counted all its tiles; ready queue: 0)
     uint32_t unit_begin;// fused unit: 1 + its first record in the unit programs (0: an ordinary group)
     uint32_t unit_count;// fused unit: its buckets (the root last)
-    uint32_t pad;
+    uint32_t n_ops;     // the bucket's operand count (the dependency check reads its producers from them)
 };
 static_assert(sizeof(DRun) == 32, "DRun layout");
 

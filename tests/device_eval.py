@@ -50,8 +50,9 @@ def emulate(pl, gammas, betas, p):
                 idx = int(op["off"]) + (2 * j + x if op["pairs_x"] else j)
                 prod = prod * arena[idx]
             acc += prod
-        if int(b["n_sum"]) == 2:  # outputs (o, s1), s1 as bit 0: add the pairs
-            acc = acc[0::2] + acc[1::2]
+        m = int(b["n_sum"]) - 1
+        if m:  # outputs (o, s2, s1), s1 as bit 0 and s2 as bit 1: add the groups of 2^m
+            acc = acc.reshape(-1, 1 << m).sum(axis=1)
         arena[int(b["out_off"]):int(b["out_off"]) + acc.size] = acc
     n_nets = nff.size - 1
     vals = np.zeros(n_nets, dtype=complex)
