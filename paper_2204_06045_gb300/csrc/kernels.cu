@@ -522,28 +522,50 @@ __device__ void publish_bucket(const DevPlan& dp, uint32_t p, int lane) {
 // ones of c-1 (their r operand bits below bit t = ctz(c) give back 2^r - 1)
 // and sets bit t (worth 2^r if the operand carries it).
 // Returns true if copies were issued (the stage's barrier will complete).
+// The group's copy parameters are read from its slot once, at its first
+// tile, into `is` (registers): the tiles of a group are issued in order, and
+// no other group's are issued between them.
+template <typename R>
+struct IssueState {
+    const typename CT<R>::c* src;  // this lane's staged operand
+    uint32_t dst;                  // its footprint's element offset in a stage
+    uint32_t mh;                   // its mask's bits above the tile
+    uint32_t plow;                 // its tile bits: the footprint is 2 << plow elements
+    uint32_t tx;                   // bytes of one tile's copies, every operand
+    bool on;                       // copies to issue (the plan's footprints fit, something is staged)
+    bool lane_on;                  // this lane copies an operand
+};
+
 template <typename R>
 __device__ __forceinline__ bool issue_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk,
-                                           bool first, int lane, uint32_t& cbase) {
+                                           bool first, int lane, uint32_t& cbase, IssueState<R>& is) {
     using C = typename CT<R>::c;
-    const RunSlot<R>& rs = ws.slot[sl];
-    if (rs.bad || rs.total_foot == 0) return false;
+    if (first) {
+        const RunSlot<R>& rs = ws.slot[sl];
+        is.on = !(rs.bad || rs.total_foot == 0);
+        is.tx = rs.total_foot * (uint32_t)sizeof(C);
+        is.lane_on = lane < rs.n_staged;
+        if (is.lane_on) {
+            const uint32_t m = rs.gmask[lane];
+            is.mh = m >> rs.cb;
+            is.plow = __popc(m & ((1u << rs.cb) - 1u));
+            is.src = static_cast<const C*>(dp.arena) + rs.goff[lane];
+            is.dst = rs.soff[lane];
+        }
+    }
+    if (!is.on) return false;
     // The stage's previous contents were read into registers and consumed
     // before the caller's __syncwarp, so the copies may overwrite it now.
-    if (lane == 0) mbar_expect_tx(&ws.bar[st], rs.total_foot * (uint32_t)sizeof(C));
+    if (lane == 0) mbar_expect_tx(&ws.bar[st], is.tx);
     __syncwarp();
-    if (lane < rs.n_staged) {
-        const uint32_t m = rs.gmask[lane];
-        const uint32_t low = (1u << rs.cb) - 1u;
-        const uint32_t mh = m >> rs.cb;
+    if (is.lane_on) {
         if (!first) {
             const uint32_t t = __ffs(chunk) - 1u;
-            const uint32_t r = __popc(mh & ((1u << t) - 1u));
-            cbase = cbase - ((1u << r) - 1u) + (((mh >> t) & 1u) << r);
+            const uint32_t r = __popc(is.mh & ((1u << t) - 1u));
+            cbase = cbase - ((1u << r) - 1u) + (((is.mh >> t) & 1u) << r);
         }
-        const uint32_t plow = __popc(m & low);
-        const C* src = static_cast<const C*>(dp.arena) + rs.goff[lane] + 2ull * ((uint64_t)cbase << plow);
-        bulk_g2s(&ws.stage[st][rs.soff[lane]], src, (2u << plow) * (uint32_t)sizeof(C), &ws.bar[st]);
+        bulk_g2s(&ws.stage[st][is.dst], is.src + 2ull * ((uint64_t)cbase << is.plow), (2u << is.plow) * (uint32_t)sizeof(C),
+                 &ws.bar[st]);
     }
     return true;
 }
@@ -937,7 +959,8 @@ __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st
         run_unit<R>(dp, ws, sl, st, lane);
         return;
     }
-    if (rs.n_leaves) gate_table<R>(ws, rs, chunk, first_of_run, tlow, hi_key, lane);
+    // the table changes within a group only if a folded tensor has a bit above the tile
+    if (rs.n_leaves && (first_of_run || rs.n_hi)) gate_table<R>(ws, rs, chunk, first_of_run, tlow, hi_key, lane);
     clk.lap(kTrGate);
     C* out = static_cast<C*>(dp.arena) + rs.out_off;
     switch (rs.n_fast) {
@@ -1061,6 +1084,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
         int sa = 0, st = 0;
         uint32_t cbase = 0, hi_key = 0;
         C tlow[2];
+        IssueState<R> iss{};
         DRun ra;
         bool ok = wait_group(dp, qa, &ra, lane);
         clk.lap(kTrDeps);
@@ -1071,7 +1095,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             clk.count(kTrRuns, 1);
             if (lane == 0) fence_proxy_async_global();  // producers' results before this warp's copies
             __syncwarp();
-            pending[st] = issue_tile<R>(dp, ws, sa, st, ra.chunk_begin, true, lane, cbase);
+            pending[st] = issue_tile<R>(dp, ws, sa, st, ra.chunk_begin, true, lane, cbase, iss);
             clk.lap(kTrIssue);
         }
         uint32_t a_chunk = ra.chunk_begin, a_left = ra.n_chunks;
@@ -1082,7 +1106,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             bool b_valid = true, b_first = false, b_issued = false, b_prepped = false;
             DRun rb;
             if (a_left > 1) {
-                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase);
+                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase, iss);
                 b_issued = true;
                 clk.lap(kTrIssue);
             } else {
@@ -1097,7 +1121,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                     clk.count(kTrRuns, 1);
                     if (lane == 0) fence_proxy_async_global();
                     __syncwarp();
-                    pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase);
+                    pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss);
                     b_issued = true;
                     b_chunk = rb.chunk_begin;
                     b_left = rb.n_chunks;
@@ -1138,7 +1162,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                 clk.count(kTrRuns, 1);
                 if (lane == 0) fence_proxy_async_global();
                 __syncwarp();
-                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase);
+                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss);
                 b_chunk = rb.chunk_begin;
                 b_left = rb.n_chunks;
                 b_first = true;
