@@ -80,7 +80,7 @@ typedef struct {
                               when a bucket's operand footprints do not fit the 8 KB stage */
     int32_t host_only;     /* nonzero: plan on the host only (statistics, export); no device
                               memory is touched and every evaluation call returns QT_ESTATE */
-    int32_t run_tiles;     /* most tiles of one bucket handed out per claim (default 0: 16) */
+    int32_t run_tiles;     /* most tiles of one bucket handed out per claim (default 0: 12) */
     int32_t trace;         /* nonzero: run the instrumented persistent kernel, which counts
                               per-warp cycles by phase (read with qt_trace_counters) */
     int32_t order;         /* claim order of the persistent kernel: 0 (default) the order of a

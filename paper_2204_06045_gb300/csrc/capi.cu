@@ -514,7 +514,7 @@ int autotune(qt_plan_t P, int reps) {
             }
         }
     }
-    for (int rt : {8, 32}) {
+    for (int rt : {8, 16, 32}) {
         qt::PlanConfig cfg = best;
         cfg.run_tiles = rt;
         double ms = 0;

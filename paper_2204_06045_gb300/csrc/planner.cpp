@@ -1432,13 +1432,7 @@ int layout_plan(HostPlan* hp) {
     hp->n_groups = 0;
     for (uint32_t b : hp->by_level) {
         DBucket& d = hp->buckets[b];
-#ifndef QT_GROUP_DIV
-#define QT_GROUP_DIV 0
-#endif
-        // QT_GROUP_DIV > 0: groups of n_tasks / QT_GROUP_DIV tiles, within [1, kRunTiles]
-        const uint32_t rt = cfg.run_tiles > 0 ? (uint32_t)cfg.run_tiles
-                            : QT_GROUP_DIV > 0 ? std::max<uint32_t>(1, std::min<uint32_t>(kRunTiles, d.n_tasks / QT_GROUP_DIV))
-                                               : (uint32_t)kRunTiles;
+        const uint32_t rt = cfg.run_tiles > 0 ? (uint32_t)cfg.run_tiles : (uint32_t)kRunTiles;
         d.group_tiles = std::min(rt, d.n_tasks);
         d.n_groups = (d.n_tasks + d.group_tiles - 1) / d.group_tiles;
         hp->n_tiles += d.n_tasks;

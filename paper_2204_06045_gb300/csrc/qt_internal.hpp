@@ -54,7 +54,7 @@ constexpr int8_t kFactorRoot = -2;  // a factor that is a root result (the other
 #define QT_FUSE_OUT_BITS 8
 #endif
 constexpr int kFuseOutBits = QT_FUSE_OUT_BITS;
-constexpr int kRunTiles = 16;        // tiles of one bucket handed out per claim (default)
+constexpr int kRunTiles = 12;        // tiles of one bucket handed out per claim (default)
 constexpr int kBwdTileBits = 8;      // outputs per reverse-sweep tile, log2
 constexpr int kBwdRedElems = 1024;   // per-warp shared-memory elements for in-tile cotangent sums
 constexpr uint32_t kZeroChunk = 1u << 16;  // elements per block of the cotangent zeroing kernel

@@ -149,7 +149,7 @@ def test_autotuned_plan_matches_state_vector(dtype):
         st = pl.stats()
         zz, E = pl.energy(g, b)
     assert st["tune_candidates"] > 1 and st["tune_seconds"] > 0
-    assert all(6 <= c <= 11 for c in st["tile_cap"]) and st["run_tiles"] in (8, 16, 32)
+    assert all(6 <= c <= 11 for c in st["tile_cap"]) and st["run_tiles"] in (8, 12, 16, 32)
     ref = oracle.sv_zz(n, edges, g, b)
     assert scaled_err(zz, ref) <= TOL[dtype]
     assert abs(E - oracle.energy_from_zz(ref)) <= TOL[dtype] * abs(E)
