@@ -396,7 +396,9 @@ int qt_kernel_time(qt_plan_t plan, double *avg_ms, int64_t *launches, int32_t re
 
 /*
  * Time the persistent kernel on the tiles of one bucket alone (no other bucket
- * runs, no consumer is notified): `reps` launches back to back after one
+ * runs, no consumer is notified). The tiles form work groups of at most the
+ * plan's group size, spread evenly over every warp of the grid in whole
+ * rounds (as a bucket that has the GPU to itself is scheduled). `reps` launches back to back after one
  * warm-up launch, on the plan's own stream, each preceded by a reset of the
  * kernel's 256-byte control word; CUDA events around the whole sequence, so
  * the host's launch latency overlaps the previous launch. *avg_ms receives the

@@ -1159,9 +1159,12 @@ int qt_bucket_time(qt_plan_t P, int64_t bucket, int32_t reps, double* avg_ms, do
     if (P->host_only || P->sched != QT_SCHED_PERSISTENT) return QT_ESTATE;
     QT_CUDA(cudaSetDevice(P->device));
     const qt::DBucket& d = P->hp.buckets[bucket];
+    // the bucket alone: its tiles spread evenly over every warp of the grid
+    const uint32_t gt =
+        qt::lone_group_tiles(d.n_tasks, (uint32_t)P->grid * (qt::kPersistentThreads / 32), d.group_tiles);
     std::vector<qt::DRun> groups;
-    for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
-        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, 0, 0, 0, d.n_ops});
+    for (uint32_t c = 0; c < d.n_tasks; c += gt)
+        groups.push_back(qt::DRun{(uint32_t)bucket, c, std::min(gt, d.n_tasks - c), d.op_begin, 0, 0, 0, d.n_ops});
     qt::DRun* d_groups = nullptr;
     QT_CUDA(cudaMalloc((void**)&d_groups, groups.size() * sizeof(qt::DRun)));
     cudaError_t e = cudaMemcpy(d_groups, groups.data(), groups.size() * sizeof(qt::DRun), cudaMemcpyHostToDevice);

@@ -181,6 +181,16 @@ constexpr int kPW = kPersistentThreads / 32;  // warps per block
 constexpr int kLeafTab = 2 << kLeafBits;       // entries of the folded gate table
 constexpr int kUnrollS = 2;                    // 64-output iterations in flight when reading shared memory
 constexpr int kFast = 4;                       // most operands of the unrolled tile loop
+constexpr int kPmBits = 7;                     // premultiplied operands: most tile bits of the footprint
+constexpr int kPmK = (1 << kPmBits) / 32;      // their footprint pairs per lane
+// Premultiplied operands in complex128 only, where the tile loop is bound by
+// FP64 throughput and a product saved per output is time saved (C2 7.0 ->
+// 5.7 ms); the complex64 loop is latency-bound, and the extra dependent
+// shared-memory round trip per tile cost more than it saved (+5%).
+template <typename R>
+struct UsePm {
+    static constexpr bool value = sizeof(R) == 8;
+};
 
 template <typename R>
 struct StageCfg;
@@ -223,6 +233,14 @@ struct RunSlot {
     uint8_t hi_ebit[kMaxFoldLeaves]; // bit of a gate-table entry's index holding the tensor's bit in the tile
     uint8_t lsh[kMaxFoldLeaves][2];  // folded tensors within the tile: the bits of a table entry's index
                                      // that give bits 0 and 1 of the tensor's entry (31: none); 255: above
+    // A staged operand whose tile bits include the gate table's and number
+    // fewer than the tile's: each tile multiplies its footprint by the table
+    // (pm_f pairs, written past every footprint, at pm_dst) and the tile loop
+    // reads that product instead of the operand and the table.
+    uint8_t pm;                      // the operand (255: none)
+    uint16_t pm_f;                   // its footprint pairs
+    uint16_t pm_dst;                 // element offset of the product in the stage
+    uint8_t pm_e[kPmK][32];          // gate-table pair of footprint pair lane + 32 k
     uint32_t unit_begin;             // a fused unit: 1 + its first entry in the unit list (0: none)
     uint32_t unit_count;
 };
@@ -364,6 +382,7 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
             us.n_leaves = 0;
             us.bad = 0;
             us.n_fast = 0;
+            us.pm = 255;
             us.n_hi = 0;
             us.merged = 0;
             us.unit_begin = run.unit_begin;
@@ -457,8 +476,33 @@ __device__ void prep_run(const DevPlan& dp, WarpSmem<R>& ws, int sl, const DRun&
         rs.lsh[lane][0] = (uint8_t)s0;
         rs.lsh[lane][1] = (uint8_t)s1;
     }
+    // the premultiplied operand: the smallest footprint that carries every
+    // tile bit of the gate table, if smaller than the tile and the stage has
+    // room for the product past the footprints
+    uint32_t pm = 255u, pmb = 32u;
+    if (UsePm<R>::value && fast && rs.n_leaves) {
+        for (int t = 0; t < rs.n_staged; ++t) {
+            const uint32_t m = rs.gmask[t] & low;
+            const uint32_t nb = __popc(m);
+            if ((rs.leaf_u & ~m) == 0u && nb < pmb) {
+                pm = (uint32_t)t;
+                pmb = nb;
+            }
+        }
+        if (pm != 255u &&
+            (pmb >= rs.cb || pmb > (uint32_t)kPmBits || rs.total_foot + (2u << pmb) > (uint32_t)StageCfg<R>::elems))
+            pm = 255u;
+    }
+    if (UsePm<R>::value && pm != 255u) {
+        const uint32_t cl = pext_u32(rs.leaf_u, rs.gmask[pm] & low);  // the table's bits in the footprint index
+#pragma unroll
+        for (int k = 0; k < kPmK; ++k) rs.pm_e[k][lane] = (uint8_t)pext_u32((uint32_t)lane + 32u * k, cl);
+    }
     if (lane == 0) {
-        rs.n_fast = fast ? (uint8_t)nf : (uint8_t)0;
+        rs.n_fast = fast ? (uint8_t)(nf - (pm != 255u ? 1 : 0)) : (uint8_t)0;
+        rs.pm = (uint8_t)pm;
+        rs.pm_f = (uint16_t)(pm != 255u ? 1u << pmb : 0u);
+        rs.pm_dst = (uint16_t)rs.total_foot;
         uint8_t nh = 0;
         for (int l = 0; l < rs.n_leaves; ++l)
             if (rs.lmask[l] & ~low) {
@@ -532,19 +576,22 @@ struct IssueState {
     uint32_t mh;                   // its mask's bits above the tile
     uint32_t plow;                 // its tile bits: the footprint is 2 << plow elements
     uint32_t tx;                   // bytes of one tile's copies, every operand
+    uint32_t n_issued;             // tiles of the group issued so far
     bool on;                       // copies to issue (the plan's footprints fit, something is staged)
     bool lane_on;                  // this lane copies an operand
 };
 
 template <typename R>
 __device__ __forceinline__ bool issue_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk,
-                                           bool first, int lane, uint32_t& cbase, IssueState<R>& is) {
+                                           bool first, int lane, uint32_t& cbase, IssueState<R>& is,
+                                           uint32_t& pm_dirty) {
     using C = typename CT<R>::c;
     if (first) {
         const RunSlot<R>& rs = ws.slot[sl];
         is.on = !(rs.bad || rs.total_foot == 0);
         is.tx = rs.total_foot * (uint32_t)sizeof(C);
         is.lane_on = lane < rs.n_staged;
+        is.n_issued = 0;
         if (is.lane_on) {
             const uint32_t m = rs.gmask[lane];
             is.mh = m >> rs.cb;
@@ -557,6 +604,15 @@ __device__ __forceinline__ bool issue_tile(const DevPlan& dp, WarpSmem<R>& ws, i
     // The stage's previous contents were read into registers and consumed
     // before the caller's __syncwarp, so the copies may overwrite it now.
     if (lane == 0) mbar_expect_tx(&ws.bar[st], is.tx);
+    if (UsePm<R>::value && is.n_issued < 2u && ((pm_dirty >> st) & 1u)) {
+        // the stage's last tile was another group's, which wrote a
+        // premultiplied footprint past its own footprints (generic stores),
+        // where this group's copies may land: order those stores first. A
+        // group's own products never overlap its copies.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        pm_dirty &= ~(1u << st);
+    }
+    ++is.n_issued;
     __syncwarp();
     if (is.lane_on) {
         if (!first) {
@@ -695,6 +751,9 @@ struct TileMath<float> {
         return make_float2(x2_lo(p.re) + x2_hi(p.re), x2_lo(p.im) + x2_hi(p.im));
     }
     static __device__ __forceinline__ P add(P a, P b) { return {x2_add(a.re, b.re), x2_add(a.im, b.im)}; }
+    static __device__ __forceinline__ void store(uint32_t a, P v) {
+        asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(v.re), "l"(v.im) : "memory");
+    }
 };
 template <>
 struct TileMath<double> {
@@ -708,6 +767,10 @@ struct TileMath<double> {
     static __device__ __forceinline__ P mul(P p, P a) { return {cmul(p.v0, a.v0), cmul(p.v1, a.v1)}; }
     static __device__ __forceinline__ double2 xsum(P p) { return cadd(p.v0, p.v1); }
     static __device__ __forceinline__ P add(P a, P b) { return {cadd(a.v0, b.v0), cadd(a.v1, b.v1)}; }
+    static __device__ __forceinline__ void store(uint32_t a, P v) {
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.v0.x), "d"(v.v1.x) : "memory");
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a + 16u), "d"(v.v0.y), "d"(v.v1.y) : "memory");
+    }
 };
 
 // Outputs o, o + 1 (o even) of a result: one planar pair, one store.
@@ -806,8 +869,9 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
     uint32_t sbase[N], smask[N];
 #pragma unroll
     for (int t = 0; t < N; ++t) {
-        const bool is_tab = t == rs.n_staged;
-        sbase[t] = tok + (is_tab ? smem_u32(ws.leaf_tab) : smem_u32(ws.stage[st] + rs.soff[t]));
+        const bool is_tab = t == rs.n_staged;  // never with a premultiplied operand: N = n_staged then
+        const uint32_t off = (UsePm<R>::value && t == rs.pm) ? rs.pm_dst : rs.soff[t];
+        sbase[t] = tok + (is_tab ? smem_u32(ws.leaf_tab) : smem_u32(ws.stage[st] + off));
         smask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
     C* tile_out = out + ((uint64_t)chunk << (rs.cb - rs.merged));
@@ -950,9 +1014,29 @@ __device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int
 }
 
 // Contract tile `chunk` of the group in slot sl from stage st.
+// The premultiplied operand's footprint in stage st times the gate table
+// (entry pairs over x on both sides), stored past the stage's footprints.
+template <typename R>
+__device__ __forceinline__ void premultiply(WarpSmem<R>& ws, const RunSlot<R>& rs, int st, int lane) {
+    using M = TileMath<R>;
+    constexpr uint32_t PB = 2 * sizeof(typename CT<R>::c);
+    const uint32_t tok = opaque_zero();  // after the stage wait and the gate table's barrier
+    const uint32_t src = tok + smem_u32(ws.stage[st] + rs.soff[rs.pm]);
+    const uint32_t tab = tok + smem_u32(ws.leaf_tab);
+    const uint32_t dst = smem_u32(ws.stage[st] + rs.pm_dst);
+    const uint32_t f = rs.pm_f;
+#pragma unroll
+    for (int k = 0; k < kPmK; ++k) {
+        const uint32_t j = (uint32_t)lane + 32u * (uint32_t)k;
+        if (j < f) M::store(dst + PB * j, M::mul(M::load(src + PB * j), M::load(tab + PB * rs.pm_e[k][lane])));
+    }
+    __syncwarp();
+}
+
 template <typename R, bool Units, typename Clock>
 __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, uint32_t chunk, bool first_of_run,
-                              typename CT<R>::c (&tlow)[2], uint32_t& hi_key, int lane, Clock& clk) {
+                              typename CT<R>::c (&tlow)[2], uint32_t& hi_key, uint32_t& pm_dirty, int lane,
+                              Clock& clk) {
     using C = typename CT<R>::c;
     const RunSlot<R>& rs = ws.slot[sl];
     if (Units && rs.unit_begin) {
@@ -961,6 +1045,10 @@ __device__ void contract_tile(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st
     }
     // the table changes within a group only if a folded tensor has a bit above the tile
     if (rs.n_leaves && (first_of_run || rs.n_hi)) gate_table<R>(ws, rs, chunk, first_of_run, tlow, hi_key, lane);
+    if (UsePm<R>::value && rs.pm != 255u) {
+        premultiply<R>(ws, rs, st, lane);
+        pm_dirty |= 1u << st;
+    }
     clk.lap(kTrGate);
     C* out = static_cast<C*>(dp.arena) + rs.out_off;
     switch (rs.n_fast) {
@@ -1085,6 +1173,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
         uint32_t cbase = 0, hi_key = 0;
         C tlow[2];
         IssueState<R> iss{};
+        uint32_t pm_dirty = 0;  // stages holding a premultiplied footprint (bit per stage)
         DRun ra;
         bool ok = wait_group(dp, qa, &ra, lane);
         clk.lap(kTrDeps);
@@ -1095,7 +1184,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             clk.count(kTrRuns, 1);
             if (lane == 0) fence_proxy_async_global();  // producers' results before this warp's copies
             __syncwarp();
-            pending[st] = issue_tile<R>(dp, ws, sa, st, ra.chunk_begin, true, lane, cbase, iss);
+            pending[st] = issue_tile<R>(dp, ws, sa, st, ra.chunk_begin, true, lane, cbase, iss, pm_dirty);
             clk.lap(kTrIssue);
         }
         uint32_t a_chunk = ra.chunk_begin, a_left = ra.n_chunks;
@@ -1106,7 +1195,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             bool b_valid = true, b_first = false, b_issued = false, b_prepped = false;
             DRun rb;
             if (a_left > 1) {
-                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase, iss);
+                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase, iss, pm_dirty);
                 b_issued = true;
                 clk.lap(kTrIssue);
             } else {
@@ -1121,7 +1210,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                     clk.count(kTrRuns, 1);
                     if (lane == 0) fence_proxy_async_global();
                     __syncwarp();
-                    pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss);
+                    pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss, pm_dirty);
                     b_issued = true;
                     b_chunk = rb.chunk_begin;
                     b_left = rb.n_chunks;
@@ -1138,7 +1227,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             }
             if (!wait_stage<R>(dp, ws, sa, st, phase, lane)) break;
             clk.lap(kTrWait);
-            contract_tile<R, Units>(dp, ws, sa, st, a_chunk, a_first, tlow, hi_key, lane, clk);
+            contract_tile<R, Units>(dp, ws, sa, st, a_chunk, a_first, tlow, hi_key, pm_dirty, lane, clk);
             clk.lap(kTrCompute);
             clk.count(kTrTiles, 1);
             pending[st] = false;
@@ -1162,7 +1251,7 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                 clk.count(kTrRuns, 1);
                 if (lane == 0) fence_proxy_async_global();
                 __syncwarp();
-                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss);
+                pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss, pm_dirty);
                 b_chunk = rb.chunk_begin;
                 b_left = rb.n_chunks;
                 b_first = true;

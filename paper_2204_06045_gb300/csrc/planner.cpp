@@ -1750,7 +1750,7 @@ int build_contract_plan(const std::vector<std::vector<int>>& labels, const std::
     const uint32_t W = (uint32_t)std::max(1, sim_workers);
     for (uint32_t b = 0; b < (uint32_t)cp->buckets.size(); ++b) {
         DBucket& d = cp->buckets[b];
-        d.group_tiles = std::max<uint32_t>(1, std::min<uint32_t>(kRunTiles, (d.n_tasks + W - 1) / W));
+        d.group_tiles = lone_group_tiles(d.n_tasks, W, kRunTiles);
         d.n_groups = (d.n_tasks + d.group_tiles - 1) / d.group_tiles;
         for (uint32_t c = 0; c < d.n_tasks; c += d.group_tiles)
             cp->runs.push_back(DRun{b, c, std::min(d.group_tiles, d.n_tasks - c), d.op_begin, d.n_deps, 0, 0, d.n_ops});

@@ -212,6 +212,16 @@ int build_host_plan(const std::vector<GraphIn>& graphs, const PlanConfig& cfg, H
 // plan whose networks are built, for the configuration in hp->cfg.
 int layout_plan(HostPlan* hp);
 
+// Tiles per work group for a bucket that has the grid's `warps` to itself:
+// the fewest whole rounds of `warps` groups of at most `cap` tiles, with the
+// tiles shared evenly, so that no warp is left a round that the others skip.
+inline uint32_t lone_group_tiles(uint32_t n_tasks, uint32_t warps, uint32_t cap) {
+    if (n_tasks == 0 || warps == 0 || cap == 0) return 1;
+    const uint64_t per_round = (uint64_t)warps * cap;
+    const uint64_t rounds = (n_tasks + per_round - 1) / per_round;
+    return (uint32_t)((n_tasks + rounds * warps - 1) / (rounds * warps));
+}
+
 int leaf_slots_per_graph(int p);
 int leaf_index(int kind, int layer);
 
