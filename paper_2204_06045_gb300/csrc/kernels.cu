@@ -306,22 +306,33 @@ struct Cursor {
     }
 };
 
+// A static-order group's dependency check: lane t holds operand t's producer
+// and the tile count it must reach (kNone: nothing to wait for).
+struct DepCheck {
+    uint32_t src = kNone, need = 0;
+    __device__ bool ready(const DevPlan& dp) const {
+        const bool ok = src == kNone || ld_acquire(&dp.tiles_done[src]) >= need;
+        return __all_sync(kFull, ok);
+    }
+};
+
 // The group at queue position q, if it may start (non-blocking): a position of
 // the static order once its bucket's producers have all finished -- lane t
-// reads, with acquire, the tile counter of operand t's producer -- a position
-// of the ready queue once it has been published.
-__device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
+// reads, with acquire, the tile counter of operand t's producer (kept in *dc
+// for later polls) -- a position of the ready queue once it has been published.
+__device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* out, int lane, DepCheck* dc) {
     uint32_t ok = 1;
     DRun r{};
+    *dc = DepCheck{};
     if (q < dp.n_static) {
         r = dp.runs[q];
         if (r.n_deps) {
             if (lane < (int)r.n_ops) {
                 const DOperand& o = dp.ops[r.op_begin + lane];
-                const uint32_t src = o.src;
-                if (src != kNone) ok = ld_acquire(&dp.tiles_done[src]) >= o.src_tiles;
+                dc->src = o.src;
+                dc->need = o.src_tiles;
             }
-            ok = __all_sync(kFull, ok != 0);
+            ok = dc->ready(dp);
         }
     } else {
         if (lane == 0) {
@@ -340,10 +351,13 @@ __device__ __forceinline__ bool group_at(const DevPlan& dp, uint32_t q, DRun* ou
     return ok != 0;
 }
 
-// Bounded wait until position q is published; records QT_ETIMEOUT on expiry.
-__device__ bool wait_group(const DevPlan& dp, uint32_t q, DRun* out, int lane) {
+// Bounded wait until position q may start; records QT_ETIMEOUT on expiry.
+// `checked`: group_at has already read position q into *out and dc, so a
+// static-order position polls only its producers' counters.
+__device__ bool wait_group(const DevPlan& dp, uint32_t q, DRun* out, int lane, DepCheck& dc, bool checked) {
     uint64_t polls = 0;
-    while (!group_at(dp, q, out, lane)) {
+    const bool counters_only = checked && q < dp.n_static;
+    while (counters_only ? !dc.ready(dp) : !group_at(dp, q, out, lane, &dc)) {
         const bool err = ld_volatile(&dp.ctl->error) != 0;
         if (__any_sync(kFull, err)) return false;
         if (++polls > dp.spin_limit) {
@@ -1175,7 +1189,8 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
         IssueState<R> iss{};
         uint32_t pm_dirty = 0;  // stages holding a premultiplied footprint (bit per stage)
         DRun ra;
-        bool ok = wait_group(dp, qa, &ra, lane);
+        DepCheck dca;
+        bool ok = wait_group(dp, qa, &ra, lane, dca, false);
         clk.lap(kTrDeps);
         if (ok) {
             prep_run<R, Units>(dp, ws, sa, ra, lane, &cbase);
@@ -1194,6 +1209,8 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             uint32_t b_chunk = a_chunk + 1, b_left = a_left - 1, qb = 0;
             bool b_valid = true, b_first = false, b_issued = false, b_prepped = false;
             DRun rb;
+            DepCheck dcb;
+            bool b_checked = false;  // group_at read position qb into rb and dcb
             if (a_left > 1) {
                 pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, b_chunk, false, lane, cbase, iss, pm_dirty);
                 b_issued = true;
@@ -1202,7 +1219,8 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
                 qb = cur.next(dp, lane);
                 b_valid = qb < dp.n_groups;
                 clk.lap(kTrClaim);
-                if (b_valid && group_at(dp, qb, &rb, lane)) {
+                b_checked = b_valid;
+                if (b_valid && group_at(dp, qb, &rb, lane, &dcb)) {
                     sb = sa ^ 1;
                     prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
                     mark_bucket<Trace>(dp, rb.bucket, false, lane);
@@ -1239,19 +1257,19 @@ __global__ void __launch_bounds__(kPersistentThreads, QT_PERSISTENT_MIN_BLOCKS) 
             if (!b_valid) break;
             if (!b_issued) {
                 // the next group was not yet published when looked at: wait for it now
-                if (!wait_group(dp, qb, &rb, lane)) break;
+                if (!wait_group(dp, qb, &rb, lane, dcb, b_checked)) break;
                 clk.lap(kTrDeps);
                 sb = sa ^ 1;
-                if (b_prepped)
-                    load_folded_results<R>(dp, ws, sb, rb, lane);
-                else
-                    prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
+                if (!b_prepped) prep_run<R, Units>(dp, ws, sb, rb, lane, &cbase);
                 mark_bucket<Trace>(dp, rb.bucket, false, lane);
                 clk.lap(kTrPrep);
                 clk.count(kTrRuns, 1);
                 if (lane == 0) fence_proxy_async_global();
                 __syncwarp();
                 pending[st ^ 1] = issue_tile<R>(dp, ws, sb, st ^ 1, rb.chunk_begin, true, lane, cbase, iss, pm_dirty);
+                // a group prepared before its producers finished reads the
+                // results folded into its gate table now, while its copies fly
+                if (b_prepped) load_folded_results<R>(dp, ws, sb, rb, lane);
                 b_chunk = rb.chunk_begin;
                 b_left = rb.n_chunks;
                 b_first = true;
