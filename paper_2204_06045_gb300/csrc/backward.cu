@@ -75,20 +75,10 @@ __global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta, uin
 // Pair (x = 0, x = 1) of an operand entry through the read-only path: every
 // value the reverse sweep reads was written by an earlier launch. Tensors are
 // stored in planar pairs (device_common.cuh).
-__device__ __forceinline__ Pair<float2> ldg_pair(const float2* p) {
-    return unpack_pair(__ldg(reinterpret_cast<const float4*>(p)));
-}
 __device__ __forceinline__ Pair<double2> ldg_pair(const double2* p) { return unpack_pair(__ldg(p), __ldg(p + 1)); }
-__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(p) = pack_pair(a, b);
-}
 __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
     p[0] = make_double2(a.x, b.x);
     p[1] = make_double2(a.y, b.y);
-}
-__device__ __forceinline__ void smem_add(float2* p, float2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
 }
 __device__ __forceinline__ void smem_add(double2* p, double2 v) {
     atomicAdd(&p->x, v.x);
@@ -278,6 +268,188 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
     }
 }
 
+// ---- complex64: the same task with packed arithmetic ------------------------
+// An operand's entry pair (x = 0, 1) is held as packed real and packed
+// imaginary parts (f32x2), as it is stored (planar pairs), so one packed
+// complex product serves both x; a value that does not depend on x (the
+// result's cotangent, the merged consumer's gate entries) is repeated in both
+// halves. The products of the other operands take 3n - 4 packed products per
+// output (prefix times suffix; none by the identity). In-tile sums go to the
+// warp's shared buffer with plain read-add-writes: after the shuffles, the
+// lanes left each own distinct entries (they differ in a bit the operand
+// carries), in every iteration. Gate sums are compensated per x and lane.
+struct PC {
+    f32x2 re, im;
+};
+__device__ __forceinline__ PC pc_mul(PC a, PC b) {
+    return {x2_fma(a.re, b.re, x2_neg(x2_mul(a.im, b.im))), x2_fma(a.re, b.im, x2_mul(a.im, b.re))};
+}
+__device__ __forceinline__ PC pc_splat(float2 v) { return {x2_pack(v.x, v.x), x2_pack(v.y, v.y)}; }
+__device__ __forceinline__ PC pc_ldg(const float2* p) {  // a planar pair, read-only path
+    PC r;
+    asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(r.re), "=l"(r.im) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void pc_stg(float2* p, PC v) {
+    asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(v.re), "l"(v.im) : "memory");
+}
+__device__ __forceinline__ void pc_sadd(float2* p, PC v) {  // shared memory, one writer per entry pair
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    f32x2 re, im;
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(re), "=l"(im) : "r"(a) : "memory");
+    re = x2_add(re, v.re);
+    im = x2_add(im, v.im);
+    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(re), "l"(im) : "memory");
+}
+__device__ __forceinline__ f32x2 shfl_xor_x2(f32x2 v, int m) { return __shfl_xor_sync(kFull, v, m); }
+
+template <int NMAX, bool Exact>
+__device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int lane, float2* red) {
+    constexpr int KB = kBwdTileBits - 5;  // iteration bits at most
+    float2* arena = static_cast<float2*>(db.arena);
+    const DBucket B = db.buckets[b];
+    const int n = Exact ? NMAX : (int)B.n_ops;
+    const int tb = min((int)B.n_out, kBwdTileBits);
+    const int kb = tb > 5 ? tb - 5 : 0;
+    const uint32_t low = (1u << tb) - 1u;
+    const uint32_t lmask = low & 31u;
+    const bool active = ((uint32_t)lane & ~lmask) == 0u;
+    const uint32_t obase = tile << tb;
+    const float2* rbar = arena + B.out_off + db.cot_delta;
+    const uint32_t rshift = bucket_n_sum(B.flags) - 1;  // a merged bucket's outputs (o, s1) share result o
+    // operand t: with x, opp = its pair base[t] (the tile's block, pair-aligned);
+    // without x (gates), opp = the tensor's first entry and nb = base[t]
+    const float2* opp[NMAX];
+    uint32_t nb[NMAX], mask[NMAX], lo[NMAX], step[NMAX][KB], roff[NMAX];
+    bool px[NMAX];
+    int mode[NMAX], prm[NMAX];
+    uint32_t red_elems = 0;
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) {
+        opp[t] = arena;
+        nb[t] = mask[t] = lo[t] = roff[t] = 0;
+        px[t] = true;
+        mode[t] = kBwdNone;
+        prm[t] = -1;
+#pragma unroll
+        for (int k = 0; k < KB; ++k) step[t][k] = 0;
+        if (t < n) {
+            const uint32_t i = B.op_begin + t;
+            const DOperand o = db.ops[i];
+            mask[t] = o.mask;
+            px[t] = (o.smask & 1u) != 0u;
+            mode[t] = db.op_bwd[i];
+            prm[t] = db.op_param[i];
+            roff[t] = db.op_roff[i];
+            const uint32_t base = pext_u32(obase, o.mask);
+            opp[t] = arena + o.off + (px[t] ? 2ull * base : 0ull);
+            nb[t] = px[t] ? 0u : base;
+            lo[t] = pext_u32((uint32_t)lane & lmask, o.mask & lmask);
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                const int bit = 5 + k;
+                step[t][k] = (k < kb && ((o.mask >> bit) & 1u)) ? (1u << __popc(o.mask & ((1u << bit) - 1u))) : 0u;
+            }
+            if (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)
+                red_elems = max(red_elems, roff[t] + (2u << __popc(o.mask & low)));
+        }
+    }
+    for (uint32_t e = lane; e < red_elems; e += 32) red[e] = float2{0.f, 0.f};
+    __syncwarp();
+    f32x2 acc[NMAX], comp[NMAX];  // compensated sums of Re(c dT), per x
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) acc[t] = comp[t] = 0ull;
+    const uint64_t dld = db.dleaf_delta, cot = db.cot_delta;
+    for (uint32_t k = 0; k < (1u << kb); ++k) {
+        const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
+        PC r = {0ull, 0ull};
+        if (active) r = pc_splat(elem_ldg(rbar, o >> rshift));
+        PC P[NMAX];
+        uint32_t li[NMAX];
+#pragma unroll
+        for (int t = 0; t < NMAX; ++t) {
+            uint32_t q = lo[t];
+#pragma unroll
+            for (int kk = 0; kk < KB; ++kk)
+                if ((k >> kk) & 1u) q += step[t][kk];
+            li[t] = q;
+            if (t < n) P[t] = px[t] ? pc_ldg(opp[t] + 2u * q) : pc_splat(elem_ldg(opp[t], nb[t] + q));
+        }
+        // suffix products suf[t] = prod_{u > t} P[u] (unset for the last operand)
+        PC suf[NMAX];
+#pragma unroll
+        for (int t = NMAX - 2; t >= 0; --t) {
+            if (t < n - 1) suf[t] = (t == n - 2) ? P[t + 1] : pc_mul(P[t + 1], suf[t + 1]);
+        }
+        PC pre = r;
+#pragma unroll
+        for (int t = 0; t < NMAX; ++t) {
+            if (t < n) {
+                const int md = mode[t];
+                if (md != kBwdNone) {
+                    const PC c = (t == n - 1) ? pre : pc_mul(pre, suf[t]);  // Rbar[o] prod_{u != t} P[u]
+                    if (md == kBwdGate) {
+                        const PC d = px[t] ? pc_ldg(opp[t] + dld + 2u * li[t])
+                                           : pc_splat(elem_ldg(opp[t] + dld, nb[t] + li[t]));
+                        const f32x2 v = x2_fma(c.re, d.re, x2_neg(x2_mul(c.im, d.im)));  // Re(c d), both x
+                        const f32x2 y = x2_add(v, x2_neg(comp[t]));
+                        const f32x2 s2 = x2_add(acc[t], y);
+                        comp[t] = x2_add(x2_add(s2, x2_neg(acc[t])), x2_neg(y));
+                        acc[t] = s2;
+                    } else if (md == kBwdDirect) {
+                        if (active) pc_stg(const_cast<float2*>(opp[t]) + cot + 2u * li[t], c);
+                    } else if (md == kBwdRedStore || md == kBwdRedAtomic) {
+                        PC v = c;
+                        const uint32_t miss = lmask & ~mask[t];
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) {
+                            if ((miss >> i) & 1u) {
+                                v.re = x2_add(v.re, shfl_xor_x2(v.re, 1 << i));
+                                v.im = x2_add(v.im, shfl_xor_x2(v.im, 1 << i));
+                            }
+                        }
+                        if (active && ((uint32_t)lane & miss) == 0u) pc_sadd(red + roff[t] + 2u * li[t], v);
+                    } else if (md == kBwdAtomic) {
+                        if (active) {
+                            float2* dst = const_cast<float2*>(opp[t]) + cot;
+                            elem_atomic_add(dst, 2ull * li[t], make_float2(x2_lo(c.re), x2_lo(c.im)));
+                            elem_atomic_add(dst, 2ull * li[t] + 1, make_float2(x2_hi(c.re), x2_hi(c.im)));
+                        }
+                    }
+                }
+                if (t < n - 1) pre = pc_mul(pre, P[t]);
+            }
+        }
+    }
+    __syncwarp();
+    // in-tile sums (planar pairs, as stored): the operand's entries for this
+    // tile are one contiguous block
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) {
+        if (t < n && (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)) {
+            const uint32_t fp = 2u << __popc(mask[t] & low);
+            float2* dst = const_cast<float2*>(opp[t]) + cot;
+            const float2* src = red + roff[t];
+            for (uint32_t e = lane; e < fp; e += 32) {
+                if (mode[t] == kBwdRedStore)
+                    elem_st(dst, e, elem_ld(src, e));
+                else
+                    elem_atomic_add(dst, e, elem_ld(src, e));
+            }
+        }
+    }
+    const uint32_t g = db.net_graph[B.net];
+#pragma unroll
+    for (int t = 0; t < NMAX; ++t) {
+        if (t < n && mode[t] == kBwdGate) {
+            double v = ((double)x2_lo(acc[t]) + (double)x2_hi(acc[t])) - ((double)x2_lo(comp[t]) + (double)x2_hi(comp[t]));
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+            if (lane == 0) atomicAdd(&db.grad[(size_t)g * 2 * db.p + prm[t]], v);
+        }
+    }
+}
+
 // One launch per level and operand-count class (buckets of at most NMAX
 // operands), so that each instantiation keeps its own register budget.
 template <typename R, int NMAX, bool Exact>
@@ -288,7 +460,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32, NMAX <= 4 ? 4 : 2) k_backward(
     const uint32_t w = blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= db.n_tasks) return;
-    bwd_tile<R, NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
+    if constexpr (sizeof(R) == 4)
+        bwd_tile_c64<NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
+    else
+        bwd_tile<R, NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
 }
 
 // Zero the cotangent pieces that receive atomic adds: (offset, count) pairs,

@@ -714,29 +714,6 @@ __device__ __forceinline__ uint32_t opaque_zero() {
     return z;
 }
 
-// Packed FP32 pairs (f32x2): two floats in one 64-bit register, operated on
-// by one instruction (sm_100 and later). A planar complex64 entry pair loads
-// as two of them: the real parts (x = 0, 1) and the imaginary parts.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_neg(f32x2 a) { return a ^ 0x8000000080000000ull; }  // both signs, exact
-__device__ __forceinline__ float x2_lo(f32x2 a) { return __uint_as_float((uint32_t)a); }
-__device__ __forceinline__ float x2_hi(f32x2 a) { return __uint_as_float((uint32_t)(a >> 32)); }
-
 // Arithmetic of the tile loop on one output's entry pair (x = 0, 1): load from
 // shared memory, multiply by another operand's pair, sum over x, and add two
 // outputs' pairs (a merged bucket's s1 = 0 and 1). complex64 keeps the pair as
