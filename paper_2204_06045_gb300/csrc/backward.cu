@@ -72,241 +72,112 @@ __global__ void k_seed_roots(DevEpilogue de, int n_nets, uint64_t cot_delta, uin
     }
 }
 
-// Pair (x = 0, x = 1) of an operand entry through the read-only path: every
-// value the reverse sweep reads was written by an earlier launch. Tensors are
-// stored in planar pairs (device_common.cuh).
-__device__ __forceinline__ Pair<double2> ldg_pair(const double2* p) { return unpack_pair(__ldg(p), __ldg(p + 1)); }
-__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
-    p[0] = make_double2(a.x, b.x);
-    p[1] = make_double2(a.y, b.y);
-}
-__device__ __forceinline__ void smem_add(double2* p, double2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-
 constexpr int kBwdWarps = 4;  // warps per block of the reverse sweep, one (bucket, tile) task each
 
 // One tile (2^tb outputs, tb = min(n_out, kBwdTileBits)) of one bucket's
 // reverse sweep, by one warp. Lane l takes outputs o = obase + l + 32 k. For
-// each output and x it forms c_s = Rbar[o] prod_{t != s} T_t[2 pext(o, M_t) + x]
-// (prefix and suffix products) and hands it to operand s by its mode. An
-// operand's pair index pext(o, M) is split, as in the forward tile loop, into
-// the tile's part (once per task), the lane's part and the steps of the
-// iteration bits, so no output pays for a bit-by-bit extract.
-template <typename R, int NMAX, bool Exact>
-__device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, typename CT<R>::c* red) {
-    using C = typename CT<R>::c;
-    constexpr int KB = kBwdTileBits - 5;  // iteration bits at most
-    C* arena = static_cast<C*>(db.arena);
-    const DBucket B = db.buckets[b];
-    const int n = Exact ? NMAX : (int)B.n_ops;  // Exact: every bucket of the launch has NMAX operands
-    const int tb = min((int)B.n_out, kBwdTileBits);
-    const int kb = tb > 5 ? tb - 5 : 0;
-    const uint32_t low = (1u << tb) - 1u;
-    const uint32_t lmask = low & 31u;
-    const bool active = ((uint32_t)lane & ~lmask) == 0u;
-    const uint32_t obase = tile << tb;
-    const C* rbar = arena + B.out_off + db.cot_delta;
-    // a merged bucket (s0, s1; s1 output bit 0 of its tiles) adds its outputs
-    // (o, s1 = 0, 1) into result o: both take the result's cotangent
-    const uint32_t rshift = bucket_n_sum(B.flags) - 1;
-    uint64_t off[NMAX];
-    uint32_t mask[NMAX], base[NMAX], lo[NMAX], step[NMAX][KB];
-    bool px[NMAX];  // pairs over x: entry 2 j + x (the merged consumer's gate tensors: entry j for both x)
-    int mode[NMAX], prm[NMAX];
-    uint32_t roff[NMAX];
-    uint32_t red_elems = 0;
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) {
-        off[t] = 0;
-        mask[t] = 0;
-        px[t] = true;
-        mode[t] = kBwdNone;
-        prm[t] = -1;
-        roff[t] = 0;
-        base[t] = lo[t] = 0;
-#pragma unroll
-        for (int k = 0; k < KB; ++k) step[t][k] = 0;
-        if (t < n) {
-            const uint32_t i = B.op_begin + t;
-            const DOperand o = db.ops[i];
-            off[t] = o.off;
-            mask[t] = o.mask;
-            px[t] = (o.smask & 1u) != 0u;
-            mode[t] = db.op_bwd[i];
-            prm[t] = db.op_param[i];
-            roff[t] = db.op_roff[i];
-            base[t] = pext_u32(obase, o.mask);
-            lo[t] = pext_u32((uint32_t)lane & lmask, o.mask & lmask);
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                const int bit = 5 + k;
-                step[t][k] = (k < kb && ((o.mask >> bit) & 1u)) ? (1u << __popc(o.mask & ((1u << bit) - 1u))) : 0u;
-            }
-            if (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)
-                red_elems = max(red_elems, roff[t] + (2u << __popc(o.mask & low)));
-        }
-    }
-    for (uint32_t e = lane; e < red_elems; e += 32) red[e] = C{};
-    __syncwarp();
-    R acc[NMAX], comp[NMAX];  // per-lane compensated (Kahan) sums of Re(c dT)
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) acc[t] = comp[t] = (R)0;
-    // every lane runs the loop (the in-tile sums shuffle across lanes); lanes
-    // beyond a tile of fewer than 32 outputs carry a zero cotangent and store nothing
-    for (uint32_t k = 0; k < (1u << kb); ++k) {
-        const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
-        C r = C{};
-        if (active) r = elem_ldg(rbar, o >> rshift);
-        Pair<C> P[NMAX];
-        uint32_t li[NMAX];  // pair index within the tile's block of the operand
-#pragma unroll
-        for (int t = 0; t < NMAX; ++t) {
-            uint32_t q = lo[t];
-#pragma unroll
-            for (int kk = 0; kk < KB; ++kk)
-                if ((k >> kk) & 1u) q += step[t][kk];
-            li[t] = q;
-            if (t < n) {
-                if (px[t]) {
-                    P[t] = ldg_pair(arena + off[t] + 2u * (base[t] + q));
-                } else {
-                    const C v = elem_ldg(arena + off[t], base[t] + q);
-                    P[t] = {v, v};
-                }
-            }
-        }
-        C cd[NMAX][2];  // contributions of this output to direct operands
-#pragma unroll
-        for (int x = 0; x < 2; ++x) {
-            C S[NMAX];  // suffix products S[t] = prod_{u > t} P[u]
-            C acc_s;
-            acc_s.x = (R)1;
-            acc_s.y = (R)0;
-#pragma unroll
-            for (int t = NMAX - 1; t >= 0; --t) {
-                if (t < n) {
-                    S[t] = acc_s;
-                    acc_s = cmul(acc_s, x ? P[t].v1 : P[t].v0);
-                }
-            }
-            C pre = r;
-#pragma unroll
-            for (int t = 0; t < NMAX; ++t) {
-                if (t < n && mode[t] != kBwdNone) {
-                    const C c = cmul(pre, S[t]);  // Rbar[o] * prod_{u != t} P[u]
-                    switch (mode[t]) {
-                        case kBwdGate: {
-                            const C d = px[t] ? elem_ldg(arena + off[t] + db.dleaf_delta + 2u * (base[t] + li[t]), x)
-                                              : elem_ldg(arena + off[t] + db.dleaf_delta, base[t] + li[t]);
-                            const R v = c.x * d.x - c.y * d.y;
-                            const R y = v - comp[t];
-                            const R s2 = acc[t] + y;
-                            comp[t] = (s2 - acc[t]) - y;
-                            acc[t] = s2;
-                            break;
-                        }
-                        case kBwdDirect:
-                            cd[t][x] = c;
-                            break;
-                        case kBwdRedStore:
-                        case kBwdRedAtomic: {
-                            // lanes that differ only in bits the operand lacks
-                            // add to the same entry: sum them by shuffles first
-                            C v = c;
-                            const uint32_t miss = lmask & ~mask[t];
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) {
-                                if ((miss >> i) & 1u) {
-                                    v.x += __shfl_xor_sync(kFull, v.x, 1 << i);
-                                    v.y += __shfl_xor_sync(kFull, v.y, 1 << i);
-                                }
-                            }
-                            if (active && ((uint32_t)lane & miss) == 0u) smem_add(red + roff[t] + 2u * li[t] + x, v);
-                            break;
-                        }
-                        case kBwdAtomic:
-                            if (active) elem_atomic_add(arena + off[t] + db.cot_delta + 2u * (base[t] + li[t]), x, c);
-                            break;
-                        default:
-                            break;
-                    }
-                }
-                if (t < n) pre = cmul(pre, x ? P[t].v1 : P[t].v0);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < NMAX; ++t)
-            if (active && t < n && mode[t] == kBwdDirect)
-                st_pair(arena + off[t] + db.cot_delta + 2u * o, cd[t][0], cd[t][1]);
-    }
-    __syncwarp();
-    // in-tile sums: the operand's entries for this tile are one contiguous block
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) {
-        if (t < n && (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)) {
-            const uint32_t fp = 2u << __popc(mask[t] & low);
-            C* dst = arena + off[t] + db.cot_delta + 2u * base[t];
-            for (uint32_t e = lane; e < fp; e += 32) {
-                if (mode[t] == kBwdRedStore)
-                    elem_st(dst, e, red[roff[t] + e]);
-                else
-                    elem_atomic_add(dst, e, red[roff[t] + e]);
-            }
-        }
-    }
-    const uint32_t g = db.net_graph[B.net];
-#pragma unroll
-    for (int t = 0; t < NMAX; ++t) {
-        if (t < n && mode[t] == kBwdGate) {
-            double v = (double)acc[t];
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-            if (lane == 0) atomicAdd(&db.grad[(size_t)g * 2 * db.p + prm[t]], v);
-        }
-    }
-}
-
-// ---- complex64: the same task with packed arithmetic ------------------------
-// An operand's entry pair (x = 0, 1) is held as packed real and packed
-// imaginary parts (f32x2), as it is stored (planar pairs), so one packed
-// complex product serves both x; a value that does not depend on x (the
-// result's cotangent, the merged consumer's gate entries) is repeated in both
-// halves. The products of the other operands take 3n - 4 packed products per
-// output (prefix times suffix; none by the identity). In-tile sums go to the
-// warp's shared buffer with plain read-add-writes: after the shuffles, the
-// lanes left each own distinct entries (they differ in a bit the operand
-// carries), in every iteration. Gate sums are compensated per x and lane.
+// each output it forms, for both x at once, c_s = Rbar[o] prod_{t != s}
+// T_t[2 pext(o, M_t) + x] and hands it to operand s by its mode. An operand's
+// pair index pext(o, M) is split, as in the forward tile loop, into the
+// tile's part (once per task), the lane's part and the steps of the iteration
+// bits, so no output pays for a bit-by-bit extract.
+//
+// An operand's entry pair (x = 0, 1) is one value of BwdMath<R>::P: complex64
+// holds it as packed real and packed imaginary parts (f32x2), as it is stored
+// (planar pairs), so one packed complex product serves both x; complex128
+// holds the two entries and multiplies each in FP64. A value that does not
+// depend on x (the result's cotangent, the merged consumer's gate entries) is
+// repeated for both x. The products of the other operands take 3n - 4 pair
+// products per output (prefix times suffix; none by the identity). In-tile
+// sums go to the warp's shared buffer with plain read-add-writes: after the
+// shuffles, the lanes left own distinct entries (they differ in a bit the
+// operand carries), in every iteration. Gate sums are compensated per x and
+// lane, then reduced in FP64.
 struct PC {
     f32x2 re, im;
 };
-__device__ __forceinline__ PC pc_mul(PC a, PC b) {
-    return {x2_fma(a.re, b.re, x2_neg(x2_mul(a.im, b.im))), x2_fma(a.re, b.im, x2_mul(a.im, b.re))};
-}
-__device__ __forceinline__ PC pc_splat(float2 v) { return {x2_pack(v.x, v.x), x2_pack(v.y, v.y)}; }
-__device__ __forceinline__ PC pc_ldg(const float2* p) {  // a planar pair, read-only path
-    PC r;
-    asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(r.re), "=l"(r.im) : "l"(p));
-    return r;
-}
-__device__ __forceinline__ void pc_stg(float2* p, PC v) {
-    asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(v.re), "l"(v.im) : "memory");
-}
-__device__ __forceinline__ void pc_sadd(float2* p, PC v) {  // shared memory, one writer per entry pair
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    f32x2 re, im;
-    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(re), "=l"(im) : "r"(a) : "memory");
-    re = x2_add(re, v.re);
-    im = x2_add(im, v.im);
-    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(re), "l"(im) : "memory");
-}
-__device__ __forceinline__ f32x2 shfl_xor_x2(f32x2 v, int m) { return __shfl_xor_sync(kFull, v, m); }
+template <typename R>
+struct BwdMath;
+template <>
+struct BwdMath<float> {
+    using P = PC;
+    using RP = f32x2;  // a real value per x
+    static __device__ __forceinline__ P mul(P a, P b) {
+        return {x2_fma(a.re, b.re, x2_neg(x2_mul(a.im, b.im))), x2_fma(a.re, b.im, x2_mul(a.im, b.re))};
+    }
+    static __device__ __forceinline__ P splat(float2 v) { return {x2_pack(v.x, v.x), x2_pack(v.y, v.y)}; }
+    static __device__ __forceinline__ P ldg(const float2* p) {  // read-only path
+        P r;
+        asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(r.re), "=l"(r.im) : "l"(p));
+        return r;
+    }
+    static __device__ __forceinline__ void stg(float2* p, P v) {
+        asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(v.re), "l"(v.im) : "memory");
+    }
+    static __device__ __forceinline__ void sadd(float2* p, P v) {  // shared memory
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+        f32x2 re, im;
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(re), "=l"(im) : "r"(a) : "memory");
+        re = x2_add(re, v.re);
+        im = x2_add(im, v.im);
+        asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(re), "l"(im) : "memory");
+    }
+    static __device__ __forceinline__ P shfl_add(P v, int m) {
+        return {x2_add(v.re, __shfl_xor_sync(kFull, v.re, m)), x2_add(v.im, __shfl_xor_sync(kFull, v.im, m))};
+    }
+    static __device__ __forceinline__ RP re_prod(P c, P d) { return x2_fma(c.re, d.re, x2_neg(x2_mul(c.im, d.im))); }
+    static __device__ __forceinline__ RP add(RP a, RP b) { return x2_add(a, b); }
+    static __device__ __forceinline__ RP sub(RP a, RP b) { return x2_add(a, x2_neg(b)); }
+    static __device__ __forceinline__ double sum(RP a) { return (double)x2_lo(a) + (double)x2_hi(a); }
+    static __device__ __forceinline__ float2 at(P v, int x) {
+        return x ? make_float2(x2_hi(v.re), x2_hi(v.im)) : make_float2(x2_lo(v.re), x2_lo(v.im));
+    }
+    static __device__ __forceinline__ P zero() { return {0ull, 0ull}; }
+    static __device__ __forceinline__ RP rzero() { return 0ull; }
+};
+template <>
+struct BwdMath<double> {
+    using P = Pair<double2>;
+    using RP = double2;
+    static __device__ __forceinline__ P mul(P a, P b) { return {cmul(a.v0, b.v0), cmul(a.v1, b.v1)}; }
+    static __device__ __forceinline__ P splat(double2 v) { return {v, v}; }
+    static __device__ __forceinline__ P ldg(const double2* p) { return unpack_pair(__ldg(p), __ldg(p + 1)); }
+    static __device__ __forceinline__ void stg(double2* p, P v) {
+        p[0] = make_double2(v.v0.x, v.v1.x);
+        p[1] = make_double2(v.v0.y, v.v1.y);
+    }
+    static __device__ __forceinline__ void sadd(double2* p, P v) {  // shared memory
+        double2 re = p[0], im = p[1];
+        re.x += v.v0.x;
+        re.y += v.v1.x;
+        im.x += v.v0.y;
+        im.y += v.v1.y;
+        p[0] = re;
+        p[1] = im;
+    }
+    static __device__ __forceinline__ double2 shfl2(double2 v, int m) {
+        return make_double2(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m));
+    }
+    static __device__ __forceinline__ P shfl_add(P v, int m) { return {cadd(v.v0, shfl2(v.v0, m)), cadd(v.v1, shfl2(v.v1, m))}; }
+    static __device__ __forceinline__ RP re_prod(P c, P d) {
+        return make_double2(c.v0.x * d.v0.x - c.v0.y * d.v0.y, c.v1.x * d.v1.x - c.v1.y * d.v1.y);
+    }
+    static __device__ __forceinline__ RP add(RP a, RP b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ RP sub(RP a, RP b) { return make_double2(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ double sum(RP a) { return a.x + a.y; }
+    static __device__ __forceinline__ double2 at(P v, int x) { return x ? v.v1 : v.v0; }
+    static __device__ __forceinline__ P zero() { return {double2{0.0, 0.0}, double2{0.0, 0.0}}; }
+    static __device__ __forceinline__ RP rzero() { return double2{0.0, 0.0}; }
+};
 
-template <int NMAX, bool Exact>
-__device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int lane, float2* red) {
+template <typename R, int NMAX, bool Exact>
+__device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, typename CT<R>::c* red) {
+    using C = typename CT<R>::c;
+    using M = BwdMath<R>;
+    using P = typename M::P;
+    using RP = typename M::RP;
     constexpr int KB = kBwdTileBits - 5;  // iteration bits at most
-    float2* arena = static_cast<float2*>(db.arena);
+    C* arena = static_cast<C*>(db.arena);
     const DBucket B = db.buckets[b];
     const int n = Exact ? NMAX : (int)B.n_ops;
     const int tb = min((int)B.n_out, kBwdTileBits);
@@ -315,11 +186,11 @@ __device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int la
     const uint32_t lmask = low & 31u;
     const bool active = ((uint32_t)lane & ~lmask) == 0u;
     const uint32_t obase = tile << tb;
-    const float2* rbar = arena + B.out_off + db.cot_delta;
+    const C* rbar = arena + B.out_off + db.cot_delta;
     const uint32_t rshift = bucket_n_sum(B.flags) - 1;  // a merged bucket's outputs (o, s1) share result o
     // operand t: with x, opp = its pair base[t] (the tile's block, pair-aligned);
     // without x (gates), opp = the tensor's first entry and nb = base[t]
-    const float2* opp[NMAX];
+    C* opp[NMAX];
     uint32_t nb[NMAX], mask[NMAX], lo[NMAX], step[NMAX][KB], roff[NMAX];
     bool px[NMAX];
     int mode[NMAX], prm[NMAX];
@@ -354,17 +225,17 @@ __device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int la
                 red_elems = max(red_elems, roff[t] + (2u << __popc(o.mask & low)));
         }
     }
-    for (uint32_t e = lane; e < red_elems; e += 32) red[e] = float2{0.f, 0.f};
+    for (uint32_t e = lane; e < red_elems; e += 32) red[e] = C{};
     __syncwarp();
-    f32x2 acc[NMAX], comp[NMAX];  // compensated sums of Re(c dT), per x
+    RP acc[NMAX], comp[NMAX];  // compensated sums of Re(c dT), per x
 #pragma unroll
-    for (int t = 0; t < NMAX; ++t) acc[t] = comp[t] = 0ull;
+    for (int t = 0; t < NMAX; ++t) acc[t] = comp[t] = M::rzero();
     const uint64_t dld = db.dleaf_delta, cot = db.cot_delta;
     for (uint32_t k = 0; k < (1u << kb); ++k) {
         const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
-        PC r = {0ull, 0ull};
-        if (active) r = pc_splat(elem_ldg(rbar, o >> rshift));
-        PC P[NMAX];
+        P r = M::zero();
+        if (active) r = M::splat(elem_ldg(rbar, o >> rshift));
+        P v[NMAX];
         uint32_t li[NMAX];
 #pragma unroll
         for (int t = 0; t < NMAX; ++t) {
@@ -373,51 +244,46 @@ __device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int la
             for (int kk = 0; kk < KB; ++kk)
                 if ((k >> kk) & 1u) q += step[t][kk];
             li[t] = q;
-            if (t < n) P[t] = px[t] ? pc_ldg(opp[t] + 2u * q) : pc_splat(elem_ldg(opp[t], nb[t] + q));
+            if (t < n) v[t] = px[t] ? M::ldg(opp[t] + 2u * q) : M::splat(elem_ldg(opp[t], nb[t] + q));
         }
-        // suffix products suf[t] = prod_{u > t} P[u] (unset for the last operand)
-        PC suf[NMAX];
+        // suffix products suf[t] = prod_{u > t} v[u] (none for the last operand)
+        P suf[NMAX];
 #pragma unroll
         for (int t = NMAX - 2; t >= 0; --t) {
-            if (t < n - 1) suf[t] = (t == n - 2) ? P[t + 1] : pc_mul(P[t + 1], suf[t + 1]);
+            if (t < n - 1) suf[t] = (t == n - 2) ? v[t + 1] : M::mul(v[t + 1], suf[t + 1]);
         }
-        PC pre = r;
+        P pre = r;
 #pragma unroll
         for (int t = 0; t < NMAX; ++t) {
             if (t < n) {
                 const int md = mode[t];
                 if (md != kBwdNone) {
-                    const PC c = (t == n - 1) ? pre : pc_mul(pre, suf[t]);  // Rbar[o] prod_{u != t} P[u]
+                    const P c = (t == n - 1) ? pre : M::mul(pre, suf[t]);  // Rbar[o] prod_{u != t} v[u]
                     if (md == kBwdGate) {
-                        const PC d = px[t] ? pc_ldg(opp[t] + dld + 2u * li[t])
-                                           : pc_splat(elem_ldg(opp[t] + dld, nb[t] + li[t]));
-                        const f32x2 v = x2_fma(c.re, d.re, x2_neg(x2_mul(c.im, d.im)));  // Re(c d), both x
-                        const f32x2 y = x2_add(v, x2_neg(comp[t]));
-                        const f32x2 s2 = x2_add(acc[t], y);
-                        comp[t] = x2_add(x2_add(s2, x2_neg(acc[t])), x2_neg(y));
+                        const P d = px[t] ? M::ldg(opp[t] + dld + 2u * li[t]) : M::splat(elem_ldg(opp[t] + dld, nb[t] + li[t]));
+                        const RP y = M::sub(M::re_prod(c, d), comp[t]);
+                        const RP s2 = M::add(acc[t], y);
+                        comp[t] = M::sub(M::sub(s2, acc[t]), y);
                         acc[t] = s2;
                     } else if (md == kBwdDirect) {
-                        if (active) pc_stg(const_cast<float2*>(opp[t]) + cot + 2u * li[t], c);
+                        if (active) M::stg(opp[t] + cot + 2u * li[t], c);
                     } else if (md == kBwdRedStore || md == kBwdRedAtomic) {
-                        PC v = c;
+                        // lanes that differ only in bits the operand lacks
+                        // add to the same entry: sum them by shuffles first
+                        P w = c;
                         const uint32_t miss = lmask & ~mask[t];
 #pragma unroll
-                        for (int i = 0; i < 5; ++i) {
-                            if ((miss >> i) & 1u) {
-                                v.re = x2_add(v.re, shfl_xor_x2(v.re, 1 << i));
-                                v.im = x2_add(v.im, shfl_xor_x2(v.im, 1 << i));
-                            }
-                        }
-                        if (active && ((uint32_t)lane & miss) == 0u) pc_sadd(red + roff[t] + 2u * li[t], v);
+                        for (int i = 0; i < 5; ++i)
+                            if ((miss >> i) & 1u) w = M::shfl_add(w, 1 << i);
+                        if (active && ((uint32_t)lane & miss) == 0u) M::sadd(red + roff[t] + 2u * li[t], w);
                     } else if (md == kBwdAtomic) {
                         if (active) {
-                            float2* dst = const_cast<float2*>(opp[t]) + cot;
-                            elem_atomic_add(dst, 2ull * li[t], make_float2(x2_lo(c.re), x2_lo(c.im)));
-                            elem_atomic_add(dst, 2ull * li[t] + 1, make_float2(x2_hi(c.re), x2_hi(c.im)));
+                            elem_atomic_add(opp[t] + cot, 2ull * li[t], M::at(c, 0));
+                            elem_atomic_add(opp[t] + cot, 2ull * li[t] + 1, M::at(c, 1));
                         }
                     }
                 }
-                if (t < n - 1) pre = pc_mul(pre, P[t]);
+                if (t < n - 1) pre = M::mul(pre, v[t]);
             }
         }
     }
@@ -428,8 +294,8 @@ __device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int la
     for (int t = 0; t < NMAX; ++t) {
         if (t < n && (mode[t] == kBwdRedStore || mode[t] == kBwdRedAtomic)) {
             const uint32_t fp = 2u << __popc(mask[t] & low);
-            float2* dst = const_cast<float2*>(opp[t]) + cot;
-            const float2* src = red + roff[t];
+            C* dst = opp[t] + cot;
+            const C* src = red + roff[t];
             for (uint32_t e = lane; e < fp; e += 32) {
                 if (mode[t] == kBwdRedStore)
                     elem_st(dst, e, elem_ld(src, e));
@@ -442,28 +308,27 @@ __device__ void bwd_tile_c64(const DevBwd& db, uint32_t b, uint32_t tile, int la
 #pragma unroll
     for (int t = 0; t < NMAX; ++t) {
         if (t < n && mode[t] == kBwdGate) {
-            double v = ((double)x2_lo(acc[t]) + (double)x2_hi(acc[t])) - ((double)x2_lo(comp[t]) + (double)x2_hi(comp[t]));
+            double s2 = M::sum(acc[t]) - M::sum(comp[t]);
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-            if (lane == 0) atomicAdd(&db.grad[(size_t)g * 2 * db.p + prm[t]], v);
+            for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(kFull, s2, d);
+            if (lane == 0) atomicAdd(&db.grad[(size_t)g * 2 * db.p + prm[t]], s2);
         }
     }
 }
 
 // One launch per level and operand-count class (buckets of at most NMAX
 // operands), so that each instantiation keeps its own register budget.
+// Blocks per SM at least: complex64 4 (3 for more than four operands: 2),
+// complex128 3 (its 64 KB of shared memory per block allow no more), 2.
 template <typename R, int NMAX, bool Exact>
-__global__ void __launch_bounds__(kBwdWarps * 32, NMAX <= 4 ? 4 : 2) k_backward(DevBwd db) {
+__global__ void __launch_bounds__(kBwdWarps * 32, NMAX <= 4 ? (sizeof(R) == 4 ? 4 : 3) : 2) k_backward(DevBwd db) {
     using C = typename CT<R>::c;
     extern __shared__ __align__(16) unsigned char bwd_smem[];
     C* red = reinterpret_cast<C*>(bwd_smem) + (threadIdx.x >> 5) * kBwdRedElems;
     const uint32_t w = blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= db.n_tasks) return;
-    if constexpr (sizeof(R) == 4)
-        bwd_tile_c64<NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
-    else
-        bwd_tile<R, NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
+    bwd_tile<R, NMAX, Exact>(db, db.task_bucket[w], db.task_tile[w], lane, red);
 }
 
 // Zero the cotangent pieces that receive atomic adds: (offset, count) pairs,
