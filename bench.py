@@ -63,6 +63,8 @@ def parse():
                     help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5, the "
                          "batch, gradient and random-contraction legs); c3: 64-graph batch; c5: gradients on "
                          "N=50 p=4; tncontract: the paper's random contraction expressions against torch.einsum")
+    ap.add_argument("--c5-n", type=int, default=50,
+                    help="--workload c5: vertices of the random 3-regular graph (50; smaller for profiler captures)")
     ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the plan-time autotuner's line")
     ap.add_argument("--no-alt", action="store_true", help="skip the alternative plan (the plain greedy order)")
@@ -861,12 +863,12 @@ def run_c3(args, world, local_rank):
 
 
 def run_c5(args, world, local_rank):
-    """dE/dgamma_k, dE/dbeta_k on the seeded random 3-regular N=50 (seed 1000), p=4."""
+    """dE/dgamma_k, dE/dbeta_k on the seeded random 3-regular N=50 (seed 1000; --c5-n), p=4."""
     import torch
     from paper_2204_06045_gb300 import build, qtgb, synth
     torch.cuda.set_device(local_rank)
     build.build()
-    n, p = 50, 4
+    n, p = args.c5_n, 4
     edges = synth.random_regular_graph(n, 1000)
     g, b = synth.angles(p, 1000)
     res = {}
@@ -881,11 +883,11 @@ def run_c5(args, world, local_rank):
             dt = (time.perf_counter() - t0) / steps
             res[dtype] = {"ms_per_step": dt * 1e3, "grad_evals_per_s": 1 / dt, "steps": steps,
                           "dE_dgamma": dg.tolist(), "dE_dbeta": db.tolist(), "energy": float(E[0])}
-    line = {"metric": "QAOA energy+gradient evals/s (3-reg N=50 p=4)", "value": res["c64"]["grad_evals_per_s"],
+    line = {"metric": f"QAOA energy+gradient evals/s (3-reg N={n} p=4)", "value": res["c64"]["grad_evals_per_s"],
             "unit": "grad-evals/s", "n_gpus": world, "steps": res["c64"]["steps"], "warmup": args.warmup,
             "ms_per_step": res["c64"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "random 3-regular N=50 seed 1000, p=4: energy and its 2p angle derivatives by "
+            "config": {"workload": f"random 3-regular N={n} seed 1000, p=4: energy and its 2p angle derivatives by "
                                    "the adjoint of the bucket elimination (host arrays in and out)"},
             "c128": res["c128"],
             "c64_vs_c128_max_abs_diff": float(np.max(np.abs(np.array(res["c64"]["dE_dgamma"] + res["c64"]["dE_dbeta"])
