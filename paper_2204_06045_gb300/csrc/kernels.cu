@@ -866,7 +866,9 @@ __device__ __forceinline__ void run_tile_n(const WarpSmem<R>& ws, int sl, int st
         smask[t] = is_tab ? rs.leaf_u : (rs.gmask[t] & low);
     }
     C* tile_out = out + ((uint64_t)chunk << (rs.cb - rs.merged));
-    if (rs.cb == 6)
+    // complex128, bound by FP64 throughput, gains nothing from two iterations
+    // in flight and loses to their registers (5.66 vs 5.79 ms on C2)
+    if (rs.cb == 6 || sizeof(R) == 8)
         tile_loop<R, N, 1, Exact>(sbase, smask, rs, tile_out, lane, n);
     else
         tile_loop<R, N, 2, Exact>(sbase, smask, rs, tile_out, lane, n);
