@@ -364,16 +364,31 @@ cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint
     return cudaGetLastError();
 }
 
+template <typename R>
+constexpr size_t bwd_smem() {
+    return (size_t)kBwdWarps * kBwdRedElems * sizeof(typename CT<R>::c);
+}
+
+template <typename R, int NMAX, bool Exact>
+static cudaError_t bwd_attr() {
+    if (bwd_smem<R>() <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_backward<R, NMAX, Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bwd_smem<R>());
+}
+
+template <typename R>
+static cudaError_t prepare_bwd() {
+    const cudaError_t es[] = {bwd_attr<R, 1, true>(), bwd_attr<R, 2, true>(), bwd_attr<R, 3, true>(),
+                              bwd_attr<R, 4, true>(), bwd_attr<R, 8, false>(), bwd_attr<R, kMaxOps, false>()};
+    for (cudaError_t e : es)
+        if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 template <typename R, int NMAX, bool Exact>
 static cudaError_t launch_bwd(const DevBwd& db, cudaStream_t s) {
     const uint32_t blocks = (db.n_tasks + kBwdWarps - 1) / kBwdWarps;
-    const size_t smem = (size_t)kBwdWarps * kBwdRedElems * sizeof(typename CT<R>::c);
-    if (smem > 48 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_backward<R, NMAX, Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_backward<R, NMAX, Exact><<<blocks, kBwdWarps * 32, smem, s>>>(db);
+    k_backward<R, NMAX, Exact><<<blocks, kBwdWarps * 32, bwd_smem<R>(), s>>>(db);
     return cudaGetLastError();
 }
 
@@ -393,6 +408,8 @@ cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStrea
     if (db.n_tasks == 0) return cudaSuccess;
     return dtype == QT_C128 ? launch_bwd_class<double>(op_class, db, s) : launch_bwd_class<float>(op_class, db, s);
 }
+
+cudaError_t prepare_backward(int dtype) { return dtype == QT_C128 ? prepare_bwd<double>() : prepare_bwd<float>(); }
 
 cudaError_t launch_zero_ranges(int dtype, void* arena, const uint64_t* ranges, uint32_t n_ranges, cudaStream_t s) {
     if (n_ranges == 0) return cudaSuccess;

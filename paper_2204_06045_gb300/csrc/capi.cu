@@ -67,6 +67,11 @@ struct qt_plan_s {
     const uint64_t* d_zero = nullptr;  // cotangent pieces zeroed before each reverse sweep (inside d_bwd)
     uint32_t n_zero = 0;
     qt::DevBwd db{};
+    // the reverse sweep as one CUDA graph: within a level, the operand-count
+    // classes (independent launches) run on parallel branches
+    cudaGraphExec_t bwd_exec = nullptr;
+    cudaStream_t side[qt::kBwdClasses - 1] = {};
+    cudaEvent_t bwd_ev[qt::kBwdClasses] = {};
 
     // autotuning record
     double tune_seconds = 0;
@@ -81,6 +86,16 @@ struct qt_plan_s {
     // Free every device-side resource and forget it (the host plan stays).
     void release_device() {
         if (stream) cudaStreamSynchronize(stream);
+        if (bwd_exec) cudaGraphExecDestroy(bwd_exec);
+        bwd_exec = nullptr;
+        for (auto& st : side) {
+            if (st) cudaStreamDestroy(st);
+            st = nullptr;
+        }
+        for (auto& e : bwd_ev) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         exec = nullptr;
@@ -1056,6 +1071,65 @@ int qt_energy_batch(qt_plan_t P, const double* gammas, const double* betas, doub
     return run_eval(P, gammas, betas, cuda_stream, edge_zz, energies, true);
 }
 
+// The reverse sweep's launches, in order: zero the atomically updated
+// cotangents and the angle sums, seed the roots, then every level from the
+// roots down (its operand-count classes forked onto the side streams and
+// joined again), then the final scaling.
+cudaError_t enqueue_sweep(qt_plan_t P, cudaStream_t s) {
+    const qt::HostPlan& hp = P->hp;
+    const int G = (int)hp.graphs.size(), p = hp.cfg.p;
+    cudaError_t e = qt::launch_zero_ranges(P->dtype, P->d_arena, P->d_zero, P->n_zero, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_grad, 0, sizeof(double) * 2 * G * p, s);
+    if (e == cudaSuccess)
+        e = qt::launch_seed_roots(P->dtype, P->de, (int)hp.nets.size(), P->db.cot_delta, P->db.dleaf_delta, P->d_grad,
+                                  p, P->db.net_graph, s);
+    for (int lv = hp.n_levels - 1; lv >= 0 && e == cudaSuccess; --lv) {
+        int used = 0;
+        e = cudaEventRecord(P->bwd_ev[0], s);  // the level's fork point
+        for (int cls = 0; cls < qt::kBwdClasses && e == cudaSuccess; ++cls) {
+            const uint32_t i0 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls];
+            const uint32_t i1 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls + 1];
+            if (i1 == i0) continue;
+            qt::DevBwd db = P->db;
+            db.task_bucket += i0;
+            db.task_tile += i0;
+            db.n_tasks = i1 - i0;
+            cudaStream_t t = used == 0 ? s : P->side[used - 1];
+            if (used > 0) e = cudaStreamWaitEvent(t, P->bwd_ev[0], 0);
+            if (e == cudaSuccess) e = qt::launch_backward(P->dtype, cls, db, t);
+            ++used;
+        }
+        for (int j = 1; j < used && e == cudaSuccess; ++j) {  // join
+            e = cudaEventRecord(P->bwd_ev[j], P->side[j - 1]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P->bwd_ev[j], 0);
+        }
+    }
+    double* d_dg = P->d_grad + 2 * G * p;
+    if (e == cudaSuccess) e = qt::launch_grad_final(P->d_grad, G, p, d_dg, d_dg + G * p, s);
+    return e;
+}
+
+int ensure_bwd_graph(qt_plan_t P) {
+    if (P->bwd_exec) return QT_OK;
+    QT_CUDA(qt::prepare_backward(P->dtype));
+    for (auto& st : P->side)
+        if (!st) QT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& ev : P->bwd_ev)
+        if (!ev) QT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    QT_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_sweep(P, P->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+    if (e == cudaSuccess) e = ce;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->bwd_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        P->bwd_exec = nullptr;
+        return cuda_fail(e, "reverse sweep graph", __LINE__);
+    }
+    return QT_OK;
+}
+
 int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, double* energy, double* dE_dgamma,
                    double* dE_dbeta, void* cuda_stream) {
     if (!P) return QT_EINVAL;
@@ -1071,24 +1145,11 @@ int qt_energy_grad(qt_plan_t P, const double* gammas, const double* betas, doubl
     if (rc != QT_OK) return rc;
     cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : P->stream;
     // reverse sweep
-    QT_CUDA(qt::launch_zero_ranges(P->dtype, P->d_arena, P->d_zero, P->n_zero, s));
-    QT_CUDA(cudaMemsetAsync(P->d_grad, 0, sizeof(double) * 2 * G * p, s));
-    QT_CUDA(qt::launch_seed_roots(P->dtype, P->de, (int)hp.nets.size(), P->db.cot_delta, P->db.dleaf_delta, P->d_grad,
-                                  hp.cfg.p, P->db.net_graph, s));
-    for (int lv = hp.n_levels - 1; lv >= 0; --lv) {
-        for (int cls = 0; cls < qt::kBwdClasses; ++cls) {
-            const uint32_t i0 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls];
-            const uint32_t i1 = hp.bwd_level_begin[qt::kBwdClasses * lv + cls + 1];
-            qt::DevBwd db = P->db;
-            db.task_bucket += i0;
-            db.task_tile += i0;
-            db.n_tasks = i1 - i0;
-            QT_CUDA(qt::launch_backward(P->dtype, cls, db, s));
-        }
-    }
+    rc = ensure_bwd_graph(P);
+    if (rc != QT_OK) return rc;
+    QT_CUDA(cudaGraphLaunch(P->bwd_exec, s));
     double* d_dg = P->d_grad + 2 * G * p;
     double* d_db = d_dg + G * p;
-    QT_CUDA(qt::launch_grad_final(P->d_grad, G, p, d_dg, d_db, s));
     QT_CUDA(cudaMemcpyAsync(P->h_err, &P->dp.ctl->error, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     bool host_out = false;
     if (energy) {

@@ -89,6 +89,9 @@ cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint
                               double* grad, int p, const uint32_t* net_graph, cudaStream_t s);
 // op_class: the level's tasks of buckets with exactly 1..4 operands (0..3), at most 8 (4) or 16 (5)
 cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s);
+// Function attributes of the reverse-sweep kernels (the shared-memory size
+// above the default); once per process and element type, before any capture.
+cudaError_t prepare_backward(int dtype);
 
 cudaError_t launch_zero_ranges(int dtype, void* arena, const uint64_t* ranges, uint32_t n_ranges, cudaStream_t s);
 cudaError_t launch_grad_final(const double* grad, int n_graphs, int p, double* dgamma, double* dbeta, cudaStream_t s);
