@@ -607,23 +607,27 @@ def c3_leg(torch, steps):
                 pl.energy_batch(gd, bd, energies=en, stream=s)
             pl.sync(s)
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            for _ in range(reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+            ev[0].record(s)
+            for i in range(reps):
                 pl.energy_batch(gd, bd, energies=en, stream=s)
-            e1.record(s)
+                ev[i + 1].record(s)
             torch.cuda.synchronize()
             pl.sync(s)
-            return e0.elapsed_time(e1) / reps, en.cpu().numpy(), st
+            steps_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)]
+            st = dict(st, max_step_ms=max(steps_ms))
+            return ev[0].elapsed_time(ev[reps]) / reps, en.cpu().numpy(), st
 
     every = list(range(64))
     sub = list(range(0, 64, 8))
-    ms, en, st = timed(every, steps, 3, dtype="c64")
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, en, st = timed(every, steps, 3, dtype="c64")
     ms_d, en_d, st_d = timed(every, steps, 3, dtype="c64", dedup=True)
     ms_p, en_p, st_p = timed(sub, 1, 1, dtype="c128", sched="per_bucket")
     ms_s, en_s, _ = timed(sub, steps, 3, dtype="c64")
     return {"workload": "64 random 3-regular graphs, N even in [50,1000] (synth.batch, seed 1000+g), p=3",
-            "c64_graph_evals_per_s": 64e3 / ms, "c64_ms_per_batch": ms, "buckets": int(st["n_buckets"]),
+            "c64_graph_evals_per_s": 64e3 / ms, "c64_ms_per_batch": ms, "c64_max_step_ms": st["max_step_ms"],
+            "c64_clocks": clk.summary(), "buckets": int(st["n_buckets"]),
             "c64_dedup_graph_evals_per_s": 64e3 / ms_d, "dedup_networks_contracted": int(st_d["n_unique"]),
             "dedup_max_rel_energy_diff": float(np.max(np.abs(en_d - en) / np.abs(en))),
             "plain_subset": "graphs 0, 8, ..., 56",

@@ -170,6 +170,17 @@ struct BwdMath<double> {
     static __device__ __forceinline__ RP rzero() { return double2{0.0, 0.0}; }
 };
 
+// 16-byte asynchronous copies global -> shared (no registers), and the wait
+// for all of this thread's.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename R, int NMAX, bool Exact>
 __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, typename CT<R>::c* red) {
     using C = typename CT<R>::c;
@@ -226,6 +237,20 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
         }
     }
     for (uint32_t e = lane; e < red_elems; e += 32) red[e] = C{};
+    // The tile's entries of the result's cotangent (at least one pair; the
+    // block starts on a pair: obase >> rshift is even or 0), copied once into
+    // the buffer's unused end when it fits, instead of a global load in every
+    // iteration below.
+    const uint32_t rcount = max(2u, (1u << tb) >> rshift);
+    const bool rstaged = red_elems + rcount <= (uint32_t)kBwdRedElems;
+    C* const rsm = red + red_elems;  // red_elems is even: pair-aligned
+    if (rstaged) {
+        const char* src = reinterpret_cast<const char*>(rbar + (obase >> rshift));
+        char* dst = reinterpret_cast<char*>(rsm);
+        const uint32_t chunks = rcount * (uint32_t)sizeof(C) / 16u;
+        for (uint32_t i = (uint32_t)lane; i < chunks; i += 32u) cp_async16(dst + 16u * i, src + 16u * i);
+        cp_async_wait_all();
+    }
     __syncwarp();
     RP acc[NMAX], comp[NMAX];  // compensated sums of Re(c dT), per x
 #pragma unroll
@@ -234,7 +259,7 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
     for (uint32_t k = 0; k < (1u << kb); ++k) {
         const uint32_t o = obase + (k << 5) + ((uint32_t)lane & lmask);
         P r = M::zero();
-        if (active) r = M::splat(elem_ldg(rbar, o >> rshift));
+        if (active) r = M::splat(rstaged ? elem_ld(rsm, (o - obase) >> rshift) : elem_ldg(rbar, o >> rshift));
         P v[NMAX];
         uint32_t li[NMAX];
 #pragma unroll
