@@ -92,7 +92,7 @@ constexpr int kBwdWarps = 4;  // warps per block of the reverse sweep, one (buck
 // sums go to the warp's shared buffer with plain read-add-writes: after the
 // shuffles, the lanes left own distinct entries (they differ in a bit the
 // operand carries), in every iteration. Gate sums are compensated per x and
-// lane, then reduced in FP64.
+// lane in complex64 (FP32), plain in complex128, then reduced in FP64.
 struct PC {
     f32x2 re, im;
 };
@@ -286,10 +286,15 @@ __device__ void bwd_tile(const DevBwd& db, uint32_t b, uint32_t tile, int lane, 
                     const P c = (t == n - 1) ? pre : M::mul(pre, suf[t]);  // Rbar[o] prod_{u != t} v[u]
                     if (md == kBwdGate) {
                         const P d = px[t] ? M::ldg(opp[t] + dld + 2u * li[t]) : M::splat(elem_ldg(opp[t] + dld, nb[t] + li[t]));
-                        const RP y = M::sub(M::re_prod(c, d), comp[t]);
-                        const RP s2 = M::add(acc[t], y);
-                        comp[t] = M::sub(M::sub(s2, acc[t]), y);
-                        acc[t] = s2;
+                        if (sizeof(R) == 8) {
+                            // FP64: a lane's few hundred terms need no compensation
+                            acc[t] = M::add(acc[t], M::re_prod(c, d));
+                        } else {
+                            const RP y = M::sub(M::re_prod(c, d), comp[t]);
+                            const RP s2 = M::add(acc[t], y);
+                            comp[t] = M::sub(M::sub(s2, acc[t]), y);
+                            acc[t] = s2;
+                        }
                     } else if (md == kBwdDirect) {
                         if (active) M::stg(opp[t] + cot + 2u * li[t], c);
                     } else if (md == kBwdRedStore || md == kBwdRedAtomic) {
