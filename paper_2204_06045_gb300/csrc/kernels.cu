@@ -947,9 +947,13 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
 
 // A fused unit: its buckets in elimination order, one output per lane at a
 // time, intermediates in stage st (free: a unit stages nothing), the root's
-// result to the arena. The unit's program is read kURecWindow records at a
-// time, one per lane, with one coalesced load; each bucket's operand records
-// go to the warp's gate-table area (unused by units) for the output loop.
+// result to the arena. Two independent buckets of at most 16 outputs that the
+// planner marked as a pair run together, one on each half of the warp. The
+// unit's program is read through two windows of kURecWindow records (one per
+// lane each, coalesced loads): once the next header lies in the second
+// window, the windows move on by one and the next one is requested. Each
+// step's operand records go to the warp's gate-table area (unused by units):
+// entries 0..15 for the first bucket, 16..31 for the second of a pair.
 __device__ __forceinline__ URec shfl_rec(const URec& r, int src) {
     URec o;
     o.a = __shfl_sync(kFull, r.a, src);
@@ -957,46 +961,89 @@ __device__ __forceinline__ URec shfl_rec(const URec& r, int src) {
     o.off = __shfl_sync(kFull, r.off, src);
     return o;
 }
+// Record i (< 2 kURecWindow) of the two windows.
+__device__ __forceinline__ URec window_rec(const URec& cur, const URec& nxt, uint32_t i) {
+    const URec rc = shfl_rec(cur, (int)(i & (kURecWindow - 1)));
+    const URec rn = shfl_rec(nxt, (int)(i & (kURecWindow - 1)));
+    return i < (uint32_t)kURecWindow ? rc : rn;
+}
 
 template <typename R>
 __device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int lane) {
     using C = typename CT<R>::c;
-    static_assert(sizeof(URec) * kMaxOps <= sizeof(ws.leaf_tab), "unit operand records");
-    static_assert(kURecWindow == 32 && kMaxOps + 1 <= kURecWindow, "one bucket's records fit the window");
+    static_assert(sizeof(URec) * 32 <= sizeof(ws.leaf_tab), "unit operand records of a pair");
+    static_assert(kURecWindow == 32 && 2 * kMaxOps + 2 <= 2 * kURecWindow, "a step's records fit the windows");
     URec* uops = reinterpret_cast<URec*>(ws.leaf_tab);
     const RunSlot<R>& rs = ws.slot[sl];
     C* scr = ws.stage[st];
     C* arena = static_cast<C*>(dp.arena);
+    // the program is padded by two windows past the last unit
     const URec* prog = dp.unit_prog + (rs.unit_begin - 1u);
-    uint32_t pos = 0, base = 0;  // next record; first record held in the window
-    URec mine = prog[lane];
-    for (uint32_t k = 0; k < rs.unit_count; ++k) {
-        if (pos + 1u + kMaxOps > base + kURecWindow) {  // refill: the bucket's records all in the window
-            base = pos;
-            mine = prog[base + lane];
+    uint32_t pos = 0, base = 0;  // next record; the windows hold records [base, base + 2 kURecWindow)
+    URec cur = prog[lane], nxt = prog[kURecWindow + lane];
+    for (uint32_t k = 0; k < rs.unit_count;) {
+        // a step spans at most 32 records, so pos - base < 64 here and one move suffices
+        if (pos >= base + kURecWindow) {
+            base += kURecWindow;
+            cur = nxt;
+            nxt = prog[base + kURecWindow + lane];
         }
-        const URec h = shfl_rec(mine, (int)(pos - base));
-        const uint32_t n_out = h.a & 0xffu, n_ops = (h.a >> 8) & 0xffu;
-        const bool root = (h.a >> 16) & 1u;
-        const int first_op = (int)(pos + 1u - base);
-        const URec r = shfl_rec(mine, (first_op + lane) & (kURecWindow - 1));  // lane t: operand t
-        if (lane < (int)n_ops) uops[lane] = r;
-        pos += 1u + n_ops;
+        const URec h = shfl_rec(cur, (int)(pos - base));
+        const uint32_t n_ops1 = (h.a >> 8) & 0xffu;
+        const bool pair = (h.a >> 17) & 1u;
+        const uint32_t pos2 = pos + 1u + n_ops1;
+        URec h2{};
+        uint32_t n_ops2 = 0;
+        if (pair) {  // the second bucket's header (uniform)
+            h2 = window_rec(cur, nxt, pos2 - base);
+            n_ops2 = (h2.a >> 8) & 0xffu;
+        }
+        // lane t < 16 takes operand t of the first bucket; lane 16 + t operand
+        // t of the second (pairs) -- singles have at most 16 operands
+        const bool upper = pair && lane >= 16;
+        const uint32_t t_lane = upper ? (uint32_t)lane - 16u : (uint32_t)lane;
+        const uint32_t my_ops = upper ? n_ops2 : n_ops1;
+        const URec r = window_rec(cur, nxt, (upper ? pos2 : pos) + 1u + t_lane - base);
+        if (t_lane < my_ops) uops[lane] = r;
+        pos = pair ? pos2 + 1u + n_ops2 : pos2;
+        k += pair ? 2u : 1u;
         __syncwarp();
-        C* dst = root ? arena + rs.out_off : scr + h.b;
-        for (uint32_t o = lane; o < (1u << n_out); o += 32) {
-            C a0, a1;
-            a0.x = a1.x = (R)1;
-            a0.y = a1.y = (R)0;
-            for (uint32_t t = 0; t < n_ops; ++t) {
-                const URec d = uops[t];
-                const uint32_t e = 2u * pext_u32(o, d.a);
-                const C* src = d.b ? scr + d.off : arena + d.off;
-                const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
-                a0 = cmul(a0, v.v0);
-                a1 = cmul(a1, v.v1);
+        if (pair) {
+            const URec& mh = upper ? h2 : h;  // neither is the unit's root
+            const uint32_t n_out = mh.a & 0xffu, ub = upper ? 16u : 0u;
+            C* dst = scr + mh.b;
+            for (uint32_t o = (uint32_t)lane & 15u; o < (1u << n_out); o += 16) {
+                C a0, a1;
+                a0.x = a1.x = (R)1;
+                a0.y = a1.y = (R)0;
+                for (uint32_t t = 0; t < my_ops; ++t) {
+                    const URec d = uops[ub + t];
+                    const uint32_t e = 2u * pext_u32(o, d.a);
+                    const C* src = d.b ? scr + d.off : arena + d.off;
+                    const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
+                    a0 = cmul(a0, v.v0);
+                    a1 = cmul(a1, v.v1);
+                }
+                elem_st(dst, o, cadd(a0, a1));
             }
-            elem_st(dst, o, cadd(a0, a1));
+        } else {
+            const uint32_t n_out = h.a & 0xffu;
+            const bool root = (h.a >> 16) & 1u;
+            C* dst = root ? arena + rs.out_off : scr + h.b;
+            for (uint32_t o = lane; o < (1u << n_out); o += 32) {
+                C a0, a1;
+                a0.x = a1.x = (R)1;
+                a0.y = a1.y = (R)0;
+                for (uint32_t t = 0; t < n_ops1; ++t) {
+                    const URec d = uops[t];
+                    const uint32_t e = 2u * pext_u32(o, d.a);
+                    const C* src = d.b ? scr + d.off : arena + d.off;
+                    const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
+                    a0 = cmul(a0, v.v0);
+                    a1 = cmul(a1, v.v1);
+                }
+                elem_st(dst, o, cadd(a0, a1));
+            }
         }
         __syncwarp();
     }

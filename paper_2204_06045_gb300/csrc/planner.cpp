@@ -809,34 +809,63 @@ static void form_units(HostPlan* hp, int stage_elems) {
         each_kid(b, [&](uint32_t c) { good = good && ok[c]; });  // producers precede their consumer
         ok[b] = good;
     }
-    // first-fit placement of a subtree's intermediates; false if it overflows
-    auto place = [&](const std::vector<uint32_t>& members, uint32_t root) {
-        std::vector<std::pair<uint32_t, uint32_t>> used;  // (offset, size), sorted by offset
-        std::vector<uint32_t> off(members.size(), 0);
-        for (size_t k = 0; k < members.size(); ++k) {
-            const uint32_t u = members[k];
-            if (u != root) {
-                const uint32_t sz = 1u << hp->buckets[u].n_out;
-                uint32_t at = 0;
-                for (auto& iv : used) {
-                    if (at + sz <= iv.first) break;
-                    at = std::max(at, iv.first + iv.second);
-                }
-                if (at + sz > (uint32_t)stage_elems) return false;
-                used.insert(std::upper_bound(used.begin(), used.end(), std::make_pair(at, 0u)), {at, sz});
-                off[k] = at;
+    // Pairs: a member and the next one run together on the two halves of the
+    // warp when both have at most 16 outputs, the second does not consume the
+    // first, neither is the root, and their records (two headers and the
+    // operands) number at most 32 (the kernel's record windows).
+    auto pair_up = [&](const std::vector<uint32_t>& members, uint32_t root, std::vector<uint8_t>& first) {
+        first.assign(members.size(), 0);
+        for (size_t k = 0; k + 1 < members.size(); ++k) {
+            const uint32_t u = members[k], v = members[k + 1];
+            const DBucket &du = hp->buckets[u], &dv = hp->buckets[v];
+            bool ok2 = u != root && v != root && du.n_out <= 4 && dv.n_out <= 4 && 2 + du.n_ops + dv.n_ops <= 32;
+            each_kid(v, [&](uint32_t c) { ok2 = ok2 && c != u; });
+            if (ok2) {
+                first[k] = 1;
+                ++k;
             }
-            // u's producers are consumed now: free their space
+        }
+    };
+    // first-fit placement of a subtree's intermediates; false if it overflows.
+    // A pair's two results are placed before either's producers are freed.
+    auto place = [&](const std::vector<uint32_t>& members, uint32_t root, const std::vector<uint8_t>& first) {
+        std::vector<std::pair<uint32_t, uint32_t>> used;  // (offset, size), sorted by offset
+        auto alloc = [&](uint32_t u) {
+            const uint32_t sz = 1u << hp->buckets[u].n_out;
+            uint32_t at = 0;
+            for (auto& iv : used) {
+                if (at + sz <= iv.first) break;
+                at = std::max(at, iv.first + iv.second);
+            }
+            if (at + sz > (uint32_t)stage_elems) return false;
+            used.insert(std::upper_bound(used.begin(), used.end(), std::make_pair(at, 0u)), {at, sz});
+            hp->buckets[u].scr_off = (uint16_t)at;
+            return true;
+        };
+        auto release = [&](uint32_t u) {  // u's producers are consumed now: free their space
             each_kid(u, [&](uint32_t c) {
                 const uint32_t co = hp->buckets[c].scr_off, cs = 1u << hp->buckets[c].n_out;
                 auto it = std::find(used.begin(), used.end(), std::make_pair(co, cs));
                 if (it != used.end()) used.erase(it);
             });
-            if (u != root) hp->buckets[u].scr_off = (uint16_t)off[k];
+        };
+        for (size_t k = 0; k < members.size(); ++k) {
+            const uint32_t u = members[k];
+            if (first[k]) {
+                const uint32_t v = members[k + 1];
+                if (!alloc(u) || !alloc(v)) return false;
+                release(u);
+                release(v);
+                ++k;
+                continue;
+            }
+            if (u != root && !alloc(u)) return false;
+            release(u);
         }
         return true;
     };
     std::vector<uint32_t> stack, members, todo;
+    std::vector<uint8_t> first;
     for (uint32_t r = nb; r-- > 0;) {  // parents before producers: maximal subtrees first
         const DBucket& d = hp->buckets[r];
         if (!ok[r] || (d.flags & kBucketInUnit)) continue;
@@ -854,15 +883,18 @@ static void form_units(HostPlan* hp, int stage_elems) {
                 each_kid(u, [&](uint32_t c) { todo.push_back(c); });
             }
             std::sort(members.begin(), members.end());  // elimination order
-            if (place(members, root)) {
+            pair_up(members, root, first);
+            if (place(members, root, first)) {
                 hp->buckets[root].flags |= kBucketUnitRoot;
                 for (uint32_t u : members)
                     if (u != root) hp->buckets[u].flags |= kBucketInUnit;
                 hp->buckets[root].unit_begin = (uint32_t)hp->unit_prog.size() + 1u;
                 hp->buckets[root].unit_count = (uint32_t)members.size();
-                for (uint32_t u : members) {
+                for (size_t k = 0; k < members.size(); ++k) {
+                    const uint32_t u = members[k];
                     const DBucket& m = hp->buckets[u];
-                    hp->unit_prog.push_back(URec{(uint32_t)m.n_out | ((uint32_t)m.n_ops << 8) | (u == root ? 1u << 16 : 0u),
+                    hp->unit_prog.push_back(URec{(uint32_t)m.n_out | ((uint32_t)m.n_ops << 8) | (u == root ? 1u << 16 : 0u) |
+                                                     (first[k] ? 1u << 17 : 0u),
                                                  u == root ? 0u : (uint32_t)m.scr_off, 0});
                     for (uint32_t i = m.op_begin; i < m.op_begin + m.n_ops; ++i) {
                         const DOperand& o = hp->operands[i];
@@ -892,7 +924,7 @@ static void form_units(HostPlan* hp, int stage_elems) {
         hp->n_units = hp->n_fused = 0;
         return;
     }
-    hp->unit_prog.resize(hp->unit_prog.size() + kURecWindow, URec{0, 0, 0});  // window reads past the last unit
+    hp->unit_prog.resize(hp->unit_prog.size() + 2 * kURecWindow, URec{0, 0, 0});  // window reads past the last unit
     // a unit is one group; its members are never claimed on their own
     hp->n_groups = 0;
     for (uint32_t b = 0; b < nb; ++b) {

@@ -148,8 +148,9 @@ static_assert(sizeof(DSlot) == 16, "DSlot layout");
 
 // A fused unit's program: for each bucket, in elimination order, a header
 // record then one record per operand. 16 bytes.
-//   header:  a = n_out | n_ops << 8 | (1 << 16 if the unit's root), b = stage
-//            offset of the result (not the root), off unused
+//   header:  a = n_out | n_ops << 8 | (1 << 16 if the unit's root) | (1 << 17
+//            if it runs with the next bucket, on the other half of the warp),
+//            b = stage offset of the result (not the root), off unused
 //   operand: a = mask, b = 1 for an intermediate of the unit (off: its stage
 //            offset), 0 for a gate tensor (off: arena offset)
 struct URec {
