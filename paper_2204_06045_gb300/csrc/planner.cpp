@@ -1016,23 +1016,19 @@ static void simulate_order(HostPlan* hp) {
             }
             if (r.next_tile == 0 && cfg.run_tiles == 0) {
                 // Group size when the bucket starts: where the GPU is nearly
-                // idle (QT_SPLIT_SHARE free warps or more per ready bucket, as
-                // on the chains that end every network), the bucket spreads
-                // over its share of them, in groups of QT_MIN_GROUP tiles or
-                // more; elsewhere group_tiles. Measured on GB300: 64 and 8 gave
-                // the N=30 p=4 plan 4.5% over fixed groups of 16; smaller groups
-                // lost (each group costs a claim, descriptor reads and a copy
-                // round trip that the host model undercounts).
-#ifndef QT_SPLIT_SHARE
-#define QT_SPLIT_SHARE 64
-#endif
-#ifndef QT_MIN_GROUP
-#define QT_MIN_GROUP 8
-#endif
+                // idle (kSplitShare free warps or more per ready bucket, as on
+                // the chains that end every network), the bucket spreads over
+                // its share of them, in groups of min_group tiles or more;
+                // elsewhere group_tiles. Measured on GB300 (N=30 p=4): groups
+                // of at least 4 tiles for complex64 (0.945 vs 0.969 ms at 8),
+                // 8 for complex128 (5.65 vs 5.75 ms at 4); larger shares or
+                // smaller ones did not help.
+                constexpr double kSplitShare = 64.0;
+                const double min_group = cfg.dtype == 1 ? 8.0 : 4.0;
                 const double share = (double)free_workers / (double)(ready.size() + 1);
-                if (share >= QT_SPLIT_SHARE) {
+                if (share >= kSplitShare) {
                     const double want = std::ceil((double)d.n_tasks / share);
-                    gsize[r.bucket] = (uint32_t)std::max<double>(std::min<double>(QT_MIN_GROUP, d.group_tiles),
+                    gsize[r.bucket] = (uint32_t)std::max<double>(std::min<double>(min_group, d.group_tiles),
                                                                  std::min<double>(d.group_tiles, want));
                 }
                 groups_left[r.bucket] = (d.n_tasks + gsize[r.bucket] - 1) / gsize[r.bucket];
