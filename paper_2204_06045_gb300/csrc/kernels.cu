@@ -945,15 +945,15 @@ __device__ __forceinline__ void gate_table(WarpSmem<R>& ws, const RunSlot<R>& rs
     __syncwarp();
 }
 
-// A fused unit: its buckets in elimination order, one output per lane at a
-// time, intermediates in stage st (free: a unit stages nothing), the root's
-// result to the arena. Two independent buckets of at most 16 outputs that the
-// planner marked as a pair run together, one on each half of the warp. The
-// unit's program is read through two windows of kURecWindow records (one per
-// lane each, coalesced loads): once the next header lies in the second
-// window, the windows move on by one and the next one is requested. Each
-// step's operand records go to the warp's gate-table area (unused by units):
-// entries 0..15 for the first bucket, 16..31 for the second of a pair.
+// A fused unit: its buckets run in steps, intermediates in stage st (free: a
+// unit stages nothing), the root's result to the arena. A step is one bucket
+// over the whole warp (one output per lane at a time), or several independent
+// buckets of at most 16 outputs that the planner packed together, one output
+// per lane (a step record gives each lane its bucket). The unit's program is
+// read through two windows of kURecWindow records (one per lane each,
+// coalesced loads): once the next step starts in the second window, the
+// windows move on by one and the next one is requested. A step's records go
+// to the warp's gate-table area (unused by units) for its output loop.
 __device__ __forceinline__ URec shfl_rec(const URec& r, int src) {
     URec o;
     o.a = __shfl_sync(kFull, r.a, src);
@@ -968,12 +968,31 @@ __device__ __forceinline__ URec window_rec(const URec& cur, const URec& nxt, uin
     return i < (uint32_t)kURecWindow ? rc : rn;
 }
 
+// One output o of a bucket whose operand records are ops[0..n_ops).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::c unit_output(const URec* ops, uint32_t n_ops, uint32_t o,
+                                                         typename CT<R>::c* scr, typename CT<R>::c* arena) {
+    using C = typename CT<R>::c;
+    C a0, a1;
+    a0.x = a1.x = (R)1;
+    a0.y = a1.y = (R)0;
+    for (uint32_t t = 0; t < n_ops; ++t) {
+        const URec d = ops[t];
+        const uint32_t e = 2u * pext_u32(o, d.a);
+        const C* src = d.b ? scr + d.off : arena + d.off;
+        const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
+        a0 = cmul(a0, v.v0);
+        a1 = cmul(a1, v.v1);
+    }
+    return cadd(a0, a1);
+}
+
 template <typename R>
 __device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int lane) {
     using C = typename CT<R>::c;
-    static_assert(sizeof(URec) * 32 <= sizeof(ws.leaf_tab), "unit operand records of a pair");
-    static_assert(kURecWindow == 32 && 2 * kMaxOps + 2 <= 2 * kURecWindow, "a step's records fit the windows");
-    URec* uops = reinterpret_cast<URec*>(ws.leaf_tab);
+    static_assert(sizeof(URec) * kURecWindow <= sizeof(ws.leaf_tab), "a step's records");
+    static_assert(kURecWindow == 32 && kMaxOps + 1 <= kURecWindow, "a step's records fit a window");
+    URec* recs = reinterpret_cast<URec*>(ws.leaf_tab);
     const RunSlot<R>& rs = ws.slot[sl];
     C* scr = ws.stage[st];
     C* arena = static_cast<C*>(dp.arena);
@@ -989,61 +1008,34 @@ __device__ void run_unit(const DevPlan& dp, WarpSmem<R>& ws, int sl, int st, int
             nxt = prog[base + kURecWindow + lane];
         }
         const URec h = shfl_rec(cur, (int)(pos - base));
-        const uint32_t n_ops1 = (h.a >> 8) & 0xffu;
-        const bool pair = (h.a >> 17) & 1u;
-        const uint32_t pos2 = pos + 1u + n_ops1;
-        URec h2{};
-        uint32_t n_ops2 = 0;
-        if (pair) {  // the second bucket's header (uniform)
-            h2 = window_rec(cur, nxt, pos2 - base);
-            n_ops2 = (h2.a >> 8) & 0xffu;
-        }
-        // lane t < 16 takes operand t of the first bucket; lane 16 + t operand
-        // t of the second (pairs) -- singles have at most 16 operands
-        const bool upper = pair && lane >= 16;
-        const uint32_t t_lane = upper ? (uint32_t)lane - 16u : (uint32_t)lane;
-        const uint32_t my_ops = upper ? n_ops2 : n_ops1;
-        const URec r = window_rec(cur, nxt, (upper ? pos2 : pos) + 1u + t_lane - base);
-        if (t_lane < my_ops) uops[lane] = r;
-        pos = pair ? pos2 + 1u + n_ops2 : pos2;
-        k += pair ? 2u : 1u;
-        __syncwarp();
-        if (pair) {
-            const URec& mh = upper ? h2 : h;  // neither is the unit's root
-            const uint32_t n_out = mh.a & 0xffu, ub = upper ? 16u : 0u;
-            C* dst = scr + mh.b;
-            for (uint32_t o = (uint32_t)lane & 15u; o < (1u << n_out); o += 16) {
-                C a0, a1;
-                a0.x = a1.x = (R)1;
-                a0.y = a1.y = (R)0;
-                for (uint32_t t = 0; t < my_ops; ++t) {
-                    const URec d = uops[ub + t];
-                    const uint32_t e = 2u * pext_u32(o, d.a);
-                    const C* src = d.b ? scr + d.off : arena + d.off;
-                    const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
-                    a0 = cmul(a0, v.v0);
-                    a1 = cmul(a1, v.v1);
-                }
-                elem_st(dst, o, cadd(a0, a1));
+        if (h.a & kUnitStep) {
+            // several buckets: stage the step's records, then each lane
+            // computes one output of its bucket
+            const uint32_t n_recs = h.a & 0x3fu, n_items = (h.a >> 20) & 7u, used = (h.a >> 24) & 0x3fu;
+            const URec r = window_rec(cur, nxt, pos + (uint32_t)lane - base);
+            if ((uint32_t)lane < n_recs) recs[lane] = r;
+            pos += n_recs;
+            k += n_items;
+            __syncwarp();
+            if ((uint32_t)lane < used) {
+                const uint32_t q = (uint32_t)(h.off >> (2 * lane)) & 3u;
+                const uint32_t at = q == 0 ? 1u : (h.b >> (8 * (q - 1))) & 0xffu;
+                const URec hq = recs[at];
+                const uint32_t n_ops = (hq.a >> 8) & 0xffu;
+                const uint32_t o = (uint32_t)lane - (uint32_t)hq.off;
+                elem_st(scr + hq.b, o, unit_output<R>(recs + at + 1, n_ops, o, scr, arena));
             }
         } else {
-            const uint32_t n_out = h.a & 0xffu;
+            // one bucket over the whole warp
+            const uint32_t n_out = h.a & 0xffu, n_ops = (h.a >> 8) & 0xffu;
             const bool root = (h.a >> 16) & 1u;
+            const URec r = window_rec(cur, nxt, pos + 1u + (uint32_t)lane - base);  // lane t: operand t
+            if ((uint32_t)lane < n_ops) recs[lane] = r;
+            pos += 1u + n_ops;
+            ++k;
+            __syncwarp();
             C* dst = root ? arena + rs.out_off : scr + h.b;
-            for (uint32_t o = lane; o < (1u << n_out); o += 32) {
-                C a0, a1;
-                a0.x = a1.x = (R)1;
-                a0.y = a1.y = (R)0;
-                for (uint32_t t = 0; t < n_ops1; ++t) {
-                    const URec d = uops[t];
-                    const uint32_t e = 2u * pext_u32(o, d.a);
-                    const C* src = d.b ? scr + d.off : arena + d.off;
-                    const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
-                    a0 = cmul(a0, v.v0);
-                    a1 = cmul(a1, v.v1);
-                }
-                elem_st(dst, o, cadd(a0, a1));
-            }
+            for (uint32_t o = lane; o < (1u << n_out); o += 32) elem_st(dst, o, unit_output<R>(recs, n_ops, o, scr, arena));
         }
         __syncwarp();
     }

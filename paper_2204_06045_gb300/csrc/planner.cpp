@@ -809,26 +809,41 @@ static void form_units(HostPlan* hp, int stage_elems) {
         each_kid(b, [&](uint32_t c) { good = good && ok[c]; });  // producers precede their consumer
         ok[b] = good;
     }
-    // Pairs: a member and the next one run together on the two halves of the
-    // warp when both have at most 16 outputs, the second does not consume the
-    // first, neither is the root, and their records (two headers and the
-    // operands) number at most 32 (the kernel's record windows).
-    auto pair_up = [&](const std::vector<uint32_t>& members, uint32_t root, std::vector<uint8_t>& first) {
-        first.assign(members.size(), 0);
-        for (size_t k = 0; k + 1 < members.size(); ++k) {
-            const uint32_t u = members[k], v = members[k + 1];
-            const DBucket &du = hp->buckets[u], &dv = hp->buckets[v];
-            bool ok2 = u != root && v != root && du.n_out <= 4 && dv.n_out <= 4 && 2 + du.n_ops + dv.n_ops <= 32;
-            each_kid(v, [&](uint32_t c) { ok2 = ok2 && c != u; });
-            if (ok2) {
-                first[k] = 1;
-                ++k;
+    // Steps: consecutive members that run together, one output per lane --
+    // at most 4 mutually independent buckets of at most 16 outputs each, 32
+    // lanes and 31 records (their headers and operands) in all, none the
+    // root; any other member is a step of its own, over the whole warp.
+    // step[k] = index of the first member of k's step.
+    auto make_steps = [&](const std::vector<uint32_t>& order, uint32_t root, std::vector<uint32_t>& step) {
+        step.assign(order.size(), 0);
+        for (size_t k = 0; k < order.size();) {
+            const uint32_t u = order[k];
+            const DBucket& du = hp->buckets[u];
+            size_t e = k + 1;
+            if (u != root && du.n_out <= 4) {
+                uint32_t lanes = 1u << du.n_out, recs = 1u + du.n_ops;
+                while (e < order.size() && e - k < 4) {
+                    const uint32_t v = order[e];
+                    const DBucket& dv = hp->buckets[v];
+                    if (v == root || dv.n_out > 4 || lanes + (1u << dv.n_out) > 32 || recs + 1u + dv.n_ops > 31) break;
+                    bool indep = true;
+                    each_kid(v, [&](uint32_t c) {
+                        for (size_t j = k; j < e; ++j) indep = indep && c != order[j];
+                    });
+                    if (!indep) break;
+                    lanes += 1u << dv.n_out;
+                    recs += 1u + dv.n_ops;
+                    ++e;
+                }
             }
+            for (size_t j = k; j < e; ++j) step[j] = (uint32_t)k;
+            k = e;
         }
     };
-    // first-fit placement of a subtree's intermediates; false if it overflows.
-    // A pair's two results are placed before either's producers are freed.
-    auto place = [&](const std::vector<uint32_t>& members, uint32_t root, const std::vector<uint8_t>& first) {
+    // first-fit placement of a subtree's intermediates in step order; false if
+    // it overflows. A step's results are all placed before any of its
+    // members' producers are freed (they run at the same time).
+    auto place = [&](const std::vector<uint32_t>& order, uint32_t root, const std::vector<uint32_t>& step) {
         std::vector<std::pair<uint32_t, uint32_t>> used;  // (offset, size), sorted by offset
         auto alloc = [&](uint32_t u) {
             const uint32_t sz = 1u << hp->buckets[u].n_out;
@@ -849,23 +864,36 @@ static void form_units(HostPlan* hp, int stage_elems) {
                 if (it != used.end()) used.erase(it);
             });
         };
-        for (size_t k = 0; k < members.size(); ++k) {
-            const uint32_t u = members[k];
-            if (first[k]) {
-                const uint32_t v = members[k + 1];
-                if (!alloc(u) || !alloc(v)) return false;
-                release(u);
-                release(v);
-                ++k;
-                continue;
-            }
-            if (u != root && !alloc(u)) return false;
-            release(u);
+        for (size_t k = 0; k < order.size();) {
+            size_t e = k + 1;
+            while (e < order.size() && step[e] == k) ++e;
+            for (size_t j = k; j < e; ++j)
+                if (order[j] != root && !alloc(order[j])) return false;
+            for (size_t j = k; j < e; ++j) release(order[j]);
+            k = e;
         }
         return true;
     };
-    std::vector<uint32_t> stack, members, todo;
-    std::vector<uint8_t> first;
+    // Depth order: a member's depth is 0 without producers in the unit, else
+    // one more than its deepest producer's; the members of one depth are
+    // independent, so they pack into steps (elimination order within a depth).
+    auto depth_order = [&](const std::vector<uint32_t>& members, std::vector<uint32_t>& order) {
+        std::vector<std::pair<uint32_t, uint32_t>> keyed;
+        std::unordered_map<uint32_t, uint32_t> depth;
+        for (uint32_t u : members) {  // elimination order: producers first
+            uint32_t dp = 0;
+            each_kid(u, [&](uint32_t c) {
+                auto it = depth.find(c);
+                if (it != depth.end()) dp = std::max(dp, it->second + 1);
+            });
+            depth[u] = dp;
+            keyed.push_back({dp, u});
+        }
+        std::sort(keyed.begin(), keyed.end());
+        order.clear();
+        for (auto& kv : keyed) order.push_back(kv.second);
+    };
+    std::vector<uint32_t> stack, members, todo, order, step;
     for (uint32_t r = nb; r-- > 0;) {  // parents before producers: maximal subtrees first
         const DBucket& d = hp->buckets[r];
         if (!ok[r] || (d.flags & kBucketInUnit)) continue;
@@ -883,25 +911,53 @@ static void form_units(HostPlan* hp, int stage_elems) {
                 each_kid(u, [&](uint32_t c) { todo.push_back(c); });
             }
             std::sort(members.begin(), members.end());  // elimination order
-            pair_up(members, root, first);
-            if (place(members, root, first)) {
+            // depth order packs the most; it keeps more results alive at once,
+            // so elimination order (consecutive independent members) is the
+            // fallback when its placement overflows the stage
+            depth_order(members, order);
+            make_steps(order, root, step);
+            bool placed = place(order, root, step);
+            if (!placed) {
+                order = members;
+                make_steps(order, root, step);
+                placed = place(order, root, step);
+            }
+            if (placed) {
                 hp->buckets[root].flags |= kBucketUnitRoot;
                 for (uint32_t u : members)
                     if (u != root) hp->buckets[u].flags |= kBucketInUnit;
                 hp->buckets[root].unit_begin = (uint32_t)hp->unit_prog.size() + 1u;
                 hp->buckets[root].unit_count = (uint32_t)members.size();
-                for (size_t k = 0; k < members.size(); ++k) {
-                    const uint32_t u = members[k];
-                    const DBucket& m = hp->buckets[u];
-                    hp->unit_prog.push_back(URec{(uint32_t)m.n_out | ((uint32_t)m.n_ops << 8) | (u == root ? 1u << 16 : 0u) |
-                                                     (first[k] ? 1u << 17 : 0u),
-                                                 u == root ? 0u : (uint32_t)m.scr_off, 0});
-                    for (uint32_t i = m.op_begin; i < m.op_begin + m.n_ops; ++i) {
-                        const DOperand& o = hp->operands[i];
-                        const bool leaf = (o.flags & kOpLeaf) != 0;
-                        hp->unit_prog.push_back(
-                            URec{o.mask, leaf ? 0u : 1u, leaf ? o.off : (uint64_t)hp->buckets[hp->op_src[i]].scr_off});
+                for (size_t k = 0; k < order.size();) {
+                    size_t e = k + 1;
+                    while (e < order.size() && step[e] == k) ++e;
+                    const size_t at = hp->unit_prog.size();
+                    if (e - k > 1) {  // the step record, completed below
+                        hp->unit_prog.push_back(URec{0, 0, 0});
                     }
+                    uint32_t lane = 0, item_off = 0;
+                    uint64_t map = 0;
+                    for (size_t j = k; j < e; ++j) {
+                        const uint32_t u = order[j];
+                        const DBucket& m = hp->buckets[u];
+                        const uint32_t rel = (uint32_t)(hp->unit_prog.size() - at);
+                        if (j > k) item_off |= rel << (8 * (j - k - 1));
+                        for (uint32_t l = lane; l < lane + (1u << m.n_out); ++l) map |= (uint64_t)(j - k) << (2 * l);
+                        hp->unit_prog.push_back(URec{(uint32_t)m.n_out | ((uint32_t)m.n_ops << 8) | (u == root ? 1u << 16 : 0u),
+                                                     u == root ? 0u : (uint32_t)m.scr_off, e - k > 1 ? (uint64_t)lane : 0});
+                        lane += 1u << m.n_out;
+                        for (uint32_t i = m.op_begin; i < m.op_begin + m.n_ops; ++i) {
+                            const DOperand& o = hp->operands[i];
+                            const bool leaf = (o.flags & kOpLeaf) != 0;
+                            hp->unit_prog.push_back(
+                                URec{o.mask, leaf ? 0u : 1u, leaf ? o.off : (uint64_t)hp->buckets[hp->op_src[i]].scr_off});
+                        }
+                    }
+                    if (e - k > 1) {
+                        const uint32_t recs = (uint32_t)(hp->unit_prog.size() - at);
+                        hp->unit_prog[at] = URec{recs | kUnitStep | ((uint32_t)(e - k) << 20) | (lane << 24), item_off, map};
+                    }
+                    k = e;
                 }
                 hp->n_units++;
                 hp->n_fused += members.size();

@@ -148,11 +148,15 @@ static_assert(sizeof(DSlot) == 16, "DSlot layout");
 
 // A fused unit's program: for each bucket, in elimination order, a header
 // record then one record per operand. 16 bytes.
-//   header:  a = n_out | n_ops << 8 | (1 << 16 if the unit's root) | (1 << 17
-//            if it runs with the next bucket, on the other half of the warp),
-//            b = stage offset of the result (not the root), off unused
+//   header:  a = n_out | n_ops << 8 | (1 << 16 if the unit's root), b = stage
+//            offset of the result (not the root), off = its first lane in a step
 //   operand: a = mask, b = 1 for an intermediate of the unit (off: its stage
 //            offset), 0 for a gate tensor (off: arena offset)
+//   step:    several independent buckets run together, one output per lane:
+//            a = records of the step (this one included) | kUnitStep | items
+//            << 20 | lanes used << 24, b = offsets of items 1..3 from this
+//            record (8 bits each), off = the item of each lane (2 bits each);
+//            item i's header and operand records follow in order
 struct URec {
     uint32_t a;
     uint32_t b;
@@ -160,6 +164,7 @@ struct URec {
 };
 static_assert(sizeof(URec) == 16, "URec layout");
 constexpr int kURecWindow = 32;  // records a warp holds at once (one per lane)
+constexpr uint32_t kUnitStep = 1u << 18;  // marks a step record
 
 // Counters the persistent kernel uses; zeroed before every run.
 struct DControl {
