@@ -978,8 +978,8 @@ __device__ __forceinline__ typename CT<R>::c unit_output(const URec* ops, uint32
     a0.y = a1.y = (R)0;
     for (uint32_t t = 0; t < n_ops; ++t) {
         const URec d = ops[t];
-        const uint32_t e = 2u * pext_u32(o, d.a);
-        const C* src = d.b ? scr + d.off : arena + d.off;
+        const uint32_t e = 2u * ((d.b & 2u) ? (o & d.a) >> (d.b >> 8) : pext_u32(o, d.a));
+        const C* src = (d.b & 1u) ? scr + d.off : arena + d.off;
         const Pair<C> v = ld_pair_smem(src + e);  // shared memory, or a gate tensor
         a0 = cmul(a0, v.v0);
         a1 = cmul(a1, v.v1);

@@ -949,8 +949,12 @@ static void form_units(HostPlan* hp, int stage_elems) {
                         for (uint32_t i = m.op_begin; i < m.op_begin + m.n_ops; ++i) {
                             const DOperand& o = hp->operands[i];
                             const bool leaf = (o.flags & kOpLeaf) != 0;
+                            // a mask that is one run of bits extracts by a shift
+                            const uint32_t sh = o.mask ? (uint32_t)__builtin_ctz(o.mask) : 0u;
+                            const uint32_t run = o.mask >> sh;
+                            const uint32_t flags = (leaf ? 0u : 1u) | ((run & (run + 1u)) == 0u ? 2u | (sh << 8) : 0u);
                             hp->unit_prog.push_back(
-                                URec{o.mask, leaf ? 0u : 1u, leaf ? o.off : (uint64_t)hp->buckets[hp->op_src[i]].scr_off});
+                                URec{o.mask, flags, leaf ? o.off : (uint64_t)hp->buckets[hp->op_src[i]].scr_off});
                         }
                     }
                     if (e - k > 1) {

@@ -150,8 +150,10 @@ static_assert(sizeof(DSlot) == 16, "DSlot layout");
 // record then one record per operand. 16 bytes.
 //   header:  a = n_out | n_ops << 8 | (1 << 16 if the unit's root), b = stage
 //            offset of the result (not the root), off = its first lane in a step
-//   operand: a = mask, b = 1 for an intermediate of the unit (off: its stage
-//            offset), 0 for a gate tensor (off: arena offset)
+//   operand: a = mask, b bit 0 = 1 for an intermediate of the unit (off: its
+//            stage offset), 0 for a gate tensor (off: arena offset); b bit 1 =
+//            1 if the mask is one run of bits, starting at bit b >> 8 (the
+//            entry index is then (o & mask) >> (b >> 8))
 //   step:    several independent buckets run together, one output per lane:
 //            a = records of the step (this one included) | kUnitStep | items
 //            << 20 | lanes used << 24, b = offsets of items 1..3 from this
