@@ -354,6 +354,41 @@ typedef struct {
  * holds at least n_items entries; *n_out receives the count. */
 int qt_plan_export_groups(qt_plan_t plan, qt_group_info *groups, int64_t *n_out);
 
+/* A fused unit (host-side inspection, tests): the subtree of n_buckets buckets
+ * rooted at `root`, whose program starts at record first_rec of the plan's
+ * unit program. */
+typedef struct {
+    int32_t root;
+    int32_t n_buckets;
+    int64_t first_rec;
+} qt_unit_info;
+
+/* One record of the unit program, as the kernel reads it. A program is a
+ * sequence of steps; a step is either one bucket over the whole warp -- a
+ * header (a = n_out | n_ops << 8 | 1 << 16 for the unit's root; b = the
+ * result's element offset in the warp's shared-memory scratch, unused for the
+ * root, whose result goes to its arena offset) followed by its operand records
+ * -- or several independent buckets run at once, one output per lane: a step
+ * record (a = records of the step | 1 << 18 | items << 20 | lanes used << 24;
+ * b = offsets of items 1..3 from the step record, 8 bits each; off = each
+ * lane's item, 2 bits per lane), then each item's header (off = its first lane)
+ * and operand records. Operand record: a = the operand's mask over the
+ * bucket's outputs (its entry for output o and summed value x is 2 pext(o, a)
+ * + x); b bit 0 = 1 for a result held in scratch (off = its scratch offset), 0
+ * for a gate tensor (off = its arena offset); b bit 1 = 1 when the mask is one
+ * run of bits, starting at bit b >> 8. */
+typedef struct {
+    uint32_t a;
+    uint32_t b;
+    uint64_t off;
+} qt_unit_rec;
+
+/* The fused units of a plan and their programs (0 of each without units).
+ * With units/recs NULL only the counts are written; otherwise the arrays hold
+ * at least *n_units and *n_recs entries (as returned by a first call). */
+int qt_plan_export_units(qt_plan_t plan, qt_unit_info *units, qt_unit_rec *recs, int64_t *n_units,
+                         int64_t *n_recs);
+
 /*
  * Energy of a single-graph plan: edge_zz[e] = e_jk of edge e (n_edges doubles,
  * host or device, may be NULL), *energy = |E|/2 - 1/2 sum e_jk (host or

@@ -1049,6 +1049,27 @@ int qt_plan_export_groups(qt_plan_t P, qt_group_info* groups, int64_t* n_out) {
     return QT_OK;
 }
 
+int qt_plan_export_units(qt_plan_t P, qt_unit_info* units, qt_unit_rec* recs, int64_t* n_units, int64_t* n_recs) {
+    if (!P || !n_units || !n_recs) return QT_EINVAL;
+    const qt::HostPlan& hp = P->hp;
+    static_assert(sizeof(qt_unit_rec) == sizeof(qt::URec), "unit record layout");
+    int64_t nu = 0;
+    for (size_t b = 0; b < hp.buckets.size(); ++b) {
+        const qt::DBucket& d = hp.buckets[b];
+        if (!(d.flags & qt::kBucketUnitRoot)) continue;
+        if (units) units[nu] = qt_unit_info{(int32_t)b, (int32_t)d.unit_count, (int64_t)d.unit_begin - 1};
+        ++nu;
+    }
+    if (recs)
+        for (size_t i = 0; i < hp.unit_prog.size(); ++i) {
+            const qt::URec& r = hp.unit_prog[i];
+            recs[i] = qt_unit_rec{r.a, r.b, r.off};
+        }
+    *n_units = nu;
+    *n_recs = (int64_t)hp.unit_prog.size();
+    return QT_OK;
+}
+
 int qt_plan_network_wires(qt_plan_t P, int32_t network, int32_t* vars_per_qubit) {
     if (!P || !vars_per_qubit || network < 0 || network >= (int32_t)P->hp.nets.size()) return QT_EINVAL;
     const qt::Network& net = P->hp.nets[network];

@@ -25,7 +25,7 @@ EXPORTS = ("qt_plan", "qt_plan_subset", "qt_plan_batch", "qt_plan_stats_get", "q
            "qt_bucket_time", "qt_trace_counters", "qt_trace_bucket_times", "qt_debug_stall_bucket", "qt_plan_free", "qt_error_string", "qt_version", "qt_last_error_detail",
            "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard", "qt_plan_export_fixed",
            "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass", "qt_contract_plan", "qt_contract_run",
-           "qt_contract_sync", "qt_contract_stats_get", "qt_contract_free")
+           "qt_contract_sync", "qt_contract_stats_get", "qt_contract_free", "qt_plan_export_units")
 
 
 class QTError(RuntimeError):
@@ -81,6 +81,8 @@ class ContractStats(ctypes.Structure):
                 ("arena_bytes", ctypes.c_int64), ("widths", ctypes.c_int32 * 32)]
 
 
+UNIT_DTYPE = np.dtype([("root", np.int32), ("n_buckets", np.int32), ("first_rec", np.int64)])
+UNIT_REC_DTYPE = np.dtype([("a", np.uint32), ("b", np.uint32), ("off", np.uint64)])
 FIXED_DTYPE = np.dtype([("network", np.int32), ("slice", np.int32), ("leaf_kind", np.int32), ("leaf_layer", np.int32),
                         ("entry", np.int32), ("pad", np.int32)])
 
@@ -116,6 +118,7 @@ def lib():
         L.qt_energy_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.qt_fma_peak.argtypes = [i32, dp]
         L.qt_plan_export_groups.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        L.qt_plan_export_units.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.qt_plan_export_fixed.argtypes = [vp, vp, ctypes.POINTER(i64)]
         L.qt_plan_export_reps.argtypes = [vp, i32p]
         L.qt_plan_export_device.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
@@ -146,7 +149,8 @@ def lib():
                      "qt_debug_stall_bucket", "qt_trace_counters", "qt_bucket_time", "qt_trace_bucket_times",
                      "qt_energy_noalloc", "qt_fma_peak", "qt_plan_export_groups", "qt_plan_shard",
                      "qt_plan_export_fixed", "qt_plan_export_reps", "qt_plan_export_device", "qt_plan_pass",
-                     "qt_contract_plan", "qt_contract_run", "qt_contract_sync", "qt_contract_stats_get"):
+                     "qt_contract_plan", "qt_contract_run", "qt_contract_sync", "qt_contract_stats_get",
+                     "qt_plan_export_units"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -348,6 +352,16 @@ class Plan:
         cnt = ctypes.c_int64(0)
         _check(lib().qt_plan_export_groups(self._h, out.ctypes.data, ctypes.byref(cnt)), "qt_plan_export_groups")
         return out[:cnt.value]
+
+    def export_units(self):
+        """The fused units (root, n_buckets, first_rec) and the unit program's records (a, b, off)."""
+        nu, nr = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().qt_plan_export_units(self._h, None, None, ctypes.byref(nu), ctypes.byref(nr)), "qt_plan_export_units")
+        units = np.zeros(max(1, nu.value), dtype=UNIT_DTYPE)
+        recs = np.zeros(max(1, nr.value), dtype=UNIT_REC_DTYPE)
+        _check(lib().qt_plan_export_units(self._h, units.ctypes.data, recs.ctypes.data, ctypes.byref(nu), ctypes.byref(nr)),
+               "qt_plan_export_units")
+        return units[:nu.value], recs[:nr.value]
 
     def export_device(self):
         """The arrays the kernels read: (buckets, operands, net_first_factor, factor, graph_owned)."""

@@ -24,8 +24,85 @@ def _slot_kind(slot):
     return 2 + (slot - 2) % 4, (slot - 2) // 4
 
 
-def emulate(pl, gammas, betas, p):
-    """(per-network complex values, per-graph energies) of plan `pl`."""
+STEP = 1 << 18  # a unit step record runs several buckets at once
+
+
+def _pext_int(o: int, mask: int) -> int:
+    r, k = 0, 0
+    while mask:
+        low = mask & -mask
+        if o & low:
+            r |= 1 << k
+        k += 1
+        mask ^= low
+    return r
+
+
+def run_unit_program(recs, first, n_buckets, arena, root_off, scratch_elems):
+    """Interpret one fused unit's program as the persistent kernel runs it:
+    steps of one bucket (outputs over the whole warp) or of several
+    independent buckets (one output per lane, the lane map in the step record).
+    Results live in a scratch array until the root's goes to the arena. Every
+    member of a step reads before any writes; the step's scratch writes must
+    not touch what any of its members reads (the planner's placement), which
+    is asserted here, as is the shift form of one-run masks. `recs` is a list
+    of (a, b, off) integer tuples."""
+    scr = [complex("nan")] * scratch_elems
+
+    def output(ops, o):
+        vals = [1 + 0j, 1 + 0j]
+        reads = []
+        for a, b, off in ops:
+            j = _pext_int(o, a)
+            if b & 2:
+                assert ((o & a) >> (b >> 8)) == j, "shift extract disagrees with the bit extract"
+            src = scr if b & 1 else arena
+            if b & 1:
+                reads += [off + 2 * j, off + 2 * j + 1]
+            vals[0] *= src[off + 2 * j]
+            vals[1] *= src[off + 2 * j + 1]
+        return vals[0] + vals[1], reads
+
+    pos, k = first, 0
+    while k < n_buckets:
+        ha, hb, hoff = recs[pos]
+        writes, reads = [], set()
+        if ha & STEP:
+            n_recs, n_items, used = ha & 0x3F, (ha >> 20) & 7, (ha >> 24) & 0x3F
+            for lane in range(used):
+                q = (hoff >> (2 * lane)) & 3
+                at = 1 if q == 0 else (hb >> (8 * (q - 1))) & 0xFF
+                qa, qb, qoff = recs[pos + at]
+                n_ops = (qa >> 8) & 0xFF
+                assert not (qa >> 16) & 1, "the unit's root in a step of several buckets"
+                o = lane - qoff
+                assert 0 <= o < (1 << (qa & 0xFF))
+                v, r = output(recs[pos + at + 1:pos + at + 1 + n_ops], o)
+                reads.update(r)
+                writes.append((qb + o, v))
+            pos += n_recs
+            k += n_items
+            assert not reads & {w for w, _ in writes}, "a step writes scratch that one of its members reads"
+        else:
+            n_out, n_ops, root = ha & 0xFF, (ha >> 8) & 0xFF, (ha >> 16) & 1
+            ops = recs[pos + 1:pos + 1 + n_ops]
+            for o in range(1 << n_out):
+                v, _ = output(ops, o)
+                writes.append(((root_off if root else hb) + o, v))
+            pos += 1 + n_ops
+            k += 1
+            if root:
+                for w, v in writes:
+                    arena[w] = v
+                continue
+        for w, v in writes:
+            scr[w] = v
+
+
+def emulate(pl, gammas, betas, p, with_units=False, scratch_elems=1024):
+    """(per-network complex values, per-graph energies) of plan `pl`. With
+    `with_units`, fused units run their programs (interpreted here) instead of
+    contracting their members one by one."""
     B, O, nff, F, GO = pl.export_device()
     G = len(GO)
     gam = np.atleast_2d(np.asarray(gammas, dtype=np.float64))
@@ -38,7 +115,20 @@ def emulate(pl, gammas, betas, p):
         for slot in range(L):
             kind, layer = _slot_kind(slot)
             arena[(g * L + slot) * 4:(g * L + slot) * 4 + 4] = leaf_tensor(kind, layer, gam[g], bet[g])
-    for b in B:
+    role = None
+    if with_units:
+        Bi, _ = pl.export()
+        role = Bi["unit_role"]
+        units, recs_arr = pl.export_units()
+        recs = [(int(r["a"]), int(r["b"]), int(r["off"])) for r in recs_arr]
+        unit_of = {int(u["root"]): u for u in units}
+    for bi, b in enumerate(B):
+        if role is not None and role[bi] == 1:
+            continue  # a unit member: its unit's program computes it in scratch
+        if role is not None and role[bi] == 2:
+            u = unit_of[bi]
+            run_unit_program(recs, int(u["first_rec"]), int(u["n_buckets"]), arena, int(b["out_off"]), scratch_elems)
+            continue
         n = int(b["n_out"])
         o = np.arange(1 << n, dtype=np.int64)
         acc = np.zeros(1 << n, dtype=complex)

@@ -150,3 +150,26 @@ def test_layout_of_energy_passes_adds_up(kw):
     ref = oracle.sv_zz(n, edges, g, b)
     np.testing.assert_allclose(zz, ref, rtol=0, atol=1e-12)
     assert E == pytest.approx(oracle.energy_from_zz(ref), abs=1e-10)
+
+
+@pytest.mark.parametrize("dtype,scratch", [("c64", 1024), ("c128", 512)])
+def test_fused_unit_programs_match_plain_contraction(dtype, scratch):
+    """The fused units' programs (steps of one bucket, or of up to four
+    independent small buckets sharing the warp's lanes), interpreted as the
+    kernel runs them -- every member of a step reading before any writes, the
+    intermediates in a scratch array of the stage's size -- give the values of
+    the bucket-by-bucket contraction, and no step writes scratch that one of
+    its members reads."""
+    graphs = synth.batch(3, 3, lo=50, hi=200, base_seed=1000)
+    spec = [(n, e) for n, e, _, _ in graphs]
+    G = np.array([gg for _, _, gg, _ in graphs])
+    Bt = np.array([bb for _, _, _, bb in graphs])
+    with qtgb.plan_batch(spec, 3, host_only=True, dtype=dtype) as pl:
+        assert pl.stats()["n_units"] > 0
+        units, recs = pl.export_units()
+        steps = (recs["a"] & (1 << 18)) != 0
+        assert steps.any(), "no step packs several buckets"
+        v_units, e_units = emulate(pl, G, Bt, 3, with_units=True, scratch_elems=scratch)
+        v_plain, e_plain = emulate(pl, G, Bt, 3)
+    np.testing.assert_allclose(v_units, v_plain, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(e_units, e_plain, rtol=1e-12)
