@@ -63,6 +63,8 @@ def parse():
                     help="c2: the headline line (N=30 p=4 evals/s, plus wide-bucket GB/s on N=1000 p=5, the "
                          "batch, gradient and random-contraction legs); c3: 64-graph batch; c5: gradients on "
                          "N=50 p=4; tncontract: the paper's random contraction expressions against torch.einsum")
+    ap.add_argument("--c3-skip-plain", action="store_true",
+                    help="--workload c3: skip the plain per-bucket complex128 form (profiler captures)")
     ap.add_argument("--c5-n", type=int, default=50,
                     help="--workload c5: vertices of the random 3-regular graph (50; smaller for profiler captures)")
     ap.add_argument("--no-buckets", action="store_true", help="skip the wide-bucket GB/s measurement")
@@ -813,9 +815,11 @@ def run_c3(args, world, local_rank):
     G = np.array([g for _, _, g, _ in graphs])
     Bt = np.array([b for _, _, _, b in graphs])
     res = {}
-    for dtype, sched, steps, dedup in (("c64", "persistent", args.steps, False),
-                                       ("c128", "persistent", args.steps, False), ("c128", "per_bucket", 1, False),
-                                       ("c64", "persistent", args.steps, True)):
+    legs = [("c64", "persistent", args.steps, False), ("c128", "persistent", args.steps, False),
+            ("c128", "per_bucket", 1, False), ("c64", "persistent", args.steps, True)]
+    if args.c3_skip_plain:
+        legs = [leg for leg in legs if leg[1] != "per_bucket"]
+    for dtype, sched, steps, dedup in legs:
         with qtgb.plan_batch([(n, e) for n, e, _, _ in graphs], 3, dtype=dtype, sched=sched, dedup=dedup) as pl:
             st = pl.stats()
             gd = torch.tensor(G.ravel(), dtype=torch.float64, device="cuda")
@@ -858,8 +862,9 @@ def run_c3(args, world, local_rank):
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": "64 seeded random 3-regular graphs, N uniform even in [50,1000] (synth.batch), "
                                    "p=3, per-graph angles; every edge's lightcone network in one persistent launch"},
-            "plain_c128_per_bucket": res["c128_per_bucket"], "c128_persistent": res["c128_persistent"],
-            "speedup_vs_plain_c128": res["c128_per_bucket"]["ms_per_step"] / main["ms_per_step"], "check": check,
+            "plain_c128_per_bucket": res.get("c128_per_bucket"), "c128_persistent": res["c128_persistent"],
+            "speedup_vs_plain_c128": (res["c128_per_bucket"]["ms_per_step"] / main["ms_per_step"]
+                                      if "c128_per_bucket" in res else None), "check": check,
             "c64_dedup": dict(res["c64_persistent_dedup"],
                               note="opts.dedup: one network per isomorphism class of lightcones per graph "
                                    "(off in the main line)")}
