@@ -409,7 +409,8 @@ static cudaError_t bwd_attr() {
 template <typename R>
 static cudaError_t prepare_bwd() {
     const cudaError_t es[] = {bwd_attr<R, 1, true>(), bwd_attr<R, 2, true>(), bwd_attr<R, 3, true>(),
-                              bwd_attr<R, 4, true>(), bwd_attr<R, 8, false>(), bwd_attr<R, kMaxOps, false>()};
+                              bwd_attr<R, 4, true>(), bwd_attr<R, 5, true>(),  bwd_attr<R, 8, false>(),
+                              bwd_attr<R, kMaxOps, false>()};
     for (cudaError_t e : es)
         if (e != cudaSuccess) return e;
     return cudaSuccess;
@@ -429,7 +430,8 @@ static cudaError_t launch_bwd_class(int op_class, const DevBwd& db, cudaStream_t
         case 1: return launch_bwd<R, 2, true>(db, s);
         case 2: return launch_bwd<R, 3, true>(db, s);
         case 3: return launch_bwd<R, 4, true>(db, s);
-        case 4: return launch_bwd<R, 8, false>(db, s);
+        case 4: return launch_bwd<R, 5, true>(db, s);
+        case 5: return launch_bwd<R, 8, false>(db, s);
         default: return launch_bwd<R, kMaxOps, false>(db, s);
     }
 }

@@ -87,7 +87,7 @@ cudaError_t launch_leaf_fill(int dtype, const double* angles, int n_graphs, int 
 // entries that slicing fixed (added to grad, n_graphs x 2p, before the -1/2 of k_grad_final).
 cudaError_t launch_seed_roots(int dtype, const DevEpilogue& de, int n_nets, uint64_t cot_delta, uint64_t dleaf_delta,
                               double* grad, int p, const uint32_t* net_graph, cudaStream_t s);
-// op_class: the level's tasks of buckets with exactly 1..4 operands (0..3), at most 8 (4) or 16 (5)
+// op_class: the level's tasks of buckets with exactly 1..5 operands (0..4), at most 8 (5) or 16 (6)
 cudaError_t launch_backward(int dtype, int op_class, const DevBwd& db, cudaStream_t s);
 // Function attributes of the reverse-sweep kernels (the shared-memory size
 // above the default); once per process and element type, before any capture.

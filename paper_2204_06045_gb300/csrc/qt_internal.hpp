@@ -58,10 +58,10 @@ constexpr int kRunTiles = 12;        // tiles of one bucket handed out per claim
 constexpr int kBwdTileBits = 9;      // outputs per reverse-sweep tile, log2 (512: 3% faster than 256 on N=50 p=4 c64; 1024 slower)
 constexpr int kBwdRedElems = 1024;   // per-warp shared-memory elements for in-tile cotangent sums
 constexpr uint32_t kZeroChunk = 1u << 16;  // elements per block of the cotangent zeroing kernel
-// Reverse-sweep launches per level: buckets of exactly 1, 2, 3 or 4 operands
+// Reverse-sweep launches per level: buckets of exactly 1, 2, 3, 4 or 5 operands
 // (compile-time counts), then at most 8, then at most 16.
-constexpr int kBwdClasses = 6;
-constexpr int bwd_op_class(int n_ops) { return n_ops <= 4 ? n_ops - 1 : n_ops <= 8 ? 4 : 5; }
+constexpr int kBwdClasses = 7;
+constexpr int bwd_op_class(int n_ops) { return n_ops <= 5 ? n_ops - 1 : n_ops <= 8 ? 5 : 6; }
 // How the reverse sweep treats an operand (per operand, fixed at plan time).
 enum : int8_t {
     kBwdNone = 0,       // a gate tensor without an angle (|+>, Z)
