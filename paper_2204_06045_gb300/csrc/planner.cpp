@@ -1018,7 +1018,10 @@ static void simulate_order(HostPlan* hp) {
     const double bw = 6.5e12;                  // bytes per second, whole GPU
     const double t_tile = 0.3e-6, t_group = 1.5e-6;
     std::vector<double> tile_s(nb), whole_s(nb), prio(nb, 0.0);
-    const double t_unit_bucket = 0.15e-6;  // one small bucket inside a fused unit
+    // one small bucket inside a fused unit: measured on GB300, 0.8 us gave the
+    // complex64 64-graph batch 1.591 vs 1.675 ms at 0.15 us, while the complex128
+    // N=30 p=4 plan (few units) ran best at 0.15 us (5.67 vs 5.79 ms)
+    const double t_unit_bucket = cfg.dtype == 1 ? 0.15e-6 : 0.8e-6;
     for (size_t b = 0; b < nb; ++b) {
         const DBucket& d = hp->buckets[b];
         const double tile_bytes =
